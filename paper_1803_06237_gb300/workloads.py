@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs shaped like the paper's waveguide workloads.
+
+This module only generates data: grids, permittivity maps, absorber
+parameters, source sheets and random vectors.  It holds none of the method's
+arithmetic (no contrast, no absorber profile, no Green function), so both the
+CUDA path and the FP64 oracle can take their inputs from it.
+
+Every generator takes an explicit seed and uses NumPy's PCG64.
+
+Workloads (sizes in units of the voxel size h unless stated):
+
+* ``cube``       lossless dielectric cube eps = 12.25 in vacuum, 12^3 voxels,
+                 side 0.4 um (h = 33.3 nm), lambda0 = 1.55 um, x-polarised
+                 plane wave along +z.
+* ``waveguide``  Si strip eps = 12.11 (core 460 x 220 nm = 23 x 11 voxels) in
+                 eps_bg = 2.085, h = 20 nm, 600 x 23 x 11 voxels (12 um),
+                 quadratic absorber over the last 4 um (x0 = 400, L = 200)
+                 with round-trip target R_rt = 1e-10, y-polarised Gaussian
+                 current sheet (waist 200 nm) on the voxel plane x = 1 um.
+* ``batch48``    48 guides of the same cross-section: absorber length
+                 {1,2,4,6,8,10} um x degree {0,1,2,3} x eps''_max {0.5, 2};
+                 nx = 250 + 50 L[um] (a 5 um body plus the absorber).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+LAMBDA0_UM = 1.55
+
+
+@dataclasses.dataclass
+class Absorber:
+    x0: float            # start of the absorber, units of h from the low-x edge
+    length: float        # absorber length L, units of h
+    degree: int          # d in s(u) = u^d
+    eps2_max: float | None = None   # eps''_max if given directly
+    r_rt: float | None = None       # else: target round-trip reflection
+    direction: int = +1
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    grid: tuple           # (nx, ny, nz)
+    h_um: float
+    k0_per_um: float
+    eps_bg: float
+    eps: np.ndarray       # relative permittivity per voxel, (nz, ny, nx) complex
+    absorbers: list
+    source: str           # "plane_wave_x" or "sheet"
+    src: np.ndarray | None = None   # impressed current (3, nz, ny, nx) for "sheet"
+    eps_core: float = 0.0
+
+    @property
+    def n_voxels(self) -> int:
+        return int(np.prod(self.grid))
+
+    @property
+    def kappa(self) -> float:
+        """k h with k = k0 sqrt(eps_bg) (dimensionless)."""
+        return self.k0_per_um * math.sqrt(self.eps_bg) * self.h_um
+
+
+def _k0() -> float:
+    return 2.0 * math.pi / LAMBDA0_UM
+
+
+def cube(n: int = 12) -> Workload:
+    eps = np.full((n, n, n), 12.25 + 0j)
+    return Workload("cube", (n, n, n), 0.4 / n, _k0(), 1.0, eps, [], "plane_wave_x",
+                    eps_core=12.25)
+
+
+def gaussian_sheet(grid, ix: int, waist_vox: float, comp: int = 1) -> np.ndarray:
+    """Impressed current: exp(-((y - yc)^2 + (z - zc)^2) / waist^2) on the
+    voxel plane ``ix``, component ``comp`` (1 = y), voxel-centre coordinates,
+    centred on the cross-section."""
+    nx, ny, nz = grid
+    y = np.arange(ny) + 0.5 - ny / 2.0
+    z = np.arange(nz) + 0.5 - nz / 2.0
+    prof = np.exp(-(z[:, None] ** 2 + y[None, :] ** 2) / waist_vox**2)
+    src = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+    src[comp, :, :, ix] = prof
+    return src
+
+
+def waveguide(nx: int = 600, ny: int = 23, nz: int = 11, h_um: float = 0.02,
+              absorber_len_um: float = 4.0, degree: int = 2, eps2_max=None,
+              r_rt: float = 1e-10, src_x_um: float = 1.0, waist_um: float = 0.2,
+              eps_core: float = 12.11, eps_bg: float = 2.085,
+              name: str = "waveguide") -> Workload:
+    eps = np.full((nz, ny, nx), eps_core + 0j)
+    L = absorber_len_um / h_um
+    ab = Absorber(x0=nx - L, length=L, degree=degree,
+                  eps2_max=eps2_max, r_rt=None if eps2_max is not None else r_rt)
+    src = gaussian_sheet((nx, ny, nz), int(round(src_x_um / h_um)), waist_um / h_um)
+    return Workload(name, (nx, ny, nz), h_um, _k0(), eps_bg, eps, [ab], "sheet", src,
+                    eps_core=eps_core)
+
+
+def batch48():
+    """The 48 uneven guides (list of Workload)."""
+    out = []
+    for L in (1, 2, 4, 6, 8, 10):
+        for d in (0, 1, 2, 3):
+            for e2 in (0.5, 2.0):
+                nx = 250 + 50 * L
+                out.append(waveguide(nx=nx, absorber_len_um=float(L), degree=d,
+                                     eps2_max=e2, name=f"guide_L{L}_d{d}_e{e2}"))
+    return out
+
+
+def random_currents(grid, seed: int, dtype=np.complex128) -> np.ndarray:
+    """Complex normal vector of shape (3, nz, ny, nx)."""
+    nx, ny, nz = grid
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((2, 3, nz, ny, nx))
+    return (v[0] + 1j * v[1]).astype(dtype)
+
+
+def random_permittivity(grid, seed: int, lossy: bool = True) -> np.ndarray:
+    """eps per voxel: real part U[1, 13], imaginary part -U[0, 2] if lossy."""
+    nx, ny, nz = grid
+    rng = np.random.Generator(np.random.PCG64(seed))
+    re = rng.uniform(1.0, 13.0, (nz, ny, nx))
+    im = -rng.uniform(0.0, 2.0, (nz, ny, nx)) if lossy else np.zeros((nz, ny, nx))
+    return re + 1j * im
+
+
+def sparse_currents(grid, seed: int, nnz: int) -> np.ndarray:
+    """Vector with ``nnz`` random non-zero (voxel, component) entries."""
+    nx, ny, nz = grid
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = np.zeros(3 * nx * ny * nz, dtype=np.complex128)
+    idx = rng.choice(v.size, size=nnz, replace=False)
+    v[idx] = rng.standard_normal(nnz) + 1j * rng.standard_normal(nnz)
+    return v.reshape(3, nz, ny, nx)
+
+
+def sample_indices(grid, seed: int, count: int) -> np.ndarray:
+    """Distinct flat (component, voxel) output indices to spot-check."""
+    n = 3 * int(np.prod(grid))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, size=min(count, n), replace=False))
