@@ -1,0 +1,317 @@
+"""Benchmark of the J-VIE operator application on one GB300 (or N replicas).
+
+Workload: the truncated Si strip guide, 600 x 23 x 11 voxels (h = 20 nm,
+eps_core = 12.11 in eps_bg = 2.085, quadratic absorber over the last 4 um),
+complex64 operator application y = w - M (N w) through the C ABI.
+
+A step is one operator application on a fresh input vector.  Inputs cycle
+through a pool whose inputs and outputs together exceed the 129 MB L2, so no
+step starts with its vector cached.  The timed region is bracketed by a
+barrier and a device synchronisation on both sides and timed with CUDA events
+on the launching stream; rank 0 prints one JSON line with the maximum time
+over ranks.  Multi-GPU runs are independent replicas (weak scaling): the
+operator does not shard.
+
+`--impl reference` times the FP64 CPU oracle (the baseline of this project)
+on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIE matvecs/s & time-to-1e-6 residual; mixed+learned vs plain FP64, 1 GB300"
+UNIT = "matvecs/s"
+L2_BYTES = 129 * 1024 * 1024
+WORKLOAD = ("Si strip waveguide 600x23x11 voxels, h=20nm, eps_core=12.11, eps_bg=2.085, "
+            "quadratic absorber over the last 4um (R_rt=1e-10), complex64 operator application")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi during the timed region (every 200 ms)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_06237_gb300 import build, vie, workloads
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build_library()
+    vie.load()
+
+    wl = workloads.waveguide()
+    ab = wl.absorbers[0]
+    e2 = vie.vie_eps2_from_round_trip(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+    absorbers = [dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2)]
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    info = plan.info()
+
+    n3 = 3 * wl.n_voxels
+    vec_bytes = n3 * 8
+    pool = max(2, int(np.ceil(1.5 * L2_BYTES / (2 * vec_bytes))))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234 + rank)
+    xs = torch.randn((pool, n3), dtype=torch.complex64, device="cuda", generator=gen)
+    ys = torch.empty_like(xs)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        vie.vie_matvec(plan, xs[i % pool], ys[i % pool], stream)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(K):
+        vie.vie_matvec(plan, xs[i % pool], ys[i % pool], stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1])
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step_ms = ms / K
+    value = world * K / (ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    Ke = min(K, args.e2e_steps)
+    hx = torch.randn((n3,), dtype=torch.complex64).pin_memory()
+    hy = torch.empty((n3,), dtype=torch.complex64).pin_memory()
+    dx = torch.empty((n3,), dtype=torch.complex64, device="cuda")
+    dy = torch.empty_like(dx)
+    for _ in range(3):
+        dx.copy_(hx, non_blocking=True)
+        vie.vie_matvec(plan, dx, dy, stream)
+        hy.copy_(dy, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        dx.copy_(hx, non_blocking=True)
+        vie.vie_matvec(plan, dx, dy, stream)
+        hy.copy_(dy, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * Ke / (e2e_ms / 1e3)
+
+    # roofline of the operator application (3 launches), algorithmic bytes
+    nx, ny, nz = wl.grid
+    Kx, Ky, Kz = (m // 2 + 1 for m in info["m"])
+    s = 8
+    alg_bytes = (3 * wl.n_voxels * 2 + wl.n_voxels) * s + 6 * Kx * Ky * Kz * s
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (per_step_ms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("matvec_c64_waveguide_bytes")
+        except Exception:
+            traffic = None
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(wl.grid), "circulant": list(info["m"]),
+                   "input_pool_vectors": pool, "l2": f"inputs+outputs cycle through {2 * pool * vec_bytes / 2**20:.0f} MiB > 129 MB L2",
+                   "parallelism": f"{world} independent replicas"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,
+                "steps": Ke},
+        "gpu_launches": 3 * K,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "operator application (passes A+B+C)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_kind},
+        "clocks": clk,
+        "setup_ms": info["setup_ms"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(seconds: float):
+    """Time the oracle's FFT matvec (scipy, complex128) on the full guide with a
+    synthetic spectrum of the right shape (spectrum values do not change the
+    cost).  Returns (matvecs/s, runs, cores)."""
+    from oracle import operator as op
+    from paper_1803_06237_gb300 import workloads
+
+    wl = workloads.waveguide()
+    nx, ny, nz = wl.grid
+    Msize = (2 * nx, 2 * ny, 2 * nz)
+    rng = np.random.default_rng(0)
+    Gh = (rng.standard_normal((6, Msize[2], Msize[1], Msize[0]))
+          + 1j * rng.standard_normal((6, Msize[2], Msize[1], Msize[0])))
+    M = np.full((nz, ny, nx), 0.5 + 0.1j)
+    x = workloads.random_currents(wl.grid, seed=5)
+    op.matvec(Gh, wl.grid, M, x)
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        op.matvec(Gh, wl.grid, M, x)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or runs >= 10000:
+            break
+    return runs / el, runs, os.cpu_count()
+
+
+def cpu_baseline(seconds: float):
+    v, runs, cores = _oracle_sample(seconds)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{runs} complex128 FFT matvecs of the oracle (scipy.fft, workers={cores}) on the full "
+                      f"600x23x11 guide, circulant 1200x46x22, synthetic spectrum; ~{seconds:.0f} s"}
+
+
+def reference_arm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    # each step one oracle matvec; the number of steps is capped to keep the run short
+    from oracle import operator as op  # noqa: F401
+    v1, _, _ = _oracle_sample(2.0)
+    per = 1.0 / v1
+    K = int(min(args.steps, max(3, args.cpu_seconds * 2 / per)))
+    W = min(args.warmup, 3)
+    v, runs, cores = _oracle_sample(per * (W + K))
+    result = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": runs, "warmup": W,
+        "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD.replace("complex64", "complex128 (FP64 oracle)"), "grid": [600, 23, 11],
+                   "circulant": [1200, 46, 22]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{runs} oracle FFT matvecs (requested {args.steps}, capped to ~{2 * args.cpu_seconds:.0f} s)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(result), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * vie.h -- C ABI of libvie: the FFT-accelerated J-VIE operator of
+ * "Adiabatic absorbers in photonics simulations with the volume integral
+ * equation method" (arXiv:1803.06237) on one NVIDIA GB300 (sm_103a).
+ *
+ * The library solves the discrete J-VIE of Sec. 6,
+ *     (I - M_eps N) w = c_e M_eps e_inc,
+ * on a uniform voxel grid with piecewise-constant currents and materials
+ * (Sec. 3.1).  N is block-Toeplitz with six unique tensor components and is
+ * applied with FFTs (Sec. 6); M_eps = (eps_r - 1)/eps_r per voxel (Sec. 3)
+ * carries the material and the graded absorber loss (Sec. 4.1-4.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid n = {nx, ny, nz}.  A current vector holds 3 components per voxel in
+ *    the layout [c][z][y][x] (x fastest), complex interleaved (re, im).  Its
+ *    length is 3*nx*ny*nz complex numbers.  A per-voxel field is [z][y][x].
+ *  - Units: h and 1/k0 are in the same length unit.  An exterior medium eps_bg
+ *    is scaled out (Sec. 2): the operator uses k = k0 sqrt(eps_bg) and the
+ *    contrast is taken relative to eps_bg.
+ *  - Complex types: VIE_C64 = two float32 per number, VIE_C128 = two float64.
+ *  - Pointers named *_host are host memory; *_dev are device memory on the
+ *    device that was current when the plan was created.  The caller owns every
+ *    buffer it passes; the library never keeps a caller pointer after a call
+ *    returns.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream); device work is enqueued on it and the call returns
+ *    without synchronising unless stated.
+ *  - Every call returns a vie_status.  Nothing is printed; vie_last_error()
+ *    returns a thread-local description of the last failure.
+ */
+#ifndef VIE_H_
+#define VIE_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vie_plan vie_plan;
+
+typedef enum {
+  VIE_OK = 0,
+  VIE_ERR_INVALID = 1,        /* bad argument: null pointer, size, flag */
+  VIE_ERR_OOM = 2,            /* device allocation failed */
+  VIE_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  VIE_ERR_NOT_CONVERGED = 4,  /* solver stopped before the tolerance */
+  VIE_ERR_TIMEOUT = 5,        /* a bounded device wait ran out */
+  VIE_ERR_NONFINITE = 6       /* NaN/Inf met in an input or an iterate */
+} vie_status;
+
+enum { VIE_C64 = 1, VIE_C128 = 2 };
+
+/* Flags for vie_plan_create. */
+enum {
+  VIE_PLAN_DEFAULT = 0,
+  VIE_PLAN_CIRC_2N = 1        /* circulant sizes exactly 2n (else the smallest
+                                 5-smooth size >= 2n - 1) */
+};
+
+typedef struct {
+  int n[3];                   /* grid nx, ny, nz */
+  int m[3];                   /* circulant sizes Mx, My, Mz (each >= 2n-1) */
+  double h, k0, eps_bg, kappa;/* kappa = k0 sqrt(eps_bg) h */
+  size_t device_bytes;        /* device memory held by the plan */
+  double setup_ms;            /* device time of entries + spectrum */
+} vie_plan_info;
+
+/* Graded absorber of Sec. 4.1-4.2: eps'' = eps2_max * u^degree with
+ * u = (x_c - x0)/length (direction +1) or (x0 - x_c)/length (direction -1),
+ * x_c = ix + 1/2 the voxel centre in units of h, 0 <= u <= 1; applied to voxels
+ * whose permittivity differs from eps_bg (the core).  eps'' = sigma/(w eps_0)
+ * (the reading under which the round-trip formula of Sec. 4.3 holds). */
+typedef struct {
+  double x0;
+  double length;
+  int degree;                 /* 0..3 in the paper; any >= 0 accepted */
+  int direction;              /* +1 or -1 */
+  double eps2_max;
+} vie_absorber;
+
+/* Create a plan for grid n with voxel size h, free-space wavenumber k0 and
+ * background permittivity eps_bg (Sec. 2 scaling).  Computes on the device,
+ * in FP64, the Galerkin Toeplitz entries T_pq(Delta) of N (Sec. 3.1,
+ * N_ij = <N P_j, P_i>) for Delta in [0,n) and the spectra of their circulant
+ * embedding (Sec. 6), stored once in complex128 and once in complex64.
+ * Synchronises the device before returning.  The contrast starts at zero
+ * (operator = identity).  Errors: VIE_ERR_INVALID (n < 1, h <= 0, k0 < 0,
+ * eps_bg <= 0), VIE_ERR_OOM, VIE_ERR_CUDA.  *out is NULL on error. */
+vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0,
+                           double eps_bg, int flags);
+
+/* Release every device buffer of the plan.  NULL is accepted. */
+vie_status vie_plan_destroy(vie_plan* plan);
+
+vie_status vie_plan_get_info(const vie_plan* plan, vie_plan_info* info);
+
+/* Contrast from a relative permittivity map (step a1; Sec. 3, M_eps):
+ * eps_host holds nx*ny*nz complex128 values (eps' - j eps'', relative to
+ * vacuum) in [z][y][x] order.  Each absorber adds -j eps''(x) on core voxels;
+ * then chi = eps/eps_bg - 1 and M = chi/(1 + chi) are formed on the device
+ * and kept in complex128 and complex64.  n_abs may be 0 (absorbers NULL).
+ * Synchronous.  Errors: VIE_ERR_INVALID, VIE_ERR_NONFINITE (eps = 0 after the
+ * absorber, or non-finite), VIE_ERR_CUDA. */
+vie_status vie_set_permittivity(vie_plan* plan, const double* eps_host,
+                                const vie_absorber* absorbers, int n_abs);
+
+/* Contrast directly from chi = eps_r/eps_bg - 1 (nx*ny*nz complex128, host).
+ * M = chi/(1 + chi).  Synchronous.  Errors as vie_set_permittivity. */
+vie_status vie_set_contrast(vie_plan* plan, const double* chi_host);
+
+/* y = w - M (N w): one application of the J-VIE operator I - M_eps N
+ * (Sec. 6 MVP): pad to the circulant, 3-D FFT, symmetric 3x3 spectral
+ * multiply, inverse FFT, crop, contrast.  x_dev and y_dev are device vectors
+ * of 3*nx*ny*nz complex numbers of type `dtype`; they must not overlap.
+ * Asynchronous on `stream`.  Uses the plan's workspace, so calls on one plan
+ * must not run concurrently on different streams.  Errors: VIE_ERR_INVALID,
+ * VIE_ERR_CUDA. */
+vie_status vie_matvec(vie_plan* plan, const void* x_dev, void* y_dev, int dtype,
+                      void* stream);
+
+/* Right-hand side of the J-VIE for an impressed current w_src radiating in
+ * the background (Sec. 3, integral representation: e_inc = (1/c_e)(N - I) w_src):
+ * b = c_e M e_inc = M ((N - I) w_src).  Same layout, types and rules as
+ * vie_matvec. */
+vie_status vie_rhs_from_source(vie_plan* plan, const void* src_dev, void* b_dev,
+                               int dtype, void* stream);
+
+/* Copy the FP64 Toeplitz octant T_pq(Delta), Delta in [0,nx)x[0,ny)x[0,nz),
+ * to the host: 6*nx*ny*nz complex128 in [comp][z][y][x] order with the
+ * component order xx, yy, zz, xy, xz, yz.  Synchronous. */
+vie_status vie_get_toeplitz(const vie_plan* plan, double* out_host);
+
+/* eps''_max for a target round-trip reflection (Sec. 4.3 closed form with
+ * p = d): -(d+1) ln(R_rt) sqrt(eps_r) / (D L eta k0).  Host-only arithmetic;
+ * length and 1/k0 in the same unit.  Errors: VIE_ERR_INVALID. */
+vie_status vie_eps2_from_round_trip(double r_rt, int degree, double length,
+                                    double k0, double eps_r, double D, double eta,
+                                    double* eps2_max);
+
+/* Thread-local description of the last error ("" if none). */
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H_ */

@@ -1,0 +1,372 @@
+// C ABI entry points: plan lifecycle, contrast, operator application.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+int smooth_size_at_least(int n) {
+  if (n < 1) n = 1;
+  for (int m = n;; ++m) {
+    int r = m;
+    while (r % 2 == 0) r /= 2;
+    while (r % 3 == 0) r /= 3;
+    while (r % 5 == 0) r /= 5;
+    if (r == 1) return m;
+  }
+}
+
+bool factor_length(int len, AxisPlan* out) {
+  out->len = len;
+  out->nstages = 0;
+  int r = len;
+  auto push = [&](int f) {
+    if (out->nstages >= kMaxStages) return false;
+    out->radix[out->nstages++] = f;
+    r /= f;
+    return true;
+  };
+  while (r % 4 == 0) if (!push(4)) return false;
+  while (r % 2 == 0) if (!push(2)) return false;
+  while (r % 3 == 0) if (!push(3)) return false;
+  while (r % 5 == 0) if (!push(5)) return false;
+  return r == 1;
+}
+
+// Twiddles exp(-2 pi i k / len) in FP64 on the host (libm cos/sin), the
+// argument reduced to the first octant through the symmetries of the circle.
+static void twiddle_host(int len, std::vector<double>& re, std::vector<double>& im) {
+  re.resize(len);
+  im.resize(len);
+  for (int k = 0; k < len; ++k) {
+    // angle = 2 pi k / len; use k' = 8k mod 8len to find the octant
+    const long long num = 8LL * k;          // angle / (pi/4) = num / len
+    const int oct = (int)(num / len);       // 0..7
+    const long long rem = num - (long long)oct * len;   // in [0, len)
+    // residual angle in [0, pi/4): theta = (pi/4) * rem / len
+    const double th = (M_PI / 4.0) * (double)rem / (double)len;
+    const double c = cos(th), s = sin(th);
+    const double h = M_SQRT1_2;
+    double cr, sr;   // cos and sin of the full angle
+    switch (oct) {
+      case 0: cr = c; sr = s; break;
+      case 1: cr = h * (c - s); sr = h * (c + s); break;
+      case 2: cr = -s; sr = c; break;
+      case 3: cr = -h * (c + s); sr = h * (c - s); break;
+      case 4: cr = -c; sr = -s; break;
+      case 5: cr = -h * (c - s); sr = -h * (c + s); break;
+      case 6: cr = s; sr = -c; break;
+      default: cr = h * (c + s); sr = -h * (c - s); break;
+    }
+    re[k] = cr;
+    im[k] = -sr;
+  }
+}
+
+static vie_status make_axis(AxisPlan* ax, int len, size_t* bytes) {
+  if (!factor_length(len, ax)) {
+    set_error("circulant length %d has a prime factor other than 2, 3, 5", len);
+    return VIE_ERR_INVALID;
+  }
+  std::vector<double> re, im;
+  twiddle_host(len, re, im);
+  std::vector<double2> t64(len);
+  std::vector<float2> t32(len);
+  for (int k = 0; k < len; ++k) {
+    t64[k] = make_double2(re[k], im[k]);
+    t32[k] = make_float2((float)re[k], (float)im[k]);
+  }
+  VIE_CUDA_TRY(cudaMalloc((void**)&ax->tw64, len * sizeof(double2)));
+  VIE_CUDA_TRY(cudaMalloc((void**)&ax->tw32, len * sizeof(float2)));
+  VIE_CUDA_TRY(cudaMemcpy(ax->tw64, t64.data(), len * sizeof(double2), cudaMemcpyHostToDevice));
+  VIE_CUDA_TRY(cudaMemcpy(ax->tw32, t32.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
+  *bytes += len * (sizeof(double2) + sizeof(float2));
+  return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// contrast (step a1): chi = eps/eps_bg - 1 with absorber loss, M = chi/(1+chi)
+// ---------------------------------------------------------------------------
+constexpr int kMaxAbsorbers = 8;
+struct AbsorberSet {
+  int n;
+  vie_absorber a[kMaxAbsorbers];
+};
+
+__global__ void contrast_kernel(double2* __restrict__ chi_io, double2* __restrict__ M64, float2* __restrict__ M32,
+                                int nx, size_t N, int from_eps, double eps_bg, AbsorberSet abs_,
+                                int* __restrict__ bad) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    double2 e = chi_io[v];
+    double cr, ci;
+    if (from_eps) {
+      const bool core = (e.x != eps_bg) || (e.y != 0.0);
+      if (core) {
+        const double xc = (double)(v % nx) + 0.5;
+        for (int k = 0; k < abs_.n; ++k) {
+          const vie_absorber& a = abs_.a[k];
+          const double u = a.direction > 0 ? (xc - a.x0) / a.length : (a.x0 - xc) / a.length;
+          if (u >= 0.0 && u <= 1.0) {
+            double pw = 1.0;
+            for (int d = 0; d < a.degree; ++d) pw *= u;
+            e.y -= a.eps2_max * pw;
+          }
+        }
+      }
+      cr = e.x / eps_bg - 1.0;
+      ci = e.y / eps_bg;
+    } else {
+      cr = e.x;
+      ci = e.y;
+    }
+    // M = chi / (1 + chi)
+    const double dr = 1.0 + cr, di = ci;
+    const double den = dr * dr + di * di;
+    double mr = (cr * dr + ci * di) / den;
+    double mi = (ci * dr - cr * di) / den;
+    if (!(isfinite(mr) && isfinite(mi)) || den == 0.0) {
+      atomicExch(bad, 1);
+      mr = 0.0;
+      mi = 0.0;
+    }
+    chi_io[v] = make_double2(cr, ci);
+    M64[v] = make_double2(mr, mi);
+    M32[v] = make_float2((float)mr, (float)mi);
+  }
+}
+
+static vie_status set_contrast_common(vie_plan* p, const double* host, const vie_absorber* abs_, int n_abs,
+                                      int from_eps) {
+  if (!p || !host) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (n_abs < 0 || n_abs > kMaxAbsorbers || (n_abs > 0 && !abs_)) {
+    set_error("n_abs must be in [0, %d] with a non-null array", kMaxAbsorbers);
+    return VIE_ERR_INVALID;
+  }
+  AbsorberSet set;
+  memset(&set, 0, sizeof(set));
+  set.n = n_abs;
+  for (int k = 0; k < n_abs; ++k) {
+    if (!(abs_[k].length > 0.0) || abs_[k].degree < 0 || (abs_[k].direction != 1 && abs_[k].direction != -1)) {
+      set_error("absorber %d: need length > 0, degree >= 0, direction +1 or -1", k);
+      return VIE_ERR_INVALID;
+    }
+    set.a[k] = abs_[k];
+  }
+  VIE_CUDA_TRY(cudaSetDevice(p->device));
+  const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  int* bad = nullptr;
+  VIE_CUDA_TRY(cudaMalloc((void**)&bad, sizeof(int)));
+  vie_status st = VIE_OK;
+  int hbad = 0;
+  cudaError_t e = cudaMemset(bad, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(p->chi64, host, N * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned blocks = (unsigned)((N + 255) / 256 < 152 * 16 ? (N + 255) / 256 : 152 * 16);
+    contrast_kernel<<<blocks, 256>>>(p->chi64, p->M64, p->M32, p->n[0], N, from_eps, p->eps_bg, set, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) {
+    set_error("set contrast: %s", cudaGetErrorString(e));
+    st = VIE_ERR_CUDA;
+  } else if (hbad) {
+    set_error("contrast is not finite (eps_r = 0 or non-finite input)");
+    st = VIE_ERR_NONFINITE;
+  }
+  return st;
+}
+
+static void free_plan(vie_plan* p) {
+  if (!p) return;
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(p->ax[a].tw32);
+    cudaFree(p->ax[a].tw64);
+  }
+  cudaFree(p->toeplitz);
+  cudaFree(p->ghat64);
+  cudaFree(p->ghat32);
+  cudaFree(p->M64);
+  cudaFree(p->M32);
+  cudaFree(p->chi64);
+  cudaFree(p->work);
+  delete p;
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+extern "C" {
+
+const char* vie_last_error(void) { return g_err; }
+
+vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0, double eps_bg, int flags) {
+  clear_error();
+  if (!out || !n) { set_error("null argument"); return VIE_ERR_INVALID; }
+  *out = nullptr;
+  if (n[0] < 1 || n[1] < 1 || n[2] < 1) { set_error("grid sizes must be >= 1"); return VIE_ERR_INVALID; }
+  if (!(h > 0.0) || !(k0 >= 0.0) || !(eps_bg > 0.0) || !isfinite(h) || !isfinite(k0) || !isfinite(eps_bg)) {
+    set_error("need h > 0, k0 >= 0, eps_bg > 0 (finite)");
+    return VIE_ERR_INVALID;
+  }
+  if ((double)n[0] * n[1] * n[2] > 2.0e9) { set_error("grid too large"); return VIE_ERR_INVALID; }
+  vie_plan* p = new vie_plan();
+  VIE_CUDA_TRY(cudaGetDevice(&p->device));
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = n[a];
+    p->m[a] = (flags & VIE_PLAN_CIRC_2N) ? 2 * n[a] : smooth_size_at_least(2 * n[a] - 1);
+    p->kf[a] = p->m[a] / 2 + 1;
+  }
+  p->h = h;
+  p->k0 = k0;
+  p->eps_bg = eps_bg;
+  p->kappa = k0 * sqrt(eps_bg) * h;
+  size_t bytes = 0;
+  vie_status st = VIE_OK;
+  for (int a = 0; a < 3 && st == VIE_OK; ++a) st = make_axis(&p->ax[a], p->m[a], &bytes);
+  if (st != VIE_OK) { free_plan(p); return st; }
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  const size_t G = (size_t)p->kf[0] * 6 * p->kf[1] * p->kf[2];
+  const size_t NL = (size_t)3 * n[1] * n[2];
+  p->work_bytes = NL * p->m[0] * sizeof(double2);
+  struct { void** ptr; size_t sz; } allocs[] = {
+      {(void**)&p->toeplitz, 6 * N * sizeof(double2)}, {(void**)&p->ghat64, G * sizeof(double2)},
+      {(void**)&p->ghat32, G * sizeof(float2)},        {(void**)&p->M64, N * sizeof(double2)},
+      {(void**)&p->M32, N * sizeof(float2)},           {(void**)&p->chi64, N * sizeof(double2)},
+      {(void**)&p->work, p->work_bytes}};
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.ptr, a.sz);
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(%zu) failed: %s", a.sz, cudaGetErrorString(e));
+      free_plan(p);
+      return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+    }
+    bytes += a.sz;
+  }
+  p->device_bytes = bytes;
+  cudaStream_t s;
+  cudaEvent_t e0, e1;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("cudaStreamCreate failed");
+    free_plan(p);
+    return VIE_ERR_CUDA;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaMemsetAsync(p->M64, 0, N * sizeof(double2), s);
+  cudaMemsetAsync(p->M32, 0, N * sizeof(float2), s);
+  cudaMemsetAsync(p->chi64, 0, N * sizeof(double2), s);
+  st = compute_toeplitz(p, s);
+  if (st == VIE_OK) st = compute_spectrum(p, s);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == VIE_OK && e != cudaSuccess) {
+    set_error("plan setup failed: %s", cudaGetErrorString(e));
+    st = VIE_ERR_CUDA;
+  }
+  float ms = 0.f;
+  if (st == VIE_OK) cudaEventElapsedTime(&ms, e0, e1);
+  p->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (st != VIE_OK) { free_plan(p); return st; }
+  *out = p;
+  return VIE_OK;
+}
+
+vie_status vie_plan_destroy(vie_plan* plan) {
+  clear_error();
+  if (!plan) return VIE_OK;
+  cudaSetDevice(plan->device);
+  free_plan(plan);
+  return VIE_OK;
+}
+
+vie_status vie_plan_get_info(const vie_plan* p, vie_plan_info* info) {
+  clear_error();
+  if (!p || !info) { set_error("null argument"); return VIE_ERR_INVALID; }
+  for (int a = 0; a < 3; ++a) { info->n[a] = p->n[a]; info->m[a] = p->m[a]; }
+  info->h = p->h;
+  info->k0 = p->k0;
+  info->eps_bg = p->eps_bg;
+  info->kappa = p->kappa;
+  info->device_bytes = p->device_bytes;
+  info->setup_ms = p->setup_ms;
+  return VIE_OK;
+}
+
+vie_status vie_set_permittivity(vie_plan* p, const double* eps_host, const vie_absorber* absorbers, int n_abs) {
+  clear_error();
+  return set_contrast_common(p, eps_host, absorbers, n_abs, 1);
+}
+
+vie_status vie_set_contrast(vie_plan* p, const double* chi_host) {
+  clear_error();
+  return set_contrast_common(p, chi_host, nullptr, 0, 0);
+}
+
+static vie_status check_vec_args(vie_plan* p, const void* x, void* y, int dtype) {
+  if (!p || !x || !y) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
+  const size_t bytes = (size_t)3 * p->n[0] * p->n[1] * p->n[2] * (dtype == VIE_C64 ? 8 : 16);
+  const char* a = (const char*)x;
+  const char* b = (const char*)y;
+  if (a < b + bytes && b < a + bytes) { set_error("x and y overlap"); return VIE_ERR_INVALID; }
+  return VIE_OK;
+}
+
+vie_status vie_matvec(vie_plan* p, const void* x, void* y, int dtype, void* stream) {
+  clear_error();
+  vie_status st = check_vec_args(p, x, y, dtype);
+  if (st != VIE_OK) return st;
+  return matvec_impl(p, x, y, dtype, MODE_OPERATOR, p->work, (cudaStream_t)stream);
+}
+
+vie_status vie_rhs_from_source(vie_plan* p, const void* src, void* b, int dtype, void* stream) {
+  clear_error();
+  vie_status st = check_vec_args(p, src, b, dtype);
+  if (st != VIE_OK) return st;
+  return matvec_impl(p, src, b, dtype, MODE_RHS, p->work, (cudaStream_t)stream);
+}
+
+vie_status vie_get_toeplitz(const vie_plan* p, double* out) {
+  clear_error();
+  if (!p || !out) { set_error("null argument"); return VIE_ERR_INVALID; }
+  const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  VIE_CUDA_TRY(cudaSetDevice(p->device));
+  VIE_CUDA_TRY(cudaMemcpy(out, p->toeplitz, 6 * N * sizeof(double2), cudaMemcpyDeviceToHost));
+  return VIE_OK;
+}
+
+vie_status vie_eps2_from_round_trip(double r_rt, int degree, double length, double k0, double eps_r, double D,
+                                    double eta, double* eps2_max) {
+  clear_error();
+  if (!eps2_max || !(r_rt > 0.0 && r_rt < 1.0) || degree < 0 || !(length > 0.0) || !(k0 > 0.0) ||
+      !(eps_r > 0.0) || !(D > 0.0) || !(eta > 0.0)) {
+    set_error("need 0 < r_rt < 1, degree >= 0 and positive length, k0, eps_r, D, eta");
+    return VIE_ERR_INVALID;
+  }
+  *eps2_max = -(degree + 1) * log(r_rt) * sqrt(eps_r) / (D * length * eta * k0);
+  return VIE_OK;
+}
+
+}  // extern "C"

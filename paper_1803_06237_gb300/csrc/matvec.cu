@@ -1,0 +1,229 @@
+// The J-VIE operator application y = w - M (N w) (Sec. 6 of arXiv:1803.06237:
+// the block-Toeplitz N, six unique tensor components, applied with FFTs; the
+// diagonal multiplier M_eps of Sec. 3 carries material and absorber).
+//
+// Three passes over a workspace X[kx][line] (line = (c nz + z) ny + y, the
+// 3 ny nz non-zero x-lines of the zero-padded currents):
+//   A  per group of x-lines: load nx values, zero-pad to Mx, forward FFT along
+//      x, write transposed so that one kx holds all lines contiguously.
+//   B  per kx: forward FFT along z (ny non-zero rows) and y (all Mz columns),
+//      u_p = sum_q G_pq w_q with the folded spectrum (parity signs restore the
+//      other octants), inverse FFT along y (keep y < ny) and z (keep z < nz),
+//      written back in place.
+//   C  per group of x-lines: inverse FFT along x, crop to nx, and
+//      y = w - M u (operator) or y = M (u - w) (right-hand side of a source).
+// The spectrum is pre-scaled by 1/(Mx My Mz), so no separate normalisation.
+#include <stdio.h>
+
+#include "fft.cuh"
+#include "vie_internal.cuh"
+
+namespace vie {
+
+template <typename V> __device__ __forceinline__ V zero_c();
+template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zero_c<double2>() { return make_double2(0.0, 0.0); }
+
+// ---------------------------------------------------------------------------
+// pass A
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(256) pass_a_kernel(const V* __restrict__ x, V* __restrict__ work, int nx, int NL,
+                                                     Radices rx, const V* __restrict__ twg, int lines_per_block) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Mx = rx.len;
+  const int pitch = Mx + 1;
+  V* tw = reinterpret_cast<V*>(smem_raw);
+  V* A = tw + Mx;
+  V* B = A + (size_t)lines_per_block * pitch;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * lines_per_block;
+  const int nl = min(lines_per_block, NL - l0);
+  for (int i = tid; i < Mx; i += nth) tw[i] = twg[i];
+  for (int e = tid; e < nl * Mx; e += nth) {
+    const int l = e / Mx, k = e - l * Mx;
+    A[l * pitch + k] = (k < nx) ? x[(size_t)(l0 + l) * nx + k] : zero_c<V>();
+  }
+  __syncthreads();
+  V* res = fft_lines<V, false>(A, B, rx, pitch, nl, tw, tid, nth);
+  for (int e = tid; e < nl * Mx; e += nth) {
+    const int kx = e / nl, l = e - kx * nl;
+    work[(size_t)kx * NL + l0 + l] = res[l * pitch + kx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass B
+// ---------------------------------------------------------------------------
+struct PassBGeom {
+  int ny, nz, NL, Mx, My, Mz, Ky, Kz;
+};
+
+template <typename V>
+__global__ void __launch_bounds__(256) pass_b_kernel(V* __restrict__ work, const V* __restrict__ ghat, PassBGeom g,
+                                                     Radices ry, Radices rz, const V* __restrict__ twyg,
+                                                     const V* __restrict__ twzg) {
+  extern __shared__ unsigned char smem_raw[];
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ny = g.ny, nz = g.nz, My = g.My, Mz = g.Mz;
+  const int pz = Mz + 1, py = My + 1;
+  const int buf = 3 * Mz * py;   // >= 3 * ny * pz since My >= ny
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + My;
+  V* U = twz + Mz;
+  V* W = U + buf;
+  for (int i = tid; i < My; i += nth) twy[i] = twyg[i];
+  for (int i = tid; i < Mz; i += nth) twz[i] = twzg[i];
+  // load the kx slab: z-rows (c, y) of length Mz, zero-padded
+  V* slab = work + (size_t)kx * g.NL;
+  for (int e = tid; e < 3 * ny * Mz; e += nth) {
+    const int row = e / Mz, z = e - row * Mz;   // row = c*ny + y
+    const int c = row / ny, y = row - c * ny;
+    U[row * pz + z] = (z < nz) ? slab[(c * nz + z) * ny + y] : zero_c<V>();
+  }
+  __syncthreads();
+  V* zr = fft_lines<V, false>(U, W, rz, pz, 3 * ny, twz, tid, nth);
+  V* other = (zr == U) ? W : U;
+  // transpose to y-rows (c, kz) of length My, zero-padded
+  for (int e = tid; e < 3 * Mz * My; e += nth) {
+    const int row = e / My, y = e - row * My;   // row = c*Mz + kz
+    const int c = row / Mz, kz = row - c * Mz;
+    other[row * py + y] = (y < ny) ? zr[(c * ny + y) * pz + kz] : zero_c<V>();
+  }
+  __syncthreads();
+  V* yr = fft_lines<V, false>(other, zr, ry, py, 3 * Mz, twy, tid, nth);
+  // spectral multiply u_p = sum_q G_pq w_q with folded spectrum and parity signs
+  {
+    const bool fx = kx > g.Mx - kx;
+    const int kxf = fx ? g.Mx - kx : kx;
+    const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
+    for (int e = tid; e < Mz * My; e += nth) {
+      const int kz = e / My, ky = e - kz * My;
+      const bool fy = ky > My - ky, fz = kz > Mz - kz;
+      const int kyf = fy ? My - ky : ky, kzf = fz ? Mz - kz : kz;
+      const size_t o = (size_t)kzf * g.Ky + kyf;
+      const size_t cs = (size_t)g.Kz * g.Ky;
+      V gxx = G[o], gyy = G[cs + o], gzz = G[2 * cs + o];
+      V gxy = G[3 * cs + o], gxz = G[4 * cs + o], gyz = G[5 * cs + o];
+      if (fx ^ fy) gxy = scale(gxy, -1.0f);
+      if (fx ^ fz) gxz = scale(gxz, -1.0f);
+      if (fy ^ fz) gyz = scale(gyz, -1.0f);
+      V* px = yr + (0 * Mz + kz) * py + ky;
+      V* pyv = yr + (1 * Mz + kz) * py + ky;
+      V* pzv = yr + (2 * Mz + kz) * py + ky;
+      const V wx = *px, wy = *pyv, wz = *pzv;
+      *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
+      *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
+      *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+    }
+  }
+  __syncthreads();
+  V* spare = (yr == U) ? W : U;
+  V* yi = fft_lines<V, true>(yr, spare, ry, py, 3 * Mz, twy, tid, nth);
+  V* other2 = (yi == U) ? W : U;
+  // back to z-rows (c, y < ny) of length Mz
+  for (int e = tid; e < 3 * ny * Mz; e += nth) {
+    const int row = e / Mz, kz = e - row * Mz;   // row = c*ny + y
+    const int c = row / ny, y = row - c * ny;
+    other2[row * pz + kz] = yi[(c * Mz + kz) * py + y];
+  }
+  __syncthreads();
+  V* spare2 = (other2 == U) ? W : U;
+  V* zi = fft_lines<V, true>(other2, spare2, rz, pz, 3 * ny, twz, tid, nth);
+  for (int e = tid; e < g.NL; e += nth) {
+    const int y = e % ny, cz = e / ny;
+    const int z = cz % nz, c = cz / nz;
+    slab[e] = zi[(c * ny + y) * pz + z];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass C
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(256) pass_c_kernel(const V* __restrict__ work, const V* __restrict__ x,
+                                                     const V* __restrict__ Mc, V* __restrict__ y, int nx, int nyz,
+                                                     int NL, Radices rx, const V* __restrict__ twg,
+                                                     int lines_per_block, int mode) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Mx = rx.len;
+  const int pitch = Mx + 1;
+  V* tw = reinterpret_cast<V*>(smem_raw);
+  V* A = tw + Mx;
+  V* B = A + (size_t)lines_per_block * pitch;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * lines_per_block;
+  const int nl = min(lines_per_block, NL - l0);
+  for (int i = tid; i < Mx; i += nth) tw[i] = twg[i];
+  for (int e = tid; e < nl * Mx; e += nth) {
+    const int kx = e / nl, l = e - kx * nl;
+    A[l * pitch + kx] = work[(size_t)kx * NL + l0 + l];
+  }
+  __syncthreads();
+  V* res = fft_lines<V, true>(A, B, rx, pitch, nl, tw, tid, nth);
+  for (int e = tid; e < nl * nx; e += nth) {
+    const int l = e / nx, ix = e - l * nx;
+    const int line = l0 + l;
+    const size_t gi = (size_t)line * nx + ix;
+    const size_t vox = (size_t)(line % nyz) * nx + ix;
+    const V u = res[l * pitch + ix];
+    const V w = x[gi];
+    const V m = Mc[vox];
+    y[gi] = (mode == MODE_OPERATOR) ? sub(w, mul(m, u)) : mul(m, sub(u, w));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+template <typename V>
+static vie_status run_passes(vie_plan* p, const V* x, V* y, const V* ghat, const V* Mc, const V* twx,
+                             const V* twy, const V* twz, int mode, V* work, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
+  const int NL = 3 * ny * nz;
+  const int threads = 256;
+  // passes A and C: lines per block from the shared-memory budget
+  const size_t line_bytes = (size_t)2 * (Mx + 1) * sizeof(V);
+  const size_t tw_bytes = (size_t)Mx * sizeof(V);
+  int lpb = 4;
+  while (lpb > 1 && tw_bytes + lpb * line_bytes > 200 * 1024) lpb >>= 1;
+  const size_t smem_ac = tw_bytes + lpb * line_bytes;
+  if (smem_ac > 220 * 1024) {
+    set_error("Mx = %d too large for the x-pass shared memory", Mx);
+    return VIE_ERR_INVALID;
+  }
+  const size_t smem_b = (size_t)(My + Mz + 2 * 3 * Mz * (My + 1)) * sizeof(V);
+  if (smem_b > 220 * 1024) {
+    set_error("y-z plane %d x %d too large for the per-kx pass", My, Mz);
+    return VIE_ERR_INVALID;
+  }
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  const unsigned blocks_ac = (unsigned)((NL + lpb - 1) / lpb);
+  pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(x, work, nx, NL, radices_of(p->ax[0]), twx, lpb);
+  VIE_LAUNCH_CHECK();
+  PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
+  pass_b_kernel<V><<<(unsigned)Mx, threads, smem_b, s>>>(work, ghat, g, radices_of(p->ax[1]), radices_of(p->ax[2]),
+                                                         twy, twz);
+  VIE_LAUNCH_CHECK();
+  pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(work, x, Mc, y, nx, ny * nz, NL, radices_of(p->ax[0]), twx,
+                                                       lpb, mode);
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
+vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, void* work, cudaStream_t s) {
+  if (dtype == VIE_C64)
+    return run_passes<float2>(p, (const float2*)x, (float2*)y, p->ghat32, p->M32, p->ax[0].tw32, p->ax[1].tw32,
+                              p->ax[2].tw32, mode, (float2*)work, s);
+  if (dtype == VIE_C128)
+    return run_passes<double2>(p, (const double2*)x, (double2*)y, p->ghat64, p->M64, p->ax[0].tw64, p->ax[1].tw64,
+                               p->ax[2].tw64, mode, (double2*)work, s);
+  set_error("unknown dtype %d", dtype);
+  return VIE_ERR_INVALID;
+}
+
+}  // namespace vie

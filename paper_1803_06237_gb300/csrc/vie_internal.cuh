@@ -1,0 +1,129 @@
+// Internal declarations shared by the libvie translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/vie.h"
+
+namespace vie {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message behind vie_last_error)
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define VIE_CUDA_TRY(expr)                                                    \
+  do {                                                                        \
+    cudaError_t e__ = (expr);                                                 \
+    if (e__ != cudaSuccess) {                                                 \
+      ::vie::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #expr,     \
+                       cudaGetErrorString(e__));                              \
+      return e__ == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;   \
+    }                                                                         \
+  } while (0)
+
+#define VIE_LAUNCH_CHECK()                                                    \
+  do {                                                                        \
+    cudaError_t e__ = cudaGetLastError();                                     \
+    if (e__ != cudaSuccess) {                                                 \
+      ::vie::set_error("%s:%d: kernel launch failed: %s", __FILE__, __LINE__, \
+                       cudaGetErrorString(e__));                              \
+      return VIE_ERR_CUDA;                                                    \
+    }                                                                         \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// complex helpers on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename R> struct cplx_t;
+template <> struct cplx_t<float> { typedef float2 type; };
+template <> struct cplx_t<double> { typedef double2 type; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename V> __host__ __device__ __forceinline__ V add(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V> __host__ __device__ __forceinline__ V sub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename V> __host__ __device__ __forceinline__ V mul(V a, V b) {
+  V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename V> __host__ __device__ __forceinline__ V mulc(V a, V b) {
+  V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename V, typename R> __host__ __device__ __forceinline__ V scale(V a, R s) { V r; r.x = a.x * s; r.y = a.y * s; return r; }
+// -i * a  and  +i * a
+template <typename V> __host__ __device__ __forceinline__ V mul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+template <typename V> __host__ __device__ __forceinline__ V mul_pi(V a) { V r; r.x = -a.y; r.y = a.x; return r; }
+
+// ---------------------------------------------------------------------------
+// FFT plans for one axis
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 16;
+
+struct AxisPlan {
+  int len = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {0};
+  float2* tw32 = nullptr;   // device, len entries: exp(-2 pi i k / len)
+  double2* tw64 = nullptr;
+};
+
+// Radix list passed by value to kernels.
+struct Radices {
+  int len;
+  int nstages;
+  int r[kMaxStages];
+};
+
+inline Radices radices_of(const AxisPlan& a) {
+  Radices r;
+  r.len = a.len;
+  r.nstages = a.nstages;
+  for (int i = 0; i < kMaxStages; ++i) r.r[i] = a.radix[i];
+  return r;
+}
+
+bool factor_length(int len, AxisPlan* out);   // radices from {4, 2, 3, 5}
+int smooth_size_at_least(int n);               // smallest 5-smooth >= n
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+}  // namespace vie
+
+struct vie_plan {
+  int n[3];
+  int m[3];
+  int kf[3];                  // folded (octant) spectrum extents m/2 + 1
+  double h, k0, eps_bg, kappa;
+  int device;
+  vie::AxisPlan ax[3];
+  // FP64 Toeplitz octant [6][nz][ny][nx]
+  double2* toeplitz = nullptr;
+  // folded spectra, pre-scaled by 1/(Mx My Mz): layout [kx'][c][kz'][ky']
+  double2* ghat64 = nullptr;
+  float2* ghat32 = nullptr;
+  // contrast M per voxel [z][y][x]
+  double2* M64 = nullptr;
+  float2* M32 = nullptr;
+  double2* chi64 = nullptr;
+  // matvec workspace: 3*ny*nz lines x Mx spectra, sized for complex128
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  size_t device_bytes = 0;
+  double setup_ms = 0.0;
+};
+
+namespace vie {
+
+vie_status compute_toeplitz(vie_plan* p, cudaStream_t s);
+vie_status compute_spectrum(vie_plan* p, cudaStream_t s);
+vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode,
+                       void* work, cudaStream_t s);
+
+enum { MODE_OPERATOR = 0, MODE_RHS = 1 };
+
+}  // namespace vie

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libvie (include/vie.h).
+
+Argument marshalling only: every step of the operator, setup and solver runs
+in the CUDA library.  Tensors are PyTorch CUDA tensors (used for device memory
+and streams); host arrays are NumPy.  If the library is missing this module
+raises at first use -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VIE_OK = 0
+VIE_C64 = 1
+VIE_C128 = 2
+VIE_PLAN_DEFAULT = 0
+VIE_PLAN_CIRC_2N = 1
+
+_STATUS = {0: "VIE_OK", 1: "VIE_ERR_INVALID", 2: "VIE_ERR_OOM", 3: "VIE_ERR_CUDA",
+           4: "VIE_ERR_NOT_CONVERGED", 5: "VIE_ERR_TIMEOUT", 6: "VIE_ERR_NONFINITE"}
+
+
+class VieError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vie_plan_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("k0", ctypes.c_double), ("eps_bg", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double)]
+
+
+class vie_absorber(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("length", ctypes.c_double), ("degree", ctypes.c_int),
+                ("direction", ctypes.c_int), ("eps2_max", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "vie_plan_create": ([ctypes.POINTER(_P), ctypes.POINTER(_I), _D, _D, _D, _I], _I),
+    "vie_plan_destroy": ([_P], _I),
+    "vie_plan_get_info": ([_P, ctypes.POINTER(vie_plan_info)], _I),
+    "vie_set_permittivity": ([_P, _P, ctypes.POINTER(vie_absorber), _I], _I),
+    "vie_set_contrast": ([_P, _P], _I),
+    "vie_matvec": ([_P, _P, _P, _I, _P], _I),
+    "vie_rhs_from_source": ([_P, _P, _P, _I, _P], _I),
+    "vie_get_toeplitz": ([_P, _P], _I),
+    "vie_eps2_from_round_trip": ([_D, _I, _D, _D, _D, _D, _D, ctypes.POINTER(_D)], _I),
+    "vie_last_error": ([], ctypes.c_char_p),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libvie.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvie.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != VIE_OK:
+        msg = load().vie_last_error()
+        raise VieError(status, where, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return VIE_C64
+    if t.dtype == torch.complex128:
+        return VIE_C128
+    raise TypeError(f"unsupported dtype {t.dtype}; use complex64 or complex128")
+
+
+class Plan:
+    """Owns a vie_plan*; destroyed with the object or by close()."""
+
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = tuple(int(v) for v in n)
+
+    @property
+    def n_vox(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def close(self):
+        if self.handle:
+            load().vie_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = vie_plan_info()
+        _check(load().vie_plan_get_info(self.handle, ctypes.byref(inf)), "vie_plan_get_info")
+        return {"n": tuple(inf.n), "m": tuple(inf.m), "h": inf.h, "k0": inf.k0, "eps_bg": inf.eps_bg,
+                "kappa": inf.kappa, "device_bytes": inf.device_bytes, "setup_ms": inf.setup_ms}
+
+
+# ----------------------------------------------------------------------------
+# entry points (same names as include/vie.h)
+# ----------------------------------------------------------------------------
+def vie_plan_create(n, h: float, k0: float, eps_bg: float, flags: int = VIE_PLAN_DEFAULT) -> Plan:
+    lib = load()
+    arr = (ctypes.c_int * 3)(*[int(v) for v in n])
+    h_out = ctypes.c_void_p()
+    _check(lib.vie_plan_create(ctypes.byref(h_out), arr, float(h), float(k0), float(eps_bg), int(flags)),
+           "vie_plan_create")
+    return Plan(h_out, n)
+
+
+def vie_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def vie_plan_get_info(plan: Plan) -> dict:
+    return plan.info()
+
+
+def _host_c128(a, count: int) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128).ravel())
+    if a.size != count:
+        raise ValueError(f"expected {count} complex values, got {a.size}")
+    return a
+
+
+def vie_set_permittivity(plan: Plan, eps, absorbers=()):
+    """eps: (nz, ny, nx) complex relative permittivity; absorbers: sequence of
+    dicts with keys x0, length, degree, eps2_max and optional direction."""
+    e = _host_c128(eps, plan.n_vox)
+    arr = (vie_absorber * max(1, len(absorbers)))()
+    for i, ab in enumerate(absorbers):
+        arr[i] = vie_absorber(float(ab["x0"]), float(ab["length"]), int(ab["degree"]),
+                              int(ab.get("direction", 1)), float(ab["eps2_max"]))
+    _check(load().vie_set_permittivity(plan.handle, e.ctypes.data_as(ctypes.c_void_p), arr, len(absorbers)),
+           "vie_set_permittivity")
+
+
+def vie_set_contrast(plan: Plan, chi):
+    c = _host_c128(chi, plan.n_vox)
+    _check(load().vie_set_contrast(plan.handle, c.ctypes.data_as(ctypes.c_void_p)), "vie_set_contrast")
+
+
+def _vec_call(fn_name, plan: Plan, x, y, stream):
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous CUDA tensors")
+    if x.dtype != y.dtype or x.numel() != 3 * plan.n_vox or y.numel() != 3 * plan.n_vox:
+        raise ValueError("x and y must be complex vectors of 3*nx*ny*nz elements and equal dtype")
+    fn = getattr(load(), fn_name)
+    _check(fn(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), _dtype_code(x),
+              _stream_handle(stream)), fn_name)
+    return y
+
+
+def vie_matvec(plan: Plan, x, y, stream=None):
+    """y = x - M (N x) on the device (stream: torch stream or None = current)."""
+    return _vec_call("vie_matvec", plan, x, y, stream)
+
+
+def vie_rhs_from_source(plan: Plan, src, b, stream=None):
+    """b = M ((N - I) src) on the device."""
+    return _vec_call("vie_rhs_from_source", plan, src, b, stream)
+
+
+def vie_get_toeplitz(plan: Plan) -> np.ndarray:
+    """FP64 octant (6, nz, ny, nx) complex128."""
+    nx, ny, nz = plan.n
+    out = np.empty((6, nz, ny, nx), dtype=np.complex128)
+    _check(load().vie_get_toeplitz(plan.handle, out.ctypes.data_as(ctypes.c_void_p)), "vie_get_toeplitz")
+    return out
+
+
+def vie_eps2_from_round_trip(r_rt, degree, length, k0, eps_r, D=2.0, eta=1.0) -> float:
+    out = ctypes.c_double()
+    _check(load().vie_eps2_from_round_trip(float(r_rt), int(degree), float(length), float(k0), float(eps_r),
+                                           float(D), float(eta), ctypes.byref(out)), "vie_eps2_from_round_trip")
+    return out.value
+
+
+def vie_last_error() -> str:
+    m = load().vie_last_error()
+    return m.decode() if m else ""

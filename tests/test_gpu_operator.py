@@ -1,0 +1,178 @@
+"""GPU parity of the setup (Toeplitz entries) and the J-VIE operator
+application against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: complex128 path, relative L2 <= 1e-12 (FP64 FFTs of length up to
+~1.4e6 accumulate ~1e-15 per element; the entries agree to ~1e-15 relative);
+complex64 path, relative L2 <= 2e-6 (FP32 unit roundoff 6e-8 times the ~20
+butterfly stages and the 3x3 multiply, with margin), element-wise
+|y_gpu - y| <= 1e-5 max|y|.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import oracle_matvec, oracle_sparse_apply, rel_l2
+from oracle import greens
+from oracle import operator as op
+from paper_1803_06237_gb300 import build, vie, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-6
+K0 = 2 * math.pi / 1.55
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    vie.load()
+    assert torch.cuda.is_available()
+
+
+def _apply(plan, x, dtype, mode="operator"):
+    xd = torch.from_numpy(np.ascontiguousarray(x.ravel())).to(dtype).cuda()
+    yd = torch.empty_like(xd)
+    if mode == "operator":
+        vie.vie_matvec(plan, xd, yd)
+    else:
+        vie.vie_rhs_from_source(plan, xd, yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("grid,h,eps_bg", [((5, 4, 3), 0.4 / 12, 1.0), ((12, 12, 12), 0.4 / 12, 1.0),
+                                           ((9, 23, 11), 0.02, 2.085)])
+def test_toeplitz_entries_match_oracle(grid, h, eps_bg):
+    plan = vie.vie_plan_create(grid, h, K0, eps_bg)
+    T_gpu = vie.vie_get_toeplitz(plan)
+    kappa = plan.info()["kappa"]
+    T_ref = greens.octant_table(kappa, grid)
+    scale = np.abs(T_ref).max()
+    assert np.abs(T_gpu - T_ref).max() <= 1e-13 * scale
+    # far entries separately, relative to their own size
+    far = np.abs(T_ref).max(axis=0) < 1e-2 * scale
+    if far.any():
+        d = np.abs(T_gpu - T_ref)[:, far].max() / np.abs(T_ref)[:, far].max()
+        assert d < 1e-12
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, TOL32)])
+def test_cube_matvec_matches_oracle(dtype, tol):
+    wl = workloads.cube(12)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    eps = workloads.random_permittivity(wl.grid, seed=21)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(wl.grid, seed=22)
+    y = _apply(plan, x, dtype)
+    M = op.contrast_M(op.chi_from_permittivity(eps, wl.eps_bg))
+    y_ref = oracle_matvec(wl.grid, wl.kappa, M, x).ravel()
+    assert rel_l2(y, y_ref) <= tol
+    assert np.abs(y - y_ref).max() <= 5 * tol * np.abs(y_ref).max()
+
+
+@pytest.mark.parametrize("grid", [(1, 1, 1), (2, 3, 5), (7, 1, 1), (1, 1, 9), (13, 4, 6), (3, 7, 2), (31, 2, 3)])
+@pytest.mark.parametrize("flags", [vie.VIE_PLAN_DEFAULT, vie.VIE_PLAN_CIRC_2N])
+def test_ragged_grids(grid, flags):
+    two_n_smooth = all(_smooth(2 * v) for v in grid)
+    if flags == vie.VIE_PLAN_CIRC_2N and not two_n_smooth:
+        with pytest.raises(vie.VieError) as ei:
+            vie.vie_plan_create(grid, 0.02, K0, 2.085, flags)
+        assert ei.value.status == 1
+        return
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085, flags)
+    m = plan.info()["m"]
+    assert all(mi >= 2 * ni - 1 for mi, ni in zip(m, grid))
+    eps = workloads.random_permittivity(grid, seed=31)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=32)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
+    assert rel_l2(_apply(plan, x, torch.complex128), y_ref) <= TOL64
+    assert rel_l2(_apply(plan, x, torch.complex64), y_ref) <= TOL32
+
+
+def _smooth(m):
+    for f in (2, 3, 5):
+        while m % f == 0:
+            m //= f
+    return m == 1
+
+
+def test_zero_contrast_is_identity_bitwise():
+    grid = (10, 6, 4)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    x = workloads.random_currents(grid, seed=3)
+    for dt in (torch.complex128, torch.complex64):
+        y = _apply(plan, x, dt)
+        assert np.array_equal(y, x.ravel().astype(dt == torch.complex64 and np.complex64 or np.complex128))
+
+
+def _waveguide_section(nx):
+    wl = workloads.waveguide(nx=nx, absorber_len_um=nx * 0.02 / 3, src_x_um=min(1.0, nx * 0.02 / 4))
+    ab = wl.absorbers[0]
+    e2 = op.eps2_max_from_rrt(1e-10, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+    absorbers = [dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2)]
+    return wl, absorbers
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, TOL32)])
+def test_waveguide_section_with_absorber(dtype, tol):
+    wl, absorbers = _waveguide_section(60)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    x = workloads.random_currents(wl.grid, seed=41)
+    M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, absorbers))
+    y_ref = oracle_matvec(wl.grid, wl.kappa, M, x).ravel()
+    assert rel_l2(_apply(plan, x, dtype), y_ref) <= tol
+
+
+def test_rhs_from_source_matches_oracle():
+    wl, absorbers = _waveguide_section(40)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    src = workloads.gaussian_sheet(wl.grid, 10, 10.0)
+    M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, absorbers))
+    b_ref = oracle_matvec(wl.grid, wl.kappa, M, src, mode="rhs").ravel()
+    assert rel_l2(_apply(plan, src, torch.complex128, mode="rhs"), b_ref) <= TOL64
+    assert rel_l2(_apply(plan, src, torch.complex64, mode="rhs"), b_ref) <= TOL32
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, 1e-5)])
+def test_full_size_waveguide_sampled(dtype, tol):
+    """600 x 23 x 11 guide, the launch configuration of the benchmark: sparse
+    input, 240 sampled outputs summed directly by the oracle."""
+    wl = workloads.waveguide()
+    ab = wl.absorbers[0]
+    e2 = op.eps2_max_from_rrt(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+    absorbers = [dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2)]
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    x = workloads.sparse_currents(wl.grid, seed=51, nnz=20)
+    y = _apply(plan, x, dtype)
+    idx = workloads.sample_indices(wl.grid, seed=52, count=200)
+    nzv = np.flatnonzero(x.ravel())
+    idx = np.unique(np.concatenate([idx, nzv, nzv + 1]))
+    idx = idx[idx < 3 * wl.n_voxels]
+    M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, absorbers))
+    ref = oracle_sparse_apply(wl.kappa, wl.grid, M, x, idx)
+    assert np.abs(y[idx] - ref).max() <= tol * np.abs(ref).max()
+    # far from every source the response is small but must still match in absolute terms
+    assert np.isfinite(y).all()
+
+
+def test_bad_inputs_report_errors():
+    grid = (4, 3, 2)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    eps = np.full((2, 3, 4), 2.0 + 0j)
+    eps[1, 1, 1] = 0.0     # eps_r = 0 -> M = chi / (1 + chi) undefined
+    with pytest.raises(vie.VieError) as ei:
+        vie.vie_set_permittivity(plan, eps)
+    assert ei.value.status == 6
+    x = torch.zeros(2 * 3 * 24, dtype=torch.complex128, device="cuda")
+    rc = vie.load().vie_matvec(plan.handle, ctypes.c_void_p(x.data_ptr()),
+                               ctypes.c_void_p(x.data_ptr() + 16), vie.VIE_C128, None)
+    assert rc == 1 and "overlap" in vie.vie_last_error()
