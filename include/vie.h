@@ -138,6 +138,56 @@ vie_status vie_eps2_from_round_trip(double r_rt, int degree, double length,
                                     double k0, double eps_r, double D, double eta,
                                     double* eps2_max);
 
+/* ------------------------------------------------------------------------ */
+/* Iterative solution of (I - M_eps N) w = b (Sec. 6 discrete J-VIE; the paper
+ * uses GMRES at relative tolerance 1e-8, Sec. 5).                            */
+/* ------------------------------------------------------------------------ */
+enum {
+  VIE_SOLVE_FP64 = 0,   /* restarted GMRES on the complex128 operator */
+  VIE_SOLVE_MIXED = 1   /* iterative refinement: residual b - A x with the
+                           complex128 operator, correction by restarted
+                           (flexible) GMRES on the complex64 operator to a
+                           loose tolerance, x accumulated in complex128 */
+};
+
+typedef struct {
+  int mode;               /* VIE_SOLVE_FP64 or VIE_SOLVE_MIXED */
+  int restart;            /* Krylov dimension m per cycle (<= 1000; 0 -> 100) */
+  int max_iters;          /* cap on Arnoldi steps over the solve (0 -> 5000) */
+  double inner_tol;       /* mixed: relative residual reduction asked of each
+                             complex64 cycle (0 -> 1e-4) */
+  int max_outer;          /* cap on cycles / refinement steps (0 -> 200) */
+  int x0_given;           /* 1: x_dev holds an initial guess on entry */
+  int use_preconditioner; /* 1: right-precondition with the learned network
+                             set by vie_set_preconditioner (flexible GMRES) */
+  int check_every;        /* host reads the device status every k steps (0 -> 4) */
+  double timeout_s;       /* host wall-clock limit (0 -> 600 s) */
+} vie_solve_opts;
+
+typedef struct {
+  int iterations;         /* Arnoldi steps (Krylov operator applications) */
+  int outer;              /* GMRES cycles (= refinement steps in mixed mode) */
+  int matvecs64;          /* complex128 operator applications */
+  int matvecs32;          /* complex64 operator applications */
+  int converged;          /* 1 if ||b - A x|| <= tol ||b|| (true FP64 residual) */
+  int fallback;           /* 1 if the preconditioner was dropped during the solve */
+  double residual;        /* final true relative residual ||b - A x|| / ||b|| */
+  double time_ms;         /* device time of the solve */
+  int history_len;        /* entries used in history */
+  double history[64];     /* true relative residual at the start of each cycle */
+} vie_solve_info;
+
+/* Solve (I - M N) x = b on the device.  b_dev and x_dev are complex128 device
+ * vectors of 3*nx*ny*nz entries (x_dev: initial guess if opts->x0_given, the
+ * solution on return; b_dev is not modified).  Convergence is judged on the
+ * true FP64 residual.  The solver workspace is allocated on the first call
+ * for a given (restart, mode) and kept by the plan.  Synchronises `stream`
+ * before returning.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA,
+ * VIE_ERR_NONFINITE, VIE_ERR_TIMEOUT (x holds the best iterate),
+ * VIE_ERR_NOT_CONVERGED (caps reached; x and info hold the last iterate). */
+vie_status vie_solve(vie_plan* plan, const void* b_dev, void* x_dev, double tol,
+                     const vie_solve_opts* opts, vie_solve_info* info, void* stream);
+
 /* Thread-local description of the last error ("" if none). */
 const char* vie_last_error(void);
 

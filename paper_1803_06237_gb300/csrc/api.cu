@@ -195,6 +195,8 @@ static vie_status set_contrast_common(vie_plan* p, const double* host, const vie
 
 static void free_plan(vie_plan* p) {
   if (!p) return;
+  free_krylov(p);
+  free_precond(p);
   for (int a = 0; a < 3; ++a) {
     cudaFree(p->ax[a].tw32);
     cudaFree(p->ax[a].tw64);

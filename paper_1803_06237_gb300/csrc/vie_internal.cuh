@@ -115,6 +115,8 @@ struct vie_plan {
   size_t work_bytes = 0;
   size_t device_bytes = 0;
   double setup_ms = 0.0;
+  void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
+  void* precond = nullptr;    // learned preconditioner state, if set
 };
 
 namespace vie {
@@ -125,5 +127,14 @@ vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode,
                        void* work, cudaStream_t s);
 
 enum { MODE_OPERATOR = 0, MODE_RHS = 1 };
+
+// Right preconditioner z = P(v) on vectors of type dtype (3 N complex).
+typedef vie_status (*vie_precond_fn)(void* ctx, int dtype, const void* v, void* z, cudaStream_t s);
+
+void free_krylov(vie_plan* p);
+void free_precond(vie_plan* p);
+vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx);
+vie_status solve_impl(vie_plan* p, const double2* b, double2* x, double tol, const vie_solve_opts* o,
+                      vie_solve_info* info, vie_precond_fn precond, void* precond_ctx, cudaStream_t s);
 
 }  // namespace vie

@@ -41,6 +41,23 @@ class vie_absorber(ctypes.Structure):
                 ("direction", ctypes.c_int), ("eps2_max", ctypes.c_double)]
 
 
+class vie_solve_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("x0_given", ctypes.c_int),
+                ("use_preconditioner", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("timeout_s", ctypes.c_double)]
+
+
+class vie_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("matvecs64", ctypes.c_int),
+                ("matvecs32", ctypes.c_int), ("converged", ctypes.c_int), ("fallback", ctypes.c_int),
+                ("residual", ctypes.c_double), ("time_ms", ctypes.c_double), ("history_len", ctypes.c_int),
+                ("history", ctypes.c_double * 64)]
+
+
+VIE_SOLVE_FP64 = 0
+VIE_SOLVE_MIXED = 1
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -56,6 +73,7 @@ _SIGNATURES = {
     "vie_rhs_from_source": ([_P, _P, _P, _I, _P], _I),
     "vie_get_toeplitz": ([_P, _P], _I),
     "vie_eps2_from_round_trip": ([_D, _I, _D, _D, _D, _D, _D, ctypes.POINTER(_D)], _I),
+    "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_last_error": ([], ctypes.c_char_p),
 }
 
@@ -212,6 +230,29 @@ def vie_eps2_from_round_trip(r_rt, degree, length, k0, eps_r, D=2.0, eta=1.0) ->
     _check(load().vie_eps2_from_round_trip(float(r_rt), int(degree), float(length), float(k0), float(eps_r),
                                            float(D), float(eta), ctypes.byref(out)), "vie_eps2_from_round_trip")
     return out.value
+
+
+def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart: int = 100,
+              max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
+              use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
+              stream=None, raise_on_not_converged: bool = True) -> dict:
+    """Solve (I - M N) x = b on the device; b, x complex128 CUDA tensors."""
+    import torch
+    for t in (b, x):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128 and t.numel() == 3 * plan.n_vox):
+            raise ValueError("b and x must be contiguous complex128 CUDA vectors of 3*nx*ny*nz entries")
+    opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
+                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s))
+    info = vie_solve_info()
+    st = load().vie_solve(plan.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+                          ctypes.byref(opts), ctypes.byref(info), _stream_handle(stream))
+    out = {"status": st, "iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
+           "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
+           "residual": info.residual, "time_ms": info.time_ms,
+           "history": [info.history[i] for i in range(min(info.history_len, 64))]}
+    if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
+        _check(st, "vie_solve")
+    return out
 
 
 def vie_last_error() -> str:
