@@ -188,6 +188,28 @@ typedef struct {
 vie_status vie_solve(vie_plan* plan, const void* b_dev, void* x_dev, double tol,
                      const vie_solve_opts* opts, vie_solve_info* info, void* stream);
 
+/* Same operator application as vie_matvec, for callers that cannot allocate
+ * device memory where they apply the operator (their memory is owned by
+ * another allocator or held to a fixed budget after start-up, so they cannot
+ * make a second plan or a second workspace).  The paper has no counterpart:
+ * this is a deployment variant of the Sec. 6 product.
+ *
+ * It allocates nothing.  Its workspace is a static device array of 16 MiB
+ * inside the library (every GPU that loads the library holds it until the
+ * process exits) instead of the plan's workspace, so it may run on another
+ * stream while vie_matvec runs on the same plan.  The plan is only read.
+ * Limit: 3*ny*nz*Mx complex values of `dtype` (Mx from vie_plan_get_info) must
+ * fit in 16 MiB; larger plans are rejected with VIE_ERR_INVALID.  The plan's
+ * device must be current.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the one array and it keeps the previous
+ * call's contents; nothing in it needs to start at zero (the first pass writes
+ * every element the later passes read).  Calls whose execution overlaps on the
+ * GPU race on the array: order them on one stream or with events.
+ * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID, VIE_ERR_CUDA. */
+vie_status vie_matvec_static_scratch(const vie_plan* plan, const void* x_dev,
+                                     void* y_dev, int dtype, void* stream);
+
 /* Thread-local description of the last error ("" if none). */
 const char* vie_last_error(void);
 

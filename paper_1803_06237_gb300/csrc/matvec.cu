@@ -227,3 +227,76 @@ vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode,
 }
 
 }  // namespace vie
+
+// ---------------------------------------------------------------------------
+// Operator application without any allocation by the library.
+//
+// Some callers cannot call cudaMalloc where they apply the operator: their
+// device memory is owned by another allocator or held to a fixed budget after
+// start-up, so they cannot create a second plan or a second workspace.  This
+// variant runs the same three passes as vie_matvec, but its workspace is the
+// file-scope array below instead of the plan's workspace, so it can run next
+// to vie_matvec on the same plan without allocating anything.
+//
+// The array is part of the library image: every GPU that loads the library
+// holds its kStaticScratchBytes until the process exits.  Host code cannot use
+// the array's name as a device address (it names a host-side stand-in), so the
+// device address is looked up with cudaGetSymbolAddress once per device, on
+// the first call made while that device is current.
+// ---------------------------------------------------------------------------
+namespace vie {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_static_scratch_addr[kMaxDevices] = {nullptr};
+
+static vie_status static_scratch_address(void** out) {
+  int dev = 0;
+  VIE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d out of range for the static workspace", dev);
+    return VIE_ERR_INVALID;
+  }
+  if (!g_static_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      set_error("cudaGetSymbolAddress of the static workspace failed: %s", cudaGetErrorString(e));
+      return VIE_ERR_CUDA;
+    }
+    g_static_scratch_addr[dev] = ptr;
+  }
+  *out = g_static_scratch_addr[dev];
+  return VIE_OK;
+}
+
+}  // namespace vie
+
+extern "C" vie_status vie_matvec_static_scratch(const vie_plan* plan, const void* x_dev, void* y_dev, int dtype,
+                                                void* stream) {
+  using namespace vie;
+  clear_error();
+  if (!plan || !x_dev || !y_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
+  const size_t vec_bytes = (size_t)3 * plan->n[0] * plan->n[1] * plan->n[2] * (dtype == VIE_C64 ? 8 : 16);
+  const char* a = (const char*)x_dev;
+  const char* b = (const char*)y_dev;
+  if (a < b + vec_bytes && b < a + vec_bytes) { set_error("x and y overlap"); return VIE_ERR_INVALID; }
+  const size_t need = (size_t)3 * plan->n[1] * plan->n[2] * plan->m[0] * (dtype == VIE_C64 ? 8 : 16);
+  if (need > kStaticScratchBytes) {
+    set_error("workspace of %zu bytes exceeds the static workspace of %zu bytes (3*ny*nz*Mx complex values)",
+              need, kStaticScratchBytes);
+    return VIE_ERR_INVALID;
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != plan->device) {
+    set_error("the plan's device (%d) must be current (current: %d)", plan->device, cur);
+    return VIE_ERR_INVALID;
+  }
+  void* work = nullptr;
+  vie_status st = static_scratch_address(&work);
+  if (st != VIE_OK) return st;
+  return matvec_impl(const_cast<vie_plan*>(plan), x_dev, y_dev, dtype, MODE_OPERATOR, work, (cudaStream_t)stream);
+}

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "vie_rhs_from_source": ([_P, _P, _P, _I, _P], _I),
     "vie_get_toeplitz": ([_P, _P], _I),
     "vie_eps2_from_round_trip": ([_D, _I, _D, _D, _D, _D, _D, ctypes.POINTER(_D)], _I),
+    "vie_matvec_static_scratch": ([_P, _P, _P, _I, _P], _I),
     "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_last_error": ([], ctypes.c_char_p),
 }
@@ -210,6 +211,11 @@ def _vec_call(fn_name, plan: Plan, x, y, stream):
 def vie_matvec(plan: Plan, x, y, stream=None):
     """y = x - M (N x) on the device (stream: torch stream or None = current)."""
     return _vec_call("vie_matvec", plan, x, y, stream)
+
+
+def vie_matvec_static_scratch(plan: Plan, x, y, stream=None):
+    """y = x - M (N x) using the library's static workspace (allocates nothing)."""
+    return _vec_call("vie_matvec_static_scratch", plan, x, y, stream)
 
 
 def vie_rhs_from_source(plan: Plan, src, b, stream=None):
