@@ -16,6 +16,7 @@
 #include <stdio.h>
 
 #include "fft.cuh"
+#include "regfft.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
@@ -139,6 +140,153 @@ __global__ void __launch_bounds__(256) pass_b_kernel(V* __restrict__ work, const
 }
 
 // ---------------------------------------------------------------------------
+// pass B with register FFTs for compile-time lengths (MY, MZ): one line per
+// thread, four barriers per plane.  Shared rows use odd pitches so that
+// threads walking their own rows hit distinct banks.
+//   S1: (c, kz) y-lines, pitch PY;  S2: (c, y) z-lines, pitch PZ.
+// ---------------------------------------------------------------------------
+template <typename V, int MY, int MZ>
+__global__ void __launch_bounds__(256) pass_b_reg_kernel(V* __restrict__ work, const V* __restrict__ ghat,
+                                                         PassBGeom g, const V* __restrict__ twyg,
+                                                         const V* __restrict__ twzg) {
+  constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
+  constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
+  extern __shared__ unsigned char smem_raw[];
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + MY;
+  V* S1 = twz + MZ;
+  V* S2 = S1 + 3 * MZ * PY;
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ny = g.ny, nz = g.nz;
+  for (int i = tid; i < MY; i += nth) twy[i] = twyg[i];
+  for (int i = tid; i < MZ; i += nth) twz[i] = twzg[i];
+  __syncthreads();
+  V* slab = work + (size_t)kx * g.NL;
+  // forward z on the 3 ny non-zero lines (c, y)
+  for (int line = tid; line < 3 * ny; line += nth) {
+    const int c = line / ny, y = line - c * ny;
+    V a[MZ];
+#pragma unroll
+    for (int z = 0; z < MZ; ++z) a[z] = (z < nz) ? slab[(c * nz + z) * ny + y] : zero_c<V>();
+    reg_fft<V, false, MZ>(a, twz);
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) S1[(c * MZ + kz) * PY + y] = a[kz];
+  }
+  __syncthreads();
+  // forward y on all 3 MZ lines (c, kz); y >= ny is zero padding
+  for (int line = tid; line < 3 * MZ; line += nth) {
+    V a[MY];
+#pragma unroll
+    for (int y = 0; y < MY; ++y) a[y] = (y < ny) ? S1[line * PY + y] : zero_c<V>();
+    reg_fft<V, false, MY>(a, twy);
+#pragma unroll
+    for (int ky = 0; ky < MY; ++ky) S1[line * PY + ky] = a[ky];
+  }
+  __syncthreads();
+  {
+    const bool fx = kx > g.Mx - kx;
+    const int kxf = fx ? g.Mx - kx : kx;
+    const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
+    const size_t cs = (size_t)g.Kz * g.Ky;
+    for (int e = tid; e < MZ * MY; e += nth) {
+      const int kz = e / MY, ky = e - kz * MY;
+      const bool fy = ky > MY - ky, fz = kz > MZ - kz;
+      const int kyf = fy ? MY - ky : ky, kzf = fz ? MZ - kz : kz;
+      const size_t o = (size_t)kzf * g.Ky + kyf;
+      V gxx = G[o], gyy = G[cs + o], gzz = G[2 * cs + o];
+      V gxy = G[3 * cs + o], gxz = G[4 * cs + o], gyz = G[5 * cs + o];
+      if (fx ^ fy) gxy = scale(gxy, -1.0f);
+      if (fx ^ fz) gxz = scale(gxz, -1.0f);
+      if (fy ^ fz) gyz = scale(gyz, -1.0f);
+      V* px = S1 + (0 * MZ + kz) * PY + ky;
+      V* pyv = S1 + (1 * MZ + kz) * PY + ky;
+      V* pzv = S1 + (2 * MZ + kz) * PY + ky;
+      const V wx = *px, wy = *pyv, wz = *pzv;
+      *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
+      *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
+      *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+    }
+  }
+  __syncthreads();
+  // inverse y; keep y < ny, stored as z-lines (c, y)
+  for (int line = tid; line < 3 * MZ; line += nth) {
+    const int c = line / MZ, kz = line - c * MZ;
+    V a[MY];
+#pragma unroll
+    for (int ky = 0; ky < MY; ++ky) a[ky] = S1[line * PY + ky];
+    reg_fft<V, true, MY>(a, twy);
+#pragma unroll
+    for (int y = 0; y < MY; ++y)
+      if (y < ny) S2[(c * ny + y) * PZ + kz] = a[y];
+  }
+  __syncthreads();
+  // inverse z; keep z < nz, back to the workspace slab
+  for (int line = tid; line < 3 * ny; line += nth) {
+    const int c = line / ny, y = line - c * ny;
+    V a[MZ];
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) a[kz] = S2[line * PZ + kz];
+    reg_fft<V, true, MZ>(a, twz);
+#pragma unroll
+    for (int z = 0; z < MZ; ++z)
+      if (z < nz) slab[(c * nz + z) * ny + y] = a[z];
+  }
+}
+
+// (MY, MZ) pairs with a register-FFT pass B; other sizes use pass_b_kernel.
+#define VIE_PASS_B_REG_SIZES(X) \
+  X(24, 24) X(45, 24) X(48, 24) X(50, 24) X(30, 24) X(40, 24) X(25, 24) X(45, 25) X(48, 25) X(24, 25)
+
+bool pass_b_reg_available(int my, int mz) {
+#define VIE_X(a, b) if (my == a && mz == b) return true;
+  VIE_PASS_B_REG_SIZES(VIE_X)
+#undef VIE_X
+  return false;
+}
+
+template <typename V, int MY, int MZ>
+static vie_status launch_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
+                                    cudaStream_t s) {
+  constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
+  constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
+  const size_t smem = (size_t)(MY + MZ + 3 * MZ * PY + 3 * g.ny * PZ) * sizeof(V);
+  if (smem > 220 * 1024) { set_error("pass B shared memory %zu too large", smem); return VIE_ERR_INVALID; }
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_reg_kernel<V, MY, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int lines = 3 * (g.ny > MZ ? g.ny : MZ);
+  int threads = ((lines + 31) / 32) * 32;
+  if (threads > 256) threads = 256;
+  pass_b_reg_kernel<V, MY, MZ><<<(unsigned)g.Mx, threads, smem, s>>>(work, ghat, g, twy, twz);
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
+// complex128 lines longer than 30 would spill registers: those keep the generic pass
+template <typename V, int MY, int MZ>
+static vie_status try_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
+                                 cudaStream_t s, bool* done) {
+  if constexpr (sizeof(V) == sizeof(float2) || (MY <= 30 && MZ <= 30)) {
+    *done = true;
+    return launch_pass_b_reg<V, MY, MZ>(work, ghat, g, twy, twz, s);
+  } else {
+    *done = false;
+    return VIE_OK;
+  }
+}
+
+template <typename V>
+static vie_status dispatch_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
+                                      cudaStream_t s, bool* done) {
+  *done = false;
+#define VIE_X(a, b) \
+  if (g.My == a && g.Mz == b) return try_pass_b_reg<V, a, b>(work, ghat, g, twy, twz, s, done);
+  VIE_PASS_B_REG_SIZES(VIE_X)
+#undef VIE_X
+  return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // pass C
 // ---------------------------------------------------------------------------
 template <typename V>
@@ -175,6 +323,180 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const V* __restrict__ work,
 }
 
 // ---------------------------------------------------------------------------
+// x passes with a four-step register FFT, Mx = L1 * L2 (compile time).
+// Index maps: input n = n1 + L1 n2, output k = k2 + L2 k1.
+//   step 1: thread (l, n1) transforms the L2 values n1 + L1 n2 and multiplies by
+//           w_Mx^(n1 k2);  step 2: thread (l, k2) transforms the L1 values.
+// Lanes run fastest over the LPB lines of the block, so the transposed
+// workspace accesses work[k][line] are contiguous across a warp.  Shared rows
+// are padded to a pitch congruent to LPB mod 16 (no bank conflicts for 8-byte
+// elements).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb - n % 16) % 16 + 16) % 16; }
+
+template <typename V, int L1, int L2, int LPB>
+__global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
+    const V* __restrict__ x, V* __restrict__ work, int nx, int NL, const V* __restrict__ twxg) {
+  constexpr int MX = L1 * L2;
+  constexpr int R = pitch_mod16(L1 * LPB, LPB);
+  extern __shared__ unsigned char smem_raw[];
+  V* twx = reinterpret_cast<V*>(smem_raw);
+  V* tw1 = twx + MX;
+  V* tw2 = tw1 + L1;
+  V* T = tw2 + L2;                 // [k2][R], element (n1, l) at n1 * LPB + l
+  V* Xs = T + L2 * R;              // [l][P]
+  const int P = pitch_mod16(nx, LPB);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * LPB;
+  const int nl = min(LPB, NL - l0);
+  for (int i = tid; i < MX; i += nth) twx[i] = twxg[i];
+  for (int i = tid; i < L1; i += nth) tw1[i] = twxg[i * L2];   // w_L1^i = w_Mx^(i L2)
+  for (int i = tid; i < L2; i += nth) tw2[i] = twxg[i * L1];
+  for (int e = tid; e < nl * nx; e += nth) {
+    const int l = e / nx, n = e - l * nx;
+    Xs[l * P + n] = x[(size_t)(l0 + l) * nx + n];
+  }
+  __syncthreads();
+  if (tid < LPB * L1) {
+    const int l = tid % LPB, n1 = tid / LPB;
+    V a[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) {
+      const int n = n1 + L1 * n2;
+      a[n2] = (l < nl && n < nx) ? Xs[l * P + n] : zero_c<V>();
+    }
+    reg_fft<V, false, L2>(a, tw2);
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) T[k2 * R + n1 * LPB + l] = (k2 == 0) ? a[0] : mul(a[k2], twx[n1 * k2]);
+  }
+  __syncthreads();
+  if (tid < LPB * L2) {
+    const int l = tid % LPB, k2 = tid / LPB;
+    V a[L1];
+#pragma unroll
+    for (int n1 = 0; n1 < L1; ++n1) a[n1] = T[k2 * R + n1 * LPB + l];
+    reg_fft<V, false, L1>(a, tw1);
+    if (l < nl) {
+#pragma unroll
+      for (int k1 = 0; k1 < L1; ++k1) work[(size_t)(k2 + L2 * k1) * NL + l0 + l] = a[k1];
+    }
+  }
+}
+
+template <typename V, int L1, int L2, int LPB>
+__global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
+    const V* __restrict__ work, const V* __restrict__ x, const V* __restrict__ Mc, V* __restrict__ y, int nx,
+    int nyz, int NL, const V* __restrict__ twxg, int mode) {
+  constexpr int MX = L1 * L2;
+  constexpr int R = pitch_mod16(L1 * LPB, LPB);
+  extern __shared__ unsigned char smem_raw[];
+  V* twx = reinterpret_cast<V*>(smem_raw);
+  V* tw1 = twx + MX;
+  V* tw2 = tw1 + L1;
+  V* T = tw2 + L2;
+  V* Ys = T + L2 * R;
+  const int P = pitch_mod16(nx, LPB);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * LPB;
+  const int nl = min(LPB, NL - l0);
+  for (int i = tid; i < MX; i += nth) twx[i] = twxg[i];
+  for (int i = tid; i < L1; i += nth) tw1[i] = twxg[i * L2];   // w_L1^i = w_Mx^(i L2)
+  for (int i = tid; i < L2; i += nth) tw2[i] = twxg[i * L1];
+  __syncthreads();
+  // inverse transform, same decomposition with conjugate twiddles:
+  // input a = a1 + L1 a2 (a spectrum index kx), output b = b2 + L2 b1 (x)
+  if (tid < LPB * L1) {
+    const int l = tid % LPB, a1 = tid / LPB;
+    V a[L2];
+#pragma unroll
+    for (int a2 = 0; a2 < L2; ++a2)
+      a[a2] = (l < nl) ? work[(size_t)(a1 + L1 * a2) * NL + l0 + l] : zero_c<V>();
+    reg_fft<V, true, L2>(a, tw2);
+#pragma unroll
+    for (int b2 = 0; b2 < L2; ++b2) T[b2 * R + a1 * LPB + l] = (b2 == 0) ? a[0] : mulc(a[b2], twx[a1 * b2]);
+  }
+  __syncthreads();
+  if (tid < LPB * L2) {
+    const int l = tid % LPB, b2 = tid / LPB;
+    V a[L1];
+#pragma unroll
+    for (int a1 = 0; a1 < L1; ++a1) a[a1] = T[b2 * R + a1 * LPB + l];
+    reg_fft<V, true, L1>(a, tw1);
+#pragma unroll
+    for (int b1 = 0; b1 < L1; ++b1) {
+      const int n = b2 + L2 * b1;
+      if (n < nx) Ys[l * P + n] = a[b1];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nl * nx; e += nth) {
+    const int l = e / nx, ix = e - l * nx;
+    const int line = l0 + l;
+    const size_t gi = (size_t)line * nx + ix;
+    const size_t vox = (size_t)(line % nyz) * nx + ix;
+    const V u = Ys[l * P + ix];
+    const V w = x[gi];
+    const V m = Mc[vox];
+    y[gi] = (mode == MODE_OPERATOR) ? sub(w, mul(m, u)) : mul(m, sub(u, w));
+  }
+}
+
+// Mx = L1 x L2 factorisations with a four-step register x pass.
+#define VIE_PASS_X4_SIZES(X) \
+  X(40, 30) X(24, 25) X(24, 30) X(30, 30) X(45, 25) X(45, 30) X(50, 30) X(40, 40) X(20, 20)
+
+constexpr int kX4Lines = 4;
+
+template <typename V, int L1, int L2>
+static vie_status launch_x4(bool forward, const V* x, V* work, const V* Mc, V* y, int nx, int nyz, int NL,
+                            const V* twx, int mode, cudaStream_t s, bool* done) {
+  if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
+    constexpr int LPB = kX4Lines;
+    constexpr int R = pitch_mod16(L1 * LPB, LPB);
+    constexpr int NT = LPB * (L1 > L2 ? L1 : L2);
+    const int P = pitch_mod16(nx, LPB);
+    const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P) * sizeof(V);
+    if (smem > 200 * 1024) { *done = false; return VIE_OK; }
+    const unsigned blocks = (unsigned)((NL + LPB - 1) / LPB);
+    if (forward) {
+      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      pass_a4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(x, work, nx, NL, twx);
+    } else {
+      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      pass_c4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(work, x, Mc, y, nx, nyz, NL, twx, mode);
+    }
+    VIE_LAUNCH_CHECK();
+    *done = true;
+    return VIE_OK;
+  } else {
+    *done = false;
+    return VIE_OK;
+  }
+}
+
+// factor (L1, L2) of Mx with a compiled four-step kernel, or (0, 0)
+void x4_factors(int mx, int* l1, int* l2) {
+  *l1 = 0;
+  *l2 = 0;
+#define VIE_X(a, b) if (mx == a * b && *l1 == 0) { *l1 = a; *l2 = b; }
+  VIE_PASS_X4_SIZES(VIE_X)
+#undef VIE_X
+}
+
+template <typename V>
+static vie_status dispatch_x4(bool forward, int l1, int l2, const V* x, V* work, const V* Mc, V* y, int nx,
+                              int nyz, int NL, const V* twx, int mode, cudaStream_t s, bool* done) {
+  *done = false;
+#define VIE_X(a, b) \
+  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, x, work, Mc, y, nx, nyz, NL, twx, mode, s, done);
+  VIE_PASS_X4_SIZES(VIE_X)
+#undef VIE_X
+  return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 template <typename V>
@@ -199,19 +521,40 @@ static vie_status run_passes(vie_plan* p, const V* x, V* y, const V* ghat, const
     set_error("y-z plane %d x %d too large for the per-kx pass", My, Mz);
     return VIE_ERR_INVALID;
   }
-  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   const unsigned blocks_ac = (unsigned)((NL + lpb - 1) / lpb);
-  pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(x, work, nx, NL, radices_of(p->ax[0]), twx, lpb);
-  VIE_LAUNCH_CHECK();
+  int l1 = 0, l2 = 0;
+  x4_factors(Mx, &l1, &l2);
+  bool done = false;
+  vie_status st = VIE_OK;
+  if (l1) {
+    st = dispatch_x4<V>(true, l1, l2, x, work, Mc, y, nx, ny * nz, NL, twx, mode, s, &done);
+    if (st != VIE_OK) return st;
+  }
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+    pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(x, work, nx, NL, radices_of(p->ax[0]), twx, lpb);
+    VIE_LAUNCH_CHECK();
+  }
   PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
-  pass_b_kernel<V><<<(unsigned)Mx, threads, smem_b, s>>>(work, ghat, g, radices_of(p->ax[1]), radices_of(p->ax[2]),
-                                                         twy, twz);
-  VIE_LAUNCH_CHECK();
-  pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(work, x, Mc, y, nx, ny * nz, NL, radices_of(p->ax[0]), twx,
-                                                       lpb, mode);
-  VIE_LAUNCH_CHECK();
+  st = dispatch_pass_b_reg<V>(work, ghat, g, twy, twz, s, &done);
+  if (st != VIE_OK) return st;
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    pass_b_kernel<V><<<(unsigned)Mx, threads, smem_b, s>>>(work, ghat, g, radices_of(p->ax[1]), radices_of(p->ax[2]),
+                                                           twy, twz);
+    VIE_LAUNCH_CHECK();
+  }
+  done = false;
+  if (l1) {
+    st = dispatch_x4<V>(false, l1, l2, x, work, Mc, y, nx, ny * nz, NL, twx, mode, s, &done);
+    if (st != VIE_OK) return st;
+  }
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+    pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(work, x, Mc, y, nx, ny * nz, NL, radices_of(p->ax[0]), twx,
+                                                         lpb, mode);
+    VIE_LAUNCH_CHECK();
+  }
   return VIE_OK;
 }
 

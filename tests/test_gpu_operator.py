@@ -176,3 +176,42 @@ def test_bad_inputs_report_errors():
     rc = vie.load().vie_matvec(plan.handle, ctypes.c_void_p(x.data_ptr()),
                                ctypes.c_void_p(x.data_ptr() + 16), vie.VIE_C128, None)
     assert rc == 1 and "overlap" in vie.vie_last_error()
+
+
+def _smooth_at_least(n):
+    m = max(1, n)
+    while not _smooth(m):
+        m += 1
+    return m
+
+
+# (ny, nz) whose circulant sizes hit each compiled register pass-B pair
+@pytest.mark.parametrize("ny,nz", [(12, 12), (23, 11), (24, 11), (25, 11), (15, 11), (20, 11), (13, 11),
+                                   (23, 13), (24, 13), (12, 13)])
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, TOL32)])
+def test_register_pass_b_sizes(ny, nz, dtype, tol):
+    grid = (5, ny, nz)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    m = plan.info()["m"]
+    assert m[1] == _smooth_at_least(2 * ny - 1) and m[2] == _smooth_at_least(2 * nz - 1)
+    eps = workloads.random_permittivity(grid, seed=ny * 100 + nz)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=ny + nz)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
+    assert rel_l2(_apply(plan, x, dtype), y_ref) <= tol
+
+
+# nx whose Mx hits each compiled four-step x-pass factorisation
+@pytest.mark.parametrize("nx", [300, 360, 450, 563, 675, 750, 800, 600, 200])
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, TOL32)])
+def test_four_step_x_sizes(nx, dtype, tol):
+    grid = (nx, 3, 2)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    assert plan.info()["m"][0] == _smooth_at_least(2 * nx - 1)
+    eps = workloads.random_permittivity(grid, seed=nx)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=nx + 1)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
+    assert rel_l2(_apply(plan, x, dtype), y_ref) <= tol
