@@ -188,6 +188,51 @@ typedef struct {
 vie_status vie_solve(vie_plan* plan, const void* b_dev, void* x_dev, double tol,
                      const vie_solve_opts* opts, vie_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches of problems (many absorbers, profiles and right-hand sides of     */
+/* uneven grid sizes solved together).                                       */
+/* ------------------------------------------------------------------------ */
+
+/* A plan with the same grid, h, k0 and eps_bg as `base` that shares base's
+ * Toeplitz entries, spectra and twiddle tables (read-only, reference
+ * counted) and owns its contrast (zero on return) and workspace.  Either plan
+ * may be destroyed first.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA. */
+vie_status vie_plan_clone(const vie_plan* base, vie_plan** out);
+
+/* y_i = x_i - M_i (N_i x_i) for count plans.  Plans of equal grid and
+ * circulant sizes are applied together, up to 16 per launch of each pass; a
+ * plan may appear once.  x[i], y[i]: device vectors of plan i of type dtype.
+ * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID, VIE_ERR_CUDA. */
+vie_status vie_matvec_batch(vie_plan* const* plans, int count, const void* const* x,
+                            void* const* y, int dtype, void* stream);
+
+/* vie_solve for count problems at once: every step advances all open
+ * problems with one launch per kernel (the operator per group of equal
+ * shape); each problem stops when its own true FP64 residual reaches tol.
+ * b_dev[i], x_dev[i]: complex128 device vectors of plan i; infos[i] its
+ * report.  Synchronises `stream`.  Returns the first non-OK status of any
+ * problem (VIE_ERR_NOT_CONVERGED etc.; every x_dev[i] then holds its last
+ * iterate).  Errors: as vie_solve. */
+vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const* b_dev,
+                           void* const* x_dev, double tol, const vie_solve_opts* opts,
+                           vie_solve_info* infos, void* stream);
+
+/* Field on the centre axis (step a12; Sec. 3 equivalent currents J =
+ * c_e chi E, so E = J/(c_e chi); the factor c_e h^(3/2) common to every
+ * field is not applied).  w_dev: complex128 solution (3*nx*ny*nz); e_dev:
+ * complex128 output of 3*n_keep values [c][ix] for ix < n_keep on the voxel
+ * row (ny/2, nz/2), using the plan's chi.  Synchronous.  Errors:
+ * VIE_ERR_INVALID, VIE_ERR_NONFINITE (chi = 0 on the axis), VIE_ERR_CUDA. */
+vie_status vie_axis_field(const vie_plan* plan, const void* w_dev, int n_keep,
+                          void* e_dev, void* stream);
+
+/* Reflection coefficient of Sec. 5.1: R = sum |E_ref - E|^2 / sum |E_ref|^2
+ * over `count` complex128 device values (e.g. two vie_axis_field outputs
+ * cut to the guide before the absorber).  FP64 sums.  Synchronous.  Errors:
+ * VIE_ERR_INVALID, VIE_ERR_NONFINITE (zero reference), VIE_ERR_CUDA. */
+vie_status vie_reflection(const void* eref_dev, const void* e_dev, int count,
+                          double* r_out, void* stream);
+
 /* Same operator application as vie_matvec, for callers that cannot allocate
  * device memory where they apply the operator (their memory is owned by
  * another allocator or held to a fixed budget after start-up, so they cannot

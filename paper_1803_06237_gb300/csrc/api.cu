@@ -197,13 +197,20 @@ static void free_plan(vie_plan* p) {
   if (!p) return;
   free_krylov(p);
   free_precond(p);
-  for (int a = 0; a < 3; ++a) {
-    cudaFree(p->ax[a].tw32);
-    cudaFree(p->ax[a].tw64);
+  bool last = true;
+  if (p->shared_refs) {
+    last = (--*p->shared_refs == 0);
+    if (last) delete p->shared_refs;
   }
-  cudaFree(p->toeplitz);
-  cudaFree(p->ghat64);
-  cudaFree(p->ghat32);
+  if (last) {
+    for (int a = 0; a < 3; ++a) {
+      cudaFree(p->ax[a].tw32);
+      cudaFree(p->ax[a].tw64);
+    }
+    cudaFree(p->toeplitz);
+    cudaFree(p->ghat64);
+    cudaFree(p->ghat32);
+  }
   cudaFree(p->M64);
   cudaFree(p->M32);
   cudaFree(p->chi64);
@@ -292,6 +299,95 @@ vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0, 
   cudaStreamDestroy(s);
   if (st != VIE_OK) { free_plan(p); return st; }
   *out = p;
+  return VIE_OK;
+}
+
+vie_status vie_plan_clone(const vie_plan* base, vie_plan** out) {
+  clear_error();
+  if (!base || !out) { set_error("null argument"); return VIE_ERR_INVALID; }
+  *out = nullptr;
+  VIE_CUDA_TRY(cudaSetDevice(base->device));
+  vie_plan* p = new vie_plan();
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = base->n[a];
+    p->m[a] = base->m[a];
+    p->kf[a] = base->kf[a];
+    p->ax[a] = base->ax[a];
+  }
+  p->h = base->h;
+  p->k0 = base->k0;
+  p->eps_bg = base->eps_bg;
+  p->kappa = base->kappa;
+  p->device = base->device;
+  p->toeplitz = base->toeplitz;
+  p->ghat64 = base->ghat64;
+  p->ghat32 = base->ghat32;
+  p->setup_ms = 0.0;
+  vie_plan* b = const_cast<vie_plan*>(base);
+  if (!b->shared_refs) b->shared_refs = new int(1);
+  p->shared_refs = b->shared_refs;
+  ++*p->shared_refs;
+  const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  p->work_bytes = base->work_bytes;
+  struct { void** ptr; size_t sz; } allocs[] = {
+      {(void**)&p->M64, N * sizeof(double2)}, {(void**)&p->M32, N * sizeof(float2)},
+      {(void**)&p->chi64, N * sizeof(double2)}, {(void**)&p->work, p->work_bytes}};
+  size_t bytes = 0;
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.ptr, a.sz);
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(%zu) failed: %s", a.sz, cudaGetErrorString(e));
+      free_plan(p);
+      return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+    }
+    bytes += a.sz;
+  }
+  p->device_bytes = bytes;
+  cudaError_t e = cudaMemset(p->M64, 0, N * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemset(p->M32, 0, N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemset(p->chi64, 0, N * sizeof(double2));
+  if (e != cudaSuccess) {
+    set_error("cudaMemset failed: %s", cudaGetErrorString(e));
+    free_plan(p);
+    return VIE_ERR_CUDA;
+  }
+  *out = p;
+  return VIE_OK;
+}
+
+vie_status vie_matvec_batch(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype,
+                            void* stream) {
+  clear_error();
+  if (!plans || !x || !y || count < 1) { set_error("null argument or count < 1"); return VIE_ERR_INVALID; }
+  if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !x[i] || !y[i]) { set_error("null plan or vector %d", i); return VIE_ERR_INVALID; }
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) { set_error("plan %d appears twice (its workspace would be shared)", i); return VIE_ERR_INVALID; }
+  }
+  // group plans of one shape, keeping the caller's order inside a group
+  std::vector<int> done(count, 0);
+  for (int i = 0; i < count; ++i) {
+    if (done[i]) continue;
+    std::vector<vie_plan*> gp;
+    std::vector<const void*> gx;
+    std::vector<void*> gy;
+    for (int j = i; j < count; ++j) {
+      if (done[j]) continue;
+      const vie_plan* a = plans[i];
+      const vie_plan* b = plans[j];
+      if (a->n[0] == b->n[0] && a->n[1] == b->n[1] && a->n[2] == b->n[2] && a->m[0] == b->m[0] &&
+          a->m[1] == b->m[1] && a->m[2] == b->m[2] && a->device == b->device) {
+        gp.push_back(plans[j]);
+        gx.push_back(x[j]);
+        gy.push_back(y[j]);
+        done[j] = 1;
+      }
+    }
+    vie_status st = matvec_group(gp.data(), (int)gp.size(), gx.data(), gy.data(), dtype, MODE_OPERATOR,
+                                 (cudaStream_t)stream);
+    if (st != VIE_OK) return st;
+  }
   return VIE_OK;
 }
 

@@ -1,17 +1,22 @@
 // Krylov solvers for the discrete J-VIE (I - M_eps N) w = b (Sec. 6 of
-// arXiv:1803.06237; the paper solves it with GMRES at tolerance 1e-8, Sec. 5).
+// arXiv:1803.06237; the paper solves it with GMRES at tolerance 1e-8, Sec. 5),
+// for one problem or a batch of problems of uneven sizes.
 //
 // * Arnoldi with classical Gram-Schmidt applied twice (CGS2); dot products and
 //   norms accumulate in FP64 whatever the vector type; the Hessenberg matrix,
 //   Givens rotations and the small least-squares problem are FP64 and stay on
-//   the device.  The host only reads a small status record every few
-//   iterations.
+//   the device.  The host reads one status record per problem every few steps.
 // * Right-preconditioned flexible GMRES keeps z_j = P(v_j) (a nonlinear P is
 //   allowed); with no preconditioner z_j = v_j and Z aliases V.
 // * Mixed precision: iterative refinement whose residual r = b - A x uses the
 //   complex128 operator and whose correction solves A d = r with the
 //   complex64 operator to a loose tolerance; x accumulates in complex128.
-//   Plain mode runs GMRES on the complex128 operator.
+//   Plain mode runs restarted GMRES on the complex128 operator.
+// * Batching: every kernel takes a table of per-problem records and
+//   blockIdx.y (or blockIdx.x for per-problem kernels) selects the problem,
+//   so one launch advances all open problems; the operator is applied per
+//   group of equal shape (matvec_group).  Problems stop individually when
+//   their true FP64 residual reaches the tolerance.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -23,18 +28,42 @@
 
 namespace vie {
 
-constexpr int kDotBlocks = 456;     // 3 x 152 SMs
+constexpr int kDotBlocks = 456;     // 3 x 152 SMs per problem
 constexpr int kThreads = 256;
+constexpr int kMaxRestart = 1000;
 
 struct SolveStatus {
   int active;        // 1 while the cycle should continue
   int j;             // Arnoldi steps completed in this cycle
   int converged;     // residual estimate reached the target
   int breakdown;     // h_{j+1,j} == 0 (exact solution in the subspace) or non-finite
-  double beta;       // ||r0|| of the cycle
+  double beta;       // ||r|| at the start of the cycle (true residual)
   double target;     // absolute residual target of the cycle
   double resid;      // |g_{j+1}| (current residual estimate)
   double inv_h;      // 1 / h_{j+1,j}
+};
+
+// Everything a kernel needs about one problem.
+struct ProbK {
+  void* V;                 // (m + 1) basis vectors of the inner type
+  void* Z;                 // m preconditioned vectors (== V without preconditioner)
+  void* w;                 // one vector of the inner type
+  size_t n;                // 3 nx ny nz
+  const double2* b;        // right-hand side (complex128)
+  double2* x64;            // iterate (complex128)
+  double2* r64;            // residual (complex128)
+  double2* y64;            // A x (complex128)
+  double2* H;              // (m + 1) x m Hessenberg, column-major, ld = m + 1
+  double2* hcol;           // CGS2 coefficients, pass 1 + pass 2
+  double2* h2;             // pass-2 coefficients
+  double2* g;              // rotated right-hand side of the least-squares problem
+  double2* ysol;           // least-squares solution
+  double* cs;
+  double2* sn;
+  double2* partial;        // (m + 2) x kDotBlocks partial sums
+  SolveStatus* st;
+  double bnorm;            // ||b||
+  double target;           // absolute target of the next cycle
 };
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2((double)v.x, (double)v.y); }
@@ -47,44 +76,64 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Sum of `count` partials (the .x parts) by one block, fixed order; every
+// thread gets the result.
+__device__ double block_sum_partials(const double2* __restrict__ part, int count) {
+  __shared__ double red[kThreads / 32];
+  __shared__ double total;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) t += part[b].x;
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    total = s;
+  }
+  __syncthreads();
+  return total;
+}
+
 // partial[i * nblk + b] = sum over block b's chunk of conj(V_i[k]) w[k], i < nv.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) dots_kernel(const V* __restrict__ Vb, size_t ld, int nv,
-                                                        const V* __restrict__ w, size_t n,
-                                                        double2* __restrict__ partial,
-                                                        const SolveStatus* __restrict__ st) {
-  if (st && !st->active) return;
+__global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict__ P, int nv) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
+  const V* __restrict__ Vb = (const V*)q.V;
+  const V* __restrict__ w = (const V*)q.w;
+  const size_t n = q.n;
   const int nblk = gridDim.x;
   const size_t chunk = (n + nblk - 1) / nblk;
   const size_t k0 = (size_t)blockIdx.x * chunk;
   const size_t k1 = min(n, k0 + chunk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = warp; i < nv; i += nw) {
-    const V* vi = Vb + (size_t)i * ld;
+    const V* vi = Vb + (size_t)i * n;
     double re = 0.0, im = 0.0;
     for (size_t k = k0 + lane; k < k1; k += 32) {
       const double2 a = to_d2(vi[k]);
-      const double2 b = to_d2(w[k]);
-      re += a.x * b.x + a.y * b.y;
-      im += a.x * b.y - a.y * b.x;
+      const double2 c = to_d2(w[k]);
+      re += a.x * c.x + a.y * c.y;
+      im += a.x * c.y - a.y * c.x;
     }
     re = warp_sum(re);
     im = warp_sum(im);
-    if (lane == 0) partial[(size_t)i * nblk + blockIdx.x] = make_double2(re, im);
+    if (lane == 0) q.partial[(size_t)i * nblk + blockIdx.x] = make_double2(re, im);
   }
 }
 
-// out[i] = sum_b partial[i * nblk + b] in a fixed order (deterministic); if
-// acc is given, acc[i] += out[i] as well.
-__global__ void reduce_partials_kernel(const double2* __restrict__ partial, int nblk, double2* __restrict__ out,
-                                       double2* __restrict__ acc, const SolveStatus* __restrict__ st) {
-  if (st && !st->active) return;
+// pass 0: hcol[i] = sum_b partial; pass 1: h2[i] = sum_b partial, hcol[i] += h2[i].
+// Fixed summation order (deterministic).  grid (nv, problems).
+__global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const ProbK* __restrict__ P, int nblk, int pass) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
   const int i = blockIdx.x;
   __shared__ double sre[kThreads], sim[kThreads];
   double re = 0.0, im = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    re += partial[(size_t)i * nblk + b].x;
-    im += partial[(size_t)i * nblk + b].y;
+    re += q.partial[(size_t)i * nblk + b].x;
+    im += q.partial[(size_t)i * nblk + b].y;
   }
   sre[threadIdx.x] = re;
   sim[threadIdx.x] = im;
@@ -97,27 +146,32 @@ __global__ void reduce_partials_kernel(const double2* __restrict__ partial, int 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[i] = make_double2(sre[0], sim[0]);
-    if (acc) {
-      acc[i].x += sre[0];
-      acc[i].y += sim[0];
+    if (pass == 0) {
+      q.hcol[i] = make_double2(sre[0], sim[0]);
+    } else {
+      q.h2[i] = make_double2(sre[0], sim[0]);
+      q.hcol[i].x += sre[0];
+      q.hcol[i].y += sim[0];
     }
   }
 }
 
-// w[k] -= sum_{i<nv} V_i[k] h[i]   (FP64 accumulation)
+// w[k] -= sum_{i<nv} V_i[k] h[i] with h = hcol (pass 0) or h2 (pass 1); FP64 accumulation
 template <typename V>
-__global__ void __launch_bounds__(kThreads) update_kernel(const V* __restrict__ Vb, size_t ld, int nv,
-                                                          const double2* __restrict__ h, V* __restrict__ w,
-                                                          size_t n, const SolveStatus* __restrict__ st) {
-  if (st && !st->active) return;
+__global__ void __launch_bounds__(kThreads) update_kernel(const ProbK* __restrict__ P, int nv, int pass) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
   extern __shared__ double2 hs[];
+  const double2* h = pass == 0 ? q.hcol : q.h2;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
   __syncthreads();
+  const V* __restrict__ Vb = (const V*)q.V;
+  V* __restrict__ w = (V*)q.w;
+  const size_t n = q.n;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     double2 acc = to_d2(w[k]);
     for (int i = 0; i < nv; ++i) {
-      const double2 v = to_d2(Vb[(size_t)i * ld + k]);
+      const double2 v = to_d2(Vb[(size_t)i * n + k]);
       acc.x -= v.x * hs[i].x - v.y * hs[i].y;
       acc.y -= v.x * hs[i].y + v.y * hs[i].x;
     }
@@ -125,120 +179,184 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const V* __restrict__ 
   }
 }
 
-// partial[b] = sum over chunk |w[k]|^2  (stored in .x)
-template <typename V>
-__global__ void __launch_bounds__(kThreads) norm2_kernel(const V* __restrict__ w, size_t n,
-                                                         double2* __restrict__ partial,
-                                                         const SolveStatus* __restrict__ st) {
-  if (st && !st->active) return;
+__device__ __forceinline__ void block_store_sum(double s, double2* out) {
   __shared__ double red[kThreads / 32];
-  double s = 0.0;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = to_d2(w[k]);
-    s += a.x * a.x + a.y * a.y;
-  }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    partial[blockIdx.x] = make_double2(t, 0.0);
+    *out = make_double2(t, 0.0);
   }
 }
 
-// dst = src * s   (types may differ; s real)
-template <typename VD, typename VS>
-__global__ void scale_copy_kernel(VD* __restrict__ dst, const VS* __restrict__ src, size_t n,
-                                  const double* __restrict__ s_dev, double s_host,
-                                  const SolveStatus* __restrict__ st, int use_inv_h) {
-  if (st && !st->active) return;
-  const double s = use_inv_h ? st->inv_h : (s_dev ? *s_dev : s_host);
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    double2 a = to_d2(src[k]);
-    a.x *= s;
-    a.y *= s;
-    dst[k] = from_d2<VD>(a);
+// partial[b] = sum over the block's elements of |w[k]|^2
+template <typename V>
+__global__ void __launch_bounds__(kThreads) norm2_w_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
+  const V* __restrict__ w = (const V*)q.w;
+  double s = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 a = to_d2(w[k]);
+    s += a.x * a.x + a.y * a.y;
+  }
+  block_store_sum(s, q.partial + blockIdx.x);
+}
+
+// partial[b] = sum |b[k]|^2 (used before any cycle: no status check)
+__global__ void __launch_bounds__(kThreads) norm2_b_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  double s = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 a = q.b[k];
+    s += a.x * a.x + a.y * a.y;
+  }
+  block_store_sum(s, q.partial + blockIdx.x);
+}
+
+// r = b - y (complex128) with norm partials of r
+__global__ void __launch_bounds__(kThreads) residual_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  double s = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = make_double2(q.b[k].x - q.y64[k].x, q.b[k].y - q.y64[k].y);
+    q.r64[k] = v;
+    s += v.x * v.x + v.y * v.y;
+  }
+  block_store_sum(s, q.partial + blockIdx.x);
+}
+
+// One block per problem: beta = ||r|| from the residual partials, status and g.
+__global__ void __launch_bounds__(kThreads) init_cycle_kernel(const ProbK* __restrict__ P, int nblk, int m) {
+  const ProbK& q = P[blockIdx.x];
+  const double beta = sqrt(block_sum_partials(q.partial, nblk));
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) q.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    SolveStatus* st = q.st;
+    st->active = (beta > 0.0 && isfinite(beta)) ? 1 : 0;
+    st->j = 0;
+    st->converged = 0;
+    st->breakdown = isfinite(beta) ? 0 : 1;
+    st->beta = beta;
+    st->target = q.target;
+    st->resid = beta;
+    st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
   }
 }
 
-// One thread: finish Arnoldi column j (h = h1 + h2 already summed into hcol),
-// apply the previous rotations, form the new one, update g and the status.
-__global__ void arnoldi_step_kernel(double2* __restrict__ H, int ldh, double2* __restrict__ hcol,
-                                    const double2* __restrict__ norm_partial, int nblk, double* __restrict__ cs,
-                                    double2* __restrict__ sn, double2* __restrict__ g, int j,
-                                    SolveStatus* __restrict__ st) {
+// V_0 = r / beta  (converted to the inner type)
+template <typename V>
+__global__ void __launch_bounds__(kThreads) start_vector_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
+  const double s = q.st->inv_h;
+  V* __restrict__ v0 = (V*)q.V;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 a = q.r64[k];
+    v0[k] = from_d2<V>(make_double2(a.x * s, a.y * s));
+  }
+}
+
+// One block per problem: h_{j+1,j} = ||w|| (parallel reduction), then thread 0
+// applies the previous rotations to column j in shared memory, forms the new
+// rotation and updates g and the status; the column goes back to H.
+__global__ void __launch_bounds__(kThreads) arnoldi_step_kernel(const ProbK* __restrict__ P, int nblk, int ldh,
+                                                               int j) {
+  const ProbK& q = P[blockIdx.x];
+  SolveStatus* st = q.st;
   if (!st->active) return;
-  double nrm2 = 0.0;
-  for (int b = 0; b < nblk; ++b) nrm2 += norm_partial[b].x;
-  const double hn = sqrt(nrm2);
-  double2* col = H + (size_t)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
-  col[j + 1] = make_double2(hn, 0.0);
-  // previous rotations
-  for (int i = 0; i < j; ++i) {
-    const double c = cs[i];
-    const double2 s = sn[i];
-    const double2 a = col[i], b = col[i + 1];
-    // t = c a + s b ; b' = -conj(s) a + c b
-    const double2 t = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-    const double2 bb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
-    col[i] = t;
-    col[i + 1] = bb;
+  __shared__ double2 col[kMaxRestart + 1];
+  __shared__ double csh[kMaxRestart];
+  __shared__ double2 snh[kMaxRestart];
+  const double hn = sqrt(block_sum_partials(q.partial, nblk));
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = q.hcol[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    csh[i] = q.cs[i];
+    snh[i] = q.sn[i];
   }
-  const double2 a = col[j], b = col[j + 1];
-  const double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
-  const double den = hypot(aa, ab);
-  double c;
-  double2 s;
-  if (den == 0.0) {
-    c = 1.0; s = make_double2(0.0, 0.0);
-  } else if (aa == 0.0) {
-    c = 0.0; s = make_double2(1.0, 0.0);
-  } else {
-    c = aa / den;
-    // s = (a/|a|) conj(b) / den
-    const double2 ua = make_double2(a.x / aa, a.y / aa);
-    s = make_double2((ua.x * b.x + ua.y * b.y) / den, (ua.y * b.x - ua.x * b.y) / den);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    col[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double c = csh[i];
+      const double2 s = snh[i];
+      const double2 a = col[i], b = col[i + 1];
+      // t = c a + s b ; b' = -conj(s) a + c b
+      col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+      col[i + 1] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
+    const double den = hypot(aa, ab);
+    double c;
+    double2 s;
+    if (den == 0.0) {
+      c = 1.0; s = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0; s = make_double2(1.0, 0.0);
+    } else {
+      c = aa / den;
+      const double2 ua = make_double2(a.x / aa, a.y / aa);   // s = (a/|a|) conj(b) / den
+      s = make_double2((ua.x * b.x + ua.y * b.y) / den, (ua.y * b.x - ua.x * b.y) / den);
+    }
+    q.cs[j] = c;
+    q.sn[j] = s;
+    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = q.g[j];
+    const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    q.g[j + 1] = g1;
+    q.g[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = hypot(g1.x, g1.y);
+    st->j = j + 1;
+    st->resid = res;
+    if (!(isfinite(hn) && isfinite(res))) {
+      st->breakdown = 1;
+      st->active = 0;
+      st->j = j;          // drop the non-finite column
+    } else {
+      if (res <= st->target) {
+        st->converged = 1;
+        st->active = 0;
+      }
+      if (hn <= 1e-300 || hn <= 1e-14 * st->beta) {
+        st->breakdown = 1;
+        st->active = 0;
+      }
+      st->inv_h = (hn > 0.0) ? 1.0 / hn : 0.0;
+    }
   }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-  col[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = g[j];
-  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  g[j] = make_double2(c * gj.x, c * gj.y);
-  const double res = hypot(g[j + 1].x, g[j + 1].y);
-  st->j = j + 1;
-  st->resid = res;
-  const bool finite = isfinite(hn) && isfinite(res);
-  if (!finite) {
-    st->breakdown = 1;
-    st->active = 0;
-    st->j = j;          // drop the non-finite column
-    return;
-  }
-  if (res <= st->target) {
-    st->converged = 1;
-    st->active = 0;
-  }
-  if (hn <= 1e-300 || hn <= 1e-14 * st->beta) {
-    st->breakdown = 1;
-    st->active = 0;
-  }
-  st->inv_h = (hn > 0.0) ? 1.0 / hn : 0.0;
+  __syncthreads();
+  double2* H = q.H + (size_t)j * ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i] = col[i];
 }
 
-// Back substitution R y = g (R upper triangular in H, m columns), one block.
-__global__ void backsolve_kernel(const double2* __restrict__ H, int ldh, const double2* __restrict__ g,
-                                 double2* __restrict__ y, const SolveStatus* __restrict__ st) {
-  const int m = st->j;
-  __shared__ double2 ys[1024];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = g[i];
+// v_{j+1} = w / h_{j+1,j}
+template <typename V>
+__global__ void __launch_bounds__(kThreads) next_vector_kernel(const ProbK* __restrict__ P, int j) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
+  const double s = q.st->inv_h;
+  const V* __restrict__ w = (const V*)q.w;
+  V* __restrict__ v = (V*)q.V + (size_t)(j + 1) * q.n;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 a = to_d2(w[k]);
+    v[k] = from_d2<V>(make_double2(a.x * s, a.y * s));
+  }
+}
+
+// Back substitution R y = g over the st->j columns, one block per problem.
+__global__ void __launch_bounds__(kThreads) backsolve_kernel(const ProbK* __restrict__ P, int ldh) {
+  const ProbK& q = P[blockIdx.x];
+  const int m = q.st->j;
+  __shared__ double2 ys[kMaxRestart];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = q.g[i];
   __syncthreads();
   for (int i = m - 1; i >= 0; --i) {
     if (threadIdx.x == 0) {
-      const double2 r = H[(size_t)i * ldh + i];
+      const double2 r = q.H[(size_t)i * ldh + i];
       const double2 v = ys[i];
       const double d = r.x * r.x + r.y * r.y;
       ys[i] = make_double2((v.x * r.x + v.y * r.y) / d, (v.y * r.x - v.x * r.y) / d);
@@ -246,70 +364,35 @@ __global__ void backsolve_kernel(const double2* __restrict__ H, int ldh, const d
     __syncthreads();
     const double2 yi = ys[i];
     for (int k = threadIdx.x; k < i; k += blockDim.x) {
-      const double2 r = H[(size_t)i * ldh + k];
+      const double2 r = q.H[(size_t)i * ldh + k];
       ys[k].x -= r.x * yi.x - r.y * yi.y;
       ys[k].y -= r.x * yi.y + r.y * yi.x;
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = ys[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) q.ysol[i] = ys[i];
 }
 
-// x[k] += scale * sum_{i<m} Z_i[k] y_i  (x complex128, FP64 accumulation)
+// x[k] += sum_{i < st->j} Z_i[k] y_i  (x complex128, FP64 accumulation)
 template <typename V>
-__global__ void __launch_bounds__(kThreads) update_x_kernel(double2* __restrict__ x, const V* __restrict__ Zb,
-                                                            size_t ld, const double2* __restrict__ y,
-                                                            const SolveStatus* __restrict__ st, size_t n,
-                                                            double scale_) {
+__global__ void __launch_bounds__(kThreads) update_x_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  const int m = q.st->j;
+  if (m == 0) return;
   extern __shared__ double2 ys[];
-  const int m = st->j;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = y[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = q.ysol[i];
   __syncthreads();
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+  const V* __restrict__ Zb = (const V*)q.Z;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
     for (int i = 0; i < m; ++i) {
-      const double2 z = to_d2(Zb[(size_t)i * ld + k]);
+      const double2 z = to_d2(Zb[(size_t)i * q.n + k]);
       acc.x += z.x * ys[i].x - z.y * ys[i].y;
       acc.y += z.x * ys[i].y + z.y * ys[i].x;
     }
-    x[k].x += scale_ * acc.x;
-    x[k].y += scale_ * acc.y;
+    q.x64[k].x += acc.x;
+    q.x64[k].y += acc.y;
   }
-}
-
-// r = b - y (complex128) with norm partials of r
-__global__ void __launch_bounds__(kThreads) residual_kernel(const double2* __restrict__ b,
-                                                            const double2* __restrict__ y,
-                                                            double2* __restrict__ r, size_t n,
-                                                            double2* __restrict__ partial) {
-  __shared__ double red[kThreads / 32];
-  double s = 0.0;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = make_double2(b[k].x - y[k].x, b[k].y - y[k].y);
-    r[k] = v;
-    s += v.x * v.x + v.y * v.y;
-  }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    partial[blockIdx.x] = make_double2(t, 0.0);
-  }
-}
-
-__global__ void init_cycle_kernel(SolveStatus* st, double2* g, int m, double beta, double target) {
-  st->active = 1;
-  st->j = 0;
-  st->converged = 0;
-  st->breakdown = 0;
-  st->beta = beta;
-  st->target = target;
-  st->resid = beta;
-  st->inv_h = 0.0;
-  for (int i = 0; i <= m; ++i) g[i] = make_double2(0.0, 0.0);
-  g[0] = make_double2(beta, 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -320,28 +403,26 @@ struct KrylovWork {
   int dtype = 0;
   bool flexible = false;
   size_t n = 0;
-  void* V = nullptr;          // (m + 1) vectors
-  void* Z = nullptr;          // m vectors (flexible only)
-  void* w = nullptr;          // 1 vector (same type)
-  double2* x64 = nullptr;     // solution accumulator / r / y (complex128)
+  void* V = nullptr;
+  void* Z = nullptr;
+  void* w = nullptr;
+  double2* x64 = nullptr;
   double2* r64 = nullptr;
   double2* y64 = nullptr;
-  double2* H = nullptr;       // (m + 1) x m, column-major, ld = m + 1
+  double2* H = nullptr;
   double2* hcol = nullptr;
   double2* h2 = nullptr;
   double2* g = nullptr;
   double2* ysol = nullptr;
   double* cs = nullptr;
   double2* sn = nullptr;
-  double2* partial = nullptr; // (m + 1) * kDotBlocks
-  SolveStatus* st = nullptr;
-  SolveStatus* st_host = nullptr;   // pinned
+  double2* partial = nullptr;
 };
 
 static void free_work(KrylovWork* k) {
   cudaFree(k->V); cudaFree(k->Z); cudaFree(k->w); cudaFree(k->x64); cudaFree(k->r64); cudaFree(k->y64);
-  cudaFree(k->H); cudaFree(k->hcol); cudaFree(k->h2); cudaFree(k->g); cudaFree(k->ysol); cudaFree(k->cs); cudaFree(k->sn);
-  cudaFree(k->partial); cudaFree(k->st); cudaFreeHost(k->st_host);
+  cudaFree(k->H); cudaFree(k->hcol); cudaFree(k->h2); cudaFree(k->g); cudaFree(k->ysol); cudaFree(k->cs);
+  cudaFree(k->sn); cudaFree(k->partial);
   *k = KrylovWork();
 }
 
@@ -351,11 +432,11 @@ static vie_status alloc_work(KrylovWork* k, size_t n, int m, int dtype, bool fle
   struct { void** p; size_t sz; } a[] = {
       {&k->V, (size_t)(m + 1) * n * es}, {&k->w, n * es}, {(void**)&k->x64, n * sizeof(double2)},
       {(void**)&k->r64, n * sizeof(double2)}, {(void**)&k->y64, n * sizeof(double2)},
-      {(void**)&k->H, (size_t)(m + 1) * m * sizeof(double2)}, {(void**)&k->hcol, (m + 1) * sizeof(double2)}, {(void**)&k->h2, (m + 1) * sizeof(double2)},
-      {(void**)&k->g, (m + 1) * sizeof(double2)}, {(void**)&k->ysol, (m + 1) * sizeof(double2)},
-      {(void**)&k->cs, (m + 1) * sizeof(double)}, {(void**)&k->sn, (m + 1) * sizeof(double2)},
-      {(void**)&k->partial, (size_t)(m + 2) * kDotBlocks * sizeof(double2)},
-      {(void**)&k->st, sizeof(SolveStatus)}};
+      {(void**)&k->H, (size_t)(m + 1) * m * sizeof(double2)}, {(void**)&k->hcol, (m + 1) * sizeof(double2)},
+      {(void**)&k->h2, (m + 1) * sizeof(double2)}, {(void**)&k->g, (m + 1) * sizeof(double2)},
+      {(void**)&k->ysol, (m + 1) * sizeof(double2)}, {(void**)&k->cs, (m + 1) * sizeof(double)},
+      {(void**)&k->sn, (m + 1) * sizeof(double2)},
+      {(void**)&k->partial, (size_t)(m + 2) * kDotBlocks * sizeof(double2)}};
   for (auto& e : a) {
     cudaError_t err = cudaMalloc(e.p, e.sz);
     if (err != cudaSuccess) {
@@ -367,85 +448,6 @@ static vie_status alloc_work(KrylovWork* k, size_t n, int m, int dtype, bool fle
   if (flexible) {
     cudaError_t err = cudaMalloc(&k->Z, (size_t)m * n * es);
     if (err != cudaSuccess) { set_error("solver workspace Z: %s", cudaGetErrorString(err)); free_work(k); return VIE_ERR_OOM; }
-  }
-  if (cudaMallocHost((void**)&k->st_host, sizeof(SolveStatus)) != cudaSuccess) {
-    set_error("cudaMallocHost failed");
-    free_work(k);
-    return VIE_ERR_OOM;
-  }
-  return VIE_OK;
-}
-
-static unsigned grid_for(size_t n) {
-  const size_t b = (n + kThreads - 1) / kThreads;
-  return (unsigned)(b < (size_t)152 * 8 ? b : (size_t)152 * 8);
-}
-
-static vie_status norm_host(const double2* partial_dev, int nblk, double* out, cudaStream_t s) {
-  std::vector<double2> h(nblk);
-  VIE_CUDA_TRY(cudaMemcpyAsync(h.data(), partial_dev, nblk * sizeof(double2), cudaMemcpyDeviceToHost, s));
-  VIE_CUDA_TRY(cudaStreamSynchronize(s));
-  double t = 0.0;
-  for (int i = 0; i < nblk; ++i) t += h[i].x;
-  *out = sqrt(t);
-  return VIE_OK;
-}
-
-// One GMRES cycle of at most m steps on the operator of type V, started from
-// r (complex128, norm beta): V_0 = r / beta; stops at |g| <= target.  Adds
-// beta_scale * Z y to x (complex128).  Returns the steps taken.
-template <typename V>
-static vie_status gmres_cycle(vie_plan* p, KrylovWork& k, int dtype, double beta, double target, int max_steps,
-                              int check_every, const vie_precond_fn precond, void* precond_ctx, int* steps,
-                              int* matvecs, SolveStatus* out_status, cudaStream_t s) {
-  const size_t n = k.n;
-  const int m = k.m;
-  V* Vb = (V*)k.V;
-  V* w = (V*)k.w;
-  V* Zb = k.flexible ? (V*)k.Z : Vb;
-  init_cycle_kernel<<<1, 1, 0, s>>>(k.st, k.g, m, beta, target);
-  scale_copy_kernel<V, double2><<<grid_for(n), kThreads, 0, s>>>(Vb, k.r64, n, nullptr, 1.0 / beta, nullptr, 0);
-  VIE_LAUNCH_CHECK();
-  int j = 0;
-  *matvecs = 0;
-  const int jmax = max_steps < m ? max_steps : m;
-  for (; j < jmax; ++j) {
-    V* vj = Vb + (size_t)j * n;
-    V* zj = Zb + (size_t)j * n;
-    if (k.flexible) {
-      vie_status ps = precond(precond_ctx, dtype, vj, zj, s);
-      if (ps != VIE_OK) return ps;
-    }
-    vie_status ms = matvec_impl(p, zj, w, dtype, MODE_OPERATOR, p->work, s);
-    if (ms != VIE_OK) return ms;
-    ++*matvecs;
-    const int nv = j + 1;
-    // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2; column = h1 + h2
-    dots_kernel<V><<<kDotBlocks, kThreads, 0, s>>>(Vb, n, nv, w, n, k.partial, k.st);
-    reduce_partials_kernel<<<nv, kThreads, 0, s>>>(k.partial, kDotBlocks, k.hcol, nullptr, k.st);
-    update_kernel<V><<<grid_for(n), kThreads, nv * sizeof(double2), s>>>(Vb, n, nv, k.hcol, w, n, k.st);
-    dots_kernel<V><<<kDotBlocks, kThreads, 0, s>>>(Vb, n, nv, w, n, k.partial, k.st);
-    reduce_partials_kernel<<<nv, kThreads, 0, s>>>(k.partial, kDotBlocks, k.h2, k.hcol, k.st);
-    update_kernel<V><<<grid_for(n), kThreads, nv * sizeof(double2), s>>>(Vb, n, nv, k.h2, w, n, k.st);
-    VIE_LAUNCH_CHECK();
-    norm2_kernel<V><<<kDotBlocks, kThreads, 0, s>>>(w, n, k.partial, k.st);
-    arnoldi_step_kernel<<<1, 1, 0, s>>>(k.H, m + 1, k.hcol, k.partial, kDotBlocks, k.cs, k.sn, k.g, j, k.st);
-    scale_copy_kernel<V, V><<<grid_for(n), kThreads, 0, s>>>(Vb + (size_t)(j + 1) * n, w, n, nullptr, 0.0, k.st, 1);
-    VIE_LAUNCH_CHECK();
-    if ((j + 1) % check_every == 0 || j + 1 == jmax) {
-      VIE_CUDA_TRY(cudaMemcpyAsync(k.st_host, k.st, sizeof(SolveStatus), cudaMemcpyDeviceToHost, s));
-      VIE_CUDA_TRY(cudaStreamSynchronize(s));
-      if (!k.st_host->active) break;
-    }
-  }
-  VIE_CUDA_TRY(cudaMemcpyAsync(k.st_host, k.st, sizeof(SolveStatus), cudaMemcpyDeviceToHost, s));
-  VIE_CUDA_TRY(cudaStreamSynchronize(s));
-  *steps = k.st_host->j;
-  *out_status = *k.st_host;
-  if (*steps > 0) {
-    backsolve_kernel<<<1, 256, 0, s>>>(k.H, m + 1, k.g, k.ysol, k.st);
-    update_x_kernel<V><<<grid_for(n), kThreads, (size_t)m * sizeof(double2), s>>>(k.x64, Zb, n, k.ysol, k.st, n, 1.0);
-    VIE_LAUNCH_CHECK();
   }
   return VIE_OK;
 }
@@ -475,21 +477,138 @@ static vie_status ensure_work(vie_plan* p, int m, int dtype, bool flexible, Kryl
   return VIE_OK;
 }
 
-// true residual r = b - A64 x into k.r64; returns ||r||
-static vie_status true_residual(vie_plan* p, KrylovWork& k, const double2* b, double* rnorm, cudaStream_t s) {
-  vie_status st = matvec_impl(p, k.x64, k.y64, VIE_C128, MODE_OPERATOR, p->work, s);
-  if (st != VIE_OK) return st;
-  residual_kernel<<<kDotBlocks, kThreads, 0, s>>>(b, k.y64, k.r64, k.n, k.partial);
-  VIE_LAUNCH_CHECK();
-  return norm_host(k.partial, kDotBlocks, rnorm, s);
+static unsigned grid_for(size_t n) {
+  const size_t b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < (size_t)152 * 8 ? b : (size_t)152 * 8);
 }
 
-vie_status solve_impl(vie_plan* p, const double2* b, double2* x, double tol, const vie_solve_opts* o,
-                      vie_solve_info* info, vie_precond_fn precond, void* precond_ctx, cudaStream_t s) {
+// Per-call state of a (batched) solve.
+struct BatchCall {
+  std::vector<vie_plan*> plans;
+  std::vector<ProbK> host;          // one record per problem
+  ProbK* table = nullptr;           // device records of the current list
+  SolveStatus* st = nullptr;        // device, one per problem
+  SolveStatus* st_host = nullptr;   // pinned mirror
+  double2* partial_host = nullptr;  // pinned, kDotBlocks per problem
+  ~BatchCall() {
+    cudaFree(table);
+    cudaFree(st);
+    cudaFreeHost(st_host);
+    cudaFreeHost(partial_host);
+  }
+};
+
+static vie_status upload_list(BatchCall& c, const std::vector<int>& list, cudaStream_t s) {
+  std::vector<ProbK> t(list.size());
+  for (size_t i = 0; i < list.size(); ++i) t[i] = c.host[list[i]];
+  VIE_CUDA_TRY(cudaMemcpyAsync(c.table, t.data(), t.size() * sizeof(ProbK), cudaMemcpyHostToDevice, s));
+  // the host vector dies at return: make the copy complete first
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return VIE_OK;
+}
+
+// Operator on z_j (inner type) or on x (complex128, outer) for every problem
+// of `list`, grouped by shape.
+static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dtype, bool outer, int j, bool flexible,
+                             cudaStream_t s) {
+  std::vector<int> used(list.size(), 0);
+  const size_t es = dtype == VIE_C64 ? sizeof(float2) : sizeof(double2);
+  for (size_t i = 0; i < list.size(); ++i) {
+    if (used[i]) continue;
+    std::vector<vie_plan*> gp;
+    std::vector<const void*> gx;
+    std::vector<void*> gy;
+    const vie_plan* a = c.plans[list[i]];
+    for (size_t k = i; k < list.size(); ++k) {
+      if (used[k]) continue;
+      const vie_plan* b = c.plans[list[k]];
+      if (a->n[0] == b->n[0] && a->n[1] == b->n[1] && a->n[2] == b->n[2] && a->m[0] == b->m[0] &&
+          a->m[1] == b->m[1] && a->m[2] == b->m[2]) {
+        const ProbK& q = c.host[list[k]];
+        used[k] = 1;
+        gp.push_back(c.plans[list[k]]);
+        if (outer) {
+          gx.push_back(q.x64);
+          gy.push_back(q.y64);
+        } else {
+          const char* zb = (const char*)(flexible ? q.Z : q.V);
+          gx.push_back(zb + (size_t)j * q.n * es);
+          gy.push_back(q.w);
+        }
+      }
+    }
+    vie_status st = matvec_group(gp.data(), (int)gp.size(), gx.data(), gy.data(), outer ? VIE_C128 : dtype,
+                                 MODE_OPERATOR, s);
+    if (st != VIE_OK) return st;
+  }
+  return VIE_OK;
+}
+
+static vie_status read_status(BatchCall& c, cudaStream_t s) {
+  VIE_CUDA_TRY(cudaMemcpyAsync(c.st_host, c.st, c.plans.size() * sizeof(SolveStatus), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return VIE_OK;
+}
+
+// One GMRES cycle of at most m steps for the problems of `list` (whose
+// records are on the device and whose status was just initialised).
+template <typename V>
+static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, int dtype, int max_steps,
+                            int check_every, bool flexible, vie_precond_fn precond, void* const* precond_ctx,
+                            cudaStream_t s) {
+  const unsigned P = (unsigned)list.size();
+  size_t nmax = 0;
+  for (int i : list) nmax = c.host[i].n > nmax ? c.host[i].n : nmax;
+  const unsigned gx = grid_for(nmax);
+  start_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table);
+  VIE_LAUNCH_CHECK();
+  std::vector<int> live = list;       // problems still iterating in this cycle
+  const int jmax = max_steps < m ? max_steps : m;
+  for (int j = 0; j < jmax && !live.empty(); ++j) {
+    if (flexible) {
+      for (int i : live) {
+        const ProbK& q = c.host[i];
+        vie_status ps = precond(precond_ctx[i], dtype, (const char*)q.V + (size_t)j * q.n * sizeof(V),
+                                (char*)q.Z + (size_t)j * q.n * sizeof(V), s);
+        if (ps != VIE_OK) return ps;
+      }
+    }
+    vie_status ms = apply_list(c, live, dtype, false, j, flexible, s);
+    if (ms != VIE_OK) return ms;
+    const int nv = j + 1;
+    dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
+    reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
+    update_kernel<V><<<dim3(gx, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 0);
+    dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
+    reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
+    update_kernel<V><<<dim3(gx, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 1);
+    norm2_w_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table);
+    arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, kDotBlocks, m + 1, j);
+    next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
+    VIE_LAUNCH_CHECK();
+    if ((j + 1) % check_every == 0 || j + 1 == jmax) {
+      vie_status rs = read_status(c, s);
+      if (rs != VIE_OK) return rs;
+      std::vector<int> still;
+      for (int i : live)
+        if (c.st_host[i].active) still.push_back(i);
+      live.swap(still);
+    }
+  }
+  backsolve_kernel<<<P, kThreads, 0, s>>>(c.table, m + 1);
+  update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(double2), s>>>(c.table);
+  VIE_LAUNCH_CHECK();
+  return read_status(c, s);
+}
+
+// Solve `count` problems; b[i], x[i] complex128 device vectors of plan i.
+vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
+                            const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,
+                            void* const* precond_ctx, cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
   const int mode = o->mode;
   const int m = o->restart > 0 ? o->restart : 100;
-  if (m > 1000) { set_error("restart must be <= 1000"); return VIE_ERR_INVALID; }
+  if (m > kMaxRestart) { set_error("restart must be <= %d", kMaxRestart); return VIE_ERR_INVALID; }
   const int max_iters = o->max_iters > 0 ? o->max_iters : 5000;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 200;
   const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
@@ -497,105 +616,193 @@ vie_status solve_impl(vie_plan* p, const double2* b, double2* x, double tol, con
   const double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
   const int dtype = (mode == VIE_SOLVE_MIXED) ? VIE_C64 : VIE_C128;
   const bool flexible = precond != nullptr;
-  KrylovWork* kp = nullptr;
-  vie_status st = ensure_work(p, m, dtype, flexible, &kp);
-  if (st != VIE_OK) return st;
-  KrylovWork& k = *kp;
-  const size_t n = k.n;
-  memset(info, 0, sizeof(*info));
+  BatchCall c;
+  c.plans.assign(plans, plans + count);
+  c.host.resize(count);
+  VIE_CUDA_TRY(cudaMalloc((void**)&c.table, count * sizeof(ProbK)));
+  VIE_CUDA_TRY(cudaMalloc((void**)&c.st, count * sizeof(SolveStatus)));
+  VIE_CUDA_TRY(cudaMallocHost((void**)&c.st_host, count * sizeof(SolveStatus)));
+  VIE_CUDA_TRY(cudaMallocHost((void**)&c.partial_host, (size_t)count * kDotBlocks * sizeof(double2)));
+  VIE_CUDA_TRY(cudaMemsetAsync(c.st, 0, count * sizeof(SolveStatus), s));
+  for (int i = 0; i < count; ++i) {
+    KrylovWork* k = nullptr;
+    vie_status st = ensure_work(plans[i], m, dtype, flexible, &k);
+    if (st != VIE_OK) return st;
+    ProbK& q = c.host[i];
+    memset(&q, 0, sizeof(q));
+    q.V = k->V; q.Z = flexible ? k->Z : k->V; q.w = k->w; q.n = k->n; q.b = b[i];
+    q.x64 = k->x64; q.r64 = k->r64; q.y64 = k->y64; q.H = k->H; q.hcol = k->hcol; q.h2 = k->h2; q.g = k->g;
+    q.ysol = k->ysol; q.cs = k->cs; q.sn = k->sn; q.partial = k->partial; q.st = c.st + i;
+    memset(&infos[i], 0, sizeof(vie_solve_info));
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  // ||b||
-  norm2_kernel<double2><<<kDotBlocks, kThreads, 0, s>>>(b, n, k.partial, nullptr);
-  VIE_LAUNCH_CHECK();
-  double bnorm = 0.0;
-  st = norm_host(k.partial, kDotBlocks, &bnorm, s);
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) all[i] = i;
+  // ||b|| of every problem
+  vie_status st = upload_list(c, all, s);
   if (st != VIE_OK) return st;
-  if (!isfinite(bnorm)) { set_error("right-hand side is not finite"); return VIE_ERR_NONFINITE; }
-  if (o->x0_given) {
-    VIE_CUDA_TRY(cudaMemcpyAsync(k.x64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  } else {
-    VIE_CUDA_TRY(cudaMemsetAsync(k.x64, 0, n * sizeof(double2), s));
+  norm2_b_kernel<<<dim3(kDotBlocks, count), kThreads, 0, s>>>(c.table);
+  VIE_LAUNCH_CHECK();
+  for (int i = 0; i < count; ++i)
+    VIE_CUDA_TRY(cudaMemcpyAsync(c.partial_host + (size_t)i * kDotBlocks, c.host[i].partial,
+                                 kDotBlocks * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int> list;
+  std::vector<int> iters(count, 0), outers(count, 0);
+  std::vector<double> rel(count, 0.0);
+  std::vector<vie_status> result(count, VIE_OK);
+  for (int i = 0; i < count; ++i) {
+    double t = 0.0;
+    for (int k = 0; k < kDotBlocks; ++k) t += c.partial_host[(size_t)i * kDotBlocks + k].x;
+    c.host[i].bnorm = sqrt(t);
+    if (!isfinite(c.host[i].bnorm)) { set_error("right-hand side %d is not finite", i); return VIE_ERR_NONFINITE; }
+    if (o->x0_given && c.host[i].bnorm != 0.0) {
+      VIE_CUDA_TRY(cudaMemcpyAsync(c.host[i].x64, x[i], c.host[i].n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    } else {
+      VIE_CUDA_TRY(cudaMemsetAsync(c.host[i].x64, 0, c.host[i].n * sizeof(double2), s));
+    }
+    if (c.host[i].bnorm == 0.0) {
+      infos[i].converged = 1;
+    } else {
+      list.push_back(i);
+    }
   }
-  if (bnorm == 0.0) {
-    VIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-    info->converged = 1;
-    VIE_CUDA_TRY(cudaStreamSynchronize(s));
-    return VIE_OK;
-  }
-  int iters = 0, outer = 0;
-  double rnorm = 0.0;
-  bool converged = false;
   st = VIE_OK;
-  while (true) {
-    st = true_residual(p, k, b, &rnorm, s);
+  while (!list.empty()) {
+    // true residual r = b - A64 x of the open problems
+    st = upload_list(c, list, s);
     if (st != VIE_OK) break;
-    info->matvecs64++;
-    if (outer < (int)(sizeof(info->history) / sizeof(info->history[0]))) info->history[outer] = rnorm / bnorm;
-    info->history_len = outer + 1;
-    if (!isfinite(rnorm)) { set_error("residual became non-finite"); st = VIE_ERR_NONFINITE; break; }
-    if (rnorm <= tol * bnorm) { converged = true; break; }
-    if (iters >= max_iters || outer >= max_outer) break;
+    st = apply_list(c, list, dtype, true, 0, false, s);
+    if (st != VIE_OK) break;
+    residual_kernel<<<dim3(kDotBlocks, (unsigned)list.size()), kThreads, 0, s>>>(c.table);
+    init_cycle_kernel<<<(unsigned)list.size(), kThreads, 0, s>>>(c.table, kDotBlocks, m);
+    VIE_LAUNCH_CHECK();
+    st = read_status(c, s);
+    if (st != VIE_OK) break;
+    std::vector<int> open;
+    for (int i : list) {
+      infos[i].matvecs64++;
+      const double rn = c.st_host[i].beta;
+      rel[i] = rn / c.host[i].bnorm;
+      if (outers[i] < 64) infos[i].history[outers[i]] = rel[i];
+      infos[i].history_len = outers[i] + 1 < 64 ? outers[i] + 1 : 64;
+      if (!isfinite(rn)) { result[i] = VIE_ERR_NONFINITE; continue; }
+      if (rn <= tol * c.host[i].bnorm) { infos[i].converged = 1; continue; }
+      if (iters[i] >= max_iters || outers[i] >= max_outer) { result[i] = VIE_ERR_NOT_CONVERGED; continue; }
+      // plain mode goes for tol ||b||; mixed asks the complex64 cycle for a
+      // reduction inner_tol, never below half the outer target
+      double target = tol * c.host[i].bnorm;
+      if (mode == VIE_SOLVE_MIXED) target = fmax(inner_tol * rn, 0.5 * tol * c.host[i].bnorm);
+      c.host[i].target = target;
+      open.push_back(i);
+    }
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (secs > timeout) { set_error("solve exceeded %.1f s", timeout); st = VIE_ERR_TIMEOUT; break; }
-    // inner target: plain mode goes straight for tol (absolute tol * ||b||);
-    // mixed mode asks the complex64 cycle for a relative reduction inner_tol,
-    // never below what the outer target needs.
-    double target = tol * bnorm;
-    if (mode == VIE_SOLVE_MIXED) target = fmax(inner_tol * rnorm, 0.5 * tol * bnorm);
-    int steps = 0, mv = 0;
-    SolveStatus cs;
-    if (dtype == VIE_C64)
-      st = gmres_cycle<float2>(p, k, dtype, rnorm, target, max_iters - iters, check_every, precond, precond_ctx,
-                               &steps, &mv, &cs, s);
-    else
-      st = gmres_cycle<double2>(p, k, dtype, rnorm, target, max_iters - iters, check_every, precond, precond_ctx,
-                                &steps, &mv, &cs, s);
+    if (!open.empty() && secs > timeout) {
+      for (int i : open) result[i] = VIE_ERR_TIMEOUT;
+      set_error("solve exceeded %.1f s", timeout);
+      open.clear();
+    }
+    list.swap(open);
+    if (list.empty()) break;
+    // records now carry the cycle targets; re-initialise the status with them
+    st = upload_list(c, list, s);
     if (st != VIE_OK) break;
-    iters += steps;
-    outer++;
-    if (dtype == VIE_C64) info->matvecs32 += mv; else info->matvecs64 += mv;
-    if (steps == 0) { set_error("Krylov cycle made no progress (breakdown at the first step)"); break; }
+    init_cycle_kernel<<<(unsigned)list.size(), kThreads, 0, s>>>(c.table, kDotBlocks, m);
+    VIE_LAUNCH_CHECK();
+    int steps_left = max_iters;
+    for (int i : list) steps_left = (max_iters - iters[i]) < steps_left ? (max_iters - iters[i]) : steps_left;
+    if (dtype == VIE_C64)
+      st = run_cycle<float2>(c, list, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+    else
+      st = run_cycle<double2>(c, list, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+    if (st != VIE_OK) break;
+    std::vector<int> next;
+    for (int i : list) {
+      const int steps = c.st_host[i].j;
+      iters[i] += steps;
+      outers[i]++;
+      if (dtype == VIE_C64) infos[i].matvecs32 += steps; else infos[i].matvecs64 += steps;
+      if (steps == 0) {
+        result[i] = VIE_ERR_NOT_CONVERGED;
+        set_error("Krylov cycle made no progress (breakdown at the first step) for problem %d", i);
+        continue;
+      }
+      next.push_back(i);
+    }
+    list.swap(next);
   }
   cudaEventRecord(e1, s);
-  if (st == VIE_OK || st == VIE_ERR_TIMEOUT) {
-    cudaError_t e = cudaMemcpyAsync(x, k.x64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess && st == VIE_OK) { set_error("copy-out failed: %s", cudaGetErrorString(e)); st = VIE_ERR_CUDA; }
-  }
+  for (int i = 0; i < count; ++i)
+    VIE_CUDA_TRY(cudaMemcpyAsync(x[i], c.host[i].x64, c.host[i].n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
   float ms = 0.f;
-  cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  info->iterations = iters;
-  info->outer = outer;
-  info->residual = rnorm / bnorm;
-  info->converged = converged ? 1 : 0;
-  info->time_ms = ms;
-  if (st == VIE_OK && !converged) {
-    if (!vie_last_error()[0]) set_error("not converged: relative residual %.3e after %d iterations", rnorm / bnorm, iters);
-    return VIE_ERR_NOT_CONVERGED;
+  vie_status worst = st;
+  for (int i = 0; i < count; ++i) {
+    infos[i].iterations = iters[i];
+    infos[i].outer = outers[i];
+    infos[i].residual = rel[i];
+    infos[i].time_ms = ms;
+    if (worst == VIE_OK && result[i] != VIE_OK) worst = result[i];
   }
-  return st;
+  if (worst == VIE_ERR_NOT_CONVERGED && !vie_last_error()[0])
+    set_error("not converged: a problem stopped above the tolerance (see its info)");
+  return worst;
 }
 
 }  // namespace vie
 
+using namespace vie;
+
 extern "C" vie_status vie_solve(vie_plan* p, const void* b_dev, void* x_dev, double tol, const vie_solve_opts* opts,
                                 vie_solve_info* info, void* stream) {
-  vie::clear_error();
-  if (!p || !b_dev || !x_dev || !opts || !info) { vie::set_error("null argument"); return VIE_ERR_INVALID; }
-  if (!(tol > 0.0 && tol < 1.0)) { vie::set_error("tol must be in (0, 1)"); return VIE_ERR_INVALID; }
-  if (opts->mode != VIE_SOLVE_FP64 && opts->mode != VIE_SOLVE_MIXED) { vie::set_error("unknown mode"); return VIE_ERR_INVALID; }
-  if (b_dev == x_dev) { vie::set_error("b and x must differ"); return VIE_ERR_INVALID; }
-  vie::vie_precond_fn fn = nullptr;
+  clear_error();
+  if (!p || !b_dev || !x_dev || !opts || !info) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must be in (0, 1)"); return VIE_ERR_INVALID; }
+  if (opts->mode != VIE_SOLVE_FP64 && opts->mode != VIE_SOLVE_MIXED) { set_error("unknown mode"); return VIE_ERR_INVALID; }
+  if (b_dev == x_dev) { set_error("b and x must differ"); return VIE_ERR_INVALID; }
+  vie_precond_fn fn = nullptr;
   void* ctx = nullptr;
   if (opts->use_preconditioner) {
-    vie_status st = vie::precond_get(p, &fn, &ctx);
+    vie_status st = precond_get(p, &fn, &ctx);
     if (st != VIE_OK) return st;
   }
-  return vie::solve_impl(p, (const double2*)b_dev, (double2*)x_dev, tol, opts, info, fn, ctx, (cudaStream_t)stream);
+  const double2* b = (const double2*)b_dev;
+  double2* x = (double2*)x_dev;
+  return solve_batch_impl(&p, 1, &b, &x, tol, opts, info, fn, &ctx, (cudaStream_t)stream);
+}
+
+extern "C" vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const* b_dev,
+                                      void* const* x_dev, double tol, const vie_solve_opts* opts,
+                                      vie_solve_info* infos, void* stream) {
+  clear_error();
+  if (!plans || !b_dev || !x_dev || !opts || !infos || count < 1) {
+    set_error("null argument or count < 1");
+    return VIE_ERR_INVALID;
+  }
+  if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must be in (0, 1)"); return VIE_ERR_INVALID; }
+  if (opts->mode != VIE_SOLVE_FP64 && opts->mode != VIE_SOLVE_MIXED) { set_error("unknown mode"); return VIE_ERR_INVALID; }
+  std::vector<void*> ctx(count, nullptr);
+  vie_precond_fn fn = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !b_dev[i] || !x_dev[i] || b_dev[i] == x_dev[i]) {
+      set_error("problem %d: null plan or vector, or b == x", i);
+      return VIE_ERR_INVALID;
+    }
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) { set_error("plan %d appears twice", i); return VIE_ERR_INVALID; }
+    if (opts->use_preconditioner) {
+      vie_precond_fn f = nullptr;
+      vie_status st = precond_get(plans[i], &f, &ctx[i]);
+      if (st != VIE_OK) return st;
+      fn = f;
+    }
+  }
+  return solve_batch_impl(plans, count, (const double2* const*)b_dev, (double2* const*)x_dev, tol, opts, infos, fn,
+                          ctx.data(), (cudaStream_t)stream);
 }

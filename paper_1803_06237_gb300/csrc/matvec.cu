@@ -13,7 +13,9 @@
 //   C  per group of x-lines: inverse FFT along x, crop to nx, and
 //      y = w - M u (operator) or y = M (u - w) (right-hand side of a source).
 // The spectrum is pre-scaled by 1/(Mx My Mz), so no separate normalisation.
+#include <cuda_pipeline.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "fft.cuh"
 #include "regfft.cuh"
@@ -25,12 +27,26 @@ template <typename V> __device__ __forceinline__ V zero_c();
 template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 zero_c<double2>() { return make_double2(0.0, 0.0); }
 
+// Per-problem pointers of one launch: blockIdx.y selects the problem.  All
+// problems of a launch share the grid and circulant sizes (and twiddles).
+constexpr int kMaxBatch = 16;
+template <typename V>
+struct PassPtrs {
+  const V* x[kMaxBatch];
+  V* y[kMaxBatch];
+  V* work[kMaxBatch];
+  const V* ghat[kMaxBatch];
+  const V* M[kMaxBatch];
+};
+
 // ---------------------------------------------------------------------------
 // pass A
 // ---------------------------------------------------------------------------
 template <typename V>
-__global__ void __launch_bounds__(256) pass_a_kernel(const V* __restrict__ x, V* __restrict__ work, int nx, int NL,
+__global__ void __launch_bounds__(256) pass_a_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int NL,
                                                      Radices rx, const V* __restrict__ twg, int lines_per_block) {
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  V* __restrict__ work = pp.work[blockIdx.y];
   extern __shared__ unsigned char smem_raw[];
   const int Mx = rx.len;
   const int pitch = Mx + 1;
@@ -61,9 +77,11 @@ struct PassBGeom {
 };
 
 template <typename V>
-__global__ void __launch_bounds__(256) pass_b_kernel(V* __restrict__ work, const V* __restrict__ ghat, PassBGeom g,
+__global__ void __launch_bounds__(256) pass_b_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                      Radices ry, Radices rz, const V* __restrict__ twyg,
                                                      const V* __restrict__ twzg) {
+  V* __restrict__ work = pp.work[blockIdx.y];
+  const V* __restrict__ ghat = pp.ghat[blockIdx.y];
   extern __shared__ unsigned char smem_raw[];
   const int kx = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -146,9 +164,10 @@ __global__ void __launch_bounds__(256) pass_b_kernel(V* __restrict__ work, const
 //   S1: (c, kz) y-lines, pitch PY;  S2: (c, y) z-lines, pitch PZ.
 // ---------------------------------------------------------------------------
 template <typename V, int MY, int MZ>
-__global__ void __launch_bounds__(256) pass_b_reg_kernel(V* __restrict__ work, const V* __restrict__ ghat,
-                                                         PassBGeom g, const V* __restrict__ twyg,
-                                                         const V* __restrict__ twzg) {
+__global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
+                                                         const V* __restrict__ twyg, const V* __restrict__ twzg) {
+  V* __restrict__ work = pp.work[blockIdx.y];
+  const V* __restrict__ ghat = pp.ghat[blockIdx.y];
   constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
   constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
   extern __shared__ unsigned char smem_raw[];
@@ -156,9 +175,19 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(V* __restrict__ work, c
   V* twz = twy + MY;
   V* S1 = twz + MZ;
   V* S2 = S1 + 3 * MZ * PY;
+  V* Gs = S2 + 3 * g.ny * PZ;          // folded spectrum chunk of this kx, 6 Kz Ky
   const int kx = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int ny = g.ny, nz = g.nz;
+  const bool fx = kx > g.Mx - kx;
+  const int kxf = fx ? g.Mx - kx : kx;
+  {
+    // asynchronous copy; it lands while the z and y transforms run
+    const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
+    const int chunk = 6 * g.Kz * g.Ky;
+    for (int i = tid; i < chunk; i += nth) __pipeline_memcpy_async(Gs + i, G + i, sizeof(V));
+    __pipeline_commit();
+  }
   for (int i = tid; i < MY; i += nth) twy[i] = twyg[i];
   for (int i = tid; i < MZ; i += nth) twz[i] = twzg[i];
   __syncthreads();
@@ -183,12 +212,11 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(V* __restrict__ work, c
 #pragma unroll
     for (int ky = 0; ky < MY; ++ky) S1[line * PY + ky] = a[ky];
   }
+  __pipeline_wait_prior(0);
   __syncthreads();
   {
-    const bool fx = kx > g.Mx - kx;
-    const int kxf = fx ? g.Mx - kx : kx;
-    const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
-    const size_t cs = (size_t)g.Kz * g.Ky;
+    const V* G = Gs;
+    const int cs = g.Kz * g.Ky;
     for (int e = tid; e < MZ * MY; e += nth) {
       const int kz = e / MY, ky = e - kz * MY;
       const bool fy = ky > MY - ky, fz = kz > MZ - kz;
@@ -246,29 +274,29 @@ bool pass_b_reg_available(int my, int mz) {
 }
 
 template <typename V, int MY, int MZ>
-static vie_status launch_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
-                                    cudaStream_t s) {
+static vie_status launch_pass_b_reg(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twy,
+                                    const V* twz, cudaStream_t s) {
   constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
   constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
-  const size_t smem = (size_t)(MY + MZ + 3 * MZ * PY + 3 * g.ny * PZ) * sizeof(V);
+  const size_t smem = (size_t)(MY + MZ + 3 * MZ * PY + 3 * g.ny * PZ + 6 * g.Kz * g.Ky) * sizeof(V);
   if (smem > 220 * 1024) { set_error("pass B shared memory %zu too large", smem); return VIE_ERR_INVALID; }
   VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_reg_kernel<V, MY, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int lines = 3 * (g.ny > MZ ? g.ny : MZ);
   int threads = ((lines + 31) / 32) * 32;
   if (threads > 256) threads = 256;
-  pass_b_reg_kernel<V, MY, MZ><<<(unsigned)g.Mx, threads, smem, s>>>(work, ghat, g, twy, twz);
+  pass_b_reg_kernel<V, MY, MZ><<<dim3((unsigned)g.Mx, (unsigned)count), threads, smem, s>>>(pp, g, twy, twz);
   VIE_LAUNCH_CHECK();
   return VIE_OK;
 }
 
 // complex128 lines longer than 30 would spill registers: those keep the generic pass
 template <typename V, int MY, int MZ>
-static vie_status try_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
-                                 cudaStream_t s, bool* done) {
+static vie_status try_pass_b_reg(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twy,
+                                 const V* twz, cudaStream_t s, bool* done) {
   if constexpr (sizeof(V) == sizeof(float2) || (MY <= 30 && MZ <= 30)) {
     *done = true;
-    return launch_pass_b_reg<V, MY, MZ>(work, ghat, g, twy, twz, s);
+    return launch_pass_b_reg<V, MY, MZ>(pp, count, g, twy, twz, s);
   } else {
     *done = false;
     return VIE_OK;
@@ -276,11 +304,11 @@ static vie_status try_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, con
 }
 
 template <typename V>
-static vie_status dispatch_pass_b_reg(V* work, const V* ghat, const PassBGeom& g, const V* twy, const V* twz,
-                                      cudaStream_t s, bool* done) {
+static vie_status dispatch_pass_b_reg(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twy,
+                                      const V* twz, cudaStream_t s, bool* done) {
   *done = false;
 #define VIE_X(a, b) \
-  if (g.My == a && g.Mz == b) return try_pass_b_reg<V, a, b>(work, ghat, g, twy, twz, s, done);
+  if (g.My == a && g.Mz == b) return try_pass_b_reg<V, a, b>(pp, count, g, twy, twz, s, done);
   VIE_PASS_B_REG_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
@@ -290,10 +318,13 @@ static vie_status dispatch_pass_b_reg(V* work, const V* ghat, const PassBGeom& g
 // pass C
 // ---------------------------------------------------------------------------
 template <typename V>
-__global__ void __launch_bounds__(256) pass_c_kernel(const V* __restrict__ work, const V* __restrict__ x,
-                                                     const V* __restrict__ Mc, V* __restrict__ y, int nx, int nyz,
+__global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int nyz,
                                                      int NL, Radices rx, const V* __restrict__ twg,
                                                      int lines_per_block, int mode) {
+  const V* __restrict__ work = pp.work[blockIdx.y];
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  const V* __restrict__ Mc = pp.M[blockIdx.y];
+  V* __restrict__ y = pp.y[blockIdx.y];
   extern __shared__ unsigned char smem_raw[];
   const int Mx = rx.len;
   const int pitch = Mx + 1;
@@ -336,7 +367,9 @@ __host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb
 
 template <typename V, int L1, int L2, int LPB>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
-    const V* __restrict__ x, V* __restrict__ work, int nx, int NL, const V* __restrict__ twxg) {
+    const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg) {
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  V* __restrict__ work = pp.work[blockIdx.y];
   constexpr int MX = L1 * L2;
   constexpr int R = pitch_mod16(L1 * LPB, LPB);
   extern __shared__ unsigned char smem_raw[];
@@ -352,9 +385,26 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
   for (int i = tid; i < MX; i += nth) twx[i] = twxg[i];
   for (int i = tid; i < L1; i += nth) tw1[i] = twxg[i * L2];   // w_L1^i = w_Mx^(i L2)
   for (int i = tid; i < L2; i += nth) tw2[i] = twxg[i * L1];
-  for (int e = tid; e < nl * nx; e += nth) {
-    const int l = e / nx, n = e - l * nx;
-    Xs[l * P + n] = x[(size_t)(l0 + l) * nx + n];
+  {
+    // the block's lines are contiguous in x; keep 8 loads in flight per thread
+    const int total = nl * nx;
+    const V* src = x + (size_t)l0 * nx;
+    for (int base = 0; base < total; base += 8 * nth) {
+      V v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = base + u * nth + tid;
+        v[u] = (e < total) ? src[e] : zero_c<V>();
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = base + u * nth + tid;
+        if (e < total) {
+          const int l = e / nx;
+          Xs[l * P + (e - l * nx)] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
   if (tid < LPB * L1) {
@@ -385,8 +435,11 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
 
 template <typename V, int L1, int L2, int LPB>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
-    const V* __restrict__ work, const V* __restrict__ x, const V* __restrict__ Mc, V* __restrict__ y, int nx,
-    int nyz, int NL, const V* __restrict__ twxg, int mode) {
+    const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode) {
+  const V* __restrict__ work = pp.work[blockIdx.y];
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  const V* __restrict__ Mc = pp.M[blockIdx.y];
+  V* __restrict__ y = pp.y[blockIdx.y];
   constexpr int MX = L1 * L2;
   constexpr int R = pitch_mod16(L1 * LPB, LPB);
   extern __shared__ unsigned char smem_raw[];
@@ -429,15 +482,31 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     }
   }
   __syncthreads();
-  for (int e = tid; e < nl * nx; e += nth) {
-    const int l = e / nx, ix = e - l * nx;
-    const int line = l0 + l;
-    const size_t gi = (size_t)line * nx + ix;
-    const size_t vox = (size_t)(line % nyz) * nx + ix;
-    const V u = Ys[l * P + ix];
-    const V w = x[gi];
-    const V m = Mc[vox];
-    y[gi] = (mode == MODE_OPERATOR) ? sub(w, mul(m, u)) : mul(m, sub(u, w));
+  {
+    // contrast epilogue with 4 pairs of loads in flight per thread
+    const int total = nl * nx;
+    const size_t g0 = (size_t)l0 * nx;
+    for (int base = 0; base < total; base += 4 * nth) {
+      V wv[4], mv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * nth + tid;
+        if (e < total) {
+          const int l = e / nx, ix = e - l * nx;
+          wv[u] = x[g0 + e];
+          mv[u] = Mc[(size_t)((l0 + l) % nyz) * nx + ix];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * nth + tid;
+        if (e < total) {
+          const int l = e / nx, ix = e - l * nx;
+          const V uu = Ys[l * P + ix];
+          y[g0 + e] = (mode == MODE_OPERATOR) ? sub(wv[u], mul(mv[u], uu)) : mul(mv[u], sub(uu, wv[u]));
+        }
+      }
+    }
   }
 }
 
@@ -448,7 +517,7 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
 constexpr int kX4Lines = 4;
 
 template <typename V, int L1, int L2>
-static vie_status launch_x4(bool forward, const V* x, V* work, const V* Mc, V* y, int nx, int nyz, int NL,
+static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
                             const V* twx, int mode, cudaStream_t s, bool* done) {
   if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
     constexpr int LPB = kX4Lines;
@@ -457,15 +526,15 @@ static vie_status launch_x4(bool forward, const V* x, V* work, const V* Mc, V* y
     const int P = pitch_mod16(nx, LPB);
     const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P) * sizeof(V);
     if (smem > 200 * 1024) { *done = false; return VIE_OK; }
-    const unsigned blocks = (unsigned)((NL + LPB - 1) / LPB);
+    const dim3 blocks((unsigned)((NL + LPB - 1) / LPB), (unsigned)count);
     if (forward) {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      pass_a4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(x, work, nx, NL, twx);
+      pass_a4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(pp, nx, NL, twx);
     } else {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      pass_c4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(work, x, Mc, y, nx, nyz, NL, twx, mode);
+      pass_c4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(pp, nx, nyz, NL, twx, mode);
     }
     VIE_LAUNCH_CHECK();
     *done = true;
@@ -486,11 +555,11 @@ void x4_factors(int mx, int* l1, int* l2) {
 }
 
 template <typename V>
-static vie_status dispatch_x4(bool forward, int l1, int l2, const V* x, V* work, const V* Mc, V* y, int nx,
-                              int nyz, int NL, const V* twx, int mode, cudaStream_t s, bool* done) {
+static vie_status dispatch_x4(bool forward, int l1, int l2, const PassPtrs<V>& pp, int count, int nx, int nyz,
+                              int NL, const V* twx, int mode, cudaStream_t s, bool* done) {
   *done = false;
 #define VIE_X(a, b) \
-  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, x, work, Mc, y, nx, nyz, NL, twx, mode, s, done);
+  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
   VIE_PASS_X4_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
@@ -499,14 +568,15 @@ static vie_status dispatch_x4(bool forward, int l1, int l2, const V* x, V* work,
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
+// The three passes for `count` problems of one shape (count <= kMaxBatch).
 template <typename V>
-static vie_status run_passes(vie_plan* p, const V* x, V* y, const V* ghat, const V* Mc, const V* twx,
-                             const V* twy, const V* twz, int mode, V* work, cudaStream_t s) {
+static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count, const V* twx, const V* twy,
+                             const V* twz, int mode, cudaStream_t s) {
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
   const int NL = 3 * ny * nz;
   const int threads = 256;
-  // passes A and C: lines per block from the shared-memory budget
+  // generic x passes: lines per block from the shared-memory budget
   const size_t line_bytes = (size_t)2 * (Mx + 1) * sizeof(V);
   const size_t tw_bytes = (size_t)Mx * sizeof(V);
   int lpb = 4;
@@ -521,50 +591,96 @@ static vie_status run_passes(vie_plan* p, const V* x, V* y, const V* ghat, const
     set_error("y-z plane %d x %d too large for the per-kx pass", My, Mz);
     return VIE_ERR_INVALID;
   }
-  const unsigned blocks_ac = (unsigned)((NL + lpb - 1) / lpb);
+  const dim3 blocks_ac((unsigned)((NL + lpb - 1) / lpb), (unsigned)count);
   int l1 = 0, l2 = 0;
   x4_factors(Mx, &l1, &l2);
   bool done = false;
   vie_status st = VIE_OK;
   if (l1) {
-    st = dispatch_x4<V>(true, l1, l2, x, work, Mc, y, nx, ny * nz, NL, twx, mode, s, &done);
+    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done);
     if (st != VIE_OK) return st;
   }
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-    pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(x, work, nx, NL, radices_of(p->ax[0]), twx, lpb);
+    pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, NL, radices_of(p->ax[0]), twx, lpb);
     VIE_LAUNCH_CHECK();
   }
   PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
-  st = dispatch_pass_b_reg<V>(work, ghat, g, twy, twz, s, &done);
+  st = dispatch_pass_b_reg<V>(pp, count, g, twy, twz, s, &done);
   if (st != VIE_OK) return st;
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-    pass_b_kernel<V><<<(unsigned)Mx, threads, smem_b, s>>>(work, ghat, g, radices_of(p->ax[1]), radices_of(p->ax[2]),
-                                                           twy, twz);
+    pass_b_kernel<V><<<dim3((unsigned)Mx, (unsigned)count), threads, smem_b, s>>>(pp, g, radices_of(p->ax[1]),
+                                                                                radices_of(p->ax[2]), twy, twz);
     VIE_LAUNCH_CHECK();
   }
   done = false;
   if (l1) {
-    st = dispatch_x4<V>(false, l1, l2, x, work, Mc, y, nx, ny * nz, NL, twx, mode, s, &done);
+    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done);
     if (st != VIE_OK) return st;
   }
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-    pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(work, x, Mc, y, nx, ny * nz, NL, radices_of(p->ax[0]), twx,
-                                                         lpb, mode);
+    pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, ny * nz, NL, radices_of(p->ax[0]), twx, lpb, mode);
     VIE_LAUNCH_CHECK();
   }
   return VIE_OK;
 }
 
+template <typename V>
+static vie_status run_one(vie_plan* p, const V* x, V* y, const V* ghat, const V* Mc, const V* twx, const V* twy,
+                          const V* twz, int mode, V* work, cudaStream_t s) {
+  PassPtrs<V> pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.x[0] = x;
+  pp.y[0] = y;
+  pp.work[0] = work;
+  pp.ghat[0] = ghat;
+  pp.M[0] = Mc;
+  return run_passes<V>(p, pp, 1, twx, twy, twz, mode, s);
+}
+
+template <typename V>
+static vie_status group_passes(vie_plan* const* plans, int count, const void* const* x, void* const* y, int mode,
+                               cudaStream_t s) {
+  const vie_plan* p0 = plans[0];
+  const bool f32 = sizeof(V) == sizeof(float2);
+  const V* twx = f32 ? (const V*)p0->ax[0].tw32 : (const V*)p0->ax[0].tw64;
+  const V* twy = f32 ? (const V*)p0->ax[1].tw32 : (const V*)p0->ax[1].tw64;
+  const V* twz = f32 ? (const V*)p0->ax[2].tw32 : (const V*)p0->ax[2].tw64;
+  for (int i0 = 0; i0 < count; i0 += kMaxBatch) {
+    const int c = (count - i0) < kMaxBatch ? (count - i0) : kMaxBatch;
+    PassPtrs<V> pp;
+    memset(&pp, 0, sizeof(pp));
+    for (int k = 0; k < c; ++k) {
+      const vie_plan* q = plans[i0 + k];
+      pp.x[k] = (const V*)x[i0 + k];
+      pp.y[k] = (V*)y[i0 + k];
+      pp.work[k] = (V*)q->work;
+      pp.ghat[k] = f32 ? (const V*)q->ghat32 : (const V*)q->ghat64;
+      pp.M[k] = f32 ? (const V*)q->M32 : (const V*)q->M64;
+    }
+    vie_status st = run_passes<V>(p0, pp, c, twx, twy, twz, mode, s);
+    if (st != VIE_OK) return st;
+  }
+  return VIE_OK;
+}
+
+vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype, int mode,
+                        cudaStream_t s) {
+  if (dtype == VIE_C64) return group_passes<float2>(plans, count, x, y, mode, s);
+  if (dtype == VIE_C128) return group_passes<double2>(plans, count, x, y, mode, s);
+  set_error("unknown dtype %d", dtype);
+  return VIE_ERR_INVALID;
+}
+
 vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, void* work, cudaStream_t s) {
   if (dtype == VIE_C64)
-    return run_passes<float2>(p, (const float2*)x, (float2*)y, p->ghat32, p->M32, p->ax[0].tw32, p->ax[1].tw32,
-                              p->ax[2].tw32, mode, (float2*)work, s);
+    return run_one<float2>(p, (const float2*)x, (float2*)y, p->ghat32, p->M32, p->ax[0].tw32, p->ax[1].tw32,
+                           p->ax[2].tw32, mode, (float2*)work, s);
   if (dtype == VIE_C128)
-    return run_passes<double2>(p, (const double2*)x, (double2*)y, p->ghat64, p->M64, p->ax[0].tw64, p->ax[1].tw64,
-                               p->ax[2].tw64, mode, (double2*)work, s);
+    return run_one<double2>(p, (const double2*)x, (double2*)y, p->ghat64, p->M64, p->ax[0].tw64, p->ax[1].tw64,
+                            p->ax[2].tw64, mode, (double2*)work, s);
   set_error("unknown dtype %d", dtype);
   return VIE_ERR_INVALID;
 }

@@ -115,6 +115,7 @@ struct vie_plan {
   size_t work_bytes = 0;
   size_t device_bytes = 0;
   double setup_ms = 0.0;
+  int* shared_refs = nullptr; // plans made by vie_plan_clone share entries, spectra and twiddles
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
   void* precond = nullptr;    // learned preconditioner state, if set
 };
@@ -134,7 +135,13 @@ typedef vie_status (*vie_precond_fn)(void* ctx, int dtype, const void* v, void* 
 void free_krylov(vie_plan* p);
 void free_precond(vie_plan* p);
 vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx);
-vie_status solve_impl(vie_plan* p, const double2* b, double2* x, double tol, const vie_solve_opts* o,
-                      vie_solve_info* info, vie_precond_fn precond, void* precond_ctx, cudaStream_t s);
+
+// Operator application for `count` plans of one shape (same n and m);
+// x[i], y[i] are device vectors of dtype; each plan's own workspace is used.
+vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype,
+                        int mode, cudaStream_t s);
+vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
+                            const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,
+                            void* const* precond_ctx, cudaStream_t s);
 
 }  // namespace vie

@@ -74,6 +74,12 @@ _SIGNATURES = {
     "vie_get_toeplitz": ([_P, _P], _I),
     "vie_eps2_from_round_trip": ([_D, _I, _D, _D, _D, _D, _D, ctypes.POINTER(_D)], _I),
     "vie_matvec_static_scratch": ([_P, _P, _P, _I, _P], _I),
+    "vie_axis_field": ([_P, _P, _I, _P, _P], _I),
+    "vie_plan_clone": ([_P, ctypes.POINTER(_P)], _I),
+    "vie_matvec_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P], _I),
+    "vie_solve_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D,
+                         ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
+    "vie_reflection": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_last_error": ([], ctypes.c_char_p),
 }
@@ -259,6 +265,85 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
     if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
         _check(st, "vie_solve")
     return out
+
+
+def vie_plan_clone(base: Plan) -> Plan:
+    """A plan sharing base's entries and spectra, with its own (zero) contrast."""
+    h_out = ctypes.c_void_p()
+    _check(load().vie_plan_clone(base.handle, ctypes.byref(h_out)), "vie_plan_clone")
+    return Plan(h_out, base.n)
+
+
+def _ptr_array(vals):
+    return (ctypes.c_void_p * len(vals))(*[ctypes.c_void_p(v) for v in vals])
+
+
+def vie_matvec_batch(plans, xs, ys, stream=None):
+    """y_i = x_i - M_i (N_i x_i) for every plan (CUDA tensors of one dtype)."""
+    if not (len(plans) == len(xs) == len(ys)) or not plans:
+        raise ValueError("plans, xs and ys must have the same non-zero length")
+    code = _dtype_code(xs[0])
+    for p, x, y in zip(plans, xs, ys):
+        if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous() and x.dtype == y.dtype
+                and x.dtype == xs[0].dtype and x.numel() == 3 * p.n_vox and y.numel() == 3 * p.n_vox):
+            raise ValueError("every x_i, y_i must be a contiguous CUDA vector of 3*nx*ny*nz entries of one dtype")
+    _check(load().vie_matvec_batch(_ptr_array([p.handle.value for p in plans]), len(plans),
+                                   _ptr_array([x.data_ptr() for x in xs]), _ptr_array([y.data_ptr() for y in ys]),
+                                   code, _stream_handle(stream)), "vie_matvec_batch")
+
+
+def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, restart: int = 100,
+                    max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
+                    use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
+                    stream=None, raise_on_not_converged: bool = True):
+    """Solve every (plan, b, x) together; returns (status, [info dict per problem])."""
+    import torch
+    n = len(plans)
+    if not (n == len(bs) == len(xs)) or n == 0:
+        raise ValueError("plans, bs and xs must have the same non-zero length")
+    for p, b, x in zip(plans, bs, xs):
+        for t in (b, x):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128 and t.numel() == 3 * p.n_vox):
+                raise ValueError("b and x must be contiguous complex128 CUDA vectors of 3*nx*ny*nz entries")
+    opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
+                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s))
+    infos = (vie_solve_info * n)()
+    st = load().vie_solve_batch(_ptr_array([p.handle.value for p in plans]), n,
+                                _ptr_array([b.data_ptr() for b in bs]), _ptr_array([x.data_ptr() for x in xs]),
+                                float(tol), ctypes.byref(opts), infos, _stream_handle(stream))
+    out = []
+    for info in infos:
+        out.append({"iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
+                    "matvecs32": info.matvecs32, "converged": bool(info.converged), "residual": info.residual,
+                    "time_ms": info.time_ms, "history": [info.history[i] for i in range(min(info.history_len, 64))]})
+    if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
+        _check(st, "vie_solve_batch")
+    return st, out
+
+
+def vie_axis_field(plan: Plan, w, n_keep: int, stream=None):
+    """E = w / chi on the centre axis for ix < n_keep: complex128 tensor (3, n_keep)."""
+    import torch
+    if not (w.is_cuda and w.dtype == torch.complex128 and w.numel() == 3 * plan.n_vox and w.is_contiguous()):
+        raise ValueError("w must be a contiguous complex128 CUDA vector of 3*nx*ny*nz entries")
+    e = torch.empty((3, int(n_keep)), dtype=torch.complex128, device=w.device)
+    _check(load().vie_axis_field(plan.handle, ctypes.c_void_p(w.data_ptr()), int(n_keep),
+                                 ctypes.c_void_p(e.data_ptr()), _stream_handle(stream)), "vie_axis_field")
+    return e
+
+
+def vie_reflection(e_ref, e, stream=None) -> float:
+    """R = sum |e_ref - e|^2 / sum |e_ref|^2 on the device (complex128 tensors)."""
+    import torch
+    for t in (e_ref, e):
+        if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+            raise ValueError("fields must be contiguous complex128 CUDA tensors")
+    if e_ref.numel() != e.numel():
+        raise ValueError("fields differ in size")
+    out = ctypes.c_double()
+    _check(load().vie_reflection(ctypes.c_void_p(e_ref.data_ptr()), ctypes.c_void_p(e.data_ptr()), e.numel(),
+                                 ctypes.byref(out), _stream_handle(stream)), "vie_reflection")
+    return out.value
 
 
 def vie_last_error() -> str:

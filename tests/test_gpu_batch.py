@@ -1,0 +1,89 @@
+"""Batched problems: shared-spectrum plans, the grouped operator and the
+batched solver, checked against single-problem calls and the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import oracle_matvec, rel_l2
+from oracle import operator as op
+from paper_1803_06237_gb300 import build, vie, workloads
+
+pytestmark = pytest.mark.gpu
+K0 = 2 * math.pi / 1.55
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    vie.load()
+
+
+def _guide(nx, L_vox, degree, e2, seed):
+    wl = workloads.waveguide(nx=nx, absorber_len_um=L_vox * 0.02, src_x_um=0.2)
+    ab = [dict(x0=float(nx - L_vox), length=float(L_vox), degree=degree, eps2_max=e2)]
+    return wl, ab
+
+
+def test_clone_shares_spectrum_and_outlives_base():
+    wl, ab = _guide(50, 15, 2, 2.0, 1)
+    base = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    clone = vie.vie_plan_clone(base)
+    vie.vie_set_permittivity(clone, wl.eps, ab)
+    ref = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(ref, wl.eps, ab)
+    x = torch.from_numpy(workloads.random_currents(wl.grid, seed=3).ravel()).cuda()
+    base.close()                       # the clone keeps the shared spectra alive
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    vie.vie_matvec(clone, x, y1)
+    vie.vie_matvec(ref, x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_grouped_operator_equals_single_calls(dtype):
+    plans, xs = [], []
+    for k, nx in enumerate((40, 60, 40, 60, 40)):
+        wl, ab = _guide(nx, 10 + k, k % 4, 0.5 + k, k)
+        p = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+        vie.vie_set_permittivity(p, wl.eps, ab)
+        plans.append(p)
+        xs.append(torch.from_numpy(workloads.random_currents(wl.grid, seed=10 + k).ravel()).to(dtype).cuda())
+    ys = [torch.empty_like(x) for x in xs]
+    vie.vie_matvec_batch(plans, xs, ys)
+    for p, x, y in zip(plans, xs, ys):
+        y1 = torch.empty_like(x)
+        vie.vie_matvec(p, x, y1)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y1)
+
+
+@pytest.mark.parametrize("mode,tol", [(vie.VIE_SOLVE_MIXED, 1e-6), (vie.VIE_SOLVE_FP64, 1e-8)])
+def test_batched_solve_matches_single_solves_and_oracle(mode, tol):
+    specs = [(60, 15, 0, 0.5), (80, 20, 2, 2.0), (60, 25, 3, 2.0), (100, 30, 1, 0.5)]
+    plans, bs, wls = [], [], []
+    for nx, L, d, e2 in specs:
+        wl, ab = _guide(nx, L, d, e2, nx)
+        p = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+        vie.vie_set_permittivity(p, wl.eps, ab)
+        src = torch.from_numpy(wl.src.ravel()).cuda()
+        b = torch.empty_like(src)
+        vie.vie_rhs_from_source(p, src, b)
+        plans.append(p)
+        bs.append(b)
+        wls.append((wl, ab))
+    xs = [torch.zeros_like(b) for b in bs]
+    st, infos = vie.vie_solve_batch(plans, bs, xs, tol, mode=mode, restart=40)
+    assert st == 0
+    for p, b, x, info, (wl, ab) in zip(plans, bs, xs, infos, wls):
+        assert info["converged"] and info["residual"] <= tol
+        x1 = torch.zeros_like(b)
+        i1 = vie.vie_solve(p, b, x1, tol, mode=mode, restart=40)
+        assert i1["converged"]
+        assert rel_l2(x.cpu().numpy(), x1.cpu().numpy()) <= 100 * tol
+        # true residual with the oracle operator
+        M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, ab))
+        r = oracle_matvec(wl.grid, wl.kappa, M, x.cpu().numpy().reshape(3, *wl.grid[::-1])).ravel() - b.cpu().numpy()
+        assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()) <= 2 * tol
