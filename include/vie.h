@@ -217,6 +217,57 @@ vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const*
                            void* const* x_dev, double tol, const vie_solve_opts* opts,
                            vie_solve_info* infos, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned right preconditioner (not in the paper, whose preconditioner is   */
+/* block-circulant, Sec. 6): a 3-D convolutional network z = Net(v, chi)     */
+/* trained on the device.  8 input channels (re/im of the three components  */
+/* of v scaled to unit RMS, re/im of chi), 4 levels (2x2 average pooling in  */
+/* x and y), 32 channels, 3x3x3 convolutions with zero padding, ReLU,        */
+/* nearest upsampling with additive skips, 6 output channels; BF16 weights,  */
+/* FP32 accumulation and activations, FP32 master weights and Adam.         */
+/* Parameter layout (FP32): per layer enc0..enc3, dec2, dec1, dec0, out:     */
+/* w[co][ci][27] (tap = 9 dz + 3 dy + dx) then b[co].                        */
+/* ------------------------------------------------------------------------ */
+typedef struct vie_net vie_net;
+
+/* Number of FP32 parameters of the network. */
+size_t vie_net_param_count(void);
+
+/* New network on the current device: parameters copied from params_host
+ * (count == vie_net_param_count()) or, if params_host is NULL, He-initialised
+ * from `seed`.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA. */
+vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
+                          unsigned long long seed);
+vie_status vie_net_destroy(vie_net* net);
+
+/* Copy the FP32 parameters / accumulated gradients to the host. */
+vie_status vie_net_get_params(const vie_net* net, float* out_host);
+vie_status vie_net_get_grads(const vie_net* net, float* out_host);
+
+/* z = |v|_rms Net(v / |v|_rms, chi of the plan) on the plan's grid; v_dev and
+ * z_dev are device vectors (3*nx*ny*nz of dtype).  A non-finite output entry
+ * is replaced by v.  Asynchronous on `stream`. */
+vie_status vie_net_apply(vie_net* net, const vie_plan* plan, const void* v_dev,
+                         void* z_dev, int dtype, void* stream);
+
+/* One training sample (r, e) with A e = r (complex64 device vectors): forward
+ * pass on r, loss |Net(r) - e|^2 / |e|^2 (both scaled by the RMS of r),
+ * backward pass; gradients are ADDED to the network's accumulators.  *loss
+ * receives the sample's loss.  Synchronises `stream`. */
+vie_status vie_net_accumulate(vie_net* net, const vie_plan* plan, const void* r_dev,
+                              const void* e_dev, double* loss, void* stream);
+vie_status vie_net_zero_grad(vie_net* net);
+
+/* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the accumulated gradients
+ * times grad_scale, refresh of the BF16 weights, gradients cleared. */
+vie_status vie_net_adam_step(vie_net* net, float lr, float grad_scale, void* stream);
+
+/* Use `net` (NULL: none) as the right preconditioner of this plan's solves
+ * with opts->use_preconditioner = 1 (flexible GMRES).  The plan keeps a
+ * reference; the caller keeps ownership and must not destroy the network
+ * while it is set. */
+vie_status vie_set_preconditioner(vie_plan* plan, vie_net* net);
+
 /* Field on the centre axis (step a12; Sec. 3 equivalent currents J =
  * c_e chi E, so E = J/(c_e chi); the factor c_e h^(3/2) common to every
  * field is not applied).  w_dev: complex128 solution (3*nx*ny*nz); e_dev:

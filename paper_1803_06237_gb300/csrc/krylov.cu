@@ -95,6 +95,58 @@ __device__ double block_sum_partials(const double2* __restrict__ part, int count
   return total;
 }
 
+__device__ __forceinline__ void block_store_sum(double s, double2* out) {
+  __shared__ double red[kThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    *out = make_double2(t, 0.0);
+  }
+}
+
+// Block b of a problem owns the element range [k0, k1) of length
+// ceil(n / gridDim.x); the CGS2 kernels below share this decomposition so
+// that the partial sums of one block can be formed right after its update.
+struct Chunk {
+  size_t k0, k1;
+};
+__device__ __forceinline__ Chunk chunk_of(size_t n) {
+  const size_t c = (n + gridDim.x - 1) / gridDim.x;
+  const size_t k0 = (size_t)blockIdx.x * c;
+  return Chunk{k0 < n ? k0 : n, min(n, k0 + c)};
+}
+
+constexpr int kGroup = 8;   // basis vectors handled together (loads in flight per thread)
+
+// Block-reduce kGroup complex sums and store them as partials of vectors
+// i0 .. i0 + kGroup - 1 (those < nv).
+__device__ __forceinline__ void store_group(double2 (&acc)[kGroup], int i0, int nv, double2* __restrict__ partial,
+                                            int nblk) {
+  __shared__ double2 red[kThreads / 32][kGroup];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < kGroup; ++u) {
+    acc[u].x = warp_sum(acc[u].x);
+    acc[u].y = warp_sum(acc[u].y);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) red[warp][u] = acc[u];
+  __syncthreads();
+  if (threadIdx.x < kGroup && i0 + threadIdx.x < nv) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t.x += red[w][threadIdx.x].x;
+      t.y += red[w][threadIdx.x].y;
+    }
+    partial[(size_t)(i0 + threadIdx.x) * nblk + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 // partial[i * nblk + b] = sum over block b's chunk of conj(V_i[k]) w[k], i < nv.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict__ P, int nv) {
@@ -103,23 +155,82 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict_
   const V* __restrict__ Vb = (const V*)q.V;
   const V* __restrict__ w = (const V*)q.w;
   const size_t n = q.n;
-  const int nblk = gridDim.x;
-  const size_t chunk = (n + nblk - 1) / nblk;
-  const size_t k0 = (size_t)blockIdx.x * chunk;
-  const size_t k1 = min(n, k0 + chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < nv; i += nw) {
-    const V* vi = Vb + (size_t)i * n;
-    double re = 0.0, im = 0.0;
-    for (size_t k = k0 + lane; k < k1; k += 32) {
-      const double2 a = to_d2(vi[k]);
+  const Chunk ch = chunk_of(n);
+  for (int i0 = 0; i0 < nv; i0 += kGroup) {
+    double2 acc[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) acc[u] = make_double2(0.0, 0.0);
+    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
       const double2 c = to_d2(w[k]);
-      re += a.x * c.x + a.y * c.y;
-      im += a.x * c.y - a.y * c.x;
+      double2 a[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        acc[u].x += a[u].x * c.x + a[u].y * c.y;
+        acc[u].y += a[u].x * c.y - a[u].y * c.x;
+      }
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) q.partial[(size_t)i * nblk + blockIdx.x] = make_double2(re, im);
+    store_group(acc, i0, nv, q.partial, gridDim.x);
+  }
+}
+
+// w[k] -= sum_{i<nv} V_i[k] h[i] over the block's chunk, then (fused) the
+// partial dot products of the updated w with every V_i (pass 0 of CGS2 ->
+// input of pass 1), or the partial |w|^2 (pass 1 -> the Arnoldi norm).
+template <typename V>
+__global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __restrict__ P, int nv, int pass) {
+  const ProbK& q = P[blockIdx.y];
+  if (!q.st->active) return;
+  extern __shared__ double2 hs[];
+  const double2* h = pass == 0 ? q.hcol : q.h2;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  const V* __restrict__ Vb = (const V*)q.V;
+  V* __restrict__ w = (V*)q.w;
+  const size_t n = q.n;
+  const Chunk ch = chunk_of(n);
+  double nrm = 0.0;
+  for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+    double2 acc = to_d2(w[k]);
+    for (int i0 = 0; i0 < nv; i0 += kGroup) {
+      double2 a[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        if (i0 + u < nv) {
+          acc.x -= a[u].x * hs[i0 + u].x - a[u].y * hs[i0 + u].y;
+          acc.y -= a[u].x * hs[i0 + u].y + a[u].y * hs[i0 + u].x;
+        }
+      }
+    }
+    const V out = from_d2<V>(acc);
+    w[k] = out;
+    const double2 r = to_d2(out);
+    nrm += r.x * r.x + r.y * r.y;
+  }
+  if (pass == 1) {
+    block_store_sum(nrm, q.partial + blockIdx.x);
+    return;
+  }
+  __syncthreads();   // this block's w is complete: dots of pass 1 on the same chunk
+  for (int i0 = 0; i0 < nv; i0 += kGroup) {
+    double2 acc[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) acc[u] = make_double2(0.0, 0.0);
+    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+      const double2 c = to_d2(w[k]);
+      double2 a[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        acc[u].x += a[u].x * c.x + a[u].y * c.y;
+        acc[u].y += a[u].x * c.y - a[u].y * c.x;
+      }
+    }
+    store_group(acc, i0, nv, q.partial, gridDim.x);
   }
 }
 
@@ -154,55 +265,6 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const ProbK* 
       q.hcol[i].y += sim[0];
     }
   }
-}
-
-// w[k] -= sum_{i<nv} V_i[k] h[i] with h = hcol (pass 0) or h2 (pass 1); FP64 accumulation
-template <typename V>
-__global__ void __launch_bounds__(kThreads) update_kernel(const ProbK* __restrict__ P, int nv, int pass) {
-  const ProbK& q = P[blockIdx.y];
-  if (!q.st->active) return;
-  extern __shared__ double2 hs[];
-  const double2* h = pass == 0 ? q.hcol : q.h2;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
-  __syncthreads();
-  const V* __restrict__ Vb = (const V*)q.V;
-  V* __restrict__ w = (V*)q.w;
-  const size_t n = q.n;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    double2 acc = to_d2(w[k]);
-    for (int i = 0; i < nv; ++i) {
-      const double2 v = to_d2(Vb[(size_t)i * n + k]);
-      acc.x -= v.x * hs[i].x - v.y * hs[i].y;
-      acc.y -= v.x * hs[i].y + v.y * hs[i].x;
-    }
-    w[k] = from_d2<V>(acc);
-  }
-}
-
-__device__ __forceinline__ void block_store_sum(double s, double2* out) {
-  __shared__ double red[kThreads / 32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    *out = make_double2(t, 0.0);
-  }
-}
-
-// partial[b] = sum over the block's elements of |w[k]|^2
-template <typename V>
-__global__ void __launch_bounds__(kThreads) norm2_w_kernel(const ProbK* __restrict__ P) {
-  const ProbK& q = P[blockIdx.y];
-  if (!q.st->active) return;
-  const V* __restrict__ w = (const V*)q.w;
-  double s = 0.0;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = to_d2(w[k]);
-    s += a.x * a.x + a.y * a.y;
-  }
-  block_store_sum(s, q.partial + blockIdx.x);
 }
 
 // partial[b] = sum |b[k]|^2 (used before any cycle: no status check)
@@ -490,6 +552,7 @@ struct BatchCall {
   SolveStatus* st = nullptr;        // device, one per problem
   SolveStatus* st_host = nullptr;   // pinned mirror
   double2* partial_host = nullptr;  // pinned, kDotBlocks per problem
+  std::vector<char> pc_on;          // preconditioner still in use, per problem
   ~BatchCall() {
     cudaFree(table);
     cudaFree(st);
@@ -568,21 +631,25 @@ static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, i
     if (flexible) {
       for (int i : live) {
         const ProbK& q = c.host[i];
-        vie_status ps = precond(precond_ctx[i], dtype, (const char*)q.V + (size_t)j * q.n * sizeof(V),
-                                (char*)q.Z + (size_t)j * q.n * sizeof(V), s);
-        if (ps != VIE_OK) return ps;
+        const char* vj = (const char*)q.V + (size_t)j * q.n * sizeof(V);
+        char* zj = (char*)q.Z + (size_t)j * q.n * sizeof(V);
+        if (c.pc_on[i]) {
+          vie_status ps = precond(precond_ctx[i], dtype, vj, zj, s);
+          if (ps != VIE_OK) return ps;
+        } else {
+          VIE_CUDA_TRY(cudaMemcpyAsync(zj, vj, q.n * sizeof(V), cudaMemcpyDeviceToDevice, s));
+        }
       }
     }
     vie_status ms = apply_list(c, live, dtype, false, j, flexible, s);
     if (ms != VIE_OK) return ms;
     const int nv = j + 1;
+    // CGS2 in three sweeps over the basis: dots; update + dots; update + norm
     dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
-    update_kernel<V><<<dim3(gx, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 0);
-    dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
+    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 0);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
-    update_kernel<V><<<dim3(gx, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 1);
-    norm2_w_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table);
+    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 1);
     arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, kDotBlocks, m + 1, j);
     next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
     VIE_LAUNCH_CHECK();
@@ -619,6 +686,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   BatchCall c;
   c.plans.assign(plans, plans + count);
   c.host.resize(count);
+  c.pc_on.assign(count, flexible ? 1 : 0);
   VIE_CUDA_TRY(cudaMalloc((void**)&c.table, count * sizeof(ProbK)));
   VIE_CUDA_TRY(cudaMalloc((void**)&c.st, count * sizeof(SolveStatus)));
   VIE_CUDA_TRY(cudaMallocHost((void**)&c.st_host, count * sizeof(SolveStatus)));
@@ -652,7 +720,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   VIE_CUDA_TRY(cudaStreamSynchronize(s));
   std::vector<int> list;
   std::vector<int> iters(count, 0), outers(count, 0);
-  std::vector<double> rel(count, 0.0);
+  std::vector<double> rel(count, 0.0), prev_rel(count, 0.0);
   std::vector<vie_status> result(count, VIE_OK);
   for (int i = 0; i < count; ++i) {
     double t = 0.0;
@@ -691,6 +759,18 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
       infos[i].history_len = outers[i] + 1 < 64 ? outers[i] + 1 : 64;
       if (!isfinite(rn)) { result[i] = VIE_ERR_NONFINITE; continue; }
       if (rn <= tol * c.host[i].bnorm) { infos[i].converged = 1; continue; }
+      // the true residual judges the preconditioner: a preconditioned cycle
+      // that did not cut it by 10 %, or a non-finite network output, switches
+      // this problem to the identity for the rest of the solve
+      if (c.pc_on[i] && outers[i] > 0) {
+        const bool stalled = rel[i] > 0.9 * prev_rel[i];
+        const bool broken = precond_fallback_flag(c.plans[i], 1) != 0;
+        if (stalled || broken) {
+          c.pc_on[i] = 0;
+          infos[i].fallback = 1;
+        }
+      }
+      prev_rel[i] = rel[i];
       if (iters[i] >= max_iters || outers[i] >= max_outer) { result[i] = VIE_ERR_NOT_CONVERGED; continue; }
       // plain mode goes for tol ||b||; mixed asks the complex64 cycle for a
       // reduction inner_tol, never below half the outer target

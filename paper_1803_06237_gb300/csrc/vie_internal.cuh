@@ -135,6 +135,7 @@ typedef vie_status (*vie_precond_fn)(void* ctx, int dtype, const void* v, void* 
 void free_krylov(vie_plan* p);
 void free_precond(vie_plan* p);
 vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx);
+int precond_fallback_flag(vie_plan* p, int clear);   // non-finite network output seen
 
 // Operator application for `count` plans of one shape (same n and m);
 // x[i], y[i] are device vectors of dtype; each plan's own workspace is used.

@@ -75,6 +75,16 @@ _SIGNATURES = {
     "vie_eps2_from_round_trip": ([_D, _I, _D, _D, _D, _D, _D, ctypes.POINTER(_D)], _I),
     "vie_matvec_static_scratch": ([_P, _P, _P, _I, _P], _I),
     "vie_axis_field": ([_P, _P, _I, _P, _P], _I),
+    "vie_net_param_count": ([], ctypes.c_size_t),
+    "vie_net_create": ([ctypes.POINTER(_P), _P, ctypes.c_size_t, ctypes.c_ulonglong], _I),
+    "vie_net_destroy": ([_P], _I),
+    "vie_net_get_params": ([_P, _P], _I),
+    "vie_net_get_grads": ([_P, _P], _I),
+    "vie_net_apply": ([_P, _P, _P, _P, _I, _P], _I),
+    "vie_net_accumulate": ([_P, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
+    "vie_net_zero_grad": ([_P], _I),
+    "vie_net_adam_step": ([_P, ctypes.c_float, ctypes.c_float, _P], _I),
+    "vie_set_preconditioner": ([_P, _P], _I),
     "vie_plan_clone": ([_P, ctypes.POINTER(_P)], _I),
     "vie_matvec_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P], _I),
     "vie_solve_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D,
@@ -319,6 +329,90 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
     if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
         _check(st, "vie_solve_batch")
     return st, out
+
+
+class Net:
+    """Owns a vie_net* (learned preconditioner)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            load().vie_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vie_net_param_count() -> int:
+    return int(load().vie_net_param_count())
+
+
+def vie_net_create(params=None, seed: int = 0) -> Net:
+    h = ctypes.c_void_p()
+    if params is None:
+        _check(load().vie_net_create(ctypes.byref(h), None, 0, int(seed)), "vie_net_create")
+    else:
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        _check(load().vie_net_create(ctypes.byref(h), a.ctypes.data_as(ctypes.c_void_p), a.size, int(seed)),
+               "vie_net_create")
+    return Net(h)
+
+
+def vie_net_destroy(net: Net):
+    net.close()
+
+
+def vie_net_get_params(net: Net) -> np.ndarray:
+    out = np.empty(vie_net_param_count(), dtype=np.float32)
+    _check(load().vie_net_get_params(net.handle, out.ctypes.data_as(ctypes.c_void_p)), "vie_net_get_params")
+    return out
+
+
+def vie_net_get_grads(net: Net) -> np.ndarray:
+    out = np.empty(vie_net_param_count(), dtype=np.float32)
+    _check(load().vie_net_get_grads(net.handle, out.ctypes.data_as(ctypes.c_void_p)), "vie_net_get_grads")
+    return out
+
+
+def vie_net_apply(net: Net, plan: Plan, v, z, stream=None):
+    if not (v.is_cuda and z.is_cuda and v.dtype == z.dtype and v.numel() == 3 * plan.n_vox == z.numel()):
+        raise ValueError("v and z must be CUDA vectors of 3*nx*ny*nz entries of one dtype")
+    _check(load().vie_net_apply(net.handle, plan.handle, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                _dtype_code(v), _stream_handle(stream)), "vie_net_apply")
+    return z
+
+
+def vie_net_accumulate(net: Net, plan: Plan, r, e, stream=None) -> float:
+    import torch
+    for t in (r, e):
+        if not (t.is_cuda and t.dtype == torch.complex64 and t.numel() == 3 * plan.n_vox and t.is_contiguous()):
+            raise ValueError("r and e must be contiguous complex64 CUDA vectors of 3*nx*ny*nz entries")
+    loss = ctypes.c_double()
+    _check(load().vie_net_accumulate(net.handle, plan.handle, ctypes.c_void_p(r.data_ptr()),
+                                     ctypes.c_void_p(e.data_ptr()), ctypes.byref(loss), _stream_handle(stream)),
+           "vie_net_accumulate")
+    return loss.value
+
+
+def vie_net_zero_grad(net: Net):
+    _check(load().vie_net_zero_grad(net.handle), "vie_net_zero_grad")
+
+
+def vie_net_adam_step(net: Net, lr: float, grad_scale: float = 1.0, stream=None):
+    _check(load().vie_net_adam_step(net.handle, float(lr), float(grad_scale), _stream_handle(stream)),
+           "vie_net_adam_step")
+
+
+def vie_set_preconditioner(plan: Plan, net):
+    _check(load().vie_set_preconditioner(plan.handle, net.handle if net is not None else None),
+           "vie_set_preconditioner")
+    plan._net = net      # keep the network alive while it is set
 
 
 def vie_axis_field(plan: Plan, w, n_keep: int, stream=None):

@@ -1,0 +1,137 @@
+"""GPU learned preconditioner: forward output and every gradient against the
+FP64 oracle (oracle.convnet) with the same BF16-rounded weights, and
+flexible GMRES with the network."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import convnet as cn
+from oracle import operator as op
+from paper_1803_06237_gb300 import build, vie, workloads
+
+pytestmark = pytest.mark.gpu
+K0 = 2 * math.pi / 1.55
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    vie.load()
+
+
+def _bf16(a):
+    """Round FP32 values to BF16 (nearest, ties to even), returned as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _oracle_params(flat):
+    p, off = {}, 0
+    for name, ci, co in cn.LAYERS:
+        nw = co * ci * 27
+        p[name + ".w"] = _bf16(flat[off:off + nw]).reshape(co, ci, 3, 3, 3)
+        off += nw
+        p[name + ".b"] = flat[off:off + co].astype(np.float64)
+        off += co
+    assert off == flat.size
+    return p
+
+
+def _oracle_grads(g):
+    return np.concatenate([np.concatenate([g[n + ".w"].ravel(), g[n + ".b"].ravel()]) for n, _, _ in cn.LAYERS])
+
+
+def _setup(grid, seed):
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    chi = op.chi_from_permittivity(workloads.random_permittivity(grid, seed=seed), 2.085)
+    vie.vie_set_contrast(plan, chi)
+    net = vie.vie_net_create(seed=seed)
+    return plan, chi, net
+
+
+def _scale(v):
+    v = np.asarray(v, np.complex64).astype(np.complex128)
+    return math.sqrt(v.size / np.sum(np.abs(v) ** 2))
+
+
+def test_param_layout():
+    n = sum(co * ci * 27 + co for _, ci, co in cn.LAYERS)
+    assert vie.vie_net_param_count() == n
+
+
+@pytest.mark.parametrize("grid", [(21, 9, 5), (16, 8, 3)])
+def test_forward_matches_oracle(grid):
+    plan, chi, net = _setup(grid, 5)
+    p = _oracle_params(vie.vie_net_get_params(net))
+    nx, ny, nz = grid
+    v = workloads.random_currents(grid, seed=6).astype(np.complex64)
+    vd = torch.from_numpy(v.ravel()).cuda()
+    zd = torch.empty_like(vd)
+    vie.vie_net_apply(net, plan, vd, zd)
+    torch.cuda.synchronize()
+    s = _scale(v)
+    X = cn.pack_input(v.astype(np.complex128) * s, chi)
+    z_ref = cn.unpack_output(cn.forward(p, X)) / s
+    z = zd.cpu().numpy().reshape(3, nz, ny, nx)
+    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 1e-4
+
+
+def test_gradients_match_oracle():
+    grid = (21, 9, 5)
+    plan, chi, net = _setup(grid, 7)
+    p = _oracle_params(vie.vie_net_get_params(net))
+    nx, ny, nz = grid
+    r = workloads.random_currents(grid, seed=8).astype(np.complex64)
+    e = workloads.random_currents(grid, seed=9).astype(np.complex64)
+    vie.vie_net_zero_grad(net)
+    loss = vie.vie_net_accumulate(net, plan, torch.from_numpy(r.ravel()).cuda(), torch.from_numpy(e.ravel()).cuda())
+    g_gpu = vie.vie_net_get_grads(net)
+    s = _scale(r)
+    X = cn.pack_input(r.astype(np.complex128) * s, chi)
+    E = np.concatenate([(e.astype(np.complex128) * s).real, (e.astype(np.complex128) * s).imag], axis=0)
+    y, cache = cn.forward(p, X, keep=True)
+    l_ref, dy = cn.relative_mse(y, E)
+    g, _ = cn.backward(p, cache, dy)
+    assert abs(loss - l_ref) <= 1e-5 * l_ref
+    off = 0
+    for name, ci, co in cn.LAYERS:
+        for part, size in (("w", co * ci * 27), ("b", co)):
+            a = g_gpu[off:off + size].astype(np.float64)
+            b = g[f"{name}.{part}"].ravel()
+            off += size
+            assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-12, (name, part)
+
+
+def test_adam_step_reduces_the_loss():
+    grid = (16, 8, 3)
+    plan, chi, net = _setup(grid, 11)
+    r = torch.from_numpy(workloads.random_currents(grid, seed=12).astype(np.complex64).ravel()).cuda()
+    e = torch.from_numpy(workloads.random_currents(grid, seed=13).astype(np.complex64).ravel()).cuda()
+    losses = []
+    for _ in range(30):
+        vie.vie_net_zero_grad(net)
+        losses.append(vie.vie_net_accumulate(net, plan, r, e))
+        vie.vie_net_adam_step(net, 1e-3)
+    assert losses[-1] < 0.7 * losses[0]
+
+
+def test_flexible_gmres_with_network_converges():
+    wl = workloads.waveguide(nx=60, absorber_len_um=0.4, src_x_um=0.2)
+    ab = [dict(x0=40.0, length=20.0, degree=2, eps2_max=2.0)]
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, ab)
+    net = vie.vie_net_create(seed=3)
+    vie.vie_set_preconditioner(plan, net)
+    src = torch.from_numpy(wl.src.ravel()).cuda()
+    b = torch.empty_like(src)
+    vie.vie_rhs_from_source(plan, src, b)
+    x = torch.zeros_like(b)
+    info = vie.vie_solve(plan, b, x, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30, use_preconditioner=True)
+    assert info["converged"] and info["residual"] <= 1e-6
+    y = torch.empty_like(x)
+    vie.vie_matvec(plan, x, y)
+    torch.cuda.synchronize()
+    assert (torch.linalg.vector_norm(y - b) / torch.linalg.vector_norm(b)).item() <= 2e-6
