@@ -228,6 +228,10 @@ def gpu_arm(args):
         "clocks": clk,
         "setup_ms": info["setup_ms"],
     }
+    if not args.no_solve:
+        result["time_to_1e-6"] = solve_section(plan, wl, absorbers, args)
+    if not args.no_batch:
+        result["batch48"] = batch_section(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -235,6 +239,102 @@ def gpu_arm(args):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed_solve(plan, b, mode, restart, use_pc):
+    import torch
+
+    from paper_1803_06237_gb300 import vie
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    info = vie.vie_solve(plan, b, x, 1e-6, mode=mode, restart=restart, use_preconditioner=use_pc,
+                         raise_on_not_converged=False)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t) * 1e3
+    return {"ms": wall, "device_ms": info["time_ms"], "iterations": info["iterations"], "cycles": info["outer"],
+            "matvecs_c128": info["matvecs64"], "matvecs_c64": info["matvecs32"], "converged": info["converged"],
+            "true_residual": info["residual"], "preconditioner_dropped": info["fallback"], "restart": restart}
+
+
+def solve_section(plan, wl, absorbers, args):
+    """Time to a true FP64 relative residual of 1e-6 on the benchmark guide
+    (Gaussian sheet source): plain complex128 GMRES, mixed precision, and
+    mixed precision with the learned preconditioner (trained first, outside
+    the timed solves, on pairs from plain solves of random strips and bends)."""
+    import torch
+
+    from paper_1803_06237_gb300 import learned, vie
+    src = torch.from_numpy(np.ascontiguousarray(wl.src.ravel())).cuda()
+    b = torch.empty_like(src)
+    vie.vie_rhs_from_source(plan, src, b)
+    _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, False)      # warm-up (workspaces)
+    out = {"fp64": _timed_solve(plan, b, vie.VIE_SOLVE_FP64, args.restart_fp64, False),
+           "mixed": _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, False)}
+    if args.train_steps > 0:
+        t0 = time.perf_counter()
+        pairs = learned.make_pairs(range(args.train_problems), grid=(160, 40, 11), restart=20, cycles=10)
+        t1 = time.perf_counter()
+        net = vie.vie_net_create(seed=1)
+        losses = learned.train(net, pairs, steps=args.train_steps, lr=1e-3, batch=4)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        vie.vie_set_preconditioner(plan, net)
+        _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)   # warm-up
+        out["mixed_learned"] = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
+        out["training"] = {"pairs": len(pairs), "problems": args.train_problems, "steps": args.train_steps,
+                           "pair_generation_s": t1 - t0, "train_s": t2 - t1,
+                           "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:]))}
+        vie.vie_set_preconditioner(plan, None)
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    if "mixed_learned" in out:
+        out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms"] / out["mixed_learned"]["ms"]
+    return out
+
+
+def batch_section(args):
+    """The 48 uneven guides solved together to 1e-6 (mixed precision), and
+    the grouped operator on all 48 (complex64 applications per second)."""
+    import torch
+
+    from paper_1803_06237_gb300 import learned, vie, workloads
+    wls = workloads.batch48()
+    plans, bs, base = [], [], {}
+    for wl in wls:
+        plan, b = learned.setup_problem(wl, base.get(wl.grid))
+        base.setdefault(wl.grid, plan)
+        plans.append(plan)
+        bs.append(b)
+    xs = [torch.zeros_like(b) for b in bs]
+    vie.vie_solve_batch(plans, bs, xs, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=args.restart_mixed,
+                        raise_on_not_converged=False)                                      # warm-up
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st, infos = vie.vie_solve_batch(plans, bs, xs, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=args.restart_mixed,
+                                    raise_on_not_converged=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    v64 = [torch.randn(3 * p.n_vox, dtype=torch.complex64, device="cuda") for p in plans]
+    y64 = [torch.empty_like(v) for v in v64]
+    for _ in range(3):
+        vie.vie_matvec_batch(plans, v64, y64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    e0.record()
+    for _ in range(reps):
+        vie.vie_matvec_batch(plans, v64, y64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    vox = sum(p.n_vox for p in plans)
+    return {"problems": len(plans), "voxels": vox, "solve_s": wall, "status": st,
+            "converged": sum(1 for i in infos if i["converged"]),
+            "max_true_residual": max(i["residual"] for i in infos),
+            "iterations_total": sum(i["iterations"] for i in infos),
+            "grouped_matvec_ms": ms, "grouped_matvecs_per_s": len(plans) * 1e3 / ms,
+            "note": "solve_s covers all 48 problems in one vie_solve_batch call"}
 
 
 def _oracle_sample(seconds: float):
@@ -304,6 +404,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--restart-fp64", type=int, default=200)
+    ap.add_argument("--restart-mixed", type=int, default=30)
+    ap.add_argument("--train-problems", type=int, default=30)
+    ap.add_argument("--train-steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

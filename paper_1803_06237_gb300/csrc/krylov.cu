@@ -2,10 +2,13 @@
 // arXiv:1803.06237; the paper solves it with GMRES at tolerance 1e-8, Sec. 5),
 // for one problem or a batch of problems of uneven sizes.
 //
-// * Arnoldi with classical Gram-Schmidt applied twice (CGS2); dot products and
-//   norms accumulate in FP64 whatever the vector type; the Hessenberg matrix,
-//   Givens rotations and the small least-squares problem are FP64 and stay on
-//   the device.  The host reads one status record per problem every few steps.
+// * Arnoldi with classical Gram-Schmidt applied twice (CGS2) in three fused
+//   sweeps over the basis.  Products and each thread's short partial sums use
+//   the vectors' precision (FP32 for complex64: this GPU's FP64 rate is a
+//   small fraction of its FP32 rate); every sum across threads and blocks is
+//   FP64, in a fixed order.  The Hessenberg matrix, Givens rotations and the
+//   small least-squares problem are FP64 and stay on the device.  The host
+//   reads one status record per problem every few steps.
 // * Right-preconditioned flexible GMRES keeps z_j = P(v_j) (a nonlinear P is
 //   allowed); with no preconditioner z_j = v_j and Z aliases V.
 // * Mixed precision: iterative refinement whose residual r = b - A x uses the
@@ -71,6 +74,20 @@ template <typename V> __device__ __forceinline__ V from_d2(double2 v);
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
 
+// Arithmetic type of per-thread work on vectors of type V: complex64 vectors
+// are multiplied and summed over a thread's few elements in FP32 (the FP64
+// rate of this GPU is a small fraction of FP32), and every sum across threads
+// and blocks is FP64.  complex128 vectors use FP64 throughout.
+template <typename V> struct Acc;
+template <> struct Acc<float2> { typedef float2 T; typedef float R; };
+template <> struct Acc<double2> { typedef double2 T; typedef double R; };
+template <typename A> __device__ __forceinline__ A zero_acc();
+template <> __device__ __forceinline__ float2 zero_acc<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zero_acc<double2>() { return make_double2(0.0, 0.0); }
+template <typename A> __device__ __forceinline__ A acc_from(double2 v);
+template <> __device__ __forceinline__ float2 acc_from<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <> __device__ __forceinline__ double2 acc_from<double2>(double2 v) { return v; }
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -123,14 +140,16 @@ constexpr int kGroup = 8;   // basis vectors handled together (loads in flight p
 
 // Block-reduce kGroup complex sums and store them as partials of vectors
 // i0 .. i0 + kGroup - 1 (those < nv).
-__device__ __forceinline__ void store_group(double2 (&acc)[kGroup], int i0, int nv, double2* __restrict__ partial,
+template <typename A>
+__device__ __forceinline__ void store_group(A (&acc_in)[kGroup], int i0, int nv, double2* __restrict__ partial,
                                             int nblk) {
   __shared__ double2 red[kThreads / 32][kGroup];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double2 acc[kGroup];
 #pragma unroll
   for (int u = 0; u < kGroup; ++u) {
-    acc[u].x = warp_sum(acc[u].x);
-    acc[u].y = warp_sum(acc[u].y);
+    acc[u].x = warp_sum((double)acc_in[u].x);
+    acc[u].y = warp_sum((double)acc_in[u].y);
   }
   if (lane == 0)
 #pragma unroll
@@ -156,15 +175,16 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict_
   const V* __restrict__ w = (const V*)q.w;
   const size_t n = q.n;
   const Chunk ch = chunk_of(n);
+  typedef typename Acc<V>::T A;
   for (int i0 = 0; i0 < nv; i0 += kGroup) {
-    double2 acc[kGroup];
+    A acc[kGroup];
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) acc[u] = make_double2(0.0, 0.0);
+    for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
     for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
-      const double2 c = to_d2(w[k]);
-      double2 a[kGroup];
+      const V c = w[k];
+      V a[kGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
 #pragma unroll
       for (int u = 0; u < kGroup; ++u) {
         acc[u].x += a[u].x * c.x + a[u].y * c.y;
@@ -182,21 +202,27 @@ template <typename V>
 __global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __restrict__ P, int nv, int pass) {
   const ProbK& q = P[blockIdx.y];
   if (!q.st->active) return;
-  extern __shared__ double2 hs[];
+  typedef typename Acc<V>::T A;
+  typedef typename Acc<V>::R AR;
+  extern __shared__ unsigned char hs_raw[];
+  A* hs = reinterpret_cast<A*>(hs_raw);
   const double2* h = pass == 0 ? q.hcol : q.h2;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = acc_from<A>(h[i]);
   __syncthreads();
   const V* __restrict__ Vb = (const V*)q.V;
   V* __restrict__ w = (V*)q.w;
   const size_t n = q.n;
   const Chunk ch = chunk_of(n);
-  double nrm = 0.0;
+  AR nrm = 0;
   for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
-    double2 acc = to_d2(w[k]);
+    const V w0 = w[k];
+    A acc;
+    acc.x = w0.x;
+    acc.y = w0.y;
     for (int i0 = 0; i0 < nv; i0 += kGroup) {
-      double2 a[kGroup];
+      V a[kGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
 #pragma unroll
       for (int u = 0; u < kGroup; ++u) {
         if (i0 + u < nv) {
@@ -205,25 +231,27 @@ __global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __r
         }
       }
     }
-    const V out = from_d2<V>(acc);
+    V out;
+    out.x = acc.x;
+    out.y = acc.y;
     w[k] = out;
-    const double2 r = to_d2(out);
-    nrm += r.x * r.x + r.y * r.y;
+    nrm += out.x * out.x + out.y * out.y;
   }
   if (pass == 1) {
-    block_store_sum(nrm, q.partial + blockIdx.x);
+    block_store_sum((double)nrm, q.partial + blockIdx.x);
     return;
   }
   __syncthreads();   // this block's w is complete: dots of pass 1 on the same chunk
+  typedef typename Acc<V>::T A;
   for (int i0 = 0; i0 < nv; i0 += kGroup) {
-    double2 acc[kGroup];
+    A acc[kGroup];
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) acc[u] = make_double2(0.0, 0.0);
+    for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
     for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
-      const double2 c = to_d2(w[k]);
-      double2 a[kGroup];
+      const V c = w[k];
+      V a[kGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? to_d2(Vb[(size_t)(i0 + u) * n + k]) : make_double2(0.0, 0.0);
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
 #pragma unroll
       for (int u = 0; u < kGroup; ++u) {
         acc[u].x += a[u].x * c.x + a[u].y * c.y;
@@ -400,12 +428,14 @@ template <typename V>
 __global__ void __launch_bounds__(kThreads) next_vector_kernel(const ProbK* __restrict__ P, int j) {
   const ProbK& q = P[blockIdx.y];
   if (!q.st->active) return;
-  const double s = q.st->inv_h;
+  const typename Acc<V>::R s = (typename Acc<V>::R)q.st->inv_h;
   const V* __restrict__ w = (const V*)q.w;
   V* __restrict__ v = (V*)q.V + (size_t)(j + 1) * q.n;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = to_d2(w[k]);
-    v[k] = from_d2<V>(make_double2(a.x * s, a.y * s));
+    V a = w[k];
+    a.x *= s;
+    a.y *= s;
+    v[k] = a;
   }
 }
 
@@ -441,19 +471,23 @@ __global__ void __launch_bounds__(kThreads) update_x_kernel(const ProbK* __restr
   const ProbK& q = P[blockIdx.y];
   const int m = q.st->j;
   if (m == 0) return;
-  extern __shared__ double2 ys[];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = q.ysol[i];
+  // the correction Z y is summed in the vector's precision (complex64: it only
+  // has to meet the loose inner tolerance); x itself accumulates in FP64
+  typedef typename Acc<V>::T A;
+  extern __shared__ unsigned char ys_raw[];
+  A* ys = reinterpret_cast<A*>(ys_raw);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = acc_from<A>(q.ysol[i]);
   __syncthreads();
   const V* __restrict__ Zb = (const V*)q.Z;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
+    A acc = zero_acc<A>();
     for (int i = 0; i < m; ++i) {
-      const double2 z = to_d2(Zb[(size_t)i * q.n + k]);
+      const V z = Zb[(size_t)i * q.n + k];
       acc.x += z.x * ys[i].x - z.y * ys[i].y;
       acc.y += z.x * ys[i].y + z.y * ys[i].x;
     }
-    q.x64[k].x += acc.x;
-    q.x64[k].y += acc.y;
+    q.x64[k].x += (double)acc.x;
+    q.x64[k].y += (double)acc.y;
   }
 }
 
@@ -647,9 +681,9 @@ static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, i
     // CGS2 in three sweeps over the basis: dots; update + dots; update + norm
     dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
-    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 0);
+    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(typename Acc<V>::T), s>>>(c.table, nv, 0);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
-    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(double2), s>>>(c.table, nv, 1);
+    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(typename Acc<V>::T), s>>>(c.table, nv, 1);
     arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, kDotBlocks, m + 1, j);
     next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
     VIE_LAUNCH_CHECK();
@@ -663,7 +697,7 @@ static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, i
     }
   }
   backsolve_kernel<<<P, kThreads, 0, s>>>(c.table, m + 1);
-  update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(double2), s>>>(c.table);
+  update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(typename Acc<V>::T), s>>>(c.table);
   VIE_LAUNCH_CHECK();
   return read_status(c, s);
 }

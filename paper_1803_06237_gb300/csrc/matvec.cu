@@ -181,15 +181,17 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__
   const int ny = g.ny, nz = g.nz;
   const bool fx = kx > g.Mx - kx;
   const int kxf = fx ? g.Mx - kx : kx;
+  for (int i = tid; i < MY; i += nth) __pipeline_memcpy_async(twy + i, twyg + i, sizeof(V));
+  for (int i = tid; i < MZ; i += nth) __pipeline_memcpy_async(twz + i, twzg + i, sizeof(V));
+  __pipeline_commit();
   {
-    // asynchronous copy; it lands while the z and y transforms run
+    // spectrum chunk: lands while the z and y transforms run
     const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
     const int chunk = 6 * g.Kz * g.Ky;
     for (int i = tid; i < chunk; i += nth) __pipeline_memcpy_async(Gs + i, G + i, sizeof(V));
     __pipeline_commit();
   }
-  for (int i = tid; i < MY; i += nth) twy[i] = twyg[i];
-  for (int i = tid; i < MZ; i += nth) twz[i] = twzg[i];
+  __pipeline_wait_prior(1);   // twiddles done; the spectrum may still be in flight
   __syncthreads();
   V* slab = work + (size_t)kx * g.NL;
   // forward z on the 3 ny non-zero lines (c, y)
@@ -382,30 +384,18 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
   const int tid = threadIdx.x, nth = blockDim.x;
   const int l0 = blockIdx.x * LPB;
   const int nl = min(LPB, NL - l0);
-  for (int i = tid; i < MX; i += nth) twx[i] = twxg[i];
-  for (int i = tid; i < L1; i += nth) tw1[i] = twxg[i * L2];   // w_L1^i = w_Mx^(i L2)
-  for (int i = tid; i < L2; i += nth) tw2[i] = twxg[i * L1];
   {
-    // the block's lines are contiguous in x; keep 8 loads in flight per thread
-    const int total = nl * nx;
+    // asynchronous copies of the twiddles and of the block's lines (contiguous in x)
+    for (int i = tid; i < MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
     const V* src = x + (size_t)l0 * nx;
-    for (int base = 0; base < total; base += 8 * nth) {
-      V v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = base + u * nth + tid;
-        v[u] = (e < total) ? src[e] : zero_c<V>();
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = base + u * nth + tid;
-        if (e < total) {
-          const int l = e / nx;
-          Xs[l * P + (e - l * nx)] = v[u];
-        }
-      }
-    }
+    for (int l = 0; l < nl; ++l)
+      for (int n = tid; n < nx; n += nth) __pipeline_memcpy_async(Xs + l * P + n, src + (size_t)l * nx + n, sizeof(V));
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
   }
+  __syncthreads();
+  for (int i = tid; i < L1; i += nth) tw1[i] = twx[i * L2];   // w_L1^i = w_Mx^(i L2)
+  for (int i = tid; i < L2; i += nth) tw2[i] = twx[i * L1];
   __syncthreads();
   if (tid < LPB * L1) {
     const int l = tid % LPB, n1 = tid / LPB;
@@ -449,12 +439,27 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
   V* T = tw2 + L2;
   V* Ys = T + L2 * R;
   const int P = pitch_mod16(nx, LPB);
+  V* Xs = Ys + LPB * P;            // the block's rows of x (epilogue operand)
+  V* Ms = Xs + LPB * nx;           // the matching rows of M
   const int tid = threadIdx.x, nth = blockDim.x;
   const int l0 = blockIdx.x * LPB;
   const int nl = min(LPB, NL - l0);
-  for (int i = tid; i < MX; i += nth) twx[i] = twxg[i];
-  for (int i = tid; i < L1; i += nth) tw1[i] = twxg[i * L2];   // w_L1^i = w_Mx^(i L2)
-  for (int i = tid; i < L2; i += nth) tw2[i] = twxg[i * L1];
+  {
+    // asynchronous copies: twiddles now, epilogue operands to land during the FFTs
+    for (int i = tid; i < MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
+    __pipeline_commit();
+    const V* xsrc = x + (size_t)l0 * nx;
+    for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
+    for (int l = 0; l < nl; ++l) {
+      const V* msrc = Mc + (size_t)((l0 + l) % nyz) * nx;
+      for (int i = tid; i < nx; i += nth) __pipeline_memcpy_async(Ms + l * nx + i, msrc + i, sizeof(V));
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(1);      // twiddles only
+  }
+  __syncthreads();
+  for (int i = tid; i < L1; i += nth) tw1[i] = twx[i * L2];   // w_L1^i = w_Mx^(i L2)
+  for (int i = tid; i < L2; i += nth) tw2[i] = twx[i * L1];
   __syncthreads();
   // inverse transform, same decomposition with conjugate twiddles:
   // input a = a1 + L1 a2 (a spectrum index kx), output b = b2 + L2 b1 (x)
@@ -482,30 +487,17 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     }
   }
   __syncthreads();
+  __pipeline_wait_prior(0);
+  __syncthreads();
   {
-    // contrast epilogue with 4 pairs of loads in flight per thread
+    // contrast epilogue from the prefetched rows
     const int total = nl * nx;
     const size_t g0 = (size_t)l0 * nx;
-    for (int base = 0; base < total; base += 4 * nth) {
-      V wv[4], mv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = base + u * nth + tid;
-        if (e < total) {
-          const int l = e / nx, ix = e - l * nx;
-          wv[u] = x[g0 + e];
-          mv[u] = Mc[(size_t)((l0 + l) % nyz) * nx + ix];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = base + u * nth + tid;
-        if (e < total) {
-          const int l = e / nx, ix = e - l * nx;
-          const V uu = Ys[l * P + ix];
-          y[g0 + e] = (mode == MODE_OPERATOR) ? sub(wv[u], mul(mv[u], uu)) : mul(mv[u], sub(uu, wv[u]));
-        }
-      }
+    for (int e = tid; e < total; e += nth) {
+      const int l = e / nx, ix = e - l * nx;
+      const V uu = Ys[l * P + ix];
+      const V wv = Xs[e], mv = Ms[e];
+      y[g0 + e] = (mode == MODE_OPERATOR) ? sub(wv, mul(mv, uu)) : mul(mv, sub(uu, wv));
     }
   }
 }
@@ -524,7 +516,7 @@ static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int 
     constexpr int R = pitch_mod16(L1 * LPB, LPB);
     constexpr int NT = LPB * (L1 > L2 ? L1 : L2);
     const int P = pitch_mod16(nx, LPB);
-    const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P) * sizeof(V);
+    const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P + (forward ? 0 : 2 * LPB * nx)) * sizeof(V);
     if (smem > 200 * 1024) { *done = false; return VIE_OK; }
     const dim3 blocks((unsigned)((NL + LPB - 1) / LPB), (unsigned)count);
     if (forward) {

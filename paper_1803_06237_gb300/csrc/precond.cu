@@ -137,6 +137,118 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const float* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core convolution: implicit GEMM with mma.sync m16n8k16 (BF16 inputs,
+// FP32 accumulation).  M = 16 consecutive x voxels per warp, N = output
+// channels in tiles of 8, K = (tap, input channel) with the channels of one
+// tap contiguous.  A block (4 warps) covers 64 x voxels of one (z, y) row:
+// its input rows (9 taps in z and y, 66 x values, all channels) are staged in
+// shared memory as BF16 with the channel index fastest and a pitch of
+// CIP + 8 channels (no bank conflicts for the fragment loads).  Weights are
+// pre-packed as wp[tap][o][CIP] BF16 (zero padding) and read from L1/L2.
+// The input of every tensor-core convolution is therefore rounded to BF16.
+// ---------------------------------------------------------------------------
+constexpr int kMmaWarps = 4;
+constexpr int kMmaX = 16 * kMmaWarps;   // voxels per block
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+  const unsigned short ua = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const unsigned short ub = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return (unsigned)ua | ((unsigned)ub << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int CIP, int NT>
+__global__ void __launch_bounds__(32 * kMmaWarps) conv_mma_kernel(const float* __restrict__ in, int ci,
+                                                                  const __nv_bfloat16* __restrict__ wp,
+                                                                  const float* __restrict__ bias, int co,
+                                                                  float* __restrict__ pre, float* __restrict__ out,
+                                                                  Dims d, int relu) {
+  constexpr int PITCH = CIP + 8;             // channels per staged voxel (bf16)
+  constexpr int XS = kMmaX + 2;
+  __shared__ __align__(16) __nv_bfloat16 tile[9 * XS * PITCH];
+  const int z = blockIdx.z, y = blockIdx.y;
+  const int x0 = blockIdx.x * kMmaX;
+  const size_t plane = (size_t)d.ny * d.nx;
+  const size_t chan = (size_t)d.nz * plane;
+  // stage: tile[zy][xs][c] = in[c][z + dz - 1][y + dy - 1][x0 + xs - 1] (zero outside / c >= ci)
+  for (int i = threadIdx.x; i < 9 * XS * CIP; i += blockDim.x) {
+    const int xs = i % XS;
+    const int c = (i / XS) % CIP;
+    const int zy = i / (XS * CIP);
+    const int zz = z + zy / 3 - 1, yy = y + zy % 3 - 1, xx = x0 + xs - 1;
+    float v = 0.f;
+    if (c < ci && zz >= 0 && zz < d.nz && yy >= 0 && yy < d.ny && xx >= 0 && xx < d.nx)
+      v = in[(size_t)c * chan + (size_t)zz * plane + (size_t)yy * d.nx + xx];
+    tile[(zy * XS + xs) * PITCH + c] = __float2bfloat16_rn(v);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int m0 = warp * 16;                    // this warp's first voxel within the block
+  float acc[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[n][r] = 0.f;
+  const unsigned* w32 = reinterpret_cast<const unsigned*>(wp);
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int zy = tap / 3, dx = tap % 3;
+    const __nv_bfloat16* row0 = tile + (zy * XS + m0 + g + dx) * PITCH;        // voxel m0 + g
+    const __nv_bfloat16* row8 = row0 + 8 * PITCH;                              // voxel m0 + g + 8
+#pragma unroll
+    for (int kc = 0; kc < CIP; kc += 16) {
+      unsigned a[4];
+      a[0] = *reinterpret_cast<const unsigned*>(row0 + kc + 2 * t4);
+      a[1] = *reinterpret_cast<const unsigned*>(row8 + kc + 2 * t4);
+      a[2] = *reinterpret_cast<const unsigned*>(row0 + kc + 8 + 2 * t4);
+      a[3] = *reinterpret_cast<const unsigned*>(row8 + kc + 8 + 2 * t4);
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        // B[k][o] = wp[tap][o][kc + k], o = 8 n + g; k pairs (2 t4, 2 t4 + 1) and (+8)
+        const size_t wb = ((size_t)tap * (NT * 8) + 8 * n + g) * CIP + kc + 2 * t4;
+        const unsigned b0 = __ldg(w32 + wb / 2);
+        const unsigned b1 = __ldg(w32 + (wb + 8) / 2);
+        mma_bf16(acc[n], a, b0, b1);
+      }
+    }
+  }
+  // D fragment: acc[n][0..1] -> voxel m0 + g, channels 8n + 2 t4 (+1); acc[n][2..3] -> voxel + 8
+  const size_t base = (size_t)z * plane + (size_t)y * d.nx;
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int o = 8 * n + 2 * t4 + (r & 1);
+      const int x = x0 + m0 + g + (r >= 2 ? 8 : 0);
+      if (o < co && x < d.nx) {
+        const float val = acc[n][r] + (bias ? bias[o] : 0.f);
+        if (pre) pre[(size_t)o * chan + base + x] = val;
+        out[(size_t)o * chan + base + x] = relu ? fmaxf(val, 0.f) : val;
+      }
+    }
+}
+
+// wp[tap][o][c] (o < NT*8, c < cip) from w[o][c][tap] (BF16), zero padding
+__global__ void pack_mma_weights_kernel(const __nv_bfloat16* __restrict__ w, int ci, int co, int cip, int no,
+                                        __nv_bfloat16* __restrict__ wp) {
+  const size_t n = (size_t)27 * no * cip;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % cip);
+    const int o = (int)((i / cip) % no);
+    const int t = (int)(i / ((size_t)cip * no));
+    wp[i] = (o < co && c < ci) ? w[((size_t)o * ci + c) * 27 + t] : __float2bfloat16_rn(0.f);
+  }
+}
+
 // dW[o][c][t] partial sums over the rows of one block, and the rows it owns:
 // rows r = blockIdx.y, blockIdx.y + gridDim.y, ...; 8 input channels per block
 // (blockIdx.x), thread = (o, c in chunk).  partial[(blockIdx.y * ci + c) * co + o][27]

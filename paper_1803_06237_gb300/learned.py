@@ -1,0 +1,95 @@
+"""Training and use of the learned right preconditioner (host orchestration).
+
+Every numerical step runs in libvie: the operator and the solver produce the
+training pairs, and the network's forward, backward and Adam kernels train
+it.  This module only chooses the problems, keeps the pairs and calls the
+library in order.
+
+Pairs: for a problem A x = b with solution x*, plain GMRES cycles (restart
+``restart``, complex64 inner solves inside FP64 refinement) from x = 0 give
+iterates x_k; each yields (r_k, e_k) with e_k = x* - x_k and r_k = A e_k
+(complex64 operator), so A e_k = r_k holds by construction.  The network is
+trained to map r_k to e_k (relative mean squared error, both scaled by the
+RMS of r_k).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import vie, workloads
+
+
+@dataclasses.dataclass
+class Pair:
+    plan: object
+    r: object      # complex64 CUDA vector
+    e: object
+
+
+def _absorbers(wl):
+    out = []
+    for ab in wl.absorbers:
+        e2 = ab.eps2_max if ab.eps2_max is not None else vie.vie_eps2_from_round_trip(
+            ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+        out.append(dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2, direction=ab.direction))
+    return out
+
+
+def setup_problem(wl, base_plan=None):
+    """Plan (a clone of base_plan when the grid matches), contrast and the
+    right-hand side of the workload's source.  Returns (plan, b)."""
+    import torch
+    if base_plan is not None and tuple(base_plan.n) == tuple(wl.grid):
+        plan = vie.vie_plan_clone(base_plan)
+    else:
+        plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, _absorbers(wl))
+    src = torch.from_numpy(np.ascontiguousarray(wl.src.ravel())).cuda()
+    b = torch.empty_like(src)
+    vie.vie_rhs_from_source(plan, src, b)
+    return plan, b
+
+
+def make_pairs(seeds, grid=(160, 40, 11), restart=20, cycles=12, tol=1e-6):
+    """Training pairs from plain solves of seeded random strip/bend guides."""
+    import torch
+    pairs = []
+    base = None
+    for seed in seeds:
+        wl = workloads.random_guide(seed, *grid)
+        plan, b = setup_problem(wl, base)
+        if base is None:
+            base = plan
+        xs = torch.zeros_like(b)
+        vie.vie_solve(plan, b, xs, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart, raise_on_not_converged=False)
+        x = torch.zeros_like(b)
+        for _ in range(cycles):
+            vie.vie_solve(plan, b, x, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart, max_iters=restart,
+                          max_outer=1, x0_given=True, raise_on_not_converged=False)
+            e = (xs - x).to(torch.complex64)
+            if torch.linalg.vector_norm(e).item() == 0.0:
+                break
+            r = torch.empty_like(e)
+            vie.vie_matvec(plan, e, r)
+            pairs.append(Pair(plan, r, e))
+    return pairs
+
+
+def train(net, pairs, steps, lr=1e-3, batch=4, seed=0, log_every=0):
+    """Adam on mini-batches of pairs; returns the per-step mean loss."""
+    rng = np.random.default_rng(seed)
+    losses = []
+    for step in range(steps):
+        vie.vie_net_zero_grad(net)
+        idx = rng.choice(len(pairs), size=min(batch, len(pairs)), replace=False)
+        tot = 0.0
+        for i in idx:
+            p = pairs[i]
+            tot += vie.vie_net_accumulate(net, p.plan, p.r, p.e)
+        vie.vie_net_adam_step(net, lr, 1.0 / len(idx))
+        losses.append(tot / len(idx))
+        if log_every and step % log_every == 0:
+            print(f"step {step} loss {losses[-1]:.4f}", flush=True)
+    return losses

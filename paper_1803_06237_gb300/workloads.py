@@ -145,3 +145,39 @@ def sample_indices(grid, seed: int, count: int) -> np.ndarray:
     n = 3 * int(np.prod(grid))
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.sort(rng.choice(n, size=min(count, n), replace=False))
+
+
+def random_guide(seed: int, nx: int = 160, ny: int = 40, nz: int = 11, h_um: float = 0.02,
+                 eps_core: float = 12.11, eps_bg: float = 2.085, absorber_len_um: float = 1.0,
+                 r_rt: float = 1e-10) -> Workload:
+    """Seeded strip or circular-bend waveguide (width U[350, 550] nm, all nz
+    layers core, i.e. 220 nm at h = 20 nm) on an nx x ny x nz grid, with a
+    quadratic absorber over the last ``absorber_len_um`` and a Gaussian
+    y-sheet 0.4 um from the left end.  Bends have radius U[2, 5] um and start
+    at a random x in the first third of the guide."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    width = rng.uniform(0.35, 0.55) / h_um                 # in voxels
+    yc = ny / 2.0 + rng.uniform(-2.0, 2.0)
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    X, Y = np.meshgrid(x, y)                               # (ny, nx)
+    if rng.random() < 0.5:
+        inside = np.abs(Y - yc) <= width / 2
+    else:
+        R = rng.uniform(2.0, 5.0) / h_um
+        x0 = rng.uniform(0.0, nx / 3.0)
+        sign = 1.0 if rng.random() < 0.5 else -1.0
+        # straight for x < x0, then an arc of radius R bending towards +/- y
+        cy = yc + sign * R
+        d_arc = np.abs(np.hypot(X - x0, Y - cy) - R)
+        inside = np.where(X < x0, np.abs(Y - yc) <= width / 2, d_arc <= width / 2)
+    eps = np.full((nz, ny, nx), eps_bg + 0j)
+    eps[:, inside] = eps_core
+    L = absorber_len_um / h_um
+    ab = Absorber(x0=nx - L, length=L, degree=2, r_rt=r_rt)
+    src = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+    ix = int(round(0.4 / h_um))
+    zz = np.arange(nz) + 0.5 - nz / 2.0
+    prof = np.exp(-(zz[:, None] ** 2 + (y[None, :] - yc) ** 2) / (0.2 / h_um) ** 2)
+    src[1, :, :, ix] = prof
+    return Workload(f"guide_{seed}", (nx, ny, nz), h_um, _k0(), eps_bg, eps, [ab], "sheet", src, eps_core=eps_core)
