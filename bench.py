@@ -279,12 +279,25 @@ def solve_section(plan, wl, absorbers, args):
         losses = learned.train(net, pairs, steps=args.train_steps, lr=1e-3, batch=4)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        v = torch.randn(b.numel(), dtype=torch.complex64, device="cuda")
+        z = torch.empty_like(v)
+        for _ in range(3):
+            vie.vie_net_apply(net, plan, v, z)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(20):
+            vie.vie_net_apply(net, plan, v, z)
+        ev1.record()
+        torch.cuda.synchronize()
+        net_ms = ev0.elapsed_time(ev1) / 20
         vie.vie_set_preconditioner(plan, net)
         _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)   # warm-up
         out["mixed_learned"] = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
         out["training"] = {"pairs": len(pairs), "problems": args.train_problems, "steps": args.train_steps,
                            "pair_generation_s": t1 - t0, "train_s": t2 - t1,
-                           "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:]))}
+                           "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
+                           "net_apply_ms": net_ms}
         vie.vie_set_preconditioner(plan, None)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     if "mixed_learned" in out:

@@ -166,7 +166,10 @@ typedef struct {
 
 typedef struct {
   int iterations;         /* Arnoldi steps (Krylov operator applications) */
-  int outer;              /* GMRES cycles (= refinement steps in mixed mode) */
+  int outer;              /* GMRES cycles (plain mode) or refinement steps
+                             (mixed mode; each step may run several
+                             complex64 cycles restarted from the complex64
+                             residual) */
   int matvecs64;          /* complex128 operator applications */
   int matvecs32;          /* complex64 operator applications */
   int converged;          /* 1 if ||b - A x|| <= tol ||b|| (true FP64 residual) */

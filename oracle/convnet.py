@@ -122,8 +122,11 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(p, x, keep=False):
-    """Net(x); with keep=True also returns the intermediate tensors."""
+def forward(p, x, keep=False, act_round=None):
+    """Net(x); with keep=True also returns the intermediate tensors.
+    ``act_round``, if given, is applied to the input of every convolution
+    (e.g. rounding to BF16, as a tensor-core convolution does)."""
+    rnd = act_round if act_round is not None else (lambda t: t)
     cache = {"x": x}
     a = x
     hs = []
@@ -131,19 +134,19 @@ def forward(p, x, keep=False):
         if lvl > 0:
             a = pool(hs[-1])
             cache[f"a{lvl}"] = a
-        z = conv3d(a, p[f"enc{lvl}.w"], p[f"enc{lvl}.b"])
+        z = conv3d(rnd(a), p[f"enc{lvl}.w"], p[f"enc{lvl}.b"])
         h = relu(z)
         cache[f"encz{lvl}"] = z
         hs.append(h)
     u = hs[3]
     for lvl in (2, 1, 0):
         s = up(u, hs[lvl].shape[2], hs[lvl].shape[3]) + hs[lvl]
-        z = conv3d(s, p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])
+        z = conv3d(rnd(s), p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])
         cache[f"decin{lvl}"] = s
         cache[f"decz{lvl}"] = z
         u = relu(z)
         cache[f"u{lvl}"] = u
-    y = conv3d(u, p["out.w"], p["out.b"])
+    y = conv3d(rnd(u), p["out.w"], p["out.b"])
     cache["hs"] = hs
     return (y, cache) if keep else y
 

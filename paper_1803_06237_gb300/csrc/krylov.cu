@@ -34,6 +34,7 @@ namespace vie {
 constexpr int kDotBlocks = 456;     // 3 x 152 SMs per problem
 constexpr int kThreads = 256;
 constexpr int kMaxRestart = 1000;
+constexpr int kMaxInnerCycles = 64;   // complex64 cycles per refinement step
 
 struct SolveStatus {
   int active;        // 1 while the cycle should continue
@@ -65,8 +66,11 @@ struct ProbK {
   double2* sn;
   double2* partial;        // (m + 2) x kDotBlocks partial sums
   SolveStatus* st;
+  void* rin;               // inner residual (inner type): start of the next inner cycle
+  void* d;                 // last cycle's correction Z y (inner type)
   double bnorm;            // ||b||
   double target;           // absolute target of the next cycle
+  int from_inner;          // 1: the next cycle starts from rin, 0: from r64
 };
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2((double)v.x, (double)v.y); }
@@ -92,6 +96,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Sum of `count` partials (the .x parts) by one block, fixed order; every
 // thread gets the result.
@@ -112,10 +120,11 @@ __device__ double block_sum_partials(const double2* __restrict__ part, int count
   return total;
 }
 
-__device__ __forceinline__ void block_store_sum(double s, double2* out) {
+template <typename R>
+__device__ __forceinline__ void block_store_sum(R s, double2* out) {
   __shared__ double red[kThreads / 32];
   s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -140,20 +149,22 @@ constexpr int kGroup = 8;   // basis vectors handled together (loads in flight p
 
 // Block-reduce kGroup complex sums and store them as partials of vectors
 // i0 .. i0 + kGroup - 1 (those < nv).
+// The warp-level part of the sum stays in the accumulator's precision (FP32
+// for complex64: FP64 adds are slow on this GPU); warps are then combined in
+// FP64.
 template <typename A>
-__device__ __forceinline__ void store_group(A (&acc_in)[kGroup], int i0, int nv, double2* __restrict__ partial,
+__device__ __forceinline__ void store_group(A (&acc)[kGroup], int i0, int nv, double2* __restrict__ partial,
                                             int nblk) {
   __shared__ double2 red[kThreads / 32][kGroup];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double2 acc[kGroup];
 #pragma unroll
   for (int u = 0; u < kGroup; ++u) {
-    acc[u].x = warp_sum((double)acc_in[u].x);
-    acc[u].y = warp_sum((double)acc_in[u].y);
+    acc[u].x = warp_sum(acc[u].x);
+    acc[u].y = warp_sum(acc[u].y);
   }
   if (lane == 0)
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) red[warp][u] = acc[u];
+    for (int u = 0; u < kGroup; ++u) red[warp][u] = make_double2((double)acc[u].x, (double)acc[u].y);
   __syncthreads();
   if (threadIdx.x < kGroup && i0 + threadIdx.x < nv) {
     double2 t = make_double2(0.0, 0.0);
@@ -166,40 +177,42 @@ __device__ __forceinline__ void store_group(A (&acc_in)[kGroup], int i0, int nv,
   __syncthreads();
 }
 
-// partial[i * nblk + b] = sum over block b's chunk of conj(V_i[k]) w[k], i < nv.
+// partial[i * nblk + b] = sum over block b's chunk of conj(V_i[k]) w[k].
+// grid (chunks, groups of kGroup vectors, problems): every block handles one
+// chunk of elements for one group of vectors.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict__ P, int nv) {
-  const ProbK& q = P[blockIdx.y];
+  const ProbK& q = P[blockIdx.z];
   if (!q.st->active) return;
+  const int i0 = blockIdx.y * kGroup;
   const V* __restrict__ Vb = (const V*)q.V;
   const V* __restrict__ w = (const V*)q.w;
   const size_t n = q.n;
   const Chunk ch = chunk_of(n);
   typedef typename Acc<V>::T A;
-  for (int i0 = 0; i0 < nv; i0 += kGroup) {
-    A acc[kGroup];
+  A acc[kGroup];
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
-    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
-      const V c = w[k];
-      V a[kGroup];
+  for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
+  for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+    const V c = w[k];
+    V a[kGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
+    for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
-        acc[u].x += a[u].x * c.x + a[u].y * c.y;
-        acc[u].y += a[u].x * c.y - a[u].y * c.x;
-      }
+    for (int u = 0; u < kGroup; ++u) {
+      acc[u].x += a[u].x * c.x + a[u].y * c.y;
+      acc[u].y += a[u].x * c.y - a[u].y * c.x;
     }
-    store_group(acc, i0, nv, q.partial, gridDim.x);
   }
+  store_group(acc, i0, nv, q.partial, gridDim.x);
 }
 
-// w[k] -= sum_{i<nv} V_i[k] h[i] over the block's chunk, then (fused) the
-// partial dot products of the updated w with every V_i (pass 0 of CGS2 ->
-// input of pass 1), or the partial |w|^2 (pass 1 -> the Arnoldi norm).
+constexpr int kUpdGroup = 16;   // basis loads in flight per thread in the update
+
+// w[k] -= sum_{i<nv} V_i[k] h[i], one element per thread, h = hcol (pass 0)
+// or h2 (pass 1); pass 1 also writes the block's partial |w|^2 (Arnoldi norm).
 template <typename V>
-__global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __restrict__ P, int nv, int pass) {
+__global__ void __launch_bounds__(kThreads) update_kernel(const ProbK* __restrict__ P, int nv, int pass) {
   const ProbK& q = P[blockIdx.y];
   if (!q.st->active) return;
   typedef typename Acc<V>::T A;
@@ -212,19 +225,18 @@ __global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __r
   const V* __restrict__ Vb = (const V*)q.V;
   V* __restrict__ w = (V*)q.w;
   const size_t n = q.n;
-  const Chunk ch = chunk_of(n);
   AR nrm = 0;
-  for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const V w0 = w[k];
     A acc;
     acc.x = w0.x;
     acc.y = w0.y;
-    for (int i0 = 0; i0 < nv; i0 += kGroup) {
-      V a[kGroup];
+    for (int i0 = 0; i0 < nv; i0 += kUpdGroup) {
+      V a[kUpdGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
+      for (int u = 0; u < kUpdGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
+      for (int u = 0; u < kUpdGroup; ++u) {
         if (i0 + u < nv) {
           acc.x -= a[u].x * hs[i0 + u].x - a[u].y * hs[i0 + u].y;
           acc.y -= a[u].x * hs[i0 + u].y + a[u].y * hs[i0 + u].x;
@@ -237,29 +249,7 @@ __global__ void __launch_bounds__(kThreads) update_fused_kernel(const ProbK* __r
     w[k] = out;
     nrm += out.x * out.x + out.y * out.y;
   }
-  if (pass == 1) {
-    block_store_sum((double)nrm, q.partial + blockIdx.x);
-    return;
-  }
-  __syncthreads();   // this block's w is complete: dots of pass 1 on the same chunk
-  typedef typename Acc<V>::T A;
-  for (int i0 = 0; i0 < nv; i0 += kGroup) {
-    A acc[kGroup];
-#pragma unroll
-    for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
-    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
-      const V c = w[k];
-      V a[kGroup];
-#pragma unroll
-      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
-#pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
-        acc[u].x += a[u].x * c.x + a[u].y * c.y;
-        acc[u].y += a[u].x * c.y - a[u].y * c.x;
-      }
-    }
-    store_group(acc, i0, nv, q.partial, gridDim.x);
-  }
+  if (pass == 1) block_store_sum(nrm, q.partial + blockIdx.x);
 }
 
 // pass 0: hcol[i] = sum_b partial; pass 1: h2[i] = sum_b partial, hcol[i] += h2[i].
@@ -343,10 +333,43 @@ __global__ void __launch_bounds__(kThreads) start_vector_kernel(const ProbK* __r
   if (!q.st->active) return;
   const double s = q.st->inv_h;
   V* __restrict__ v0 = (V*)q.V;
+  const V* __restrict__ rin = (const V*)q.rin;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = q.r64[k];
+    const double2 a = q.from_inner ? to_d2(rin[k]) : q.r64[k];
     v0[k] = from_d2<V>(make_double2(a.x * s, a.y * s));
   }
+}
+
+// rin = r64 (converted to the inner type), norm partials of rin
+template <typename V>
+__global__ void __launch_bounds__(kThreads) inner_from_outer_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  V* __restrict__ rin = (V*)q.rin;
+  double s = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    const V v = from_d2<V>(q.r64[k]);
+    rin[k] = v;
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  block_store_sum(s, q.partial + blockIdx.x);
+}
+
+// rin -= w (w = A d from the inner operator), norm partials of rin
+template <typename V>
+__global__ void __launch_bounds__(kThreads) inner_residual_kernel(const ProbK* __restrict__ P) {
+  const ProbK& q = P[blockIdx.y];
+  V* __restrict__ rin = (V*)q.rin;
+  const V* __restrict__ ad = (const V*)q.w;
+  typename Acc<V>::R s = 0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
+    V r = rin[k];
+    const V a = ad[k];
+    r.x -= a.x;
+    r.y -= a.y;
+    rin[k] = r;
+    s += r.x * r.x + r.y * r.y;
+  }
+  block_store_sum(s, q.partial + blockIdx.x);
 }
 
 // One block per problem: h_{j+1,j} = ||w|| (parallel reduction), then thread 0
@@ -488,6 +511,12 @@ __global__ void __launch_bounds__(kThreads) update_x_kernel(const ProbK* __restr
     }
     q.x64[k].x += (double)acc.x;
     q.x64[k].y += (double)acc.y;
+    if (q.d) {
+      V dv;
+      dv.x = acc.x;
+      dv.y = acc.y;
+      ((V*)q.d)[k] = dv;
+    }
   }
 }
 
@@ -513,12 +542,14 @@ struct KrylovWork {
   double* cs = nullptr;
   double2* sn = nullptr;
   double2* partial = nullptr;
+  void* rin = nullptr;      // inner residual (mixed mode)
+  void* d = nullptr;        // inner correction (mixed mode)
 };
 
 static void free_work(KrylovWork* k) {
   cudaFree(k->V); cudaFree(k->Z); cudaFree(k->w); cudaFree(k->x64); cudaFree(k->r64); cudaFree(k->y64);
   cudaFree(k->H); cudaFree(k->hcol); cudaFree(k->h2); cudaFree(k->g); cudaFree(k->ysol); cudaFree(k->cs);
-  cudaFree(k->sn); cudaFree(k->partial);
+  cudaFree(k->sn); cudaFree(k->partial); cudaFree(k->rin); cudaFree(k->d);
   *k = KrylovWork();
 }
 
@@ -532,7 +563,8 @@ static vie_status alloc_work(KrylovWork* k, size_t n, int m, int dtype, bool fle
       {(void**)&k->h2, (m + 1) * sizeof(double2)}, {(void**)&k->g, (m + 1) * sizeof(double2)},
       {(void**)&k->ysol, (m + 1) * sizeof(double2)}, {(void**)&k->cs, (m + 1) * sizeof(double)},
       {(void**)&k->sn, (m + 1) * sizeof(double2)},
-      {(void**)&k->partial, (size_t)(m + 2) * kDotBlocks * sizeof(double2)}};
+      {(void**)&k->partial, (size_t)(m + 2) * kDotBlocks * sizeof(double2)},
+      {&k->rin, n * es}, {&k->d, n * es}};
   for (auto& e : a) {
     cudaError_t err = cudaMalloc(e.p, e.sz);
     if (err != cudaSuccess) {
@@ -606,8 +638,14 @@ static vie_status upload_list(BatchCall& c, const std::vector<int>& list, cudaSt
 
 // Operator on z_j (inner type) or on x (complex128, outer) for every problem
 // of `list`, grouped by shape.
-static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dtype, bool outer, int j, bool flexible,
+enum { APPLY_Z = 0, APPLY_X = 1, APPLY_D = 2 };
+
+// Operator on z_j (inner type, -> w), on x (complex128, -> y64) or on the
+// last correction d (inner type, -> w) for every problem of `list`, grouped
+// by shape.
+static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dtype, int which, int j, bool flexible,
                              cudaStream_t s) {
+  const bool outer = which == APPLY_X;
   std::vector<int> used(list.size(), 0);
   const size_t es = dtype == VIE_C64 ? sizeof(float2) : sizeof(double2);
   for (size_t i = 0; i < list.size(); ++i) {
@@ -627,6 +665,9 @@ static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dty
         if (outer) {
           gx.push_back(q.x64);
           gy.push_back(q.y64);
+        } else if (which == APPLY_D) {
+          gx.push_back(q.d);
+          gy.push_back(q.w);
         } else {
           const char* zb = (const char*)(flexible ? q.Z : q.V);
           gx.push_back(zb + (size_t)j * q.n * es);
@@ -675,16 +716,19 @@ static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, i
         }
       }
     }
-    vie_status ms = apply_list(c, live, dtype, false, j, flexible, s);
+    vie_status ms = apply_list(c, live, dtype, APPLY_Z, j, flexible, s);
     if (ms != VIE_OK) return ms;
     const int nv = j + 1;
-    // CGS2 in three sweeps over the basis: dots; update + dots; update + norm
-    dots_kernel<V><<<dim3(kDotBlocks, P), kThreads, 0, s>>>(c.table, nv);
+    // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2 (+ norm); column h1 + h2
+    const dim3 gdots(kDotBlocks, (unsigned)((nv + kGroup - 1) / kGroup), P);
+    const size_t hs_bytes = nv * sizeof(typename Acc<V>::T);
+    dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
-    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(typename Acc<V>::T), s>>>(c.table, nv, 0);
+    update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 0);
+    dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv);
     reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
-    update_fused_kernel<V><<<dim3(kDotBlocks, P), kThreads, nv * sizeof(typename Acc<V>::T), s>>>(c.table, nv, 1);
-    arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, kDotBlocks, m + 1, j);
+    update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 1);
+    arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, (int)gx, m + 1, j);
     next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
     VIE_LAUNCH_CHECK();
     if ((j + 1) % check_every == 0 || j + 1 == jmax) {
@@ -735,6 +779,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
     q.V = k->V; q.Z = flexible ? k->Z : k->V; q.w = k->w; q.n = k->n; q.b = b[i];
     q.x64 = k->x64; q.r64 = k->r64; q.y64 = k->y64; q.H = k->H; q.hcol = k->hcol; q.h2 = k->h2; q.g = k->g;
     q.ysol = k->ysol; q.cs = k->cs; q.sn = k->sn; q.partial = k->partial; q.st = c.st + i;
+    q.rin = k->rin; q.d = mode == VIE_SOLVE_MIXED ? k->d : nullptr; q.from_inner = 0;
     memset(&infos[i], 0, sizeof(vie_solve_info));
   }
   cudaEvent_t e0, e1;
@@ -777,7 +822,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
     // true residual r = b - A64 x of the open problems
     st = upload_list(c, list, s);
     if (st != VIE_OK) break;
-    st = apply_list(c, list, dtype, true, 0, false, s);
+    st = apply_list(c, list, dtype, APPLY_X, 0, false, s);
     if (st != VIE_OK) break;
     residual_kernel<<<dim3(kDotBlocks, (unsigned)list.size()), kThreads, 0, s>>>(c.table);
     init_cycle_kernel<<<(unsigned)list.size(), kThreads, 0, s>>>(c.table, kDotBlocks, m);
@@ -793,16 +838,10 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
       infos[i].history_len = outers[i] + 1 < 64 ? outers[i] + 1 : 64;
       if (!isfinite(rn)) { result[i] = VIE_ERR_NONFINITE; continue; }
       if (rn <= tol * c.host[i].bnorm) { infos[i].converged = 1; continue; }
-      // the true residual judges the preconditioner: a preconditioned cycle
-      // that did not cut it by 10 %, or a non-finite network output, switches
-      // this problem to the identity for the rest of the solve
-      if (c.pc_on[i] && outers[i] > 0) {
-        const bool stalled = rel[i] > 0.9 * prev_rel[i];
-        const bool broken = precond_fallback_flag(c.plans[i], 1) != 0;
-        if (stalled || broken) {
-          c.pc_on[i] = 0;
-          infos[i].fallback = 1;
-        }
+      // the true residual judges the preconditioner across refinement steps
+      if (c.pc_on[i] && outers[i] > 0 && rel[i] > 0.9 * prev_rel[i]) {
+        c.pc_on[i] = 0;
+        infos[i].fallback = 1;
       }
       prev_rel[i] = rel[i];
       if (iters[i] >= max_iters || outers[i] >= max_outer) { result[i] = VIE_ERR_NOT_CONVERGED; continue; }
@@ -821,31 +860,64 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
     }
     list.swap(open);
     if (list.empty()) break;
-    // records now carry the cycle targets; re-initialise the status with them
-    st = upload_list(c, list, s);
+    // One refinement step.  Plain mode: one complex128 cycle from r.  Mixed
+    // mode: complex64 cycles towards the step's target, each restarted from
+    // the complex64 residual r <- r - A d (d = the cycle's correction), so the
+    // complex128 operator runs once per step instead of once per cycle.
+    std::vector<int> inner = list, next;
+    for (int i : list) c.host[i].from_inner = (mode == VIE_SOLVE_MIXED) ? 1 : 0;
+    st = upload_list(c, inner, s);
     if (st != VIE_OK) break;
-    init_cycle_kernel<<<(unsigned)list.size(), kThreads, 0, s>>>(c.table, kDotBlocks, m);
-    VIE_LAUNCH_CHECK();
-    int steps_left = max_iters;
-    for (int i : list) steps_left = (max_iters - iters[i]) < steps_left ? (max_iters - iters[i]) : steps_left;
-    if (dtype == VIE_C64)
-      st = run_cycle<float2>(c, list, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
-    else
-      st = run_cycle<double2>(c, list, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
-    if (st != VIE_OK) break;
-    std::vector<int> next;
-    for (int i : list) {
-      const int steps = c.st_host[i].j;
-      iters[i] += steps;
-      outers[i]++;
-      if (dtype == VIE_C64) infos[i].matvecs32 += steps; else infos[i].matvecs64 += steps;
-      if (steps == 0) {
-        result[i] = VIE_ERR_NOT_CONVERGED;
-        set_error("Krylov cycle made no progress (breakdown at the first step) for problem %d", i);
-        continue;
-      }
-      next.push_back(i);
+    if (mode == VIE_SOLVE_MIXED) {
+      inner_from_outer_kernel<float2><<<dim3(kDotBlocks, (unsigned)inner.size()), kThreads, 0, s>>>(c.table);
+      VIE_LAUNCH_CHECK();
     }
+    for (int round = 0; !inner.empty(); ++round) {
+      init_cycle_kernel<<<(unsigned)inner.size(), kThreads, 0, s>>>(c.table, kDotBlocks, m);
+      VIE_LAUNCH_CHECK();
+      int steps_left = max_iters;
+      for (int i : inner) steps_left = (max_iters - iters[i]) < steps_left ? (max_iters - iters[i]) : steps_left;
+      if (dtype == VIE_C64)
+        st = run_cycle<float2>(c, inner, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+      else
+        st = run_cycle<double2>(c, inner, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+      if (st != VIE_OK) break;
+      std::vector<int> again;
+      for (int i : inner) {
+        const int steps = c.st_host[i].j;
+        iters[i] += steps;
+        if (dtype == VIE_C64) infos[i].matvecs32 += steps; else infos[i].matvecs64 += steps;
+        if (steps == 0) {
+          result[i] = VIE_ERR_NOT_CONVERGED;
+          set_error("Krylov cycle made no progress (breakdown at the first step) for problem %d", i);
+          continue;
+        }
+        // a preconditioned cycle that cut the residual by less than 10 %, or a
+        // non-finite network output, switches this problem to the identity
+        if (c.pc_on[i] && !c.st_host[i].converged) {
+          const bool stalled = c.st_host[i].resid > 0.9 * c.st_host[i].beta;
+          const bool broken = precond_fallback_flag(c.plans[i], 1) != 0;
+          if (stalled || broken) {
+            c.pc_on[i] = 0;
+            infos[i].fallback = 1;
+          }
+        }
+        const bool more = mode == VIE_SOLVE_MIXED && !c.st_host[i].converged && !c.st_host[i].breakdown &&
+                          round + 1 < kMaxInnerCycles && iters[i] < max_iters;
+        if (more) again.push_back(i); else next.push_back(i);
+      }
+      if (again.empty()) break;
+      st = upload_list(c, again, s);
+      if (st != VIE_OK) break;
+      st = apply_list(c, again, dtype, APPLY_D, 0, false, s);
+      if (st != VIE_OK) break;
+      inner_residual_kernel<float2><<<dim3(kDotBlocks, (unsigned)again.size()), kThreads, 0, s>>>(c.table);
+      VIE_LAUNCH_CHECK();
+      for (int i : again) infos[i].matvecs32++;
+      inner.swap(again);
+    }
+    if (st != VIE_OK) break;
+    for (int i : next) outers[i]++;
     list.swap(next);
   }
   cudaEventRecord(e1, s);

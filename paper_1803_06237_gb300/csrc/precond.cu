@@ -30,6 +30,7 @@ struct vie_net {
   float* m2 = nullptr;
   __nv_bfloat16* wbf = nullptr;   // BF16 copy of the parameters (same offsets)
   __nv_bfloat16* wflip = nullptr; // per layer w'[c][o][26 - t] (backward data)
+  __nv_bfloat16* wpack = nullptr; // per layer tensor-core layout wp[tap][o][c] (inference)
   long step = 0;
   float* ws = nullptr;            // activation workspace
   size_t ws_cap = 0;
@@ -55,6 +56,15 @@ static size_t layer_w_off(int l) {
 }
 static size_t layer_b_off(int l) { return layer_w_off(l) + (size_t)kLayerDefs[l].co * kLayerDefs[l].ci * 27; }
 static size_t total_params() { return layer_w_off(kNumLayers); }
+
+static int mma_cip(int ci) { return ci <= 16 ? 16 : 32; }
+static int mma_no(int co) { return co <= 8 ? 8 : 32; }
+static size_t pack_size(int l) { return (size_t)27 * mma_no(kLayerDefs[l].co) * mma_cip(kLayerDefs[l].ci); }
+static size_t pack_off(int l) {
+  size_t off = 0;
+  for (int i = 0; i < l; ++i) off += pack_size(i);
+  return off;
+}
 
 struct Dims {
   int nz, ny, nx;
@@ -604,6 +614,38 @@ static vie_status layout(vie_net* net, const int n[3], NetTensors* T) {
   return VIE_OK;
 }
 
+// Tensor-core convolution of layer `layer` with the packed weights.
+static vie_status conv_mma(vie_net* net, int layer, const float* in, const float* bias, float* pre, float* out,
+                           Dims d, int relu, cudaStream_t s) {
+  const int ci = kLayerDefs[layer].ci, co = kLayerDefs[layer].co;
+  const __nv_bfloat16* wp = net->wpack + pack_off(layer);
+  const dim3 grid((unsigned)((d.nx + kMmaX - 1) / kMmaX), (unsigned)d.ny, (unsigned)d.nz);
+  const int cip = mma_cip(ci), no = mma_no(co);
+  if (cip == 16 && no == 32)
+    conv_mma_kernel<16, 4><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
+  else if (cip == 32 && no == 32)
+    conv_mma_kernel<32, 4><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
+  else if (cip == 32 && no == 8)
+    conv_mma_kernel<32, 1><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
+  else {
+    set_error("no tensor-core convolution for %d -> %d channels", ci, co);
+    return VIE_ERR_INVALID;
+  }
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
+static vie_status pack_weights(vie_net* net, cudaStream_t s) {
+  for (int l = 0; l < kNumLayers; ++l) {
+    const size_t n = pack_size(l);
+    pack_mma_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        net->wbf + layer_w_off(l), kLayerDefs[l].ci, kLayerDefs[l].co, mma_cip(kLayerDefs[l].ci),
+        mma_no(kLayerDefs[l].co), net->wpack + pack_off(l));
+  }
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
 static vie_status conv(vie_net* net, int layer, const float* in, const __nv_bfloat16* w, const float* bias, int ci,
                        int co, float* pre, float* out, Dims d, int relu, cudaStream_t s) {
   (void)net;
@@ -628,27 +670,33 @@ static const __nv_bfloat16* W(vie_net* n, int l) { return n->wbf + layer_w_off(l
 static const float* B(vie_net* n, int l) { return n->master + layer_b_off(l); }
 
 // forward pass; keeps every intermediate in T
-static vie_status net_forward(vie_net* net, NetTensors& T, cudaStream_t s) {
+// Forward pass; keeps every intermediate in T.  use_mma selects the
+// tensor-core convolutions (inference) instead of the FP32 ones (training).
+static vie_status net_forward(vie_net* net, NetTensors& T, bool use_mma, cudaStream_t s) {
   vie_status st;
+  auto cv = [&](int layer, const float* in, float* pre, float* out, Dims d, int relu) {
+    if (use_mma) return conv_mma(net, layer, in, B(net, layer), pre, out, d, relu, s);
+    return conv(net, layer, in, W(net, layer), B(net, layer), kLayerDefs[layer].ci, kLayerDefs[layer].co, pre, out,
+                d, relu, s);
+  };
   for (int l = 0; l < 4; ++l) {
     const float* a = T.X;
     if (l > 0) {
       pool_kernel<<<ew_blocks(32 * T.L[l].vox()), 256, 0, s>>>(T.h[l - 1], T.L[l - 1], T.a[l], T.L[l], 32);
       a = T.a[l];
     }
-    st = conv(net, ENC0 + l, a, W(net, ENC0 + l), B(net, ENC0 + l), kLayerDefs[ENC0 + l].ci, 32, T.encz[l], T.h[l],
-              T.L[l], 1, s);
+    st = cv(ENC0 + l, a, T.encz[l], T.h[l], T.L[l], 1);
     if (st != VIE_OK) return st;
   }
   const float* u = T.h[3];
   for (int l = 2; l >= 0; --l) {
     const int layer = DEC0 - l;   // dec2 = 4, dec1 = 5, dec0 = 6
     up_add_kernel<<<ew_blocks(32 * T.L[l].vox()), 256, 0, s>>>(u, T.L[l + 1], T.h[l], T.decin[l], T.L[l], 32);
-    st = conv(net, layer, T.decin[l], W(net, layer), B(net, layer), 32, 32, T.decz[l], T.u[l], T.L[l], 1, s);
+    st = cv(layer, T.decin[l], T.decz[l], T.u[l], T.L[l], 1);
     if (st != VIE_OK) return st;
     u = T.u[l];
   }
-  return conv(net, OUTL, T.u[0], W(net, OUTL), B(net, OUTL), 32, 6, nullptr, T.Y, T.L[0], 0, s);
+  return cv(OUTL, T.u[0], nullptr, T.Y, T.L[0], 0);
 }
 
 // gradient of a layer's weights and bias, accumulated into net->grad
@@ -734,7 +782,7 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
   sumsq_kernel<V><<<ew_blocks(3 * V0), 256, 0, s>>>(v, 3 * V0, (double*)net->scal);
   pack_kernel<V><<<ew_blocks(V0), 256, 0, s>>>(v, p->chi64, V0, (double*)net->scal, T.X);
   VIE_LAUNCH_CHECK();
-  st = net_forward(net, T, s);
+  st = net_forward(net, T, true, s);
   if (st != VIE_OK) return st;
   unpack_kernel<V><<<ew_blocks(V0), 256, 0, s>>>(T.Y, V0, (double*)net->scal, v, z, net->bad);
   VIE_LAUNCH_CHECK();
@@ -821,6 +869,7 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
   struct { void** p; size_t sz; } a[] = {
       {(void**)&n->master, np * 4}, {(void**)&n->grad, np * 4}, {(void**)&n->m1, np * 4}, {(void**)&n->m2, np * 4},
       {(void**)&n->wbf, np * 2},    {(void**)&n->wflip, np * 2}, {(void**)&n->scal, 8 * sizeof(double)},
+      {(void**)&n->wpack, pack_off(kNumLayers) * 2},
       {(void**)&n->bad, sizeof(int)}};
   for (auto& e : a) {
     cudaError_t err = cudaMalloc(e.p, e.sz);
@@ -836,6 +885,7 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
   cudaMemset(n->m2, 0, np * 4);
   cudaMemset(n->bad, 0, sizeof(int));
   to_bf16_kernel<<<ew_blocks(np), 256>>>(n->master, n->wbf, np);
+  pack_weights(n, 0);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     set_error("network init: %s", cudaGetErrorString(e));
@@ -849,6 +899,7 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
 vie_status vie_net_destroy(vie_net* n) {
   if (!n) return VIE_OK;
   cudaFree(n->master); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2); cudaFree(n->wbf); cudaFree(n->wflip);
+  cudaFree(n->wpack);
   cudaFree(n->ws); cudaFree(n->partial); cudaFree(n->scal); cudaFree(n->bad);
   delete n;
   return VIE_OK;
@@ -893,7 +944,7 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   pack_kernel<float2><<<ew_blocks(V0), 256, 0, s>>>((const float2*)r_dev, p->chi64, V0, scal, T.X);
   pack_target_kernel<<<ew_blocks(V0), 256, 0, s>>>((const float2*)e_dev, V0, scal, T.E);
   VIE_LAUNCH_CHECK();
-  st = net_forward(n, T, s);
+  st = net_forward(n, T, false, s);
   if (st != VIE_OK) return st;
   loss_sums_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, 6 * V0, scal + 1);
   loss_grad_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, 6 * V0, scal + 1, T.dY);
@@ -925,6 +976,8 @@ vie_status vie_net_adam_step(vie_net* n, float lr, float grad_scale, void* strea
                                                     c1, c2, grad_scale);
   to_bf16_kernel<<<ew_blocks(n->nparams), 256, 0, s>>>(n->master, n->wbf, n->nparams);
   VIE_LAUNCH_CHECK();
+  vie_status st = pack_weights(n, s);
+  if (st != VIE_OK) return st;
   VIE_CUDA_TRY(cudaMemsetAsync(n->grad, 0, n->nparams * 4, s));
   return VIE_OK;
 }

@@ -62,8 +62,12 @@ def test_param_layout():
     assert vie.vie_net_param_count() == n
 
 
-@pytest.mark.parametrize("grid", [(21, 9, 5), (16, 8, 3)])
+@pytest.mark.parametrize("grid", [(21, 9, 5), (16, 8, 3), (70, 7, 4)])
 def test_forward_matches_oracle(grid):
+    """Inference (tensor-core convolutions, BF16 weights and BF16-rounded
+    convolution inputs, FP32 accumulation) against the FP64 oracle with the
+    same roundings; the tolerance covers inputs that land on the other side
+    of a BF16 rounding boundary in FP32 and FP64."""
     plan, chi, net = _setup(grid, 5)
     p = _oracle_params(vie.vie_net_get_params(net))
     nx, ny, nz = grid
@@ -74,9 +78,9 @@ def test_forward_matches_oracle(grid):
     torch.cuda.synchronize()
     s = _scale(v)
     X = cn.pack_input(v.astype(np.complex128) * s, chi)
-    z_ref = cn.unpack_output(cn.forward(p, X)) / s
+    z_ref = cn.unpack_output(cn.forward(p, X, act_round=_bf16)) / s
     z = zd.cpu().numpy().reshape(3, nz, ny, nx)
-    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 1e-4
+    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 3e-3
 
 
 def test_gradients_match_oracle():
