@@ -506,13 +506,10 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
 #define VIE_PASS_X4_SIZES(X) \
   X(40, 30) X(24, 25) X(24, 30) X(30, 30) X(45, 25) X(45, 30) X(50, 30) X(40, 40) X(20, 20)
 
-constexpr int kX4Lines = 4;
-
-template <typename V, int L1, int L2>
-static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
-                            const V* twx, int mode, cudaStream_t s, bool* done) {
-  if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
-    constexpr int LPB = kX4Lines;
+template <typename V, int L1, int L2, int LPB>
+static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
+                                const V* twx, int mode, cudaStream_t s, bool* done) {
+  {
     constexpr int R = pitch_mod16(L1 * LPB, LPB);
     constexpr int NT = LPB * (L1 > L2 ? L1 : L2);
     const int P = pitch_mod16(nx, LPB);
@@ -531,6 +528,19 @@ static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int 
     VIE_LAUNCH_CHECK();
     *done = true;
     return VIE_OK;
+  }
+}
+
+// Four lines per block, or two when four would leave fewer than two blocks
+// per SM (more blocks hide the latency of the small per-line work).
+template <typename V, int L1, int L2>
+static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
+                            const V* twx, int mode, cudaStream_t s, bool* done) {
+  if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
+    const long blocks4 = (long)((NL + 3) / 4) * count;
+    if (blocks4 < 2L * 152)
+      return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
+    return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
   } else {
     *done = false;
     return VIE_OK;

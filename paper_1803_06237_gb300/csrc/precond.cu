@@ -10,9 +10,12 @@
 // in FP32 for the optimiser and used as BF16 by the convolutions, which
 // accumulate in FP32; activations are FP32.
 //
-// The preconditioner is positively homogeneous: v is scaled to unit RMS
-// before the network and the output is scaled back, so P(a v) = a P(v) for
-// a > 0.  A non-finite output is replaced by v (identity) and reported.
+// The preconditioner is z = v + Net(v): the network learns the correction
+// to the identity, and its output layer starts at zero, so an untrained
+// network is exactly the identity.  It is positively homogeneous: v is scaled
+// to unit RMS before the network and the output is scaled back, so
+// P(a v) = a P(v) for a > 0.  A non-finite output is replaced by v and
+// reported.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -451,7 +454,7 @@ __global__ void pack_kernel(const V* __restrict__ v, const double2* __restrict__
   }
 }
 
-// z_c = (Y_c + i Y_{3+c}) / s; non-finite -> z = v and flag
+// z_c = v_c + (Y_c + i Y_{3+c}) / s; non-finite -> z = v and flag
 template <typename V>
 __global__ void unpack_kernel(const float* __restrict__ Y, size_t vox, const double* __restrict__ sumsq,
                               const V* __restrict__ v, V* __restrict__ z, int* __restrict__ bad) {
@@ -462,8 +465,9 @@ __global__ void unpack_kernel(const float* __restrict__ Y, size_t vox, const dou
       const double re = Y[(size_t)c * vox + i] * inv, im = Y[(size_t)(3 + c) * vox + i] * inv;
       V out;
       if (isfinite(re) && isfinite(im)) {
-        out.x = re;
-        out.y = im;
+        const V vi = v[(size_t)c * vox + i];
+        out.x = vi.x + re;
+        out.y = vi.y + im;
       } else {
         out = v[(size_t)c * vox + i];
         atomicExch(bad, 1);
@@ -473,28 +477,36 @@ __global__ void unpack_kernel(const float* __restrict__ Y, size_t vox, const dou
   }
 }
 
-// target channels from e (c64) scaled like the input: E[c] = re/im e_c * s
-__global__ void pack_target_kernel(const float2* __restrict__ e, size_t vox, const double* __restrict__ sumsq_r,
-                                   float* __restrict__ E) {
+// target of the network (the correction to the identity), scaled like the
+// input: E[c] = re/im (e_c - r_c) * s
+__global__ void pack_target_kernel(const float2* __restrict__ e, const float2* __restrict__ r, size_t vox,
+                                   const double* __restrict__ sumsq_r, float* __restrict__ E) {
   const double ss = *sumsq_r;
   const float s = ss > 0.0 ? (float)sqrt(3.0 * (double)vox / ss) : 0.f;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x)
     for (int c = 0; c < 3; ++c) {
-      E[(size_t)c * vox + i] = e[(size_t)c * vox + i].x * s;
-      E[(size_t)(3 + c) * vox + i] = e[(size_t)c * vox + i].y * s;
+      const float2 ev = e[(size_t)c * vox + i], rv = r[(size_t)c * vox + i];
+      E[(size_t)c * vox + i] = (ev.x - rv.x) * s;
+      E[(size_t)(3 + c) * vox + i] = (ev.y - rv.y) * s;
     }
 }
 
-// loss = sum (Y - E)^2 / sum E^2 (two sums accumulated in scal[0], scal[1])
-__global__ void loss_sums_kernel(const float* __restrict__ Y, const float* __restrict__ E, size_t n,
+// loss = sum (Y - E)^2 / sum |e s|^2 with E = (e - r) s: the error of
+// z = r + Net(r) relative to e (sums accumulated in sums[0], sums[1])
+__global__ void loss_sums_kernel(const float* __restrict__ Y, const float* __restrict__ E,
+                                 const float2* __restrict__ e, size_t vox, const double* __restrict__ sumsq_r,
                                  double* __restrict__ sums) {
   __shared__ double r0[256], r1[256];
+  const size_t n = 6 * vox;
+  const double ss = *sumsq_r;
+  const double s2 = ss > 0.0 ? 3.0 * (double)vox / ss : 0.0;
   double a = 0.0, b = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double d = (double)Y[i] - E[i];
     a += d * d;
-    b += (double)E[i] * E[i];
   }
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * vox; i += (size_t)gridDim.x * blockDim.x)
+    b += ((double)e[i].x * e[i].x + (double)e[i].y * e[i].y) * s2;
   r0[threadIdx.x] = a;
   r1[threadIdx.x] = b;
   __syncthreads();
@@ -865,6 +877,8 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
       }
       for (int o = 0; o < kLayerDefs[l].co; ++o) h[layer_b_off(l) + o] = 0.f;
     }
+    // output layer at zero: the untrained preconditioner is the identity
+    for (size_t i = 0; i < (size_t)kLayerDefs[OUTL].co * kLayerDefs[OUTL].ci * 27; ++i) h[layer_w_off(OUTL) + i] = 0.f;
   }
   struct { void** p; size_t sz; } a[] = {
       {(void**)&n->master, np * 4}, {(void**)&n->grad, np * 4}, {(void**)&n->m1, np * 4}, {(void**)&n->m2, np * 4},
@@ -942,11 +956,11 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   VIE_CUDA_TRY(cudaMemsetAsync(scal, 0, 4 * sizeof(double), s));
   sumsq_kernel<float2><<<ew_blocks(3 * V0), 256, 0, s>>>((const float2*)r_dev, 3 * V0, scal);
   pack_kernel<float2><<<ew_blocks(V0), 256, 0, s>>>((const float2*)r_dev, p->chi64, V0, scal, T.X);
-  pack_target_kernel<<<ew_blocks(V0), 256, 0, s>>>((const float2*)e_dev, V0, scal, T.E);
+  pack_target_kernel<<<ew_blocks(V0), 256, 0, s>>>((const float2*)e_dev, (const float2*)r_dev, V0, scal, T.E);
   VIE_LAUNCH_CHECK();
   st = net_forward(n, T, false, s);
   if (st != VIE_OK) return st;
-  loss_sums_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, 6 * V0, scal + 1);
+  loss_sums_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, (const float2*)e_dev, V0, scal, scal + 1);
   loss_grad_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, 6 * V0, scal + 1, T.dY);
   VIE_LAUNCH_CHECK();
   st = net_backward(n, T, s);

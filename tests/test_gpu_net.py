@@ -44,11 +44,17 @@ def _oracle_grads(g):
     return np.concatenate([np.concatenate([g[n + ".w"].ravel(), g[n + ".b"].ravel()]) for n, _, _ in cn.LAYERS])
 
 
+def _flat_params(p):
+    return np.concatenate([np.concatenate([p[n + ".w"].reshape(-1), p[n + ".b"]]) for n, _, _ in cn.LAYERS]).astype(np.float32)
+
+
 def _setup(grid, seed):
+    """Plan with a random contrast and a network with random parameters in
+    every layer (the default initialisation zeroes the output layer)."""
     plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
     chi = op.chi_from_permittivity(workloads.random_permittivity(grid, seed=seed), 2.085)
     vie.vie_set_contrast(plan, chi)
-    net = vie.vie_net_create(seed=seed)
+    net = vie.vie_net_create(_flat_params(cn.init_params(seed)))
     return plan, chi, net
 
 
@@ -57,9 +63,17 @@ def _scale(v):
     return math.sqrt(v.size / np.sum(np.abs(v) ** 2))
 
 
-def test_param_layout():
+def test_param_layout_and_identity_at_start():
     n = sum(co * ci * 27 + co for _, ci, co in cn.LAYERS)
     assert vie.vie_net_param_count() == n
+    grid = (16, 8, 3)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    net = vie.vie_net_create(seed=4)          # output layer starts at zero
+    v = torch.from_numpy(workloads.random_currents(grid, seed=2).astype(np.complex64).ravel()).cuda()
+    z = torch.empty_like(v)
+    vie.vie_net_apply(net, plan, v, z)
+    torch.cuda.synchronize()
+    assert torch.equal(z, v)
 
 
 @pytest.mark.parametrize("grid", [(21, 9, 5), (16, 8, 3), (70, 7, 4)])
@@ -78,7 +92,7 @@ def test_forward_matches_oracle(grid):
     torch.cuda.synchronize()
     s = _scale(v)
     X = cn.pack_input(v.astype(np.complex128) * s, chi)
-    z_ref = cn.unpack_output(cn.forward(p, X, act_round=_bf16)) / s
+    z_ref = v.astype(np.complex128) + cn.unpack_output(cn.forward(p, X, act_round=_bf16)) / s
     z = zd.cpu().numpy().reshape(3, nz, ny, nx)
     assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 3e-3
 
@@ -95,9 +109,12 @@ def test_gradients_match_oracle():
     g_gpu = vie.vie_net_get_grads(net)
     s = _scale(r)
     X = cn.pack_input(r.astype(np.complex128) * s, chi)
-    E = np.concatenate([(e.astype(np.complex128) * s).real, (e.astype(np.complex128) * s).imag], axis=0)
+    d = (e.astype(np.complex128) - r.astype(np.complex128)) * s      # correction to the identity
+    E = np.concatenate([d.real, d.imag], axis=0)
     y, cache = cn.forward(p, X, keep=True)
-    l_ref, dy = cn.relative_mse(y, E)
+    den = np.sum(np.abs(e.astype(np.complex128) * s) ** 2)               # error relative to |e|
+    l_ref = float(np.sum((y - E) ** 2) / den)
+    dy = 2.0 * (y - E) / den
     g, _ = cn.backward(p, cache, dy)
     assert abs(loss - l_ref) <= 1e-5 * l_ref
     off = 0
