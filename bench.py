@@ -320,6 +320,7 @@ def solve_section(plan, wl, absorbers, args):
         _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)   # warm-up
         out["mixed_learned"] = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
         out["training"] = {"pairs": len(pairs), "problems": args.train_problems, "steps": args.train_steps,
+                           "identity_loss": learned.identity_loss(pairs),
                            "pair_generation_s": t1 - t0, "train_s": t2 - t1,
                            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
                            "net_apply_ms": net_ms}

@@ -17,11 +17,31 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <utility>
+
 #include "fft.cuh"
 #include "regfft.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
+
+// Launch with programmatic stream serialisation (see pdl_wait in
+// vie_internal.cuh).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <typename V> __device__ __forceinline__ V zero_c();
 template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }
@@ -45,6 +65,7 @@ struct PassPtrs {
 template <typename V>
 __global__ void __launch_bounds__(256) pass_a_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int NL,
                                                      Radices rx, const V* __restrict__ twg, int lines_per_block) {
+  pdl_wait();
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
   extern __shared__ unsigned char smem_raw[];
@@ -80,6 +101,7 @@ template <typename V>
 __global__ void __launch_bounds__(256) pass_b_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                      Radices ry, Radices rz, const V* __restrict__ twyg,
                                                      const V* __restrict__ twzg) {
+  pdl_wait();
   V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ ghat = pp.ghat[blockIdx.y];
   extern __shared__ unsigned char smem_raw[];
@@ -181,6 +203,8 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__
   const int ny = g.ny, nz = g.nz;
   const bool fx = kx > g.Mx - kx;
   const int kxf = fx ? g.Mx - kx : kx;
+  pdl_launch_dependents();
+  // plan constants first (allowed before the dependency wait)
   for (int i = tid; i < MY; i += nth) __pipeline_memcpy_async(twy + i, twyg + i, sizeof(V));
   for (int i = tid; i < MZ; i += nth) __pipeline_memcpy_async(twz + i, twzg + i, sizeof(V));
   __pipeline_commit();
@@ -191,6 +215,7 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__
     for (int i = tid; i < chunk; i += nth) __pipeline_memcpy_async(Gs + i, G + i, sizeof(V));
     __pipeline_commit();
   }
+  pdl_wait();                 // the x pass that wrote the slab has completed
   __pipeline_wait_prior(1);   // twiddles done; the spectrum may still be in flight
   __syncthreads();
   V* slab = work + (size_t)kx * g.NL;
@@ -287,8 +312,8 @@ static vie_status launch_pass_b_reg(const PassPtrs<V>& pp, int count, const Pass
   int lines = 3 * (g.ny > MZ ? g.ny : MZ);
   int threads = ((lines + 31) / 32) * 32;
   if (threads > 256) threads = 256;
-  pass_b_reg_kernel<V, MY, MZ><<<dim3((unsigned)g.Mx, (unsigned)count), threads, smem, s>>>(pp, g, twy, twz);
-  VIE_LAUNCH_CHECK();
+  VIE_CUDA_TRY(launch_pdl(pass_b_reg_kernel<V, MY, MZ>, dim3((unsigned)g.Mx, (unsigned)count), dim3(threads), smem,
+                          s, pp, g, twy, twz));
   return VIE_OK;
 }
 
@@ -323,6 +348,7 @@ template <typename V>
 __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int nyz,
                                                      int NL, Radices rx, const V* __restrict__ twg,
                                                      int lines_per_block, int mode) {
+  pdl_wait();
   const V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ x = pp.x[blockIdx.y];
   const V* __restrict__ Mc = pp.M[blockIdx.y];
@@ -384,9 +410,12 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
   const int tid = threadIdx.x, nth = blockDim.x;
   const int l0 = blockIdx.x * LPB;
   const int nl = min(LPB, NL - l0);
+  pdl_launch_dependents();
   {
-    // asynchronous copies of the twiddles and of the block's lines (contiguous in x)
+    // asynchronous copies of the twiddles (plan constants) and, once the
+    // producer of x is done, of the block's lines (contiguous in x)
     for (int i = tid; i < MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
+    pdl_wait();
     const V* src = x + (size_t)l0 * nx;
     for (int l = 0; l < nl; ++l)
       for (int n = tid; n < nx; n += nth) __pipeline_memcpy_async(Xs + l * P + n, src + (size_t)l * nx + n, sizeof(V));
@@ -444,16 +473,19 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
   const int tid = threadIdx.x, nth = blockDim.x;
   const int l0 = blockIdx.x * LPB;
   const int nl = min(LPB, NL - l0);
+  pdl_launch_dependents();
   {
-    // asynchronous copies: twiddles now, epilogue operands to land during the FFTs
+    // asynchronous copies: twiddles now, epilogue operands to land during the
+    // FFTs; the contrast rows are plan data, x only after the dependency wait
     for (int i = tid; i < MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
     __pipeline_commit();
-    const V* xsrc = x + (size_t)l0 * nx;
-    for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
     for (int l = 0; l < nl; ++l) {
       const V* msrc = Mc + (size_t)((l0 + l) % nyz) * nx;
       for (int i = tid; i < nx; i += nth) __pipeline_memcpy_async(Ms + l * nx + i, msrc + i, sizeof(V));
     }
+    pdl_wait();
+    const V* xsrc = x + (size_t)l0 * nx;
+    for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
     __pipeline_commit();
     __pipeline_wait_prior(1);      // twiddles only
   }
@@ -519,11 +551,11 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
     if (forward) {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      pass_a4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(pp, nx, NL, twx);
+      VIE_CUDA_TRY(launch_pdl(pass_a4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, NL, twx));
     } else {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      pass_c4_kernel<V, L1, L2, LPB><<<blocks, NT, smem, s>>>(pp, nx, nyz, NL, twx, mode);
+      VIE_CUDA_TRY(launch_pdl(pass_c4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, nyz, NL, twx, mode));
     }
     VIE_LAUNCH_CHECK();
     *done = true;

@@ -59,6 +59,17 @@ template <typename V> __host__ __device__ __forceinline__ V mul_mi(V a) { V r; r
 template <typename V> __host__ __device__ __forceinline__ V mul_pi(V a) { V r; r.x = -a.y; r.y = a.x; return r; }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start before the previous kernel in the
+// stream has finished.  It may read immutable plan data before pdl_wait(),
+// but must call pdl_wait() before it reads anything an earlier kernel writes
+// or writes anything at all.  pdl_launch_dependents() lets the next kernel
+// start launching.  Both are no-ops for ordinary launches.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// ---------------------------------------------------------------------------
 // FFT plans for one axis
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 16;

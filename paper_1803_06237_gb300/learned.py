@@ -8,9 +8,11 @@ library in order.
 Pairs: for a problem A x = b with solution x*, plain GMRES cycles (restart
 ``restart``, complex64 inner solves inside FP64 refinement) from x = 0 give
 iterates x_k; each yields (r_k, e_k) with e_k = x* - x_k and r_k = A e_k
-(complex64 operator), so A e_k = r_k holds by construction.  The network is
-trained to map r_k to e_k (relative mean squared error, both scaled by the
-RMS of r_k).
+(complex64 operator), so A e_k = r_k holds by construction.  The
+preconditioner is z = r + Net(r); the network is trained so that z matches
+e_k (squared error relative to |e_k|^2, both scaled by the RMS of r_k).  The
+identity (Net = 0) has loss |e_k - r_k|^2 / |e_k|^2, reported by
+``identity_loss`` as the level training has to beat.
 """
 from __future__ import annotations
 
@@ -75,6 +77,13 @@ def make_pairs(seeds, grid=(160, 40, 11), restart=20, cycles=12, tol=1e-6):
             vie.vie_matvec(plan, e, r)
             pairs.append(Pair(plan, r, e))
     return pairs
+
+
+def identity_loss(pairs) -> float:
+    """Mean of |e - r|^2 / |e|^2 over the pairs: the loss of z = r."""
+    import torch
+    vals = [(torch.linalg.vector_norm(p.e - p.r) ** 2 / torch.linalg.vector_norm(p.e) ** 2).item() for p in pairs]
+    return float(np.mean(vals))
 
 
 def train(net, pairs, steps, lr=1e-3, batch=4, seed=0, log_every=0):
