@@ -227,7 +227,11 @@ vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const*
 /* of v scaled to unit RMS, re/im of chi), 4 levels (2x2 average pooling in  */
 /* x and y), 32 channels, 3x3x3 convolutions with zero padding, ReLU,        */
 /* nearest upsampling with additive skips, 6 output channels; BF16 weights,  */
-/* FP32 accumulation and activations, FP32 master weights and Adam.         */
+/* FP32 master weights and Adam.  Training keeps FP32 activations; the      */
+/* inference path runs every convolution as an implicit GEMM on the tcgen05 */
+/* tensor cores with channels-last BF16 activations, FP32 accumulation.     */
+/* The preconditioner is z = v + Net(v): an untrained network (output layer */
+/* at zero) is the identity.                                                */
 /* Parameter layout (FP32): per layer enc0..enc3, dec2, dec1, dec0, out:     */
 /* w[co][ci][27] (tap = 9 dz + 3 dy + dx) then b[co].                        */
 /* ------------------------------------------------------------------------ */
@@ -247,14 +251,15 @@ vie_status vie_net_destroy(vie_net* net);
 vie_status vie_net_get_params(const vie_net* net, float* out_host);
 vie_status vie_net_get_grads(const vie_net* net, float* out_host);
 
-/* z = |v|_rms Net(v / |v|_rms, chi of the plan) on the plan's grid; v_dev and
- * z_dev are device vectors (3*nx*ny*nz of dtype).  A non-finite output entry
- * is replaced by v.  Asynchronous on `stream`. */
+/* z = v + |v|_rms Net(v / |v|_rms, chi of the plan) on the plan's grid; v_dev
+ * and z_dev are device vectors (3*nx*ny*nz of dtype, not overlapping).  A
+ * non-finite output entry is replaced by v and recorded (vie_net_status).
+ * Asynchronous on `stream`. */
 vie_status vie_net_apply(vie_net* net, const vie_plan* plan, const void* v_dev,
                          void* z_dev, int dtype, void* stream);
 
 /* One training sample (r, e) with A e = r (complex64 device vectors): forward
- * pass on r, loss |Net(r) - e|^2 / |e|^2 (both scaled by the RMS of r),
+ * pass on r, loss |r + Net(r) - e|^2 / |e|^2 (all scaled by the RMS of r),
  * backward pass; gradients are ADDED to the network's accumulators.  *loss
  * receives the sample's loss.  Synchronises `stream`. */
 vie_status vie_net_accumulate(vie_net* net, const vie_plan* plan, const void* r_dev,
@@ -264,6 +269,12 @@ vie_status vie_net_zero_grad(vie_net* net);
 /* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the accumulated gradients
  * times grad_scale, refresh of the BF16 weights, gradients cleared. */
 vie_status vie_net_adam_step(vie_net* net, float lr, float grad_scale, void* stream);
+
+/* Status of the applications since the last clear (synchronises the device):
+ * *flag = 0 all fine, 1 a non-finite output was replaced by v, 2 a wait inside
+ * a tensor-core convolution timed out (its output is not valid).  clear != 0
+ * resets it. */
+vie_status vie_net_status(vie_net* net, int* flag, int clear);
 
 /* Use `net` (NULL: none) as the right preconditioner of this plan's solves
  * with opts->use_preconditioner = 1 (flexible GMRES).  The plan keeps a

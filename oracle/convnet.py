@@ -122,11 +122,14 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(p, x, keep=False, act_round=None):
+def forward(p, x, keep=False, act_round=None, store_round=None):
     """Net(x); with keep=True also returns the intermediate tensors.
     ``act_round``, if given, is applied to the input of every convolution
-    (e.g. rounding to BF16, as a tensor-core convolution does)."""
+    (e.g. rounding to BF16, as a tensor-core convolution does);
+    ``store_round`` to every hidden activation after its ReLU (h_l and u_l),
+    for an implementation that stores them in a narrower type."""
     rnd = act_round if act_round is not None else (lambda t: t)
+    sto = store_round if store_round is not None else (lambda t: t)
     cache = {"x": x}
     a = x
     hs = []
@@ -135,7 +138,7 @@ def forward(p, x, keep=False, act_round=None):
             a = pool(hs[-1])
             cache[f"a{lvl}"] = a
         z = conv3d(rnd(a), p[f"enc{lvl}.w"], p[f"enc{lvl}.b"])
-        h = relu(z)
+        h = sto(relu(z))
         cache[f"encz{lvl}"] = z
         hs.append(h)
     u = hs[3]
@@ -144,7 +147,7 @@ def forward(p, x, keep=False, act_round=None):
         z = conv3d(rnd(s), p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])
         cache[f"decin{lvl}"] = s
         cache[f"decz{lvl}"] = z
-        u = relu(z)
+        u = sto(relu(z))
         cache[f"u{lvl}"] = u
     y = conv3d(rnd(u), p["out.w"], p["out.b"])
     cache["hs"] = hs

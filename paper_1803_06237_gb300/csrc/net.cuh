@@ -1,0 +1,64 @@
+// Shared declarations of the learned preconditioner's kernels: the FP32
+// training path in precond.cu and the tensor-core inference path in
+// conv_tc.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+struct Dims {
+  int nz, ny, nx;
+  __host__ __device__ size_t vox() const { return (size_t)nz * ny * nx; }
+};
+
+// Padded channel counts of the tensor-core convolution: the input channels
+// (the K extent of one tap) are 16 or 32, the output channels (N) 16 or 32.
+inline int tc_cpad(int ci) { return ci <= 16 ? 16 : 32; }
+inline int tc_npad(int co) { return co <= 16 ? 16 : 32; }
+
+// Epilogues of the tensor-core convolution.
+enum TcMode {
+  TC_RELU_BF16 = 0,   // out[vox][32] = bf16(relu(acc + bias))
+  TC_UNPACK_C64 = 1,  // z_c = v_c + (y_c + i y_{3+c}) / s, complex64 planar
+  TC_UNPACK_C128 = 2  // the same in complex128
+};
+
+struct TcConvArgs {
+  Dims d;                       // grid of this level
+  int bx, by;                   // output tile: bx consecutive x times by rows in y (bx * by = 128)
+  const float* bias;            // co biases (FP32)
+  int co;                       // real output channels
+  __nv_bfloat16* out;           // TC_RELU_BF16: channels-last output, 32 channels
+  const void* v;                // TC_UNPACK_*: the preconditioned vector (3 planar components)
+  void* z;                      //              and the result
+  const double* sumsq;          //              sum |v|^2 (the input scale)
+  int* bad;                     // non-finite output (1) or a wait that timed out (2)
+};
+
+// Tile shape for a level: minimises the padded voxels times the halo rows
+// that one tile loads ((by + 2) / by).
+void tc_pick_tile(Dims d, int* bx, int* by);
+
+// Tensor maps: channels-last BF16 activation [nz][ny][nx][C] with the box
+// {C, bx, by + 2, 1}; packed weights [27][N][C] with the box {C, N, 1}.
+vie_status tc_encode_act(CUtensorMap* map, const __nv_bfloat16* base, int C, Dims d, int bx, int by);
+vie_status tc_encode_w(CUtensorMap* map, const __nv_bfloat16* w, int C, int N);
+
+// One 3x3x3 convolution (zero padding) as an implicit GEMM on the tensor
+// cores: M = the 128 voxels of a tile, N = output channels, K = 27 taps x C.
+vie_status tc_conv(const CUtensorMap& A, const CUtensorMap& W, int C, int N, int mode, const TcConvArgs& args,
+                   cudaStream_t s);
+
+// Channels-last BF16 helpers of the inference path.
+template <typename V>
+vie_status tc_pack_input(const V* v, const double2* chi, Dims d, const double* sumsq, __nv_bfloat16* X,
+                         cudaStream_t s);
+vie_status tc_pool(const __nv_bfloat16* in, Dims f, __nv_bfloat16* out, Dims c, cudaStream_t s);
+vie_status tc_up_add(const __nv_bfloat16* coarse, Dims c, const __nv_bfloat16* skip, __nv_bfloat16* out, Dims f,
+                     cudaStream_t s);
+
+}  // namespace vie

@@ -8,7 +8,9 @@
 // with zero padding and bias, ReLU, nearest upsampling with additive skips,
 // 6 output channels (re/im of the three components of z).  Weights are kept
 // in FP32 for the optimiser and used as BF16 by the convolutions, which
-// accumulate in FP32; activations are FP32.
+// accumulate in FP32.  Training (this file) keeps FP32 planar activations;
+// inference (conv_tc.cu) runs the convolutions on the tcgen05 tensor cores
+// with channels-last BF16 activations.
 //
 // The preconditioner is z = v + Net(v): the network learns the correction
 // to the identity, and its output layer starts at zero, so an untrained
@@ -22,7 +24,10 @@
 
 #include <vector>
 
+#include "net.cuh"
 #include "vie_internal.cuh"
+
+namespace vie { struct TcCache; }
 
 struct vie_net {
   int device = 0;
@@ -34,6 +39,7 @@ struct vie_net {
   __nv_bfloat16* wbf = nullptr;   // BF16 copy of the parameters (same offsets)
   __nv_bfloat16* wflip = nullptr; // per layer w'[c][o][26 - t] (backward data)
   __nv_bfloat16* wpack = nullptr; // per layer tensor-core layout wp[tap][o][c] (inference)
+  vie::TcCache* tc = nullptr;     // inference workspace and tensor maps
   long step = 0;
   float* ws = nullptr;            // activation workspace
   size_t ws_cap = 0;
@@ -60,19 +66,12 @@ static size_t layer_w_off(int l) {
 static size_t layer_b_off(int l) { return layer_w_off(l) + (size_t)kLayerDefs[l].co * kLayerDefs[l].ci * 27; }
 static size_t total_params() { return layer_w_off(kNumLayers); }
 
-static int mma_cip(int ci) { return ci <= 16 ? 16 : 32; }
-static int mma_no(int co) { return co <= 8 ? 8 : 32; }
-static size_t pack_size(int l) { return (size_t)27 * mma_no(kLayerDefs[l].co) * mma_cip(kLayerDefs[l].ci); }
+static size_t pack_size(int l) { return (size_t)27 * tc_npad(kLayerDefs[l].co) * tc_cpad(kLayerDefs[l].ci); }
 static size_t pack_off(int l) {
   size_t off = 0;
   for (int i = 0; i < l; ++i) off += pack_size(i);
   return off;
 }
-
-struct Dims {
-  int nz, ny, nx;
-  __host__ __device__ size_t vox() const { return (size_t)nz * ny * nx; }
-};
 
 // ---------------------------------------------------------------------------
 // convolution (forward; also the backward-data pass with flipped weights)
@@ -150,107 +149,8 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const float* __r
   }
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core convolution: implicit GEMM with mma.sync m16n8k16 (BF16 inputs,
-// FP32 accumulation).  M = 16 consecutive x voxels per warp, N = output
-// channels in tiles of 8, K = (tap, input channel) with the channels of one
-// tap contiguous.  A block (4 warps) covers 64 x voxels of one (z, y) row:
-// its input rows (9 taps in z and y, 66 x values, all channels) are staged in
-// shared memory as BF16 with the channel index fastest and a pitch of
-// CIP + 8 channels (no bank conflicts for the fragment loads).  Weights are
-// pre-packed as wp[tap][o][CIP] BF16 (zero padding) and read from L1/L2.
-// The input of every tensor-core convolution is therefore rounded to BF16.
-// ---------------------------------------------------------------------------
-constexpr int kMmaWarps = 4;
-constexpr int kMmaX = 16 * kMmaWarps;   // voxels per block
-
-__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
-  const unsigned short ua = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-  const unsigned short ub = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-  return (unsigned)ua | ((unsigned)ub << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int CIP, int NT>
-__global__ void __launch_bounds__(32 * kMmaWarps) conv_mma_kernel(const float* __restrict__ in, int ci,
-                                                                  const __nv_bfloat16* __restrict__ wp,
-                                                                  const float* __restrict__ bias, int co,
-                                                                  float* __restrict__ pre, float* __restrict__ out,
-                                                                  Dims d, int relu) {
-  constexpr int PITCH = CIP + 8;             // channels per staged voxel (bf16)
-  constexpr int XS = kMmaX + 2;
-  __shared__ __align__(16) __nv_bfloat16 tile[9 * XS * PITCH];
-  const int z = blockIdx.z, y = blockIdx.y;
-  const int x0 = blockIdx.x * kMmaX;
-  const size_t plane = (size_t)d.ny * d.nx;
-  const size_t chan = (size_t)d.nz * plane;
-  // stage: tile[zy][xs][c] = in[c][z + dz - 1][y + dy - 1][x0 + xs - 1] (zero outside / c >= ci)
-  for (int i = threadIdx.x; i < 9 * XS * CIP; i += blockDim.x) {
-    const int xs = i % XS;
-    const int c = (i / XS) % CIP;
-    const int zy = i / (XS * CIP);
-    const int zz = z + zy / 3 - 1, yy = y + zy % 3 - 1, xx = x0 + xs - 1;
-    float v = 0.f;
-    if (c < ci && zz >= 0 && zz < d.nz && yy >= 0 && yy < d.ny && xx >= 0 && xx < d.nx)
-      v = in[(size_t)c * chan + (size_t)zz * plane + (size_t)yy * d.nx + xx];
-    tile[(zy * XS + xs) * PITCH + c] = __float2bfloat16_rn(v);
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  const int m0 = warp * 16;                    // this warp's first voxel within the block
-  float acc[NT][4];
-#pragma unroll
-  for (int n = 0; n < NT; ++n)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) acc[n][r] = 0.f;
-  const unsigned* w32 = reinterpret_cast<const unsigned*>(wp);
-#pragma unroll 1
-  for (int tap = 0; tap < 27; ++tap) {
-    const int zy = tap / 3, dx = tap % 3;
-    const __nv_bfloat16* row0 = tile + (zy * XS + m0 + g + dx) * PITCH;        // voxel m0 + g
-    const __nv_bfloat16* row8 = row0 + 8 * PITCH;                              // voxel m0 + g + 8
-#pragma unroll
-    for (int kc = 0; kc < CIP; kc += 16) {
-      unsigned a[4];
-      a[0] = *reinterpret_cast<const unsigned*>(row0 + kc + 2 * t4);
-      a[1] = *reinterpret_cast<const unsigned*>(row8 + kc + 2 * t4);
-      a[2] = *reinterpret_cast<const unsigned*>(row0 + kc + 8 + 2 * t4);
-      a[3] = *reinterpret_cast<const unsigned*>(row8 + kc + 8 + 2 * t4);
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        // B[k][o] = wp[tap][o][kc + k], o = 8 n + g; k pairs (2 t4, 2 t4 + 1) and (+8)
-        const size_t wb = ((size_t)tap * (NT * 8) + 8 * n + g) * CIP + kc + 2 * t4;
-        const unsigned b0 = __ldg(w32 + wb / 2);
-        const unsigned b1 = __ldg(w32 + (wb + 8) / 2);
-        mma_bf16(acc[n], a, b0, b1);
-      }
-    }
-  }
-  // D fragment: acc[n][0..1] -> voxel m0 + g, channels 8n + 2 t4 (+1); acc[n][2..3] -> voxel + 8
-  const size_t base = (size_t)z * plane + (size_t)y * d.nx;
-#pragma unroll
-  for (int n = 0; n < NT; ++n)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int o = 8 * n + 2 * t4 + (r & 1);
-      const int x = x0 + m0 + g + (r >= 2 ? 8 : 0);
-      if (o < co && x < d.nx) {
-        const float val = acc[n][r] + (bias ? bias[o] : 0.f);
-        if (pre) pre[(size_t)o * chan + base + x] = val;
-        out[(size_t)o * chan + base + x] = relu ? fmaxf(val, 0.f) : val;
-      }
-    }
-}
-
-// wp[tap][o][c] (o < NT*8, c < cip) from w[o][c][tap] (BF16), zero padding
+// wp[tap][o][c] (o < no, c < cip) from w[o][c][tap] (BF16), zero padding: the
+// tensor-core layout, K-major rows of cip channels for each output channel
 __global__ void pack_mma_weights_kernel(const __nv_bfloat16* __restrict__ w, int ci, int co, int cip, int no,
                                         __nv_bfloat16* __restrict__ wp) {
   const size_t n = (size_t)27 * no * cip;
@@ -454,29 +354,6 @@ __global__ void pack_kernel(const V* __restrict__ v, const double2* __restrict__
   }
 }
 
-// z_c = v_c + (Y_c + i Y_{3+c}) / s; non-finite -> z = v and flag
-template <typename V>
-__global__ void unpack_kernel(const float* __restrict__ Y, size_t vox, const double* __restrict__ sumsq,
-                              const V* __restrict__ v, V* __restrict__ z, int* __restrict__ bad) {
-  const double ss = *sumsq;
-  const double inv = ss > 0.0 ? sqrt(ss / (3.0 * (double)vox)) : 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x) {
-    for (int c = 0; c < 3; ++c) {
-      const double re = Y[(size_t)c * vox + i] * inv, im = Y[(size_t)(3 + c) * vox + i] * inv;
-      V out;
-      if (isfinite(re) && isfinite(im)) {
-        const V vi = v[(size_t)c * vox + i];
-        out.x = vi.x + re;
-        out.y = vi.y + im;
-      } else {
-        out = v[(size_t)c * vox + i];
-        atomicExch(bad, 1);
-      }
-      z[(size_t)c * vox + i] = out;
-    }
-  }
-}
-
 // target of the network (the correction to the identity), scaled like the
 // input: E[c] = re/im (e_c - r_c) * s
 __global__ void pack_target_kernel(const float2* __restrict__ e, const float2* __restrict__ r, size_t vox,
@@ -626,33 +503,12 @@ static vie_status layout(vie_net* net, const int n[3], NetTensors* T) {
   return VIE_OK;
 }
 
-// Tensor-core convolution of layer `layer` with the packed weights.
-static vie_status conv_mma(vie_net* net, int layer, const float* in, const float* bias, float* pre, float* out,
-                           Dims d, int relu, cudaStream_t s) {
-  const int ci = kLayerDefs[layer].ci, co = kLayerDefs[layer].co;
-  const __nv_bfloat16* wp = net->wpack + pack_off(layer);
-  const dim3 grid((unsigned)((d.nx + kMmaX - 1) / kMmaX), (unsigned)d.ny, (unsigned)d.nz);
-  const int cip = mma_cip(ci), no = mma_no(co);
-  if (cip == 16 && no == 32)
-    conv_mma_kernel<16, 4><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
-  else if (cip == 32 && no == 32)
-    conv_mma_kernel<32, 4><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
-  else if (cip == 32 && no == 8)
-    conv_mma_kernel<32, 1><<<grid, 32 * kMmaWarps, 0, s>>>(in, ci, wp, bias, co, pre, out, d, relu);
-  else {
-    set_error("no tensor-core convolution for %d -> %d channels", ci, co);
-    return VIE_ERR_INVALID;
-  }
-  VIE_LAUNCH_CHECK();
-  return VIE_OK;
-}
-
 static vie_status pack_weights(vie_net* net, cudaStream_t s) {
   for (int l = 0; l < kNumLayers; ++l) {
     const size_t n = pack_size(l);
     pack_mma_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        net->wbf + layer_w_off(l), kLayerDefs[l].ci, kLayerDefs[l].co, mma_cip(kLayerDefs[l].ci),
-        mma_no(kLayerDefs[l].co), net->wpack + pack_off(l));
+        net->wbf + layer_w_off(l), kLayerDefs[l].ci, kLayerDefs[l].co, tc_cpad(kLayerDefs[l].ci),
+        tc_npad(kLayerDefs[l].co), net->wpack + pack_off(l));
   }
   VIE_LAUNCH_CHECK();
   return VIE_OK;
@@ -681,13 +537,10 @@ static vie_status conv(vie_net* net, int layer, const float* in, const __nv_bflo
 static const __nv_bfloat16* W(vie_net* n, int l) { return n->wbf + layer_w_off(l); }
 static const float* B(vie_net* n, int l) { return n->master + layer_b_off(l); }
 
-// forward pass; keeps every intermediate in T
-// Forward pass; keeps every intermediate in T.  use_mma selects the
-// tensor-core convolutions (inference) instead of the FP32 ones (training).
-static vie_status net_forward(vie_net* net, NetTensors& T, bool use_mma, cudaStream_t s) {
+// Training forward pass (FP32 activations); keeps every intermediate in T.
+static vie_status net_forward(vie_net* net, NetTensors& T, cudaStream_t s) {
   vie_status st;
   auto cv = [&](int layer, const float* in, float* pre, float* out, Dims d, int relu) {
-    if (use_mma) return conv_mma(net, layer, in, B(net, layer), pre, out, d, relu, s);
     return conv(net, layer, in, W(net, layer), B(net, layer), kLayerDefs[layer].ci, kLayerDefs[layer].co, pre, out,
                 d, relu, s);
   };
@@ -784,21 +637,124 @@ static vie_status net_backward(vie_net* net, NetTensors& T, cudaStream_t s) {
   return VIE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// inference on the tensor cores (channels-last BF16 activations)
+// ---------------------------------------------------------------------------
+struct TcCache {
+  int n[3] = {0, 0, 0};
+  __nv_bfloat16* ws = nullptr;
+  size_t cap = 0;
+  Dims L[4];
+  int bx[4], by[4];
+  __nv_bfloat16 *X = nullptr, *h[4] = {}, *a[4] = {}, *decin[3] = {}, *u[3] = {};
+  CUtensorMap mA[kNumLayers];   // input activation of each layer
+  CUtensorMap mW[kNumLayers];   // packed weights of each layer
+  bool wmaps = false;
+};
+
+static size_t tc_ws_elems(const Dims* L) {
+  size_t t = 16 * L[0].vox();
+  for (int l = 0; l < 4; ++l) t += 32 * L[l].vox() * (l >= 1 ? 2 : 1);
+  for (int l = 0; l < 3; ++l) t += 2 * 32 * L[l].vox();
+  return t;
+}
+
+// (Re)build the workspace and the tensor maps for the grid n.
+static vie_status tc_prepare(vie_net* net, const int n[3], TcCache** out) {
+  if (!net->tc) net->tc = new TcCache();
+  TcCache* c = net->tc;
+  if (!c->wmaps) {
+    for (int l = 0; l < kNumLayers; ++l) {
+      vie_status st = tc_encode_w(&c->mW[l], net->wpack + pack_off(l), tc_cpad(kLayerDefs[l].ci),
+                                  tc_npad(kLayerDefs[l].co));
+      if (st != VIE_OK) return st;
+    }
+    c->wmaps = true;
+  }
+  if (c->ws && c->n[0] == n[0] && c->n[1] == n[1] && c->n[2] == n[2]) {
+    *out = c;
+    return VIE_OK;
+  }
+  c->L[0] = Dims{n[2], n[1], n[0]};
+  for (int l = 1; l < 4; ++l) c->L[l] = Dims{c->L[l - 1].nz, (c->L[l - 1].ny + 1) / 2, (c->L[l - 1].nx + 1) / 2};
+  const size_t need = tc_ws_elems(c->L);
+  if (need > c->cap) {
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->cap = 0;
+    VIE_CUDA_TRY(cudaMalloc((void**)&c->ws, need * sizeof(__nv_bfloat16)));
+    c->cap = need;
+  }
+  __nv_bfloat16* p = c->ws;
+  auto take = [&](size_t k) { __nv_bfloat16* r = p; p += k; return r; };
+  c->X = take(16 * c->L[0].vox());
+  for (int l = 0; l < 4; ++l) {
+    c->h[l] = take(32 * c->L[l].vox());
+    c->a[l] = l >= 1 ? take(32 * c->L[l].vox()) : nullptr;
+    tc_pick_tile(c->L[l], &c->bx[l], &c->by[l]);
+  }
+  for (int l = 0; l < 3; ++l) {
+    c->decin[l] = take(32 * c->L[l].vox());
+    c->u[l] = take(32 * c->L[l].vox());
+  }
+  // layer inputs: enc0 X, enc1..3 pooled a_l, dec_l decin_l, out u_0
+  struct { int layer, level; const __nv_bfloat16* in; int C; } m[kNumLayers] = {
+      {ENC0, 0, c->X, 16},       {ENC1, 1, c->a[1], 32},    {ENC2, 2, c->a[2], 32},    {ENC3, 3, c->a[3], 32},
+      {DEC2, 2, c->decin[2], 32}, {DEC1, 1, c->decin[1], 32}, {DEC0, 0, c->decin[0], 32}, {OUTL, 0, c->u[0], 32}};
+  for (auto& e : m) {
+    vie_status st = tc_encode_act(&c->mA[e.layer], e.in, e.C, c->L[e.level], c->bx[e.level], c->by[e.level]);
+    if (st != VIE_OK) return st;
+  }
+  c->n[0] = n[0];
+  c->n[1] = n[1];
+  c->n[2] = n[2];
+  *out = c;
+  return VIE_OK;
+}
+
+static void tc_free(TcCache* c) {
+  if (!c) return;
+  cudaFree(c->ws);
+  delete c;
+}
+
 template <typename V>
 static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z, cudaStream_t s) {
-  NetTensors T;
-  vie_status st = layout(net, p->n, &T);
+  TcCache* c = nullptr;
+  vie_status st = tc_prepare(net, p->n, &c);
   if (st != VIE_OK) return st;
-  const size_t V0 = T.L[0].vox();
+  const size_t V0 = c->L[0].vox();
+  double* sumsq = (double*)net->scal;
   VIE_CUDA_TRY(cudaMemsetAsync(net->scal, 0, 4 * sizeof(double), s));
-  sumsq_kernel<V><<<ew_blocks(3 * V0), 256, 0, s>>>(v, 3 * V0, (double*)net->scal);
-  pack_kernel<V><<<ew_blocks(V0), 256, 0, s>>>(v, p->chi64, V0, (double*)net->scal, T.X);
+  sumsq_kernel<V><<<ew_blocks(3 * V0), 256, 0, s>>>(v, 3 * V0, sumsq);
   VIE_LAUNCH_CHECK();
-  st = net_forward(net, T, true, s);
+  st = tc_pack_input<V>(v, p->chi64, c->L[0], sumsq, c->X, s);
   if (st != VIE_OK) return st;
-  unpack_kernel<V><<<ew_blocks(V0), 256, 0, s>>>(T.Y, V0, (double*)net->scal, v, z, net->bad);
-  VIE_LAUNCH_CHECK();
-  return VIE_OK;
+  auto conv = [&](int layer, int level, int mode, __nv_bfloat16* out) {
+    TcConvArgs a{};
+    a.d = c->L[level];
+    a.bx = c->bx[level];
+    a.by = c->by[level];
+    a.bias = B(net, layer);
+    a.co = kLayerDefs[layer].co;
+    a.out = out;
+    a.v = v;
+    a.z = z;
+    a.sumsq = sumsq;
+    a.bad = net->bad;
+    return tc_conv(c->mA[layer], c->mW[layer], tc_cpad(kLayerDefs[layer].ci), tc_npad(kLayerDefs[layer].co), mode,
+                   a, s);
+  };
+  for (int l = 0; l < 4; ++l) {
+    if (l > 0 && (st = tc_pool(c->h[l - 1], c->L[l - 1], c->a[l], c->L[l], s)) != VIE_OK) return st;
+    if ((st = conv(ENC0 + l, l, TC_RELU_BF16, c->h[l])) != VIE_OK) return st;
+  }
+  for (int l = 2; l >= 0; --l) {
+    const __nv_bfloat16* coarse = l == 2 ? c->h[3] : c->u[l + 1];
+    if ((st = tc_up_add(coarse, c->L[l + 1], c->h[l], c->decin[l], c->L[l], s)) != VIE_OK) return st;
+    if ((st = conv(DEC0 - l, l, TC_RELU_BF16, c->u[l])) != VIE_OK) return st;
+  }
+  return conv(OUTL, 0, sizeof(V) == 8 ? TC_UNPACK_C64 : TC_UNPACK_C128, nullptr);
 }
 
 struct PrecondCtx {
@@ -915,6 +871,7 @@ vie_status vie_net_destroy(vie_net* n) {
   cudaFree(n->master); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2); cudaFree(n->wbf); cudaFree(n->wflip);
   cudaFree(n->wpack);
   cudaFree(n->ws); cudaFree(n->partial); cudaFree(n->scal); cudaFree(n->bad);
+  tc_free(n->tc);
   delete n;
   return VIE_OK;
 }
@@ -958,7 +915,7 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   pack_kernel<float2><<<ew_blocks(V0), 256, 0, s>>>((const float2*)r_dev, p->chi64, V0, scal, T.X);
   pack_target_kernel<<<ew_blocks(V0), 256, 0, s>>>((const float2*)e_dev, (const float2*)r_dev, V0, scal, T.E);
   VIE_LAUNCH_CHECK();
-  st = net_forward(n, T, false, s);
+  st = net_forward(n, T, s);
   if (st != VIE_OK) return st;
   loss_sums_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, (const float2*)e_dev, V0, scal, scal + 1);
   loss_grad_kernel<<<ew_blocks(6 * V0), 256, 0, s>>>(T.Y, T.E, 6 * V0, scal + 1, T.dY);
@@ -993,6 +950,14 @@ vie_status vie_net_adam_step(vie_net* n, float lr, float grad_scale, void* strea
   vie_status st = pack_weights(n, s);
   if (st != VIE_OK) return st;
   VIE_CUDA_TRY(cudaMemsetAsync(n->grad, 0, n->nparams * 4, s));
+  return VIE_OK;
+}
+
+vie_status vie_net_status(vie_net* n, int* flag, int clear) {
+  clear_error();
+  if (!n || !flag) { set_error("null argument"); return VIE_ERR_INVALID; }
+  VIE_CUDA_TRY(cudaMemcpy(flag, n->bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (clear) VIE_CUDA_TRY(cudaMemset(n->bad, 0, sizeof(int)));
   return VIE_OK;
 }
 

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "vie_net_accumulate": ([_P, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
     "vie_net_zero_grad": ([_P], _I),
     "vie_net_adam_step": ([_P, ctypes.c_float, ctypes.c_float, _P], _I),
+    "vie_net_status": ([_P, ctypes.POINTER(_I), _I], _I),
     "vie_set_preconditioner": ([_P, _P], _I),
     "vie_plan_clone": ([_P, ctypes.POINTER(_P)], _I),
     "vie_matvec_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P], _I),
@@ -386,6 +387,14 @@ def vie_net_apply(net: Net, plan: Plan, v, z, stream=None):
     _check(load().vie_net_apply(net.handle, plan.handle, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                 _dtype_code(v), _stream_handle(stream)), "vie_net_apply")
     return z
+
+
+def vie_net_status(net: Net, clear: bool = False) -> int:
+    """0 fine, 1 a non-finite output was replaced by v, 2 a tensor-core wait
+    timed out (synchronises the device)."""
+    flag = ctypes.c_int()
+    _check(load().vie_net_status(net.handle, ctypes.byref(flag), int(bool(clear))), "vie_net_status")
+    return flag.value
 
 
 def vie_net_accumulate(net: Net, plan: Plan, r, e, stream=None) -> float:

@@ -76,25 +76,36 @@ def test_param_layout_and_identity_at_start():
     assert torch.equal(z, v)
 
 
-@pytest.mark.parametrize("grid", [(21, 9, 5), (16, 8, 3), (70, 7, 4)])
-def test_forward_matches_oracle(grid):
-    """Inference (tensor-core convolutions, BF16 weights and BF16-rounded
-    convolution inputs, FP32 accumulation) against the FP64 oracle with the
-    same roundings; the tolerance covers inputs that land on the other side
-    of a BF16 rounding boundary in FP32 and FP64."""
+@pytest.mark.parametrize("grid,dtype", [((21, 9, 5), np.complex64), ((16, 8, 3), np.complex64),
+                                        ((70, 7, 4), np.complex64), ((33, 17, 2), np.complex128),
+                                        ((160, 40, 11), np.complex64), ((600, 23, 11), np.complex64)])
+def test_forward_matches_oracle(grid, dtype):
+    """Inference (tcgen05 convolutions, BF16 weights, channels-last BF16
+    activations, FP32 accumulation) against the FP64 oracle with the same
+    roundings (convolution inputs and stored activations rounded to BF16);
+    the tolerance covers values that land on the other side of a BF16
+    rounding boundary in FP32 and FP64.  The two largest grids give every
+    persistent CTA several tiles (the 600 x 23 x 11 guide is the benchmark
+    workload's grid)."""
     plan, chi, net = _setup(grid, 5)
     p = _oracle_params(vie.vie_net_get_params(net))
     nx, ny, nz = grid
-    v = workloads.random_currents(grid, seed=6).astype(np.complex64)
+    v = workloads.random_currents(grid, seed=6).astype(dtype)
     vd = torch.from_numpy(v.ravel()).cuda()
     zd = torch.empty_like(vd)
     vie.vie_net_apply(net, plan, vd, zd)
     torch.cuda.synchronize()
-    s = _scale(v)
-    X = cn.pack_input(v.astype(np.complex128) * s, chi)
-    z_ref = v.astype(np.complex128) + cn.unpack_output(cn.forward(p, X, act_round=_bf16)) / s
+    assert vie.vie_net_status(net, clear=True) == 0
+    vr = v.astype(np.complex128)
+    s = _scale(v) if dtype == np.complex64 else math.sqrt(vr.size / np.sum(np.abs(vr) ** 2))
+    X = cn.pack_input(vr * s, chi)
+    z_ref = vr + cn.unpack_output(cn.forward(p, X, act_round=_bf16, store_round=_bf16)) / s
     z = zd.cpu().numpy().reshape(3, nz, ny, nx)
     assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 3e-3
+    # the correction alone, against the oracle's correction
+    dz = (z - vr).ravel()
+    dz_ref = (z_ref - vr).ravel()
+    assert np.linalg.norm(dz - dz_ref) / np.linalg.norm(dz_ref) < 2e-2
 
 
 def test_gradients_match_oracle():
