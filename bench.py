@@ -64,6 +64,64 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s (burst), measured if available."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops" in d:
+            return d["bf16_tflops"], "measured"
+    return 1900.0, "fallback"
+
+
+NET_LAYERS = [(8, 32, 0), (32, 32, 1), (32, 32, 2), (32, 32, 3), (32, 32, 2), (32, 32, 1), (32, 32, 0), (32, 6, 0)]
+
+
+def net_flops(grid) -> float:
+    """Algorithmic tensor flops of one network application: 2 x 27 x ci x co
+    per voxel of each convolution's level (levels halve nx and ny, ceil)."""
+    nx, ny, nz = grid
+    vox = []
+    for _ in range(4):
+        vox.append(nx * ny * nz)
+        nx, ny = (nx + 1) // 2, (ny + 1) // 2
+    return sum(2.0 * 27 * ci * co * vox[lvl] for ci, co, lvl in NET_LAYERS)
+
+
+def net_section(plan, grid, reps=50):
+    """Inference cost of the learned preconditioner on the benchmark grid
+    (random parameters in every layer; the cost does not depend on them)."""
+    import torch
+
+    from paper_1803_06237_gb300 import vie
+    n = vie.vie_net_param_count()
+    rng = np.random.default_rng(3)
+    net = vie.vie_net_create(rng.standard_normal(n).astype(np.float32) * 0.05)
+    v = torch.randn(3 * plan.n_vox, dtype=torch.complex64, device="cuda")
+    z = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        vie.vie_net_apply(net, plan, v, z, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        vie.vie_net_apply(net, plan, v, z, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    net.close()
+    flops = net_flops(grid)
+    peak, kind = _bf16_peak()
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"ms_per_apply": ms, "algorithmic_flops": flops,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_source": kind + " dense bf16 (burst)"},
+            "launches_per_apply": 17,
+            "note": "8 tcgen05 convolutions + 3 pools + 3 upsample-adds + input packing + |v|^2; "
+                    "the convolutions' implicit-GEMM flops only"}
+
+
 class ClockSampler:
     """Samples nvidia-smi during the timed region (every 200 ms)."""
 
@@ -253,6 +311,8 @@ def gpu_arm(args):
         "clocks": clk,
         "setup_ms": info["setup_ms"],
     }
+    if not args.no_net:
+        result["net_inference"] = net_section(plan, wl.grid)
     if not args.no_solve:
         result["time_to_1e-6"] = solve_section(plan, wl, absorbers, args)
     if not args.no_batch:
@@ -451,6 +511,17 @@ def profile_solve(iters: int):
     print(json.dumps({"profile_solve": iters, "iterations": info["iterations"], "time_ms": info["time_ms"]}))
 
 
+def profile_net(reps: int):
+    """`reps` applications of a network with random parameters on the
+    benchmark guide: a short, fixed launch sequence for kernel launch lists."""
+    from paper_1803_06237_gb300 import build, learned, vie, workloads
+    build.build_library()
+    vie.load()
+    plan, _ = learned.setup_problem(workloads.waveguide())
+    out = net_section(plan, (600, 23, 11), reps=reps)
+    print(json.dumps({"profile_net": reps, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,11 +537,17 @@ def main():
     ap.add_argument("--restart-mixed", type=int, default=30)
     ap.add_argument("--train-problems", type=int, default=30)
     ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--profile-net", type=int, default=0,
+                    help="only run network applications (for kernel launch lists)")
+    ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run a capped mixed solve (for kernel launch lists)")
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve(args.profile_solve)
+        return
+    if args.profile_net:
+        profile_net(args.profile_net)
         return
     if args.warmup < 3:
         args.warmup = 3

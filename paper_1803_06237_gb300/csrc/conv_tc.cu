@@ -20,6 +20,11 @@
 //            step z = v + Net(v) / s of the preconditioner.
 // Stages are handed over with mbarriers (TMA transaction counts,
 // tcgen05.commit); every wait is bounded and a timeout is reported in *bad.
+//
+// Every kernel of the inference chain is launched with programmatic stream
+// serialisation: it lets its dependents launch at entry, sets up barriers
+// and tensor memory and prefetches the (immutable) weights, and only then
+// waits (griddepcontrol.wait) for the kernel that produced its input.
 #include <stdio.h>
 
 #include <type_traits>
@@ -29,7 +34,7 @@
 
 namespace vie {
 
-constexpr int kTcStages = 4;
+constexpr int kTcMaxStages = 8;
 constexpr int kTcThreads = 192;
 
 template <int C, int N, int MODE>
@@ -46,10 +51,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
   unsigned char* sW = base;
   unsigned char* sA = base + 27 * WTAP;
   const int bx = a.bx, by = a.by;
+  const uint32_t S = (uint32_t)a.stages;
   const uint32_t stage_bytes = (uint32_t)((by + 2) * bx * ROWB);
-  uint64_t* full = (uint64_t*)(sA + kTcStages * stage_bytes);
-  uint64_t* empty = full + kTcStages;
-  uint64_t* wbar = empty + kTcStages;
+  uint64_t* full = (uint64_t*)(sA + S * stage_bytes);
+  uint64_t* empty = full + kTcMaxStages;
+  uint64_t* wbar = empty + kTcMaxStages;
   uint64_t* tfull = wbar + 1;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
@@ -60,8 +66,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
   const int tiles_x = (a.d.nx + bx - 1) / bx, tiles_y = (a.d.ny + by - 1) / by;
   const int ntiles = tiles_x * tiles_y * a.d.nz;
 
+  pdl_launch_dependents();
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kTcStages; ++i) {
+    for (uint32_t i = 0; i < S; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
@@ -88,12 +95,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
     tc::prefetch_tensormap(&tmW);
     tc::mbar_arrive_expect_tx(wbar, 27 * WTAP);
     for (int t = 0; t < 27; ++t) tc::tma_load_3d(sW + t * WTAP, &tmW, wbar, 0, 0, t);
+    pdl_wait();                     // the producer of the input activation has completed
     uint32_t it = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
       const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, z = tile / (tiles_x * tiles_y);
       for (int s9 = 0; s9 < 9; ++s9, ++it) {
         const int dz = s9 / 3, dx = s9 % 3;
-        const uint32_t stage = it % kTcStages, round = it / kTcStages;
+        const uint32_t stage = it % S, round = it / S;
         if (!tc::mbar_wait(&empty[stage], (round & 1) ^ 1, abort)) break;
         tc::mbar_arrive_expect_tx(&full[stage], stage_bytes);
         tc::tma_load_4d(sA + stage * stage_bytes, &tmA, &full[stage], 0, tx * bx + dx - 1, ty * by - 1,
@@ -102,10 +110,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
     }
     if (*abort) {
       // let the copies already issued land before the CTA exits
-      for (uint32_t k = 0; k < kTcStages && k < it; ++k) {
+      for (uint32_t k = 0; k < S && k < it; ++k) {
         const uint32_t last = it - 1 - k;
         volatile int never = 0;
-        tc::mbar_wait(&full[last % kTcStages], (last / kTcStages) & 1, &never);
+        tc::mbar_wait(&full[last % S], (last / S) & 1, &never);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
         bool ok = true;
         for (int s9 = 0; s9 < 9; ++s9, ++it) {
           const int dz = s9 / 3, dx = s9 % 3;
-          const uint32_t stage = it % kTcStages, round = it / kTcStages;
+          const uint32_t stage = it % S, round = it / S;
           if (!tc::mbar_wait(&full[stage], round & 1, abort)) { ok = false; break; }
           tc::fence_after_sync();
 #pragma unroll
@@ -149,6 +157,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
+    pdl_wait();                     // writes and the input scale come after the producer
     const int q = warp & 3;
     const int row = 32 * q + lane;
     const int xl = row % bx, yl = row / bx;
@@ -286,28 +295,75 @@ vie_status tc_encode_w(CUtensorMap* map, const __nv_bfloat16* w, int C, int N) {
   return encode(map, w, 3, dims, strides, box, C);
 }
 
+struct DevInfo {
+  int sms = 0;
+  int smem_sm = 0;        // shared memory per SM (bytes)
+  int smem_reserved = 0;  // reserved by the system per block
+};
+
+static const DevInfo& dev_info() {
+  static DevInfo d;
+  if (!d.sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&d.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return d;
+}
+
+constexpr size_t kTcBarrierBytes = 32 * sizeof(uint64_t);
+
+// Stages and resident CTAs per SM for a tile: two CTAs per SM with the
+// deepest ring that still fits (at least three stages), else one CTA with
+// up to kTcMaxStages stages.
+static void plan_stages(size_t fixed, size_t stage, const DevInfo& d, int* stages, int* per_sm) {
+  const size_t sm = (size_t)d.smem_sm, rsv = (size_t)d.smem_reserved;
+  for (int s = kTcMaxStages; s >= 3; --s)
+    if (2 * (fixed + s * stage + rsv) <= sm) {
+      *stages = s;
+      *per_sm = 2;
+      return;
+    }
+  for (int s = kTcMaxStages; s >= 2; --s)
+    if (fixed + s * stage + rsv <= sm) {
+      *stages = s;
+      *per_sm = 1;
+      return;
+    }
+  *stages = 0;
+  *per_sm = 0;
+}
+
 template <int C, int N, int MODE>
-static vie_status launch_conv(const CUtensorMap& A, const CUtensorMap& W, const TcConvArgs& args, cudaStream_t s) {
-  const size_t stage = (size_t)(args.by + 2) * args.bx * C * 2;
-  const size_t smem = 1024 + 27 * (size_t)N * C * 2 + kTcStages * stage + 16 * sizeof(uint64_t);
+static vie_status launch_conv(const CUtensorMap& A, const CUtensorMap& W, TcConvArgs args, cudaStream_t s) {
+  static bool configured = false;
   auto kern = conv_tc_kernel<C, N, MODE>;
-  VIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
-  VIE_CUDA_TRY(cudaGetDevice(&dev));
-  VIE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  VIE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
-  if (per_sm < 1) {
-    set_error("tensor-core convolution does not fit on an SM (%zu B shared memory)", smem);
+  const DevInfo& dv = dev_info();
+  const size_t fixed = 1024 + 27 * (size_t)N * C * 2 + kTcBarrierBytes;
+  if (!configured) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      dv.smem_sm - dv.smem_reserved));
+    VIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    configured = true;
+  }
+  const size_t stage = (size_t)(args.by + 2) * args.bx * C * 2;
+  int stages = 0, per_sm = 0;
+  plan_stages(fixed, stage, dv, &stages, &per_sm);
+  if (per_sm < 1 || dv.sms < 1) {
+    set_error("tensor-core convolution does not fit on an SM (%zu B per stage)", stage);
     return VIE_ERR_INVALID;
   }
-  if (per_sm > 2) per_sm = 2;
+  args.stages = stages;
+  const size_t smem = fixed + (size_t)stages * stage;
   const Dims d = args.d;
   const long ntiles = (long)((d.nx + args.bx - 1) / args.bx) * ((d.ny + args.by - 1) / args.by) * d.nz;
-  long grid = (long)sms * per_sm;
+  long grid = (long)dv.sms * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return VIE_OK;
-  kern<<<(unsigned)grid, kTcThreads, smem, s>>>(A, W, args);
-  VIE_LAUNCH_CHECK();
+  VIE_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(kTcThreads), smem, s, A, W, args));
   return VIE_OK;
 }
 
@@ -333,11 +389,49 @@ static unsigned grid_for(size_t n) {
   return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
 }
 
-// X[vox][16]: re v_c s (c = 0..2), im v_c s, re chi, im chi, 8 zeros; s = sqrt(3 V / sum|v|^2)
+// sum |v|^2 over the 3 V entries as kTcNormBlocks partial sums (no atomics)
 template <typename V>
-__global__ void pack_cl_kernel(const V* __restrict__ v, const double2* __restrict__ chi, size_t vox,
-                               const double* __restrict__ sumsq, __nv_bfloat16* __restrict__ X) {
-  const double ss = *sumsq;
+__global__ void __launch_bounds__(256) sumsq_partial_kernel(const V* __restrict__ v, size_t n,
+                                                            double* __restrict__ part) {
+  pdl_launch_dependents();
+  pdl_wait();
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const V a = v[i];
+    acc += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// X[vox][16]: re v_c s (c = 0..2), im v_c s, re chi, im chi, 8 zeros;
+// s = sqrt(3 V / sum|v|^2).  Every block totals the partial sums; block 0
+// also stores the total in part[kTcNormBlocks] for the output step.
+template <typename V>
+__global__ void __launch_bounds__(256) pack_cl_kernel(const V* __restrict__ v, const double2* __restrict__ chi,
+                                                      size_t vox, double* __restrict__ part,
+                                                      __nv_bfloat16* __restrict__ X) {
+  pdl_launch_dependents();
+  pdl_wait();
+  __shared__ double tot;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < kTcNormBlocks; i += 32) t += part[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) {
+      tot = t;
+      if (blockIdx.x == 0) part[kTcNormBlocks] = t;
+    }
+  }
+  __syncthreads();
+  const double ss = tot;
   const float s = ss > 0.0 ? (float)sqrt(3.0 * (double)vox / ss) : 0.f;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x) {
     float f[8];
@@ -384,6 +478,8 @@ __device__ __forceinline__ uint4 f_to_bf8(const float (&f)[8]) {
 // (coarse voxel, group of 8 channels), 32 channels
 __global__ void pool_cl_kernel(const __nv_bfloat16* __restrict__ in, Dims f, __nv_bfloat16* __restrict__ out,
                                Dims c) {
+  pdl_launch_dependents();
+  pdl_wait();
   const size_t n = c.vox() * 4;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int g = (int)(i & 3);
@@ -411,6 +507,8 @@ __global__ void pool_cl_kernel(const __nv_bfloat16* __restrict__ in, Dims f, __n
 // out = up(coarse) + skip (nearest neighbour in y and x), 32 channels
 __global__ void up_add_cl_kernel(const __nv_bfloat16* __restrict__ coarse, Dims c,
                                  const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ out, Dims f) {
+  pdl_launch_dependents();
+  pdl_wait();
   const size_t n = f.vox() * 4;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int g = (int)(i & 3);
@@ -426,27 +524,23 @@ __global__ void up_add_cl_kernel(const __nv_bfloat16* __restrict__ coarse, Dims 
 }
 
 template <typename V>
-vie_status tc_pack_input(const V* v, const double2* chi, Dims d, const double* sumsq, __nv_bfloat16* X,
-                         cudaStream_t s) {
-  pack_cl_kernel<V><<<grid_for(d.vox()), 256, 0, s>>>(v, chi, d.vox(), sumsq, X);
-  VIE_LAUNCH_CHECK();
+vie_status tc_pack_input(const V* v, const double2* chi, Dims d, double* part, __nv_bfloat16* X, cudaStream_t s) {
+  VIE_CUDA_TRY(launch_pdl(sumsq_partial_kernel<V>, dim3(kTcNormBlocks), dim3(256), 0, s, v, 3 * d.vox(), part));
+  VIE_CUDA_TRY(launch_pdl(pack_cl_kernel<V>, dim3(grid_for(d.vox())), dim3(256), 0, s, v, chi, d.vox(), part, X));
   return VIE_OK;
 }
-template vie_status tc_pack_input<float2>(const float2*, const double2*, Dims, const double*, __nv_bfloat16*,
-                                          cudaStream_t);
-template vie_status tc_pack_input<double2>(const double2*, const double2*, Dims, const double*, __nv_bfloat16*,
+template vie_status tc_pack_input<float2>(const float2*, const double2*, Dims, double*, __nv_bfloat16*, cudaStream_t);
+template vie_status tc_pack_input<double2>(const double2*, const double2*, Dims, double*, __nv_bfloat16*,
                                            cudaStream_t);
 
 vie_status tc_pool(const __nv_bfloat16* in, Dims f, __nv_bfloat16* out, Dims c, cudaStream_t s) {
-  pool_cl_kernel<<<grid_for(c.vox() * 4), 256, 0, s>>>(in, f, out, c);
-  VIE_LAUNCH_CHECK();
+  VIE_CUDA_TRY(launch_pdl(pool_cl_kernel, dim3(grid_for(c.vox() * 4)), dim3(256), 0, s, in, f, out, c));
   return VIE_OK;
 }
 
 vie_status tc_up_add(const __nv_bfloat16* coarse, Dims c, const __nv_bfloat16* skip, __nv_bfloat16* out, Dims f,
                      cudaStream_t s) {
-  up_add_cl_kernel<<<grid_for(f.vox() * 4), 256, 0, s>>>(coarse, c, skip, out, f);
-  VIE_LAUNCH_CHECK();
+  VIE_CUDA_TRY(launch_pdl(up_add_cl_kernel, dim3(grid_for(f.vox() * 4)), dim3(256), 0, s, coarse, c, skip, out, f));
   return VIE_OK;
 }
 

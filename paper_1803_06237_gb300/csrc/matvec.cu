@@ -17,31 +17,11 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <utility>
-
 #include "fft.cuh"
 #include "regfft.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
-
-// Launch with programmatic stream serialisation (see pdl_wait in
-// vie_internal.cuh).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 template <typename V> __device__ __forceinline__ V zero_c();
 template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }

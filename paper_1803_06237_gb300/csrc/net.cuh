@@ -30,6 +30,7 @@ enum TcMode {
 struct TcConvArgs {
   Dims d;                       // grid of this level
   int bx, by;                   // output tile: bx consecutive x times by rows in y (bx * by = 128)
+  int stages;                   // depth of the TMA ring (set by tc_conv)
   const float* bias;            // co biases (FP32)
   int co;                       // real output channels
   __nv_bfloat16* out;           // TC_RELU_BF16: channels-last output, 32 channels
@@ -53,10 +54,12 @@ vie_status tc_encode_w(CUtensorMap* map, const __nv_bfloat16* w, int C, int N);
 vie_status tc_conv(const CUtensorMap& A, const CUtensorMap& W, int C, int N, int mode, const TcConvArgs& args,
                    cudaStream_t s);
 
-// Channels-last BF16 helpers of the inference path.
+// Channels-last BF16 helpers of the inference path.  tc_pack_input sums
+// |v|^2 into kTcNormBlocks partials (part[0 .. kTcNormBlocks), total in
+// part[kTcNormBlocks]) and packs the scaled input X[vox][16].
+constexpr int kTcNormBlocks = 256;
 template <typename V>
-vie_status tc_pack_input(const V* v, const double2* chi, Dims d, const double* sumsq, __nv_bfloat16* X,
-                         cudaStream_t s);
+vie_status tc_pack_input(const V* v, const double2* chi, Dims d, double* part, __nv_bfloat16* X, cudaStream_t s);
 vie_status tc_pool(const __nv_bfloat16* in, Dims f, __nv_bfloat16* out, Dims c, cudaStream_t s);
 vie_status tc_up_add(const __nv_bfloat16* coarse, Dims c, const __nv_bfloat16* skip, __nv_bfloat16* out, Dims f,
                      cudaStream_t s);

@@ -647,6 +647,7 @@ struct TcCache {
   Dims L[4];
   int bx[4], by[4];
   __nv_bfloat16 *X = nullptr, *h[4] = {}, *a[4] = {}, *decin[3] = {}, *u[3] = {};
+  double* norm = nullptr;       // kTcNormBlocks partial sums of |v|^2, then the total
   CUtensorMap mA[kNumLayers];   // input activation of each layer
   CUtensorMap mW[kNumLayers];   // packed weights of each layer
   bool wmaps = false;
@@ -663,6 +664,7 @@ static size_t tc_ws_elems(const Dims* L) {
 static vie_status tc_prepare(vie_net* net, const int n[3], TcCache** out) {
   if (!net->tc) net->tc = new TcCache();
   TcCache* c = net->tc;
+  if (!c->norm) VIE_CUDA_TRY(cudaMalloc((void**)&c->norm, (kTcNormBlocks + 1) * sizeof(double)));
   if (!c->wmaps) {
     for (int l = 0; l < kNumLayers; ++l) {
       vie_status st = tc_encode_w(&c->mW[l], net->wpack + pack_off(l), tc_cpad(kLayerDefs[l].ci),
@@ -715,6 +717,7 @@ static vie_status tc_prepare(vie_net* net, const int n[3], TcCache** out) {
 static void tc_free(TcCache* c) {
   if (!c) return;
   cudaFree(c->ws);
+  cudaFree(c->norm);
   delete c;
 }
 
@@ -723,12 +726,8 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
   TcCache* c = nullptr;
   vie_status st = tc_prepare(net, p->n, &c);
   if (st != VIE_OK) return st;
-  const size_t V0 = c->L[0].vox();
-  double* sumsq = (double*)net->scal;
-  VIE_CUDA_TRY(cudaMemsetAsync(net->scal, 0, 4 * sizeof(double), s));
-  sumsq_kernel<V><<<ew_blocks(3 * V0), 256, 0, s>>>(v, 3 * V0, sumsq);
-  VIE_LAUNCH_CHECK();
-  st = tc_pack_input<V>(v, p->chi64, c->L[0], sumsq, c->X, s);
+  double* sumsq = c->norm + kTcNormBlocks;
+  st = tc_pack_input<V>(v, p->chi64, c->L[0], c->norm, c->X, s);
   if (st != VIE_OK) return st;
   auto conv = [&](int layer, int level, int mode, __nv_bfloat16* out) {
     TcConvArgs a{};
