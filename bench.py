@@ -117,9 +117,9 @@ def net_section(plan, grid, reps=50):
     return {"ms_per_apply": ms, "algorithmic_flops": flops,
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                          "peak_source": kind + " dense bf16 (burst)"},
-            "launches_per_apply": 17,
-            "note": "8 tcgen05 convolutions + 3 pools + 3 upsample-adds + input packing + |v|^2; "
-                    "the convolutions' implicit-GEMM flops only"}
+            "launches_per_apply": 10,
+            "note": "|v|^2, input packing and 8 tcgen05 convolutions (pooling, upsample-add and the output "
+                    "step fused into their epilogues); the convolutions' 3x3x3 flops only"}
 
 
 class ClockSampler:

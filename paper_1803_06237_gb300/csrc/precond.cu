@@ -645,18 +645,22 @@ struct TcCache {
   __nv_bfloat16* ws = nullptr;
   size_t cap = 0;
   Dims L[4];
-  int bx[4], by[4];
-  __nv_bfloat16 *X = nullptr, *h[4] = {}, *a[4] = {}, *decin[3] = {}, *u[3] = {};
+  int bx[kNumLayers], by[kNumLayers];   // tile of each layer
+  // h_l (l < 3, skips), pooled inputs a_l (l >= 1), decoder inputs decin_l, u_0
+  __nv_bfloat16 *X = nullptr, *h[3] = {}, *a[4] = {}, *decin[3] = {}, *u0 = nullptr;
   double* norm = nullptr;       // kTcNormBlocks partial sums of |v|^2, then the total
   CUtensorMap mA[kNumLayers];   // input activation of each layer
   CUtensorMap mW[kNumLayers];   // packed weights of each layer
   bool wmaps = false;
 };
 
+// level of each layer: enc0..enc3, dec2, dec1, dec0, out
+static const int kLayerLevel[kNumLayers] = {0, 1, 2, 3, 2, 1, 0, 0};
+
 static size_t tc_ws_elems(const Dims* L) {
-  size_t t = 16 * L[0].vox();
-  for (int l = 0; l < 4; ++l) t += 32 * L[l].vox() * (l >= 1 ? 2 : 1);
-  for (int l = 0; l < 3; ++l) t += 2 * 32 * L[l].vox();
+  size_t t = 16 * L[0].vox() + 32 * L[0].vox();         // X, u_0
+  for (int l = 0; l < 3; ++l) t += 2 * 32 * L[l].vox();  // h_l, decin_l
+  for (int l = 1; l < 4; ++l) t += 32 * L[l].vox();      // a_l
   return t;
 }
 
@@ -690,21 +694,19 @@ static vie_status tc_prepare(vie_net* net, const int n[3], TcCache** out) {
   __nv_bfloat16* p = c->ws;
   auto take = [&](size_t k) { __nv_bfloat16* r = p; p += k; return r; };
   c->X = take(16 * c->L[0].vox());
-  for (int l = 0; l < 4; ++l) {
-    c->h[l] = take(32 * c->L[l].vox());
-    c->a[l] = l >= 1 ? take(32 * c->L[l].vox()) : nullptr;
-    tc_pick_tile(c->L[l], &c->bx[l], &c->by[l]);
-  }
+  c->u0 = take(32 * c->L[0].vox());
   for (int l = 0; l < 3; ++l) {
+    c->h[l] = take(32 * c->L[l].vox());
     c->decin[l] = take(32 * c->L[l].vox());
-    c->u[l] = take(32 * c->L[l].vox());
   }
-  // layer inputs: enc0 X, enc1..3 pooled a_l, dec_l decin_l, out u_0
-  struct { int layer, level; const __nv_bfloat16* in; int C; } m[kNumLayers] = {
-      {ENC0, 0, c->X, 16},       {ENC1, 1, c->a[1], 32},    {ENC2, 2, c->a[2], 32},    {ENC3, 3, c->a[3], 32},
-      {DEC2, 2, c->decin[2], 32}, {DEC1, 1, c->decin[1], 32}, {DEC0, 0, c->decin[0], 32}, {OUTL, 0, c->u[0], 32}};
-  for (auto& e : m) {
-    vie_status st = tc_encode_act(&c->mA[e.layer], e.in, e.C, c->L[e.level], c->bx[e.level], c->by[e.level]);
+  c->a[0] = nullptr;
+  for (int l = 1; l < 4; ++l) c->a[l] = take(32 * c->L[l].vox());
+  // layer inputs: enc0 X, enc1..3 pooled a_l, dec_l decin_l, out u_0; the
+  // encoders below the coarsest level pool in their epilogue (16-wide tiles)
+  const __nv_bfloat16* in[kNumLayers] = {c->X, c->a[1], c->a[2], c->a[3], c->decin[2], c->decin[1], c->decin[0], c->u0};
+  for (int l = 0; l < kNumLayers; ++l) {
+    tc_pick_tile(c->L[kLayerLevel[l]], l <= ENC2, &c->bx[l], &c->by[l]);
+    vie_status st = tc_encode_act(&c->mA[l], in[l], l == ENC0 ? 16 : 32, c->L[kLayerLevel[l]], c->bx[l], c->by[l]);
     if (st != VIE_OK) return st;
   }
   c->n[0] = n[0];
@@ -721,6 +723,9 @@ static void tc_free(TcCache* c) {
   delete c;
 }
 
+// Inference: |v|^2 and the packed input, then eight convolutions whose
+// epilogues also pool (enc0..enc2) or upsample and add the skip (enc3, dec2,
+// dec1); the output layer's epilogue forms z = v + Net(v) / s.
 template <typename V>
 static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z, cudaStream_t s) {
   TcCache* c = nullptr;
@@ -729,14 +734,18 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
   double* sumsq = c->norm + kTcNormBlocks;
   st = tc_pack_input<V>(v, p->chi64, c->L[0], c->norm, c->X, s);
   if (st != VIE_OK) return st;
-  auto conv = [&](int layer, int level, int mode, __nv_bfloat16* out) {
+  auto conv = [&](int layer, int mode, __nv_bfloat16* out, __nv_bfloat16* out2, int level2,
+                  const __nv_bfloat16* skip) {
     TcConvArgs a{};
-    a.d = c->L[level];
-    a.bx = c->bx[level];
-    a.by = c->by[level];
+    a.d = c->L[kLayerLevel[layer]];
+    a.d2 = level2 >= 0 ? c->L[level2] : a.d;
+    a.bx = c->bx[layer];
+    a.by = c->by[layer];
     a.bias = B(net, layer);
     a.co = kLayerDefs[layer].co;
     a.out = out;
+    a.out2 = out2;
+    a.skip = skip;
     a.v = v;
     a.z = z;
     a.sumsq = sumsq;
@@ -744,16 +753,13 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
     return tc_conv(c->mA[layer], c->mW[layer], tc_cpad(kLayerDefs[layer].ci), tc_npad(kLayerDefs[layer].co), mode,
                    a, s);
   };
-  for (int l = 0; l < 4; ++l) {
-    if (l > 0 && (st = tc_pool(c->h[l - 1], c->L[l - 1], c->a[l], c->L[l], s)) != VIE_OK) return st;
-    if ((st = conv(ENC0 + l, l, TC_RELU_BF16, c->h[l])) != VIE_OK) return st;
-  }
-  for (int l = 2; l >= 0; --l) {
-    const __nv_bfloat16* coarse = l == 2 ? c->h[3] : c->u[l + 1];
-    if ((st = tc_up_add(coarse, c->L[l + 1], c->h[l], c->decin[l], c->L[l], s)) != VIE_OK) return st;
-    if ((st = conv(DEC0 - l, l, TC_RELU_BF16, c->u[l])) != VIE_OK) return st;
-  }
-  return conv(OUTL, 0, sizeof(V) == 8 ? TC_UNPACK_C64 : TC_UNPACK_C128, nullptr);
+  for (int l = 0; l < 3; ++l)
+    if ((st = conv(ENC0 + l, TC_RELU_POOL, c->h[l], c->a[l + 1], l + 1, nullptr)) != VIE_OK) return st;
+  if ((st = conv(ENC3, TC_RELU_UPADD, nullptr, c->decin[2], 2, c->h[2])) != VIE_OK) return st;
+  if ((st = conv(DEC2, TC_RELU_UPADD, nullptr, c->decin[1], 1, c->h[1])) != VIE_OK) return st;
+  if ((st = conv(DEC1, TC_RELU_UPADD, nullptr, c->decin[0], 0, c->h[0])) != VIE_OK) return st;
+  if ((st = conv(DEC0, TC_RELU_BF16, c->u0, nullptr, -1, nullptr)) != VIE_OK) return st;
+  return conv(OUTL, sizeof(V) == 8 ? TC_UNPACK_C64 : TC_UNPACK_C128, nullptr, nullptr, -1, nullptr);
 }
 
 struct PrecondCtx {

@@ -45,6 +45,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Wait until the phase with the given parity has completed; false on timeout
 // or when *abort becomes non-zero.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;     // fast path: no clock read
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
@@ -105,6 +106,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int row_bytes) {
   const uint64_t swz = row_bytes == 64 ? 4 : 6;
   return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (swz << 61);
 }
+
+// The start address is the low 14-bit field (in 16-byte units): a
+// descriptor for base + off is the base's descriptor plus off >> 4, as long
+// as base + off stays below 256 KB (all of shared memory).
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t off_bytes) { return desc + (off_bytes >> 4); }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
 // and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
