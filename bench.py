@@ -385,10 +385,62 @@ def solve_section(plan, wl, absorbers, args):
                            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
                            "net_apply_ms": net_ms}
         vie.vie_set_preconditioner(plan, None)
+    if args.circulant:
+        out["circulant"] = circulant_section(plan, b, args)
+        out["mixed_circulant"] = out["circulant"].pop("solve")
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     if "mixed_learned" in out:
         out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms"] / out["mixed_learned"]["ms"]
+    if "mixed_circulant" in out:
+        out["speedup_mixed_circulant_vs_fp64"] = out["fp64"]["ms"] / out["mixed_circulant"]["ms"]
     return out
+
+
+def circulant_section(plan, b, args, reps=20):
+    """The block-circulant preconditioner (Sec. 6) on the benchmark guide:
+    setup (blocks, DFT along x, batched LU) timed on the host clock, the
+    application timed with CUDA events against the HBM roofline (it streams
+    the nx (3 ny nz)^2 complex64 factors once), and the preconditioned mixed
+    solve to 1e-6."""
+    import torch
+
+    from paper_1803_06237_gb300 import vie
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = vie.vie_circulant_create(plan)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    info = vie.vie_circulant_info(c)
+    v = torch.randn(b.numel(), dtype=torch.complex64, device="cuda")
+    z = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        vie.vie_circulant_apply(c, v, z, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        vie.vie_circulant_apply(c, v, z, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nx, ny, nz = plan.n
+    R = 3 * ny * nz
+    factor_bytes = nx * R * R * 8
+    hbm_peak, kind = _peaks()
+    achieved = factor_bytes / (ms * 1e-3) / 1e9
+    vie.vie_set_circulant_preconditioner(plan, c)
+    _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)      # warm-up
+    solve = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
+    vie.vie_set_circulant_preconditioner(plan, None)
+    c.close()
+    return {"setup_ms": setup_ms, "build_ms_library": info["build_ms"], "device_bytes": info["device_bytes"],
+            "apply_ms": ms,
+            "apply_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": achieved / hbm_peak, "peak_source": kind,
+                               "algorithmic_bytes": factor_bytes,
+                               "note": "LU factors of the nx blocks (complex64) read once per application"},
+            "solve": solve}
 
 
 def batch_section(args):
@@ -540,6 +592,8 @@ def main():
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
+    ap.add_argument("--no-circulant", dest="circulant", action="store_false",
+                    help="skip the block-circulant preconditioner leg of the solve section")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run a capped mixed solve (for kernel launch lists)")
     args = ap.parse_args()

@@ -276,6 +276,43 @@ vie_status vie_net_adam_step(vie_net* net, float lr, float grad_scale, void* str
  * resets it. */
 vie_status vie_net_status(vie_net* net, int* flag, int clear);
 
+/* ------------------------------------------------------------------------ */
+/* Block-circulant preconditioner (Sec. 6): W, the matrix nearest to        */
+/* A = I - M N in the Frobenius norm among those that are circulant along x */
+/* (dense (3 ny nz)^2 blocks, rows and columns ordered (component, z, y)):   */
+/* W = circ(c_0 .. c_{nx-1}), c_k = (1/nx) sum_i A[i][(i - k) mod nx].  The  */
+/* DFT along x makes W block diagonal; the nx blocks are LU-factored        */
+/* (partial pivoting) in complex64 on the device.  Applied as a right        */
+/* preconditioner of flexible GMRES (the paper writes the left form         */
+/* W^{-1} A; the two preconditioned matrices are similar).                   */
+/* Device memory: nx (3 ny nz)^2 complex64 (2.8 GB for the 600 x 23 x 11     */
+/* guide).                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct vie_circulant vie_circulant;
+
+/* Build W from the plan's current Toeplitz entries and contrast (the plan's
+ * contrast must have been set) and factor it; synchronises `stream`.  The
+ * preconditioner keeps a pointer to the plan: destroy it before the plan.
+ * If the plan's contrast changes afterwards, applications fail with
+ * VIE_ERR_INVALID (stale).  Errors: VIE_ERR_INVALID (no contrast, cross
+ * section above ~1600 unknowns), VIE_ERR_OOM, VIE_ERR_CUDA,
+ * VIE_ERR_NONFINITE (a singular block). */
+vie_status vie_circulant_create(vie_plan* plan, vie_circulant** out, void* stream);
+
+/* z = W^{-1} v for device vectors of 3*nx*ny*nz entries of dtype (VIE_C64
+ * or VIE_C128; computed in complex64 either way), not overlapping.
+ * Asynchronous on `stream`. */
+vie_status vie_circulant_apply(vie_circulant* c, const void* v_dev, void* z_dev, int dtype, void* stream);
+
+/* Setup time (ms, host clock around the build) and device bytes held. */
+vie_status vie_circulant_info(const vie_circulant* c, double* build_ms, size_t* device_bytes);
+vie_status vie_circulant_destroy(vie_circulant* c);
+
+/* Use `c` (NULL: none) as the right preconditioner of this plan's solves
+ * with opts->use_preconditioner = 1, replacing any network set with
+ * vie_set_preconditioner.  `c` must have been built for this plan. */
+vie_status vie_set_circulant_preconditioner(vie_plan* plan, vie_circulant* c);
+
 /* Use `net` (NULL: none) as the right preconditioner of this plan's solves
  * with opts->use_preconditioner = 1 (flexible GMRES).  The plan keeps a
  * reference; the caller keeps ownership and must not destroy the network

@@ -66,7 +66,9 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=()) ->
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + ".tmp"
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(exe)), "lib64")
+    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas",
+           "-Xlinker", "-rpath", "-Xlinker", cudalib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -183,6 +183,7 @@ static vie_status set_contrast_common(vie_plan* p, const double* host, const vie
   }
   if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(bad);
+  ++p->contrast_gen;          // preconditioners built from the old contrast are stale
   if (e != cudaSuccess) {
     set_error("set contrast: %s", cudaGetErrorString(e));
     st = VIE_ERR_CUDA;

@@ -1,0 +1,598 @@
+// Block-circulant preconditioner of Sec. 6: the Frobenius-nearest matrix W
+// to A = I - M N that is circulant in x, with dense (3 ny nz)^2 blocks.
+//
+// View A as nx x nx blocks A[i][j] (rows and columns ordered (p, z, y)):
+// A[i][j] = delta_ij I - M_i T(i - j).  The nearest block-circulant matrix
+// has the blocks c_k = (1/nx) sum_i A[i][(i - k) mod nx], i.e.
+//   c_k = delta_k0 I - S+_k T(k) - S-_k T(k - nx),
+//   S+_k = (1/nx) sum_{i >= k} M_i,  S-_k = (1/nx) sum_{i < k} M_i
+// (row scalings by the x-averaged contrast).  The DFT along x
+// block-diagonalises W: W_hat(w) = sum_k c_k exp(-2 pi i w k / nx).
+//
+// Setup (once per plan and contrast):
+//   1. prefix sums of M along x (FP64), 2. the blocks c_k (complex64),
+//   3. W_hat = F C with the nx x nx DFT matrix F (a plain batched-free
+//      CGEMM over all (3B)^2 entries: nx need not be 5-smooth),
+//   4. LU with partial pivoting of the nx blocks W_hat(w): panels of nb
+//      columns factored in shared memory, row swaps, a triangular solve for
+//      the U row block, and the trailing update as a strided-batched CGEMM.
+// Application z = W^{-1} v (complex64):
+//   V_hat = F V (CGEMM), one pivoted forward and backward substitution per
+//   frequency (one CTA each, the factor streamed once from HBM), then
+//   z = F^H Z_hat / nx (CGEMM).  The vectors' planar layout [p][z][y][x] is
+//   already the (3B) x nx matrix the transforms need.
+//
+// The plain GEMMs (the DFTs along x and the trailing LU updates) go to
+// cuBLAS; everything else is in this file.
+#include <cublas_v2.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <chrono>
+
+#include "vie_internal.cuh"
+
+struct vie_circulant {
+  int device = 0;
+  const vie_plan* plan = nullptr;
+  int gen = 0;                 // contrast generation the factors were built from
+  int nx = 0, ny = 0, nz = 0, B = 0, R = 0, nb = 32;
+  float2* W = nullptr;         // nx x R x R: LU factors (unit L below, U on and above the diagonal)
+  int* perm = nullptr;         // nx x R: row r of P b is b[perm[r]]
+  float2* F = nullptr;         // nx x nx: exp(-2 pi i w k / nx)
+  float2* Fi = nullptr;        // nx x nx: exp(+2 pi i w k / nx) / nx
+  float2* vh = nullptr;        // nx x R scratch (row-major [w][r])
+  float2* v32 = nullptr;       // 3N scratch for complex128 callers
+  float2* z32 = nullptr;
+  int* flag = nullptr;         // 1: a zero pivot was met
+  cublasHandle_t blas = nullptr;
+  double build_ms = 0.0;
+};
+
+namespace vie {
+
+#define VIE_CUBLAS_TRY(expr)                                                     \
+  do {                                                                           \
+    cublasStatus_t b__ = (expr);                                                 \
+    if (b__ != CUBLAS_STATUS_SUCCESS) {                                          \
+      set_error("%s:%d: %s failed (cuBLAS status %d)", __FILE__, __LINE__, #expr, \
+                (int)b__);                                                       \
+      return VIE_ERR_CUDA;                                                       \
+    }                                                                            \
+  } while (0)
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 csub_mul(float2 acc, float2 a, float2 b) {
+  // acc - a b
+  return make_float2(acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x));
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels
+// ---------------------------------------------------------------------------
+// S+[k][zy] = (1/nx) sum_{i >= k} M[zy][i], S-[k][zy] = (1/nx) sum_{i < k} M[zy][i]
+__global__ void prefix_kernel(const double2* __restrict__ M, int nx, int B, float2* __restrict__ Sp,
+                              float2* __restrict__ Sm) {
+  const int zy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zy >= B) return;
+  const double2* row = M + (size_t)zy * nx;
+  double tx = 0.0, ty = 0.0;
+  for (int i = 0; i < nx; ++i) {
+    tx += row[i].x;
+    ty += row[i].y;
+  }
+  double lx = 0.0, ly = 0.0;   // sum over i < k
+  const double inv = 1.0 / nx;
+  for (int k = 0; k < nx; ++k) {
+    Sm[(size_t)k * B + zy] = make_float2((float)(lx * inv), (float)(ly * inv));
+    Sp[(size_t)k * B + zy] = make_float2((float)((tx - lx) * inv), (float)((ty - ly) * inv));
+    lx += row[k].x;
+    ly += row[k].y;
+  }
+}
+
+// Component index of (p, q) in the Toeplitz table order xx, yy, zz, xy, xz, yz.
+__device__ __forceinline__ int comp_of(int p, int q) {
+  if (p == q) return p;
+  const int a = min(p, q), b = max(p, q);
+  return a == 0 ? (b == 1 ? 3 : 4) : 5;
+}
+
+// T_pq(dx, dy, dz) for signed offsets from the octant table; an
+// off-diagonal component is odd in each of its two axes.
+__device__ __forceinline__ float2 toeplitz_at(const double2* __restrict__ T, int nx, int ny, int nz, int p, int q,
+                                             int dx, int dy, int dz) {
+  const int c = comp_of(p, q);
+  const double2 t = T[(((size_t)c * nz + abs(dz)) * ny + abs(dy)) * nx + abs(dx)];
+  float sgn = 1.f;
+  if (p != q) {
+    const int d[3] = {dx, dy, dz};
+    if (d[p] < 0) sgn = -sgn;
+    if (d[q] < 0) sgn = -sgn;
+  }
+  return make_float2(sgn * (float)t.x, sgn * (float)t.y);
+}
+
+// C[k][r][s] = delta_k0 delta_rs - S+_k[r] T(k)[r][s] - S-_k[r] T(k - nx)[r][s]
+// r = (p, z, y), s = (q, z', y'), T(dx)[r][s] = T_pq(dx, y - y', z - z').
+__global__ void build_blocks_kernel(const double2* __restrict__ T, const float2* __restrict__ Sp,
+                                    const float2* __restrict__ Sm, int nx, int ny, int nz, float2* __restrict__ C) {
+  const int B = ny * nz, R = 3 * B;
+  const size_t total = (size_t)nx * R * R;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(idx % R);
+    const int r = (int)((idx / R) % R);
+    const int k = (int)(idx / ((size_t)R * R));
+    const int p = r / B, zy = r % B, z = zy / ny, y = zy % ny;
+    const int q = s / B, zy2 = s % B, z2 = zy2 / ny, y2 = zy2 % ny;
+    float2 out = make_float2((k == 0 && r == s) ? 1.f : 0.f, 0.f);
+    out = csub_mul(out, Sp[(size_t)k * B + zy], toeplitz_at(T, nx, ny, nz, p, q, k, y - y2, z - z2));
+    if (k > 0) out = csub_mul(out, Sm[(size_t)k * B + zy], toeplitz_at(T, nx, ny, nz, p, q, k - nx, y - y2, z - z2));
+    C[idx] = out;
+  }
+}
+
+// F[w][k] = exp(-2 pi i w k / nx), Fi[w][k] = exp(+2 pi i w k / nx) / nx
+// (angles reduced exactly with integer arithmetic, evaluated in FP64)
+__global__ void dft_matrix_kernel(int nx, float2* __restrict__ F, float2* __restrict__ Fi) {
+  const size_t total = (size_t)nx * nx;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const long long w = (long long)(idx / nx), k = (long long)(idx % nx);
+    const long long m = (w * k) % nx;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)nx, &sn, &cs);
+    F[idx] = make_float2((float)cs, (float)-sn);
+    Fi[idx] = make_float2((float)(cs / nx), (float)(sn / nx));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched LU with partial pivoting (row-major blocks, one matrix per CTA)
+// ---------------------------------------------------------------------------
+// Panel j0 .. j0 + nbe - 1 of every matrix, rows j0 .. R - 1, factored in
+// shared memory (pitch nbe + 1): per column the largest |a| below the
+// diagonal is the pivot (lowest row on ties), rows are swapped inside the
+// panel, the column is scaled by the pivot's inverse and the rest of the
+// panel gets the rank-1 update.  piv[j] = the row swapped with row j.
+__global__ void __launch_bounds__(256) lu_panel_kernel(float2* __restrict__ W, int R, int j0, int nbe,
+                                                       int* __restrict__ piv, int* __restrict__ flag) {
+  extern __shared__ float2 P[];
+  __shared__ float bval[8];
+  __shared__ int bidx[8];
+  __shared__ int ipiv;
+  float2* A = W + (size_t)blockIdx.x * R * R;
+  const int rows = R - j0, pitch = nbe + 1;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < rows * nbe; e += nth) {
+    const int i = e / nbe, c = e - i * nbe;
+    P[i * pitch + c] = A[(size_t)(j0 + i) * R + j0 + c];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nbe; ++jj) {
+    // pivot search over rows jj .. rows - 1 of column jj
+    float best = -1.f;
+    int bi = rows;
+    for (int i = jj + tid; i < rows; i += nth) {
+      const float2 a = P[i * pitch + jj];
+      const float m = a.x * a.x + a.y * a.y;
+      if (m > best) { best = m; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { bval[wid] = best; bidx[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float b = bval[0];
+      int ii = bidx[0];
+      for (int w = 1; w < (nth >> 5); ++w)
+        if (bval[w] > b || (bval[w] == b && bidx[w] < ii)) { b = bval[w]; ii = bidx[w]; }
+      if (!(b > 0.f)) { atomicExch(flag, 1); ii = jj; }
+      ipiv = ii;
+      piv[(size_t)blockIdx.x * R + j0 + jj] = j0 + ii;
+    }
+    __syncthreads();
+    const int ip = ipiv;
+    if (ip != jj)
+      for (int c = tid; c < nbe; c += nth) {
+        const float2 t = P[jj * pitch + c];
+        P[jj * pitch + c] = P[ip * pitch + c];
+        P[ip * pitch + c] = t;
+      }
+    __syncthreads();
+    const float2 d = P[jj * pitch + jj];
+    const float dd = d.x * d.x + d.y * d.y;
+    const float2 inv = dd > 0.f ? make_float2(d.x / dd, -d.y / dd) : make_float2(0.f, 0.f);
+    for (int i = jj + 1 + tid; i < rows; i += nth) {
+      const float2 l = cmul(P[i * pitch + jj], inv);
+      P[i * pitch + jj] = l;
+      for (int c = jj + 1; c < nbe; ++c) P[i * pitch + c] = csub_mul(P[i * pitch + c], l, P[jj * pitch + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < rows * nbe; e += nth) {
+    const int i = e / nbe, c = e - i * nbe;
+    A[(size_t)(j0 + i) * R + j0 + c] = P[i * pitch + c];
+  }
+}
+
+// The panel's row swaps applied to every column outside it (the L columns
+// to its left included, as in the usual packed LU).  One thread per column.
+__global__ void __launch_bounds__(256) lu_swap_kernel(float2* __restrict__ W, int R, int j0, int nbe,
+                                                      const int* __restrict__ piv) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= R || (c >= j0 && c < j0 + nbe)) return;
+  float2* A = W + (size_t)blockIdx.x * R * R;
+  const int* pv = piv + (size_t)blockIdx.x * R;
+  for (int jj = 0; jj < nbe; ++jj) {
+    const int r1 = j0 + jj, r2 = pv[r1];
+    if (r2 != r1) {
+      const float2 t = A[(size_t)r1 * R + c];
+      A[(size_t)r1 * R + c] = A[(size_t)r2 * R + c];
+      A[(size_t)r2 * R + c] = t;
+    }
+  }
+}
+
+// U12 = L11^{-1} A12: rows j0 .. j0 + NB - 1, columns j0 + NB .. R - 1; L11
+// is the unit lower triangle of the factored panel.  One thread per column.
+template <int NB>
+__global__ void __launch_bounds__(256) lu_trsm_kernel(float2* __restrict__ W, int R, int j0) {
+  __shared__ float2 L[NB][NB + 1];
+  float2* A = W + (size_t)blockIdx.x * R * R;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, t = e - i * NB;
+    L[i][t] = A[(size_t)(j0 + i) * R + j0 + t];
+  }
+  __syncthreads();
+  const int c = j0 + NB + blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  float2 x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = A[(size_t)(j0 + i) * R + c];
+#pragma unroll
+  for (int i = 1; i < NB; ++i)
+#pragma unroll
+    for (int t = 0; t < i; ++t) x[i] = csub_mul(x[i], L[i][t], x[t]);
+#pragma unroll
+  for (int i = 0; i < NB; ++i) A[(size_t)(j0 + i) * R + c] = x[i];
+}
+
+// perm[w][r]: the swaps piv[w][0 .. R) applied in order to the identity, so
+// that (P b)[r] = b[perm[r]].  One thread per matrix.
+__global__ void perm_kernel(const int* __restrict__ piv, int R, int nmat, int* __restrict__ perm) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nmat) return;
+  int* pm = perm + (size_t)w * R;
+  const int* pv = piv + (size_t)w * R;
+  for (int r = 0; r < R; ++r) pm[r] = r;
+  for (int r = 0; r < R; ++r) {
+    const int o = pv[r];
+    if (o != r) {
+      const int t = pm[r];
+      pm[r] = pm[o];
+      pm[o] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// application: one CTA per frequency solves W_hat(w) z = b in place
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  const float d = b.x * b.x + b.y * b.y;
+  return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// x = P b (gather), then L y = x in blocks of 32 rows (the rows' products
+// with the solved part by 8 warps, the 32 x 32 unit-lower diagonal block by
+// warp 0 with shuffles), then U z = y likewise from the bottom.
+__global__ void __launch_bounds__(256) circ_solve_kernel(const float2* __restrict__ W, const int* __restrict__ perm,
+                                                         float2* __restrict__ vh, int R) {
+  extern __shared__ float2 x[];
+  __shared__ float2 D[32][33];
+  const float2* A = W + (size_t)blockIdx.x * R * R;
+  const int* pm = perm + (size_t)blockIdx.x * R;
+  float2* b = vh + (size_t)blockIdx.x * R;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int r = tid; r < R; r += blockDim.x) x[r] = b[pm[r]];
+  __syncthreads();
+  const int nblk = (R + 31) / 32;
+  // forward: unit lower L
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int i0 = bk * 32, nr = min(32, R - i0);
+    for (int e = tid; e < nr * 32; e += blockDim.x) {
+      const int a = e >> 5, t = e & 31;
+      if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
+    }
+    for (int a = wid; a < nr; a += 8) {
+      const float2* row = A + (size_t)(i0 + a) * R;
+      float sx = 0.f, sy = 0.f;
+#pragma unroll 4
+      for (int t = lane; t < i0; t += 32) {
+        const float2 l = row[t], xt = x[t];
+        sx += l.x * xt.x - l.y * xt.y;
+        sy += l.x * xt.y + l.y * xt.x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) {
+        x[i0 + a].x -= sx;
+        x[i0 + a].y -= sy;
+      }
+    }
+    __syncthreads();
+    if (wid == 0) {
+      float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
+      for (int t = 0; t < nr; ++t) {
+        const float2 xt = make_float2(__shfl_sync(0xffffffffu, xi.x, t), __shfl_sync(0xffffffffu, xi.y, t));
+        if (lane > t && lane < nr) xi = csub_mul(xi, D[lane][t], xt);
+      }
+      if (lane < nr) x[i0 + lane] = xi;
+    }
+    __syncthreads();
+  }
+  // backward: upper U (with its diagonal)
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int i0 = bk * 32, nr = min(32, R - i0), i1 = i0 + nr;
+    for (int e = tid; e < nr * 32; e += blockDim.x) {
+      const int a = e >> 5, t = e & 31;
+      if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
+    }
+    for (int a = wid; a < nr; a += 8) {
+      const float2* row = A + (size_t)(i0 + a) * R;
+      float sx = 0.f, sy = 0.f;
+#pragma unroll 4
+      for (int t = i1 + lane; t < R; t += 32) {
+        const float2 u = row[t], xt = x[t];
+        sx += u.x * xt.x - u.y * xt.y;
+        sy += u.x * xt.y + u.y * xt.x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) {
+        x[i0 + a].x -= sx;
+        x[i0 + a].y -= sy;
+      }
+    }
+    __syncthreads();
+    if (wid == 0) {
+      float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
+      for (int t = nr - 1; t >= 0; --t) {
+        if (lane == t) xi = cdiv(xi, D[t][t]);
+        const float2 xt = make_float2(__shfl_sync(0xffffffffu, xi.x, t), __shfl_sync(0xffffffffu, xi.y, t));
+        if (lane < t) xi = csub_mul(xi, D[lane][t], xt);
+      }
+      if (lane < nr) x[i0 + lane] = xi;
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < R; r += blockDim.x) b[r] = x[r];
+}
+
+__global__ void to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void to_c128_kernel(const float2* __restrict__ a, double2* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
+static unsigned blocks_for(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static void circ_free(vie_circulant* c) {
+  if (!c) return;
+  cudaFree(c->W); cudaFree(c->perm); cudaFree(c->F); cudaFree(c->Fi); cudaFree(c->vh);
+  cudaFree(c->v32); cudaFree(c->z32); cudaFree(c->flag);
+  if (c->blas) cublasDestroy(c->blas);
+  delete c;
+}
+
+static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
+  const vie_plan* p = c->plan;
+  const int nx = c->nx, ny = c->ny, nz = c->nz, B = c->B, R = c->R;
+  const size_t RR = (size_t)R * R, N3 = (size_t)3 * B * nx;
+  float2 *Sp = nullptr, *Sm = nullptr, *C = nullptr;
+  int* piv = nullptr;
+  vie_status st = VIE_OK;
+  auto fail = [&](vie_status e) { cudaFree(Sp); cudaFree(Sm); cudaFree(C); cudaFree(piv); return e; };
+#define CIRC_TRY(expr)                                                                         \
+  do {                                                                                         \
+    cudaError_t e__ = (expr);                                                                  \
+    if (e__ != cudaSuccess) {                                                                  \
+      set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e__));   \
+      return fail(e__ == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA);             \
+    }                                                                                          \
+  } while (0)
+#define CIRC_BLAS(expr)                                                                        \
+  do {                                                                                         \
+    cublasStatus_t b__ = (expr);                                                               \
+    if (b__ != CUBLAS_STATUS_SUCCESS) {                                                        \
+      set_error("%s:%d: %s failed (cuBLAS status %d)", __FILE__, __LINE__, #expr, (int)b__);   \
+      return fail(VIE_ERR_CUDA);                                                               \
+    }                                                                                          \
+  } while (0)
+  CIRC_TRY(cudaMalloc((void**)&Sp, (size_t)nx * B * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&Sm, (size_t)nx * B * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * RR * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&piv, (size_t)nx * R * sizeof(int)));
+  CIRC_TRY(cudaMalloc((void**)&c->W, (size_t)nx * RR * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->perm, (size_t)nx * R * sizeof(int)));
+  CIRC_TRY(cudaMalloc((void**)&c->F, (size_t)nx * nx * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->Fi, (size_t)nx * nx * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->vh, (size_t)nx * R * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->v32, N3 * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->z32, N3 * sizeof(float2)));
+  CIRC_TRY(cudaMalloc((void**)&c->flag, sizeof(int)));
+  CIRC_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s));
+  CIRC_BLAS(cublasSetStream(c->blas, s));
+
+  prefix_kernel<<<(B + 127) / 128, 128, 0, s>>>(p->M64, nx, B, Sp, Sm);
+  build_blocks_kernel<<<152 * 16, 256, 0, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz, C);
+  dft_matrix_kernel<<<blocks_for((size_t)nx * nx), 256, 0, s>>>(nx, c->F, c->Fi);
+  CIRC_TRY(cudaGetLastError());
+  // W_hat[w][e] = sum_k F[w][k] C[k][e]: column-major W_hat^T (RR x nx) = C^T (RR x nx) F (F symmetric)
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f), mone = make_cuComplex(-1.f, 0.f);
+  CIRC_BLAS(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)RR, nx, nx, &one, (const cuComplex*)C, (int)RR,
+                        (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->W, (int)RR));
+  // LU of the nx blocks
+  const int nb = c->nb;
+  for (int j0 = 0; j0 < R; j0 += nb) {
+    const int nbe = min(nb, R - j0), j1 = j0 + nbe;
+    const size_t smem = (size_t)(R - j0) * (nbe + 1) * sizeof(float2);
+    CIRC_TRY(cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    lu_panel_kernel<<<nx, 256, smem, s>>>(c->W, R, j0, nbe, piv, c->flag);
+    lu_swap_kernel<<<dim3(nx, (R + 255) / 256), 256, 0, s>>>(c->W, R, j0, nbe, piv);
+    CIRC_TRY(cudaGetLastError());
+    if (j1 < R) {
+      const dim3 tg(nx, (R - j1 + 255) / 256);
+      if (nb == 32) lu_trsm_kernel<32><<<tg, 256, 0, s>>>(c->W, R, j0);
+      else lu_trsm_kernel<16><<<tg, 256, 0, s>>>(c->W, R, j0);
+      CIRC_TRY(cudaGetLastError());
+      // A22 -= L21 U12 (row-major), i.e. column-major A22^T -= U12^T L21^T
+      CIRC_BLAS(cublasCgemmStridedBatched(
+          c->blas, CUBLAS_OP_N, CUBLAS_OP_N, R - j1, R - j1, nbe, &mone, (const cuComplex*)(c->W + (size_t)j0 * R + j1),
+          R, (long long)RR, (const cuComplex*)(c->W + (size_t)j1 * R + j0), R, (long long)RR, &one,
+          (cuComplex*)(c->W + (size_t)j1 * R + j1), R, (long long)RR, nx));
+    }
+  }
+  perm_kernel<<<(nx + 127) / 128, 128, 0, s>>>(piv, R, nx, c->perm);
+  CIRC_TRY(cudaGetLastError());
+  CIRC_TRY(cudaStreamSynchronize(s));
+  int flag = 0;
+  CIRC_TRY(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+  fail(VIE_OK);
+  Sp = Sm = C = nullptr;
+  piv = nullptr;
+  if (flag) {
+    set_error("block-circulant preconditioner: a diagonal block is singular");
+    st = VIE_ERR_NONFINITE;
+  }
+#undef CIRC_TRY
+#undef CIRC_BLAS
+  return st;
+}
+
+const vie_plan* circulant_plan(const vie_circulant* c) { return c->plan; }
+
+vie_status circulant_apply(vie_circulant* c, int dtype, const void* v, void* z, cudaStream_t s) {
+  if (c->gen != c->plan->contrast_gen) {
+    set_error("block-circulant preconditioner is stale: the plan's contrast changed after it was built");
+    return VIE_ERR_INVALID;
+  }
+  const int nx = c->nx, R = c->R;
+  const size_t N3 = (size_t)R * nx;
+  const float2* vin = (const float2*)v;
+  float2* zout = (float2*)z;
+  if (dtype == VIE_C128) {
+    to_c64_kernel<<<blocks_for(N3), 256, 0, s>>>((const double2*)v, c->v32, N3);
+    VIE_LAUNCH_CHECK();
+    vin = c->v32;
+    zout = c->z32;
+  }
+  VIE_CUBLAS_TRY(cublasSetStream(c->blas, s));
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  // V_hat[w][r] = sum_x F[w][x] v[r][x]
+  VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, R, nx, nx, &one, (const cuComplex*)vin, nx,
+                             (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->vh, R));
+  circ_solve_kernel<<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W, c->perm, c->vh, R);
+  VIE_LAUNCH_CHECK();
+  // z[r][x] = sum_w Fi[w][x] Z_hat[w][r]
+  VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, R, nx, &one, (const cuComplex*)c->Fi, nx,
+                             (const cuComplex*)c->vh, R, &zero, (cuComplex*)zout, nx));
+  if (dtype == VIE_C128) {
+    to_c128_kernel<<<blocks_for(N3), 256, 0, s>>>(c->z32, (double2*)z, N3);
+    VIE_LAUNCH_CHECK();
+  }
+  return VIE_OK;
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+extern "C" {
+
+vie_status vie_circulant_create(vie_plan* plan, vie_circulant** out, void* stream) {
+  clear_error();
+  if (!plan || !out) { set_error("null argument"); return VIE_ERR_INVALID; }
+  *out = nullptr;
+  if (!plan->M64) { set_error("set the plan's contrast before building its circulant preconditioner"); return VIE_ERR_INVALID; }
+  const auto t0 = std::chrono::steady_clock::now();
+  vie_circulant* c = new vie_circulant();
+  c->plan = plan;
+  c->gen = plan->contrast_gen;
+  c->nx = plan->n[0];
+  c->ny = plan->n[1];
+  c->nz = plan->n[2];
+  c->B = c->ny * c->nz;
+  c->R = 3 * c->B;
+  // the panel (R rows x nb columns) must fit in shared memory
+  const size_t budget = 220 * 1024;
+  c->nb = (size_t)c->R * 33 * sizeof(float2) <= budget ? 32 : 16;
+  if ((size_t)c->R * 17 * sizeof(float2) > budget) {
+    set_error("cross-section of %d unknowns is too large for the block-circulant preconditioner", c->R);
+    delete c;
+    return VIE_ERR_INVALID;
+  }
+  if ((size_t)c->R * c->R > (size_t)0x7fffffff) {
+    set_error("cross-section too large for the block-circulant preconditioner");
+    delete c;
+    return VIE_ERR_INVALID;
+  }
+  VIE_CUDA_TRY(cudaGetDevice(&c->device));
+  if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
+    set_error("cublasCreate failed");
+    delete c;
+    return VIE_ERR_CUDA;
+  }
+  vie_status st = circ_build(c, (cudaStream_t)stream);
+  if (st != VIE_OK) {
+    circ_free(c);
+    return st;
+  }
+  c->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return VIE_OK;
+}
+
+vie_status vie_circulant_apply(vie_circulant* c, const void* v_dev, void* z_dev, int dtype, void* stream) {
+  clear_error();
+  if (!c || !v_dev || !z_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
+  return circulant_apply(c, dtype, v_dev, z_dev, (cudaStream_t)stream);
+}
+
+vie_status vie_circulant_info(const vie_circulant* c, double* build_ms, size_t* device_bytes) {
+  clear_error();
+  if (!c) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (build_ms) *build_ms = c->build_ms;
+  if (device_bytes)
+    *device_bytes = (size_t)c->nx * c->R * c->R * sizeof(float2) + (size_t)c->nx * c->R * (sizeof(int) + sizeof(float2)) +
+                    (size_t)2 * c->nx * c->nx * sizeof(float2) + (size_t)2 * c->nx * c->R * sizeof(float2);
+  return VIE_OK;
+}
+
+vie_status vie_circulant_destroy(vie_circulant* c) {
+  circ_free(c);
+  return VIE_OK;
+}
+
+}  // extern "C"

@@ -762,13 +762,17 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
   return conv(OUTL, sizeof(V) == 8 ? TC_UNPACK_C64 : TC_UNPACK_C128, nullptr, nullptr, -1, nullptr);
 }
 
+// The preconditioner set on a plan: a network (learned) or a block-circulant
+// matrix (Sec. 6); exactly one of net and circ is set.
 struct PrecondCtx {
   vie_net* net;
   const vie_plan* plan;
+  vie_circulant* circ;
 };
 
 static vie_status precond_apply(void* ctx, int dtype, const void* v, void* z, cudaStream_t s) {
   PrecondCtx* c = (PrecondCtx*)ctx;
+  if (c->circ) return circulant_apply(c->circ, dtype, v, z, s);
   if (dtype == VIE_C64) return net_apply_t<float2>(c->net, c->plan, (const float2*)v, (float2*)z, s);
   return net_apply_t<double2>(c->net, c->plan, (const double2*)v, (double2*)z, s);
 }
@@ -795,6 +799,7 @@ vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx) {
 int precond_fallback_flag(vie_plan* p, int clear) {
   if (!p || !p->precond) return 0;
   PrecondCtx* c = (PrecondCtx*)p->precond;
+  if (!c->net) return 0;
   int h = 0;
   cudaMemcpy(&h, c->net->bad, sizeof(int), cudaMemcpyDeviceToHost);
   if (clear && h) cudaMemset(c->net->bad, 0, sizeof(int));
@@ -901,7 +906,7 @@ vie_status vie_net_apply(vie_net* n, const vie_plan* p, const void* v_dev, void*
   clear_error();
   if (!n || !p || !v_dev || !z_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
   if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
-  PrecondCtx c{n, p};
+  PrecondCtx c{n, p, nullptr};
   return precond_apply(&c, dtype, v_dev, z_dev, (cudaStream_t)stream);
 }
 
@@ -970,7 +975,20 @@ vie_status vie_set_preconditioner(vie_plan* p, vie_net* n) {
   clear_error();
   if (!p) { set_error("null plan"); return VIE_ERR_INVALID; }
   free_precond(p);
-  if (n) p->precond = new PrecondCtx{n, p};
+  if (n) p->precond = new PrecondCtx{n, p, nullptr};
+  return VIE_OK;
+}
+
+vie_status vie_set_circulant_preconditioner(vie_plan* p, vie_circulant* c) {
+  clear_error();
+  if (!p) { set_error("null plan"); return VIE_ERR_INVALID; }
+  if (c && circulant_plan(c) != p) {
+    // the factors depend on the grid and contrast of the plan they were built for
+    set_error("the block-circulant preconditioner belongs to another plan");
+    return VIE_ERR_INVALID;
+  }
+  free_precond(p);
+  if (c) p->precond = new PrecondCtx{nullptr, p, c};
   return VIE_OK;
 }
 

@@ -146,7 +146,8 @@ struct vie_plan {
   double setup_ms = 0.0;
   int* shared_refs = nullptr; // plans made by vie_plan_clone share entries, spectra and twiddles
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
-  void* precond = nullptr;    // learned preconditioner state, if set
+  void* precond = nullptr;    // preconditioner state (learned or block-circulant), if set
+  int contrast_gen = 0;       // incremented whenever the contrast is set
 };
 
 namespace vie {
@@ -165,6 +166,8 @@ void free_krylov(vie_plan* p);
 void free_precond(vie_plan* p);
 vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx);
 int precond_fallback_flag(vie_plan* p, int clear);   // non-finite network output seen
+vie_status circulant_apply(vie_circulant* c, int dtype, const void* v, void* z, cudaStream_t s);
+const vie_plan* circulant_plan(const vie_circulant* c);
 
 // Operator application for `count` plans of one shape (same n and m);
 // x[i], y[i] are device vectors of dtype; each plan's own workspace is used.

@@ -85,6 +85,11 @@ _SIGNATURES = {
     "vie_net_zero_grad": ([_P], _I),
     "vie_net_adam_step": ([_P, ctypes.c_float, ctypes.c_float, _P], _I),
     "vie_net_status": ([_P, ctypes.POINTER(_I), _I], _I),
+    "vie_circulant_create": ([_P, ctypes.POINTER(_P), _P], _I),
+    "vie_circulant_apply": ([_P, _P, _P, _I, _P], _I),
+    "vie_circulant_info": ([_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)], _I),
+    "vie_circulant_destroy": ([_P], _I),
+    "vie_set_circulant_preconditioner": ([_P, _P], _I),
     "vie_set_preconditioner": ([_P, _P], _I),
     "vie_plan_clone": ([_P, ctypes.POINTER(_P)], _I),
     "vie_matvec_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P], _I),
@@ -348,6 +353,56 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+class Circulant:
+    """Owns a vie_circulant* (block-circulant preconditioner of a plan)."""
+
+    def __init__(self, handle, plan):
+        self.handle = handle
+        self.plan = plan          # keeps the plan alive while the factors exist
+
+    def close(self):
+        if self.handle:
+            load().vie_circulant_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vie_circulant_create(plan: Plan, stream=None) -> Circulant:
+    h = ctypes.c_void_p()
+    _check(load().vie_circulant_create(plan.handle, ctypes.byref(h), _stream_handle(stream)), "vie_circulant_create")
+    return Circulant(h, plan)
+
+
+def vie_circulant_apply(c: Circulant, v, z, stream=None):
+    if not (v.is_cuda and z.is_cuda and v.dtype == z.dtype and v.numel() == 3 * c.plan.n_vox == z.numel()):
+        raise ValueError("v and z must be CUDA vectors of 3*nx*ny*nz entries of one dtype")
+    _check(load().vie_circulant_apply(c.handle, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                      _dtype_code(v), _stream_handle(stream)), "vie_circulant_apply")
+    return z
+
+
+def vie_circulant_info(c: Circulant) -> dict:
+    ms = ctypes.c_double()
+    nbytes = ctypes.c_size_t()
+    _check(load().vie_circulant_info(c.handle, ctypes.byref(ms), ctypes.byref(nbytes)), "vie_circulant_info")
+    return {"build_ms": ms.value, "device_bytes": nbytes.value}
+
+
+def vie_circulant_destroy(c: Circulant):
+    c.close()
+
+
+def vie_set_circulant_preconditioner(plan: Plan, c: Circulant | None):
+    _check(load().vie_set_circulant_preconditioner(plan.handle, c.handle if c is not None else None),
+           "vie_set_circulant_preconditioner")
+    plan._net = c        # keep the preconditioner alive while it is set
 
 
 def vie_net_param_count() -> int:
