@@ -574,6 +574,28 @@ def profile_net(reps: int):
     print(json.dumps({"profile_net": reps, **out}))
 
 
+def profile_circulant(reps: int):
+    """One block-circulant build and `reps` applications on the benchmark
+    guide: a short, fixed launch sequence for kernel launch lists."""
+    import torch
+
+    from paper_1803_06237_gb300 import build, learned, vie, workloads
+    build.build_library()
+    vie.load()
+    plan, b = learned.setup_problem(workloads.waveguide())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = vie.vie_circulant_create(plan)
+    torch.cuda.synchronize()
+    setup = (time.perf_counter() - t0) * 1e3
+    v = torch.randn(b.numel(), dtype=torch.complex64, device="cuda")
+    z = torch.empty_like(v)
+    for _ in range(reps):
+        vie.vie_circulant_apply(c, v, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_circulant": reps, "setup_ms": setup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,6 +611,8 @@ def main():
     ap.add_argument("--restart-mixed", type=int, default=30)
     ap.add_argument("--train-problems", type=int, default=30)
     ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--profile-circulant", type=int, default=0,
+                    help="only build the block-circulant preconditioner and apply it (for kernel launch lists)")
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
@@ -602,6 +626,9 @@ def main():
         return
     if args.profile_net:
         profile_net(args.profile_net)
+        return
+    if args.profile_circulant:
+        profile_circulant(args.profile_circulant)
         return
     if args.warmup < 3:
         args.warmup = 3

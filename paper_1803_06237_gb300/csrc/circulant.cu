@@ -10,9 +10,11 @@
 // block-diagonalises W: W_hat(w) = sum_k c_k exp(-2 pi i w k / nx).
 //
 // Setup (once per plan and contrast):
-//   1. prefix sums of M along x (FP64), 2. the blocks c_k (complex64),
-//   3. W_hat = F C with the nx x nx DFT matrix F (a plain batched-free
-//      CGEMM over all (3B)^2 entries: nx need not be 5-smooth),
+//   1. prefix sums of M along x (FP64),
+//   2. W_hat: when nx has only the factors 2, 3, 5, the blocks c_k of 16
+//      entries at a time are formed in shared memory and transformed along k
+//      by a Stockham FFT; otherwise the blocks are stored and W_hat = F C is
+//      one CGEMM with the nx x nx DFT matrix F,
 //   4. LU with partial pivoting of the nx blocks W_hat(w): panels of nb
 //      columns factored in shared memory, row swaps, a triangular solve for
 //      the U row block, and the trailing update as a strided-batched CGEMM.
@@ -30,6 +32,7 @@
 
 #include <chrono>
 
+#include "fft.cuh"
 #include "vie_internal.cuh"
 
 struct vie_circulant {
@@ -72,7 +75,7 @@ __device__ __forceinline__ float2 csub_mul(float2 acc, float2 a, float2 b) {
 // ---------------------------------------------------------------------------
 // setup kernels
 // ---------------------------------------------------------------------------
-// S+[k][zy] = (1/nx) sum_{i >= k} M[zy][i], S-[k][zy] = (1/nx) sum_{i < k} M[zy][i]
+// S+[zy][k] = (1/nx) sum_{i >= k} M[zy][i], S-[zy][k] = (1/nx) sum_{i < k} M[zy][i]
 __global__ void prefix_kernel(const double2* __restrict__ M, int nx, int B, float2* __restrict__ Sp,
                               float2* __restrict__ Sm) {
   const int zy = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,8 +89,8 @@ __global__ void prefix_kernel(const double2* __restrict__ M, int nx, int B, floa
   double lx = 0.0, ly = 0.0;   // sum over i < k
   const double inv = 1.0 / nx;
   for (int k = 0; k < nx; ++k) {
-    Sm[(size_t)k * B + zy] = make_float2((float)(lx * inv), (float)(ly * inv));
-    Sp[(size_t)k * B + zy] = make_float2((float)((tx - lx) * inv), (float)((ty - ly) * inv));
+    Sm[(size_t)zy * nx + k] = make_float2((float)(lx * inv), (float)(ly * inv));
+    Sp[(size_t)zy * nx + k] = make_float2((float)((tx - lx) * inv), (float)((ty - ly) * inv));
     lx += row[k].x;
     ly += row[k].y;
   }
@@ -129,8 +132,8 @@ __global__ void build_blocks_kernel(const double2* __restrict__ T, const float2*
     const int p = r / B, zy = r % B, z = zy / ny, y = zy % ny;
     const int q = s / B, zy2 = s % B, z2 = zy2 / ny, y2 = zy2 % ny;
     float2 out = make_float2((k == 0 && r == s) ? 1.f : 0.f, 0.f);
-    out = csub_mul(out, Sp[(size_t)k * B + zy], toeplitz_at(T, nx, ny, nz, p, q, k, y - y2, z - z2));
-    if (k > 0) out = csub_mul(out, Sm[(size_t)k * B + zy], toeplitz_at(T, nx, ny, nz, p, q, k - nx, y - y2, z - z2));
+    out = csub_mul(out, Sp[(size_t)zy * nx + k], toeplitz_at(T, nx, ny, nz, p, q, k, y - y2, z - z2));
+    if (k > 0) out = csub_mul(out, Sm[(size_t)zy * nx + k], toeplitz_at(T, nx, ny, nz, p, q, k - nx, y - y2, z - z2));
     C[idx] = out;
   }
 }
@@ -148,6 +151,81 @@ __global__ void dft_matrix_kernel(int nx, float2* __restrict__ F, float2* __rest
     F[idx] = make_float2((float)cs, (float)-sn);
     Fi[idx] = make_float2((float)(cs / nx), (float)(sn / nx));
   }
+}
+
+// W_hat[w][e] for kTL consecutive entries e = r R + s at once, when nx has
+// only the factors 2, 3, 5: c_k[e] for every k is formed in shared memory
+// and transformed along k by the Stockham FFT, so the blocks c_k are never
+// stored.  tw = exp(-2 pi i k / nx).
+constexpr int kTL = 16;
+__global__ void __launch_bounds__(256) build_fft_kernel(const double2* __restrict__ T, const float2* __restrict__ Sp,
+                                                        const float2* __restrict__ Sm, int nx, int ny, int nz,
+                                                        Radices rd, const float2* __restrict__ twg,
+                                                        float2* __restrict__ What) {
+  extern __shared__ float2 sb[];
+  __shared__ const double2* tline[kTL];
+  __shared__ float sgn_yz[kTL], sgn_neg[kTL];
+  __shared__ int zyrow[kTL], diag[kTL];
+  const int B = ny * nz, R = 3 * B;
+  const long long RR = (long long)R * R;
+  const int pitch = nx + 1;
+  float2* tw = sb;
+  float2* A = tw + nx;
+  float2* Bf = A + kTL * pitch;
+  const long long e0 = (long long)blockIdx.x * kTL;
+  const int nl = (int)min((long long)kTL, RR - e0);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < nx; i += nth) tw[i] = twg[i];
+  if (tid < nl) {
+    const long long e = e0 + tid;
+    const int r = (int)(e / R), s2 = (int)(e % R);
+    const int p = r / B, zy = r % B, z = zy / ny, y = zy % ny;
+    const int q = s2 / B, zy2 = s2 % B, z2 = zy2 / ny, y2 = zy2 % ny;
+    const int dy = y - y2, dz = z - z2;
+    const int c = comp_of(p, q);
+    float sg = 1.f, sx = 1.f;
+    if (p != q) {
+      // odd in the axes of both components: y (1) and z (2) here, x (0) for the negative offsets k - nx
+      if ((p == 1 || q == 1) && dy < 0) sg = -sg;
+      if ((p == 2 || q == 2) && dz < 0) sg = -sg;
+      if (p == 0 || q == 0) sx = -1.f;
+    }
+    tline[tid] = T + (((size_t)c * nz + abs(dz)) * ny + abs(dy)) * nx;
+    sgn_yz[tid] = sg;
+    sgn_neg[tid] = sg * sx;
+    zyrow[tid] = zy;
+    diag[tid] = (r == s2);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nl * nx; idx += nth) {
+    const int l = idx / nx, k = idx - l * nx;
+    const double2* tl = tline[l];
+    const double2 tp = tl[k];
+    float2 out = make_float2((k == 0 && diag[l]) ? 1.f : 0.f, 0.f);
+    const float2 sp = Sp[(size_t)zyrow[l] * nx + k];
+    out = csub_mul(out, sp, make_float2(sgn_yz[l] * (float)tp.x, sgn_yz[l] * (float)tp.y));
+    if (k > 0) {
+      const double2 tn = tl[nx - k];
+      const float2 sm = Sm[(size_t)zyrow[l] * nx + k];
+      out = csub_mul(out, sm, make_float2(sgn_neg[l] * (float)tn.x, sgn_neg[l] * (float)tn.y));
+    }
+    A[l * pitch + k] = out;
+  }
+  for (int idx = nl * nx + tid; idx < kTL * nx; idx += nth) A[(idx / nx) * pitch + idx % nx] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* res = fft_lines<float2, false>(A, Bf, rd, pitch, kTL, tw, tid, nth);
+  for (int idx = tid; idx < nx * kTL; idx += nth) {
+    const int w = idx / kTL, l = idx - w * kTL;
+    if (l < nl) What[(size_t)w * RR + e0 + l] = res[l * pitch + w];
+  }
+}
+
+__global__ void twiddle_kernel(int nx, float2* __restrict__ tw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx) return;
+  double sn, cs;
+  sincospi(2.0 * (double)k / (double)nx, &sn, &cs);
+  tw[k] = make_float2((float)cs, (float)-sn);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,10 +368,50 @@ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
   return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// x = P b (gather), then L y = x in blocks of 32 rows (the rows' products
-// with the solved part by 8 warps, the 32 x 32 unit-lower diagonal block by
-// warp 0 with shuffles), then U z = y likewise from the bottom.
-__global__ void __launch_bounds__(256) circ_solve_kernel(const float2* __restrict__ W, const int* __restrict__ perm,
+// Rows i0 .. i0 + nr - 1 of A times x over the columns [c0, c1), subtracted
+// from x: 8 threads per row (256 threads = 32 rows), each over the columns
+// c0 + sub + 8 u, sixteen independent loads in flight per thread; the eight
+// partial sums of a row are combined with shuffles.
+__device__ __forceinline__ void block_row_update(const float2* __restrict__ A, int R, int i0, int nr, int c0,
+                                                 int c1, float2* __restrict__ x) {
+  const int a = threadIdx.x >> 3, sub = threadIdx.x & 7;
+  float sx = 0.f, sy = 0.f;
+  if (a < nr) {
+    const float2* row = A + (size_t)(i0 + a) * R;
+    int t = c0 + sub;
+    for (; t + 8 * 15 < c1; t += 8 * 16) {
+      float2 l[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) l[u] = row[t + 8 * u];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float2 xt = x[t + 8 * u];
+        sx += l[u].x * xt.x - l[u].y * xt.y;
+        sy += l[u].x * xt.y + l[u].y * xt.x;
+      }
+    }
+    for (; t < c1; t += 8) {
+      const float2 l = row[t], xt = x[t];
+      sx += l.x * xt.x - l.y * xt.y;
+      sy += l.x * xt.y + l.y * xt.x;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (a < nr && sub == 0) {
+    x[i0 + a].x -= sx;
+    x[i0 + a].y -= sy;
+  }
+}
+
+// x = P b (gather), then L y = x in blocks of 32 rows (the block row's
+// products with the solved part by all threads, the 32 x 32 unit-lower
+// diagonal block by warp 0 with shuffles), then U z = y likewise from the
+// bottom.  256 threads.
+__global__ void __launch_bounds__(256, 4) circ_solve_kernel(const float2* __restrict__ W, const int* __restrict__ perm,
                                                          float2* __restrict__ vh, int R) {
   extern __shared__ float2 x[];
   __shared__ float2 D[32][33];
@@ -311,24 +429,7 @@ __global__ void __launch_bounds__(256) circ_solve_kernel(const float2* __restric
       const int a = e >> 5, t = e & 31;
       if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
     }
-    for (int a = wid; a < nr; a += 8) {
-      const float2* row = A + (size_t)(i0 + a) * R;
-      float sx = 0.f, sy = 0.f;
-#pragma unroll 4
-      for (int t = lane; t < i0; t += 32) {
-        const float2 l = row[t], xt = x[t];
-        sx += l.x * xt.x - l.y * xt.y;
-        sy += l.x * xt.y + l.y * xt.x;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_down_sync(0xffffffffu, sx, o);
-        sy += __shfl_down_sync(0xffffffffu, sy, o);
-      }
-      if (lane == 0) {
-        x[i0 + a].x -= sx;
-        x[i0 + a].y -= sy;
-      }
-    }
+    block_row_update(A, R, i0, nr, 0, i0, x);
     __syncthreads();
     if (wid == 0) {
       float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
@@ -347,24 +448,7 @@ __global__ void __launch_bounds__(256) circ_solve_kernel(const float2* __restric
       const int a = e >> 5, t = e & 31;
       if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
     }
-    for (int a = wid; a < nr; a += 8) {
-      const float2* row = A + (size_t)(i0 + a) * R;
-      float sx = 0.f, sy = 0.f;
-#pragma unroll 4
-      for (int t = i1 + lane; t < R; t += 32) {
-        const float2 u = row[t], xt = x[t];
-        sx += u.x * xt.x - u.y * xt.y;
-        sy += u.x * xt.y + u.y * xt.x;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_down_sync(0xffffffffu, sx, o);
-        sy += __shfl_down_sync(0xffffffffu, sy, o);
-      }
-      if (lane == 0) {
-        x[i0 + a].x -= sx;
-        x[i0 + a].y -= sy;
-      }
-    }
+    block_row_update(A, R, i0, nr, i1, R, x);
     __syncthreads();
     if (wid == 0) {
       float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
@@ -431,7 +515,6 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
   } while (0)
   CIRC_TRY(cudaMalloc((void**)&Sp, (size_t)nx * B * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&Sm, (size_t)nx * B * sizeof(float2)));
-  CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * RR * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&piv, (size_t)nx * R * sizeof(int)));
   CIRC_TRY(cudaMalloc((void**)&c->W, (size_t)nx * RR * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->perm, (size_t)nx * R * sizeof(int)));
@@ -445,13 +528,29 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
   CIRC_BLAS(cublasSetStream(c->blas, s));
 
   prefix_kernel<<<(B + 127) / 128, 128, 0, s>>>(p->M64, nx, B, Sp, Sm);
-  build_blocks_kernel<<<152 * 16, 256, 0, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz, C);
   dft_matrix_kernel<<<blocks_for((size_t)nx * nx), 256, 0, s>>>(nx, c->F, c->Fi);
   CIRC_TRY(cudaGetLastError());
-  // W_hat[w][e] = sum_k F[w][k] C[k][e]: column-major W_hat^T (RR x nx) = C^T (RR x nx) F (F symmetric)
   const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f), mone = make_cuComplex(-1.f, 0.f);
-  CIRC_BLAS(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)RR, nx, nx, &one, (const cuComplex*)C, (int)RR,
-                        (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->W, (int)RR));
+  AxisPlan ax;
+  const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * kTL * (nx + 1) * sizeof(float2);
+  if (factor_length(nx, &ax) && fft_smem <= 200 * 1024) {
+    // blocks formed and transformed along x in shared memory
+    CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * sizeof(float2)));   // here C holds only the twiddles
+    float2* tw = C;
+    twiddle_kernel<<<(nx + 127) / 128, 128, 0, s>>>(nx, tw);
+    CIRC_TRY(cudaFuncSetAttribute(build_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+    build_fft_kernel<<<(unsigned)((RR + kTL - 1) / kTL), 256, fft_smem, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz,
+                                                                             radices_of(ax), tw, c->W);
+    CIRC_TRY(cudaGetLastError());
+  } else {
+    // any nx: the blocks, then W_hat[w][e] = sum_k F[w][k] C[k][e] as one CGEMM
+    // (column-major W_hat^T (RR x nx) = C^T (RR x nx) F, F symmetric)
+    CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * RR * sizeof(float2)));
+    build_blocks_kernel<<<152 * 16, 256, 0, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz, C);
+    CIRC_TRY(cudaGetLastError());
+    CIRC_BLAS(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)RR, nx, nx, &one, (const cuComplex*)C, (int)RR,
+                          (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->W, (int)RR));
+  }
   // LU of the nx blocks
   const int nb = c->nb;
   for (int j0 = 0; j0 < R; j0 += nb) {
