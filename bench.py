@@ -388,15 +388,18 @@ def solve_section(plan, wl, absorbers, args):
     if args.circulant:
         out["circulant"] = circulant_section(plan, b, args)
         out["mixed_circulant"] = out["circulant"].pop("solve")
+        out["circulant_fp16"] = circulant_section(plan, b, args, fp16=True)
+        out["mixed_circulant_fp16"] = out["circulant_fp16"].pop("solve")
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     if "mixed_learned" in out:
         out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms"] / out["mixed_learned"]["ms"]
     if "mixed_circulant" in out:
         out["speedup_mixed_circulant_vs_fp64"] = out["fp64"]["ms"] / out["mixed_circulant"]["ms"]
+        out["speedup_mixed_circulant_fp16_vs_fp64"] = out["fp64"]["ms"] / out["mixed_circulant_fp16"]["ms"]
     return out
 
 
-def circulant_section(plan, b, args, reps=20):
+def circulant_section(plan, b, args, reps=20, fp16=False):
     """The block-circulant preconditioner (Sec. 6) on the benchmark guide:
     setup (blocks, DFT along x, batched LU) timed on the host clock, the
     application timed with CUDA events against the HBM roofline (it streams
@@ -407,7 +410,7 @@ def circulant_section(plan, b, args, reps=20):
     from paper_1803_06237_gb300 import vie
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    c = vie.vie_circulant_create(plan)
+    c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = vie.vie_circulant_info(c)
@@ -426,7 +429,7 @@ def circulant_section(plan, b, args, reps=20):
     ms = e0.elapsed_time(e1) / reps
     nx, ny, nz = plan.n
     R = 3 * ny * nz
-    factor_bytes = nx * R * R * 8
+    factor_bytes = nx * R * R * (4 if fp16 else 8)
     hbm_peak, kind = _peaks()
     achieved = factor_bytes / (ms * 1e-3) / 1e9
     vie.vie_set_circulant_preconditioner(plan, c)
@@ -439,7 +442,8 @@ def circulant_section(plan, b, args, reps=20):
             "apply_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                                "frac": achieved / hbm_peak, "peak_source": kind,
                                "algorithmic_bytes": factor_bytes,
-                               "note": "LU factors of the nx blocks (complex64) read once per application"},
+                               "note": "LU factors of the nx blocks (%s) read once per application"
+                                       % ("complex half" if fp16 else "complex64")},
             "solve": solve}
 
 

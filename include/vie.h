@@ -290,6 +290,11 @@ vie_status vie_net_status(vie_net* net, int* flag, int clear);
 /* ------------------------------------------------------------------------ */
 typedef struct vie_circulant vie_circulant;
 
+/* Flags of vie_circulant_create. */
+#define VIE_CIRC_DEFAULT 0
+#define VIE_CIRC_FP16_FACTORS 1   /* keep the LU factors in complex half precision (half the memory and
+                                     half the bytes per application; the factorisation itself is complex64) */
+
 /* Build W from the plan's current Toeplitz entries and contrast (the plan's
  * contrast must have been set) and factor it; synchronises `stream`.  The
  * preconditioner keeps a pointer to the plan: destroy it before the plan.
@@ -297,10 +302,11 @@ typedef struct vie_circulant vie_circulant;
  * VIE_ERR_INVALID (stale).  Errors: VIE_ERR_INVALID (no contrast, cross
  * section above ~1600 unknowns), VIE_ERR_OOM, VIE_ERR_CUDA,
  * VIE_ERR_NONFINITE (a singular block). */
-vie_status vie_circulant_create(vie_plan* plan, vie_circulant** out, void* stream);
+vie_status vie_circulant_create(vie_plan* plan, int flags, vie_circulant** out, void* stream);
 
 /* z = W^{-1} v for device vectors of 3*nx*ny*nz entries of dtype (VIE_C64
- * or VIE_C128; computed in complex64 either way), not overlapping.
+ * or VIE_C128; computed in complex64 either way, with complex-half factors
+ * if built with VIE_CIRC_FP16_FACTORS), not overlapping.
  * Asynchronous on `stream`. */
 vie_status vie_circulant_apply(vie_circulant* c, const void* v_dev, void* z_dev, int dtype, void* stream);
 

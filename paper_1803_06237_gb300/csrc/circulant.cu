@@ -19,14 +19,15 @@
 //      columns factored in shared memory, row swaps, a triangular solve for
 //      the U row block, and the trailing update as a strided-batched CGEMM.
 // Application z = W^{-1} v (complex64):
-//   V_hat = F V (CGEMM), one pivoted forward and backward substitution per
-//   frequency (one CTA each, the factor streamed once from HBM), then
-//   z = F^H Z_hat / nx (CGEMM).  The vectors' planar layout [p][z][y][x] is
+//   V_hat = F V (an FFT along x for 5-smooth nx, else a CGEMM), one pivoted
+//   forward and backward substitution per frequency (one CTA each, the
+//   factor streamed once from HBM), then z = F^H Z_hat / nx (likewise).  The vectors' planar layout [p][z][y][x] is
 //   already the (3B) x nx matrix the transforms need.
 //
 // The plain GEMMs (the DFTs along x and the trailing LU updates) go to
 // cuBLAS; everything else is in this file.
 #include <cublas_v2.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -41,6 +42,8 @@ struct vie_circulant {
   int gen = 0;                 // contrast generation the factors were built from
   int nx = 0, ny = 0, nz = 0, B = 0, R = 0, nb = 32;
   float2* W = nullptr;         // nx x R x R: LU factors (unit L below, U on and above the diagonal)
+  __half2* W16 = nullptr;      // the same in complex half precision (VIE_CIRC_FP16_FACTORS; W is then freed)
+  bool fp16 = false;
   int* perm = nullptr;         // nx x R: row r of P b is b[perm[r]]
   float2* F = nullptr;         // nx x nx: exp(-2 pi i w k / nx)
   float2* Fi = nullptr;        // nx x nx: exp(+2 pi i w k / nx) / nx
@@ -48,6 +51,8 @@ struct vie_circulant {
   float2* v32 = nullptr;       // 3N scratch for complex128 callers
   float2* z32 = nullptr;
   int* flag = nullptr;         // 1: a zero pivot was met
+  float2* tw = nullptr;        // nx twiddles exp(-2 pi i k / nx) when nx has only the factors 2, 3, 5
+  vie::Radices rd;             //   and its radices: the DFTs along x are then FFTs
   cublasHandle_t blas = nullptr;
   double build_ms = 0.0;
 };
@@ -228,6 +233,41 @@ __global__ void twiddle_kernel(int nx, float2* __restrict__ tw) {
   tw[k] = make_float2((float)cs, (float)-sn);
 }
 
+// DFTs along x of the application as FFTs (nx with factors 2, 3, 5 only),
+// kLines rows per block.  Forward: vh[w][r] = sum_x v[r][x] exp(-2 pi i w x /
+// nx); inverse: z[r][x] = (1/nx) sum_w vh[w][r] exp(+2 pi i w x / nx).
+constexpr int kLines = 4;
+template <bool INV>
+__global__ void __launch_bounds__(256) lines_fft_kernel(const float2* __restrict__ in, float2* __restrict__ out, int R,
+                                                        int nx, Radices rd, const float2* __restrict__ twg) {
+  extern __shared__ float2 sb[];
+  const int pitch = nx + 1;
+  float2* tw = sb;
+  float2* A = tw + nx;
+  float2* Bf = A + kLines * pitch;
+  const int r0 = blockIdx.x * kLines, nl = min(kLines, R - r0);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < nx; i += nth) tw[i] = twg[i];
+  for (int idx = tid; idx < kLines * nx; idx += nth) {
+    int l, k;
+    if (INV) { k = idx / kLines; l = idx - k * kLines; } else { l = idx / nx; k = idx - l * nx; }
+    float2 v = make_float2(0.f, 0.f);
+    if (l < nl) v = INV ? in[(size_t)k * R + r0 + l] : in[(size_t)(r0 + l) * nx + k];
+    A[l * pitch + k] = v;
+  }
+  __syncthreads();
+  const float2* res = fft_lines<float2, INV>(A, Bf, rd, pitch, kLines, tw, tid, nth);
+  const float inv = 1.f / (float)nx;
+  for (int idx = tid; idx < kLines * nx; idx += nth) {
+    int l, k;
+    if (INV) { l = idx / nx; k = idx - l * nx; } else { k = idx / kLines; l = idx - k * kLines; }
+    if (l >= nl) continue;
+    const float2 v = res[l * pitch + k];
+    if (INV) out[(size_t)(r0 + l) * nx + k] = make_float2(v.x * inv, v.y * inv);
+    else out[(size_t)k * R + r0 + l] = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // batched LU with partial pivoting (row-major blocks, one matrix per CTA)
 // ---------------------------------------------------------------------------
@@ -370,28 +410,35 @@ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
 
 // Rows i0 .. i0 + nr - 1 of A times x over the columns [c0, c1), subtracted
 // from x: 8 threads per row (256 threads = 32 rows), each over the columns
-// c0 + sub + 8 u, sixteen independent loads in flight per thread; the eight
+// c0 + sub + 8 u, 16 (complex64) or 32 (complex half) independent loads in
+// flight per thread; the eight
 // partial sums of a row are combined with shuffles.
-__device__ __forceinline__ void block_row_update(const float2* __restrict__ A, int R, int i0, int nr, int c0,
+__device__ __forceinline__ float2 ld_factor(const float2* p) { return *p; }
+__device__ __forceinline__ float2 ld_factor(const __half2* p) { return __half22float2(*p); }
+
+template <typename T>
+__device__ __forceinline__ void block_row_update(const T* __restrict__ A, int R, int i0, int nr, int c0,
                                                  int c1, float2* __restrict__ x) {
   const int a = threadIdx.x >> 3, sub = threadIdx.x & 7;
   float sx = 0.f, sy = 0.f;
   if (a < nr) {
-    const float2* row = A + (size_t)(i0 + a) * R;
+    // loads in flight per thread: 16 complex64 or 32 complex-half factors
+    constexpr int U = sizeof(T) == 4 ? 32 : 16;
+    const T* row = A + (size_t)(i0 + a) * R;
     int t = c0 + sub;
-    for (; t + 8 * 15 < c1; t += 8 * 16) {
-      float2 l[16];
+    for (; t + 8 * (U - 1) < c1; t += 8 * U) {
+      float2 l[U];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) l[u] = row[t + 8 * u];
+      for (int u = 0; u < U; ++u) l[u] = ld_factor(row + t + 8 * u);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < U; ++u) {
         const float2 xt = x[t + 8 * u];
         sx += l[u].x * xt.x - l[u].y * xt.y;
         sy += l[u].x * xt.y + l[u].y * xt.x;
       }
     }
     for (; t < c1; t += 8) {
-      const float2 l = row[t], xt = x[t];
+      const float2 l = ld_factor(row + t), xt = x[t];
       sx += l.x * xt.x - l.y * xt.y;
       sy += l.x * xt.y + l.y * xt.x;
     }
@@ -411,11 +458,12 @@ __device__ __forceinline__ void block_row_update(const float2* __restrict__ A, i
 // products with the solved part by all threads, the 32 x 32 unit-lower
 // diagonal block by warp 0 with shuffles), then U z = y likewise from the
 // bottom.  256 threads.
-__global__ void __launch_bounds__(256, 4) circ_solve_kernel(const float2* __restrict__ W, const int* __restrict__ perm,
+template <typename T>
+__global__ void __launch_bounds__(256, 4) circ_solve_kernel(const T* __restrict__ W, const int* __restrict__ perm,
                                                          float2* __restrict__ vh, int R) {
   extern __shared__ float2 x[];
   __shared__ float2 D[32][33];
-  const float2* A = W + (size_t)blockIdx.x * R * R;
+  const T* A = W + (size_t)blockIdx.x * R * R;
   const int* pm = perm + (size_t)blockIdx.x * R;
   float2* b = vh + (size_t)blockIdx.x * R;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -427,7 +475,7 @@ __global__ void __launch_bounds__(256, 4) circ_solve_kernel(const float2* __rest
     const int i0 = bk * 32, nr = min(32, R - i0);
     for (int e = tid; e < nr * 32; e += blockDim.x) {
       const int a = e >> 5, t = e & 31;
-      if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
+      if (t < nr) D[a][t] = ld_factor(A + (size_t)(i0 + a) * R + i0 + t);
     }
     block_row_update(A, R, i0, nr, 0, i0, x);
     __syncthreads();
@@ -446,7 +494,7 @@ __global__ void __launch_bounds__(256, 4) circ_solve_kernel(const float2* __rest
     const int i0 = bk * 32, nr = min(32, R - i0), i1 = i0 + nr;
     for (int e = tid; e < nr * 32; e += blockDim.x) {
       const int a = e >> 5, t = e & 31;
-      if (t < nr) D[a][t] = A[(size_t)(i0 + a) * R + i0 + t];
+      if (t < nr) D[a][t] = ld_factor(A + (size_t)(i0 + a) * R + i0 + t);
     }
     block_row_update(A, R, i0, nr, i1, R, x);
     __syncthreads();
@@ -462,6 +510,11 @@ __global__ void __launch_bounds__(256, 4) circ_solve_kernel(const float2* __rest
     __syncthreads();
   }
   for (int r = tid; r < R; r += blockDim.x) b[r] = x[r];
+}
+
+__global__ void to_half_kernel(const float2* __restrict__ a, __half2* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = __float22half2_rn(a[i]);
 }
 
 __global__ void to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
@@ -483,7 +536,7 @@ static unsigned blocks_for(size_t n) {
 // ---------------------------------------------------------------------------
 static void circ_free(vie_circulant* c) {
   if (!c) return;
-  cudaFree(c->W); cudaFree(c->perm); cudaFree(c->F); cudaFree(c->Fi); cudaFree(c->vh);
+  cudaFree(c->W); cudaFree(c->W16); cudaFree(c->tw); cudaFree(c->perm); cudaFree(c->F); cudaFree(c->Fi); cudaFree(c->vh);
   cudaFree(c->v32); cudaFree(c->z32); cudaFree(c->flag);
   if (c->blas) cublasDestroy(c->blas);
   delete c;
@@ -535,9 +588,10 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
   const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * kTL * (nx + 1) * sizeof(float2);
   if (factor_length(nx, &ax) && fft_smem <= 200 * 1024) {
     // blocks formed and transformed along x in shared memory
-    CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * sizeof(float2)));   // here C holds only the twiddles
-    float2* tw = C;
+    CIRC_TRY(cudaMalloc((void**)&c->tw, (size_t)nx * sizeof(float2)));
+    float2* tw = c->tw;
     twiddle_kernel<<<(nx + 127) / 128, 128, 0, s>>>(nx, tw);
+    c->rd = radices_of(ax);
     CIRC_TRY(cudaFuncSetAttribute(build_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
     build_fft_kernel<<<(unsigned)((RR + kTL - 1) / kTL), 256, fft_smem, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz,
                                                                              radices_of(ax), tw, c->W);
@@ -606,16 +660,33 @@ vie_status circulant_apply(vie_circulant* c, int dtype, const void* v, void* z, 
     vin = c->v32;
     zout = c->z32;
   }
+  const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * kLines * (nx + 1) * sizeof(float2);
+  const bool fft = c->tw != nullptr;
+  if (fft) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+    VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+  }
   VIE_CUBLAS_TRY(cublasSetStream(c->blas, s));
   const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
   // V_hat[w][r] = sum_x F[w][x] v[r][x]
-  VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, R, nx, nx, &one, (const cuComplex*)vin, nx,
-                             (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->vh, R));
-  circ_solve_kernel<<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W, c->perm, c->vh, R);
+  if (fft) {
+    lines_fft_kernel<false><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(vin, c->vh, R, nx, c->rd, c->tw);
+    VIE_LAUNCH_CHECK();
+  } else {
+    VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, R, nx, nx, &one, (const cuComplex*)vin, nx,
+                               (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->vh, R));
+  }
+  if (c->fp16) circ_solve_kernel<__half2><<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W16, c->perm, c->vh, R);
+  else circ_solve_kernel<float2><<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W, c->perm, c->vh, R);
   VIE_LAUNCH_CHECK();
   // z[r][x] = sum_w Fi[w][x] Z_hat[w][r]
-  VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, R, nx, &one, (const cuComplex*)c->Fi, nx,
-                             (const cuComplex*)c->vh, R, &zero, (cuComplex*)zout, nx));
+  if (fft) {
+    lines_fft_kernel<true><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(c->vh, zout, R, nx, c->rd, c->tw);
+    VIE_LAUNCH_CHECK();
+  } else {
+    VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, R, nx, &one, (const cuComplex*)c->Fi, nx,
+                               (const cuComplex*)c->vh, R, &zero, (cuComplex*)zout, nx));
+  }
   if (dtype == VIE_C128) {
     to_c128_kernel<<<blocks_for(N3), 256, 0, s>>>(c->z32, (double2*)z, N3);
     VIE_LAUNCH_CHECK();
@@ -629,9 +700,10 @@ using namespace vie;
 
 extern "C" {
 
-vie_status vie_circulant_create(vie_plan* plan, vie_circulant** out, void* stream) {
+vie_status vie_circulant_create(vie_plan* plan, int flags, vie_circulant** out, void* stream) {
   clear_error();
   if (!plan || !out) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (flags & ~VIE_CIRC_FP16_FACTORS) { set_error("unknown flags 0x%x", flags); return VIE_ERR_INVALID; }
   *out = nullptr;
   if (!plan->M64) { set_error("set the plan's contrast before building its circulant preconditioner"); return VIE_ERR_INVALID; }
   const auto t0 = std::chrono::steady_clock::now();
@@ -663,6 +735,24 @@ vie_status vie_circulant_create(vie_plan* plan, vie_circulant** out, void* strea
     return VIE_ERR_CUDA;
   }
   vie_status st = circ_build(c, (cudaStream_t)stream);
+  if (st == VIE_OK && (flags & VIE_CIRC_FP16_FACTORS)) {
+    // keep only a complex-half copy of the factors
+    const size_t ne = (size_t)c->nx * c->R * c->R;
+    cudaError_t e = cudaMalloc((void**)&c->W16, ne * sizeof(__half2));
+    if (e == cudaSuccess) {
+      to_half_kernel<<<blocks_for(ne), 256, 0, (cudaStream_t)stream>>>(c->W, c->W16, ne);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      set_error("half-precision factors: %s", cudaGetErrorString(e));
+      st = e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+    } else {
+      cudaFree(c->W);
+      c->W = nullptr;
+      c->fp16 = true;
+    }
+  }
   if (st != VIE_OK) {
     circ_free(c);
     return st;
@@ -684,7 +774,7 @@ vie_status vie_circulant_info(const vie_circulant* c, double* build_ms, size_t* 
   if (!c) { set_error("null argument"); return VIE_ERR_INVALID; }
   if (build_ms) *build_ms = c->build_ms;
   if (device_bytes)
-    *device_bytes = (size_t)c->nx * c->R * c->R * sizeof(float2) + (size_t)c->nx * c->R * (sizeof(int) + sizeof(float2)) +
+    *device_bytes = (size_t)c->nx * c->R * c->R * (c->fp16 ? sizeof(__half2) : sizeof(float2)) + (size_t)c->nx * c->R * (sizeof(int) + sizeof(float2)) +
                     (size_t)2 * c->nx * c->nx * sizeof(float2) + (size_t)2 * c->nx * c->R * sizeof(float2);
   return VIE_OK;
 }

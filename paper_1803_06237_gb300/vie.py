@@ -85,7 +85,7 @@ _SIGNATURES = {
     "vie_net_zero_grad": ([_P], _I),
     "vie_net_adam_step": ([_P, ctypes.c_float, ctypes.c_float, _P], _I),
     "vie_net_status": ([_P, ctypes.POINTER(_I), _I], _I),
-    "vie_circulant_create": ([_P, ctypes.POINTER(_P), _P], _I),
+    "vie_circulant_create": ([_P, _I, ctypes.POINTER(_P), _P], _I),
     "vie_circulant_apply": ([_P, _P, _P, _I, _P], _I),
     "vie_circulant_info": ([_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)], _I),
     "vie_circulant_destroy": ([_P], _I),
@@ -374,9 +374,14 @@ class Circulant:
             pass
 
 
-def vie_circulant_create(plan: Plan, stream=None) -> Circulant:
+VIE_CIRC_DEFAULT = 0
+VIE_CIRC_FP16_FACTORS = 1
+
+
+def vie_circulant_create(plan: Plan, flags: int = VIE_CIRC_DEFAULT, stream=None) -> Circulant:
     h = ctypes.c_void_p()
-    _check(load().vie_circulant_create(plan.handle, ctypes.byref(h), _stream_handle(stream)), "vie_circulant_create")
+    _check(load().vie_circulant_create(plan.handle, int(flags), ctypes.byref(h), _stream_handle(stream)),
+           "vie_circulant_create")
     return Circulant(h, plan)
 
 

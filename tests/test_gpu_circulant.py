@@ -33,9 +33,13 @@ def _plan_with_contrast(grid, seed):
 # (nx, ny, nz): R = 3 ny nz unknowns per slice; nb = 32 panels
 @pytest.mark.parametrize("grid", [(7, 3, 2), (13, 4, 3), (20, 6, 2), (24, 8, 5), (9, 11, 4)])
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
-def test_apply_matches_oracle(grid, dtype):
+@pytest.mark.parametrize("fp16", [False, True])
+def test_apply_matches_oracle(grid, dtype, fp16):
+    """complex64 factors: rounding error times the blocks' condition number;
+    complex-half factors (unit roundoff 2^-11): the same bound with that
+    roundoff."""
     plan, M = _plan_with_contrast(grid, 3)
-    c = vie.vie_circulant_create(plan)
+    c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT)
     kappa = K0 * math.sqrt(EPS_BG) * H
     What = circ.blocks_hat(circ.circulant_blocks(grid, kappa, M))
     v = workloads.random_currents(grid, seed=4).astype(dtype)
@@ -45,9 +49,8 @@ def test_apply_matches_oracle(grid, dtype):
     torch.cuda.synchronize()
     z = zd.cpu().numpy().reshape(3, grid[2], grid[1], grid[0]).astype(np.complex128)
     z_ref = circ.apply_inverse(What, v.astype(np.complex128))
-    # complex64 factors: rounding error times the blocks' condition number
     cond = max(np.linalg.cond(What[w]) for w in range(grid[0]))
-    tol = 2e-6 * cond
+    tol = (4e-3 if fp16 else 2e-6) * cond
     assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < tol
 
 
@@ -108,14 +111,15 @@ def test_preconditioned_solve_small_guide(mode):
     vie.vie_set_circulant_preconditioner(plan, None)
 
 
-def test_full_size_guide_solve():
+@pytest.mark.parametrize("fp16", [False, True])
+def test_full_size_guide_solve(fp16):
     """The 600 x 23 x 11 benchmark guide (R = 759 unknowns per slice, 24 LU
     panels): the preconditioned mixed solve converges to 1e-6 in few steps
-    and agrees with the plain solve."""
+    and agrees with the plain solve, with complex64 or complex-half factors."""
     plan, b = _guide_problem(600, 4.0)
-    c = vie.vie_circulant_create(plan)
+    c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT)
     info = vie.vie_circulant_info(c)
-    assert info["device_bytes"] >= 600 * 759 * 759 * 8
+    assert info["device_bytes"] >= 600 * 759 * 759 * (4 if fp16 else 8)
     vie.vie_set_circulant_preconditioner(plan, c)
     x1 = torch.zeros_like(b)
     i1 = vie.vie_solve(plan, b, x1, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30, use_preconditioner=True)
