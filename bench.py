@@ -579,24 +579,28 @@ def profile_net(reps: int):
 
 
 def profile_circulant(reps: int):
-    """One block-circulant build and `reps` applications on the benchmark
-    guide: a short, fixed launch sequence for kernel launch lists."""
+    """Block-circulant builds (complex64 factors, then complex-half factors)
+    and `reps` applications of each on the benchmark guide: a short, fixed
+    launch sequence for kernel launch lists."""
     import torch
 
     from paper_1803_06237_gb300 import build, learned, vie, workloads
     build.build_library()
     vie.load()
     plan, b = learned.setup_problem(workloads.waveguide())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    c = vie.vie_circulant_create(plan)
-    torch.cuda.synchronize()
-    setup = (time.perf_counter() - t0) * 1e3
     v = torch.randn(b.numel(), dtype=torch.complex64, device="cuda")
     z = torch.empty_like(v)
-    for _ in range(reps):
-        vie.vie_circulant_apply(c, v, z)
-    torch.cuda.synchronize()
+    setup = {}
+    for name, flags in (("complex64", vie.VIE_CIRC_DEFAULT), ("complex_half", vie.VIE_CIRC_FP16_FACTORS)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = vie.vie_circulant_create(plan, flags)
+        torch.cuda.synchronize()
+        setup[name] = (time.perf_counter() - t0) * 1e3
+        for _ in range(reps):
+            vie.vie_circulant_apply(c, v, z)
+        torch.cuda.synchronize()
+        c.close()
     print(json.dumps({"profile_circulant": reps, "setup_ms": setup}))
 
 

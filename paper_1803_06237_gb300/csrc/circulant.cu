@@ -408,104 +408,137 @@ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
   return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// Rows i0 .. i0 + nr - 1 of A times x over the columns [c0, c1), subtracted
-// from x: 8 threads per row (256 threads = 32 rows), each over the columns
-// c0 + sub + 8 u, 16 (complex64) or 32 (complex half) independent loads in
-// flight per thread; the eight
-// partial sums of a row are combined with shuffles.
 __device__ __forceinline__ float2 ld_factor(const float2* p) { return *p; }
 __device__ __forceinline__ float2 ld_factor(const __half2* p) { return __half22float2(*p); }
 
+// Streamer part of the pipelined substitution: 224 threads (warps 1-7),
+// seven per row of a 32-row block row.  Thread (row, sub) sums
+// A[j0 + row][t] x[t] over t = c0 + sub + 7 u < c1 with 16 (complex64) or 32
+// (complex half) loads in flight and leaves the sum in red[row][sub].
 template <typename T>
-__device__ __forceinline__ void block_row_update(const T* __restrict__ A, int R, int i0, int nr, int c0,
-                                                 int c1, float2* __restrict__ x) {
-  const int a = threadIdx.x >> 3, sub = threadIdx.x & 7;
+__device__ __forceinline__ void stream_partial(const T* __restrict__ A, int R, int j0, int nr, int c0, int c1,
+                                               const float2* __restrict__ x, float2 (*red)[8], int st) {
+  const int row = st / 7, sub = st - row * 7;
   float sx = 0.f, sy = 0.f;
-  if (a < nr) {
-    // loads in flight per thread: 16 complex64 or 32 complex-half factors
+  if (row < nr) {
     constexpr int U = sizeof(T) == 4 ? 32 : 16;
-    const T* row = A + (size_t)(i0 + a) * R;
+    const T* rp = A + (size_t)(j0 + row) * R;
     int t = c0 + sub;
-    for (; t + 8 * (U - 1) < c1; t += 8 * U) {
+    for (; t + 7 * (U - 1) < c1; t += 7 * U) {
       float2 l[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) l[u] = ld_factor(row + t + 8 * u);
+      for (int u = 0; u < U; ++u) l[u] = ld_factor(rp + t + 7 * u);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const float2 xt = x[t + 8 * u];
+        const float2 xt = x[t + 7 * u];
         sx += l[u].x * xt.x - l[u].y * xt.y;
         sy += l[u].x * xt.y + l[u].y * xt.x;
       }
     }
-    for (; t < c1; t += 8) {
-      const float2 l = ld_factor(row + t), xt = x[t];
+    for (; t < c1; t += 7) {
+      const float2 l = ld_factor(rp + t), xt = x[t];
       sx += l.x * xt.x - l.y * xt.y;
       sy += l.x * xt.y + l.y * xt.x;
     }
   }
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-  }
-  if (a < nr && sub == 0) {
-    x[i0 + a].x -= sx;
-    x[i0 + a].y -= sy;
-  }
+  red[row][sub] = make_float2(sx, sy);
 }
 
-// x = P b (gather), then L y = x in blocks of 32 rows (the block row's
-// products with the solved part by all threads, the 32 x 32 unit-lower
-// diagonal block by warp 0 with shuffles), then U z = y likewise from the
-// bottom.  256 threads.
+// x = P b (gather), then L y = x and U z = y in blocks of 32 rows, pipelined:
+// while warp 0 solves block k (its rows minus the streamed partial and the
+// coupling to the block solved just before, then the 32 x 32 diagonal block
+// with shuffles), warps 1-7 stream block k+1's products with every column
+// that is already final and prefetch block k+1's diagonal block and its
+// coupling block into the other half of double-buffered shared memory.  One
+// barrier per block.  256 threads.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) circ_solve_kernel(const T* __restrict__ W, const int* __restrict__ perm,
                                                          float2* __restrict__ vh, int R) {
   extern __shared__ float2 x[];
-  __shared__ float2 D[32][33];
+  __shared__ float2 D[2][32][33];   // diagonal block
+  __shared__ float2 E[2][32][33];   // coupling to the previously solved block
+  __shared__ float2 red[2][32][8];  // streamed partial sums, 7 per row
   const T* A = W + (size_t)blockIdx.x * R * R;
   const int* pm = perm + (size_t)blockIdx.x * R;
   float2* b = vh + (size_t)blockIdx.x * R;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int r = tid; r < R; r += blockDim.x) x[r] = b[pm[r]];
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, st = tid - 32;
   const int nblk = (R + 31) / 32;
-  // forward: unit lower L
-  for (int bk = 0; bk < nblk; ++bk) {
-    const int i0 = bk * 32, nr = min(32, R - i0);
-    for (int e = tid; e < nr * 32; e += blockDim.x) {
+  auto nrows = [&](int k) { return min(32, R - 32 * k); };
+  for (int r = tid; r < R; r += blockDim.x) x[r] = b[pm[r]];
+  // ---------------- forward: unit lower L ----------------
+  {
+    const int nr = nrows(0);
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
       const int a = e >> 5, t = e & 31;
-      if (t < nr) D[a][t] = ld_factor(A + (size_t)(i0 + a) * R + i0 + t);
+      D[0][a][t] = (a < nr && t < nr) ? ld_factor(A + (size_t)a * R + t) : make_float2(0.f, 0.f);
+      if (t < 8) red[0][a][t] = make_float2(0.f, 0.f);
     }
-    block_row_update(A, R, i0, nr, 0, i0, x);
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int k = 0; k < nblk; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1, i0 = 32 * k, nr = nrows(k);
     if (wid == 0) {
       float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
+      if (lane < nr) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) xi = make_float2(xi.x - red[cur][lane][q].x, xi.y - red[cur][lane][q].y);
+        if (k > 0)
+          for (int t = 0; t < 32; ++t) xi = csub_mul(xi, E[cur][lane][t], x[i0 - 32 + t]);
+      }
       for (int t = 0; t < nr; ++t) {
         const float2 xt = make_float2(__shfl_sync(0xffffffffu, xi.x, t), __shfl_sync(0xffffffffu, xi.y, t));
-        if (lane > t && lane < nr) xi = csub_mul(xi, D[lane][t], xt);
+        if (lane > t && lane < nr) xi = csub_mul(xi, D[cur][lane][t], xt);
       }
       if (lane < nr) x[i0 + lane] = xi;
+    } else if (k + 1 < nblk) {
+      const int j0 = i0 + 32, nr1 = nrows(k + 1);
+      stream_partial(A, R, j0, nr1, 0, i0, x, red[nxt], st);
+      for (int e = st; e < 32 * 32; e += blockDim.x - 32) {
+        const int a = e >> 5, t = e & 31;
+        const bool in = a < nr1;
+        D[nxt][a][t] = (in && t < nr1) ? ld_factor(A + (size_t)(j0 + a) * R + j0 + t) : make_float2(0.f, 0.f);
+        E[nxt][a][t] = in ? ld_factor(A + (size_t)(j0 + a) * R + i0 + t) : make_float2(0.f, 0.f);
+      }
     }
     __syncthreads();
   }
-  // backward: upper U (with its diagonal)
-  for (int bk = nblk - 1; bk >= 0; --bk) {
-    const int i0 = bk * 32, nr = min(32, R - i0), i1 = i0 + nr;
-    for (int e = tid; e < nr * 32; e += blockDim.x) {
+  // ---------------- backward: upper U with its diagonal ----------------
+  {
+    const int kl = nblk - 1, i0 = 32 * kl, nr = nrows(kl);
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
       const int a = e >> 5, t = e & 31;
-      if (t < nr) D[a][t] = ld_factor(A + (size_t)(i0 + a) * R + i0 + t);
+      D[0][a][t] = (a < nr && t < nr) ? ld_factor(A + (size_t)(i0 + a) * R + i0 + t) : make_float2(0.f, 0.f);
+      if (t < 8) red[0][a][t] = make_float2(0.f, 0.f);
     }
-    block_row_update(A, R, i0, nr, i1, R, x);
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int it = 0; it < nblk; ++it) {
+    const int k = nblk - 1 - it, cur = it & 1, nxt = cur ^ 1;
+    const int i0 = 32 * k, nr = nrows(k), i1 = i0 + nr;
     if (wid == 0) {
       float2 xi = lane < nr ? x[i0 + lane] : make_float2(0.f, 0.f);
+      if (lane < nr) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) xi = make_float2(xi.x - red[cur][lane][q].x, xi.y - red[cur][lane][q].y);
+        if (k + 1 < nblk) {
+          const int nrn = nrows(k + 1);
+          for (int t = 0; t < nrn; ++t) xi = csub_mul(xi, E[cur][lane][t], x[i1 + t]);
+        }
+      }
       for (int t = nr - 1; t >= 0; --t) {
-        if (lane == t) xi = cdiv(xi, D[t][t]);
+        if (lane == t) xi = cdiv(xi, D[cur][t][t]);
         const float2 xt = make_float2(__shfl_sync(0xffffffffu, xi.x, t), __shfl_sync(0xffffffffu, xi.y, t));
-        if (lane < t) xi = csub_mul(xi, D[lane][t], xt);
+        if (lane < t) xi = csub_mul(xi, D[cur][lane][t], xt);
       }
       if (lane < nr) x[i0 + lane] = xi;
+    } else if (k > 0) {
+      const int j0 = i0 - 32;      // block k - 1 has 32 rows
+      stream_partial(A, R, j0, 32, i1, R, x, red[nxt], st);
+      for (int e = st; e < 32 * 32; e += blockDim.x - 32) {
+        const int a = e >> 5, t = e & 31;
+        D[nxt][a][t] = ld_factor(A + (size_t)(j0 + a) * R + j0 + t);
+        E[nxt][a][t] = t < nr ? ld_factor(A + (size_t)(j0 + a) * R + i0 + t) : make_float2(0.f, 0.f);
+      }
     }
     __syncthreads();
   }
