@@ -330,8 +330,9 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
     out = []
     for info in infos:
         out.append({"iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
-                    "matvecs32": info.matvecs32, "converged": bool(info.converged), "residual": info.residual,
-                    "time_ms": info.time_ms, "history": [info.history[i] for i in range(min(info.history_len, 64))]})
+                    "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
+                    "residual": info.residual, "time_ms": info.time_ms,
+                    "history": [info.history[i] for i in range(min(info.history_len, 64))]})
     if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
         _check(st, "vie_solve_batch")
     return st, out
