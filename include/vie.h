@@ -293,7 +293,8 @@ typedef struct vie_circulant vie_circulant;
 /* Flags of vie_circulant_create. */
 #define VIE_CIRC_DEFAULT 0
 #define VIE_CIRC_FP16_FACTORS 1   /* keep the LU factors in complex half precision (half the memory and
-                                     half the bytes per application; the factorisation itself is complex64) */
+                                     half the bytes per application); the factorisation runs in complex64
+                                     with its trailing updates on TF32 tensor cores */
 
 /* Build W from the plan's current Toeplitz entries and contrast (the plan's
  * contrast must have been set) and factor it; synchronises `stream`.  The

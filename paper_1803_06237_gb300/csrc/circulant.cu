@@ -575,7 +575,9 @@ static void circ_free(vie_circulant* c) {
   delete c;
 }
 
-static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
+// tf32: the trailing LU updates may use TF32 tensor cores (for factors that
+// are rounded to complex half afterwards).
+static vie_status circ_build(vie_circulant* c, cudaStream_t s, bool tf32) {
   const vie_plan* p = c->plan;
   const int nx = c->nx, ny = c->ny, nz = c->nz, B = c->B, R = c->R;
   const size_t RR = (size_t)R * R, N3 = (size_t)3 * B * nx;
@@ -612,6 +614,7 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s) {
   CIRC_TRY(cudaMalloc((void**)&c->flag, sizeof(int)));
   CIRC_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s));
   CIRC_BLAS(cublasSetStream(c->blas, s));
+  CIRC_BLAS(cublasSetMathMode(c->blas, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH));
 
   prefix_kernel<<<(B + 127) / 128, 128, 0, s>>>(p->M64, nx, B, Sp, Sm);
   dft_matrix_kernel<<<blocks_for((size_t)nx * nx), 256, 0, s>>>(nx, c->F, c->Fi);
@@ -767,7 +770,7 @@ vie_status vie_circulant_create(vie_plan* plan, int flags, vie_circulant** out, 
     delete c;
     return VIE_ERR_CUDA;
   }
-  vie_status st = circ_build(c, (cudaStream_t)stream);
+  vie_status st = circ_build(c, (cudaStream_t)stream, (flags & VIE_CIRC_FP16_FACTORS) != 0);
   if (st == VIE_OK && (flags & VIE_CIRC_FP16_FACTORS)) {
     // keep only a complex-half copy of the factors
     const size_t ne = (size_t)c->nx * c->R * c->R;
