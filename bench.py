@@ -204,7 +204,8 @@ def gpu_arm(args):
     ab = wl.absorbers[0]
     e2 = vie.vie_eps2_from_round_trip(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
     absorbers = [dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2)]
-    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg,
+                               vie.VIE_PLAN_AUTOTUNE if args.autotune else vie.VIE_PLAN_DEFAULT)
     vie.vie_set_permittivity(plan, wl.eps, absorbers)
     info = plan.info()
 
@@ -302,6 +303,8 @@ def gpu_arm(args):
         "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(wl.grid), "circulant": list(info["m"]),
+                   "autotune": ({"candidates": info["tune_candidates"], "ms": round(info["tune_ms"], 1),
+                                 "x_lines_per_block": info["x_lines_per_block"]} if args.autotune else None),
                    "input_pool_vectors": pool, "l2": f"inputs+outputs cycle through {2 * pool * vec_bytes / 2**20:.0f} MiB > 129 MB L2",
                    "parallelism": f"{world} independent replicas"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,
@@ -651,6 +654,8 @@ def main():
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="create the guide's plan without VIE_PLAN_AUTOTUNE (circulant sizes, x-pass shape)")
     ap.add_argument("--no-circulant", dest="circulant", action="store_false",
                     help="skip the block-circulant preconditioner leg of the solve section")
     ap.add_argument("--profile-solve", type=int, default=0,

@@ -54,8 +54,13 @@ enum { VIE_C64 = 1, VIE_C128 = 2 };
 /* Flags for vie_plan_create. */
 enum {
   VIE_PLAN_DEFAULT = 0,
-  VIE_PLAN_CIRC_2N = 1        /* circulant sizes exactly 2n (else the smallest
+  VIE_PLAN_CIRC_2N = 1,       /* circulant sizes exactly 2n (else the smallest
                                  5-smooth size >= 2n - 1) */
+  VIE_PLAN_AUTOTUNE = 2       /* time complex64 operator applications for the
+                                 three smallest 5-smooth sizes >= 2n - 1 per axis
+                                 and 2 or 4 lines per x-pass block, keep the
+                                 fastest (any M >= 2n - 1 embeds the operator
+                                 exactly); ignored with VIE_PLAN_CIRC_2N */
 };
 
 typedef struct {
@@ -64,6 +69,9 @@ typedef struct {
   double h, k0, eps_bg, kappa;/* kappa = k0 sqrt(eps_bg) h */
   size_t device_bytes;        /* device memory held by the plan */
   double setup_ms;            /* device time of entries + spectrum */
+  double tune_ms;             /* host time spent by VIE_PLAN_AUTOTUNE (0 without) */
+  int tune_candidates;        /* configurations timed (0 without) */
+  int x_lines_per_block;      /* x-pass lines per block chosen by the tuner (0: heuristic) */
 } vie_plan_info;
 
 /* Graded absorber of Sec. 4.1-4.2: eps'' = eps2_max * u^degree with

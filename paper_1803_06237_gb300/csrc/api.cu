@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <chrono>
+
 #include <vector>
 
 #include "vie_internal.cuh"
@@ -223,6 +225,112 @@ static void free_plan(vie_plan* p) {
 
 using namespace vie;
 
+// VIE_PLAN_AUTOTUNE: every combination of the three smallest 5-smooth
+// sizes >= 2n - 1 per axis and, where the x passes are four-step kernels, 2
+// or 4 lines per x-pass block is timed over 3 + 10 complex64 operator
+// applications (CUDA events) on a zero spectrum and contrast (the time does
+// not depend on the values); the fastest is kept.  Candidates the passes
+// reject (shared-memory limits) are skipped.
+static vie_status autotune(vie_plan* p, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int cand[3][3];
+  for (int a = 0; a < 3; ++a) {
+    int m = 2 * p->n[a] - 1;
+    for (int c = 0; c < 3; ++c) {
+      m = smooth_size_at_least(m);
+      cand[a][c] = m;
+      ++m;
+    }
+  }
+  const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  const size_t NL = (size_t)3 * p->n[1] * p->n[2];
+  const size_t G = (size_t)(cand[0][2] / 2 + 1) * 6 * (cand[1][2] / 2 + 1) * (cand[2][2] / 2 + 1);
+  float2 *ghat = nullptr, *M = nullptr, *x = nullptr, *y = nullptr, *work = nullptr;
+  AxisPlan ax[3][3];
+  size_t scratch = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  vie_status st = VIE_OK;
+  auto cleanup = [&]() {
+    cudaFree(ghat); cudaFree(M); cudaFree(x); cudaFree(y); cudaFree(work);
+    for (auto& row : ax)
+      for (auto& a : row) { cudaFree(a.tw32); cudaFree(a.tw64); a = AxisPlan(); }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    p->ghat32 = nullptr;
+    p->M32 = nullptr;
+    for (int a = 0; a < 3; ++a) p->ax[a] = AxisPlan();
+  };
+  cudaError_t e = cudaMalloc((void**)&ghat, G * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&M, N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&x, 3 * N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&y, 3 * N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&work, NL * cand[0][2] * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(ghat, 0, G * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M, 0, N * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, 3 * N * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    set_error("autotune buffers: %s", cudaGetErrorString(e));
+    cleanup();
+    return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+  }
+  for (int a = 0; a < 3 && st == VIE_OK; ++a)
+    for (int c = 0; c < 3 && st == VIE_OK; ++c) st = make_axis(&ax[a][c], cand[a][c], &scratch);
+  if (st != VIE_OK) { cleanup(); return st; }
+  p->ghat32 = ghat;
+  p->M32 = M;
+  float best = 1e30f;
+  int bm[3] = {p->m[0], p->m[1], p->m[2]}, blpb = 0, count = 0;
+  for (int cx = 0; cx < 3; ++cx)
+    for (int cy = 0; cy < 3; ++cy)
+      for (int cz = 0; cz < 3; ++cz) {
+        p->m[0] = cand[0][cx];
+        p->m[1] = cand[1][cy];
+        p->m[2] = cand[2][cz];
+        for (int a = 0; a < 3; ++a) p->kf[a] = p->m[a] / 2 + 1;
+        p->ax[0] = ax[0][cx];
+        p->ax[1] = ax[1][cy];
+        p->ax[2] = ax[2][cz];
+        int l1 = 0, l2 = 0;
+        x4_factors(p->m[0], &l1, &l2);
+        const int lpbs[2] = {2, 4};
+        for (int li = 0; li < (l1 ? 2 : 1); ++li) {
+          p->x_lpb = l1 ? lpbs[li] : 0;
+          vie_status ms = VIE_OK;
+          for (int r = 0; r < 3 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, s);
+          cudaEventRecord(e0, s);
+          for (int r = 0; r < 10 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, s);
+          cudaEventRecord(e1, s);
+          const cudaError_t se = cudaStreamSynchronize(s);
+          if (se != cudaSuccess) {
+            set_error("autotune: %s", cudaGetErrorString(se));
+            cleanup();
+            return VIE_ERR_CUDA;
+          }
+          if (ms != VIE_OK) { clear_error(); continue; }
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ++count;
+          if (t < best) {
+            best = t;
+            bm[0] = p->m[0]; bm[1] = p->m[1]; bm[2] = p->m[2];
+            blpb = p->x_lpb;
+          }
+        }
+      }
+  cleanup();
+  if (count == 0) { set_error("autotune: no candidate configuration ran"); return VIE_ERR_INVALID; }
+  for (int a = 0; a < 3; ++a) {
+    p->m[a] = bm[a];
+    p->kf[a] = bm[a] / 2 + 1;
+  }
+  p->x_lpb = blpb;
+  p->tune_candidates = count;
+  p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return VIE_OK;
+}
+
 extern "C" {
 
 const char* vie_last_error(void) { return g_err; }
@@ -250,6 +358,17 @@ vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0, 
   p->kappa = k0 * sqrt(eps_bg) * h;
   size_t bytes = 0;
   vie_status st = VIE_OK;
+  if ((flags & VIE_PLAN_AUTOTUNE) && !(flags & VIE_PLAN_CIRC_2N)) {
+    cudaStream_t ts;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cudaStreamCreate failed");
+      free_plan(p);
+      return VIE_ERR_CUDA;
+    }
+    st = autotune(p, ts);
+    cudaStreamDestroy(ts);
+    if (st != VIE_OK) { free_plan(p); return st; }
+  }
   for (int a = 0; a < 3 && st == VIE_OK; ++a) st = make_axis(&p->ax[a], p->m[a], &bytes);
   if (st != VIE_OK) { free_plan(p); return st; }
   const size_t N = (size_t)n[0] * n[1] * n[2];
@@ -312,6 +431,7 @@ vie_status vie_plan_clone(const vie_plan* base, vie_plan** out) {
   for (int a = 0; a < 3; ++a) {
     p->n[a] = base->n[a];
     p->m[a] = base->m[a];
+    p->x_lpb = base->x_lpb;
     p->kf[a] = base->kf[a];
     p->ax[a] = base->ax[a];
   }
@@ -410,6 +530,9 @@ vie_status vie_plan_get_info(const vie_plan* p, vie_plan_info* info) {
   info->kappa = p->kappa;
   info->device_bytes = p->device_bytes;
   info->setup_ms = p->setup_ms;
+  info->tune_ms = p->tune_ms;
+  info->tune_candidates = p->tune_candidates;
+  info->x_lines_per_block = p->x_lpb;
   return VIE_OK;
 }
 

@@ -544,12 +544,15 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
 }
 
 // Four lines per block, or two when four would leave fewer than two blocks
-// per SM (more blocks hide the latency of the small per-line work).
+// per SM (more blocks hide the latency of the small per-line work), unless
+// the plan's tuner chose (lpb = 2 or 4).
 template <typename V, int L1, int L2>
 static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
-                            const V* twx, int mode, cudaStream_t s, bool* done) {
+                            const V* twx, int mode, cudaStream_t s, bool* done, int lpb) {
   if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
     const long blocks4 = (long)((NL + 3) / 4) * count;
+    if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
+    if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
     if (blocks4 < 2L * 152)
       return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
     return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
@@ -570,10 +573,10 @@ void x4_factors(int mx, int* l1, int* l2) {
 
 template <typename V>
 static vie_status dispatch_x4(bool forward, int l1, int l2, const PassPtrs<V>& pp, int count, int nx, int nyz,
-                              int NL, const V* twx, int mode, cudaStream_t s, bool* done) {
+                              int NL, const V* twx, int mode, cudaStream_t s, bool* done, int lpb) {
   *done = false;
 #define VIE_X(a, b) \
-  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
+  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb);
   VIE_PASS_X4_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
@@ -611,7 +614,7 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   bool done = false;
   vie_status st = VIE_OK;
   if (l1) {
-    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done);
+    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb);
     if (st != VIE_OK) return st;
   }
   if (!done) {
@@ -630,7 +633,7 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   }
   done = false;
   if (l1) {
-    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done);
+    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb);
     if (st != VIE_OK) return st;
   }
   if (!done) {

@@ -116,6 +116,7 @@ inline Radices radices_of(const AxisPlan& a) {
 }
 
 bool factor_length(int len, AxisPlan* out);   // radices from {4, 2, 3, 5}
+void x4_factors(int mx, int* l1, int* l2);    // compiled four-step split of Mx, or (0, 0)
 int smooth_size_at_least(int n);               // smallest 5-smooth >= n
 
 // ---------------------------------------------------------------------------
@@ -148,6 +149,9 @@ struct vie_plan {
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
   void* precond = nullptr;    // preconditioner state (learned or block-circulant), if set
   int contrast_gen = 0;       // incremented whenever the contrast is set
+  int x_lpb = 0;              // four-step x-pass lines per block (0: heuristic)
+  double tune_ms = 0.0;       // VIE_PLAN_AUTOTUNE host time
+  int tune_candidates = 0;
 };
 
 namespace vie {

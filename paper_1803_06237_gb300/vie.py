@@ -19,6 +19,7 @@ VIE_C64 = 1
 VIE_C128 = 2
 VIE_PLAN_DEFAULT = 0
 VIE_PLAN_CIRC_2N = 1
+VIE_PLAN_AUTOTUNE = 2
 
 _STATUS = {0: "VIE_OK", 1: "VIE_ERR_INVALID", 2: "VIE_ERR_OOM", 3: "VIE_ERR_CUDA",
            4: "VIE_ERR_NOT_CONVERGED", 5: "VIE_ERR_TIMEOUT", 6: "VIE_ERR_NONFINITE"}
@@ -33,7 +34,8 @@ class VieError(RuntimeError):
 class vie_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("h", ctypes.c_double),
                 ("k0", ctypes.c_double), ("eps_bg", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double), ("tune_ms", ctypes.c_double),
+                ("tune_candidates", ctypes.c_int), ("x_lines_per_block", ctypes.c_int)]
 
 
 class vie_absorber(ctypes.Structure):
@@ -172,7 +174,9 @@ class Plan:
         inf = vie_plan_info()
         _check(load().vie_plan_get_info(self.handle, ctypes.byref(inf)), "vie_plan_get_info")
         return {"n": tuple(inf.n), "m": tuple(inf.m), "h": inf.h, "k0": inf.k0, "eps_bg": inf.eps_bg,
-                "kappa": inf.kappa, "device_bytes": inf.device_bytes, "setup_ms": inf.setup_ms}
+                "kappa": inf.kappa, "device_bytes": inf.device_bytes, "setup_ms": inf.setup_ms,
+                "tune_ms": inf.tune_ms, "tune_candidates": inf.tune_candidates,
+                "x_lines_per_block": inf.x_lines_per_block}
 
 
 # ----------------------------------------------------------------------------

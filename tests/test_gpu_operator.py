@@ -215,3 +215,26 @@ def test_four_step_x_sizes(nx, dtype, tol):
     M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
     y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
     assert rel_l2(_apply(plan, x, dtype), y_ref) <= tol
+
+
+@pytest.mark.parametrize("grid", [(13, 4, 6), (1, 1, 9), (150, 23, 11)])
+def test_autotuned_plan_matches_oracle(grid):
+    """Any circulant size M >= 2n - 1 embeds the Toeplitz operator exactly
+    (Sec. 3), so the tuner's choice changes the time, never the result."""
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085, vie.VIE_PLAN_AUTOTUNE)
+    info = plan.info()
+    assert info["tune_candidates"] >= 1 and info["tune_ms"] > 0
+    assert all(mi >= 2 * ni - 1 and _smooth(mi) for mi, ni in zip(info["m"], grid))
+    assert info["x_lines_per_block"] in (0, 2, 4)
+    eps = workloads.random_permittivity(grid, seed=41)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=42)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, info["kappa"], M, x).ravel()
+    assert rel_l2(_apply(plan, x, torch.complex128), y_ref) <= TOL64
+    assert rel_l2(_apply(plan, x, torch.complex64), y_ref) <= TOL32
+    # a clone keeps the tuned shapes
+    clone = vie.vie_plan_clone(plan)
+    assert clone.info()["m"] == info["m"] and clone.info()["x_lines_per_block"] == info["x_lines_per_block"]
+    vie.vie_set_permittivity(clone, eps)
+    assert rel_l2(_apply(clone, x, torch.complex64), y_ref) <= TOL32
