@@ -42,17 +42,21 @@ WORKLOAD = ("Si strip waveguide 600x23x11 voxels, h=20nm, eps_core=12.11, eps_bg
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
 
 
-def operator_flops(grid, m) -> float:
+def operator_flops(grid, m, y_first: bool = False) -> float:
     """Algorithmic FP32 flops of one operator application: 5 L log2 L per
     complex FFT of length L on the lines that carry data (x: the 3 ny nz
     non-zero lines, forward and inverse; per kx plane: 3 ny z-lines and 3 Mz
-    y-lines, forward and inverse) plus 72 flops per spectral cell for the
-    symmetric 3x3 complex multiply."""
+    y-lines, forward and inverse, or 3 nz y-lines and 3 My z-lines when y is
+    transformed first) plus 72 flops per spectral cell for the symmetric 3x3
+    complex multiply."""
     nx, ny, nz = grid
     Mx, My, Mz = m
     f = lambda L: 5.0 * L * math.log2(L) if L > 1 else 0.0
     x_part = 3 * ny * nz * 2 * f(Mx)
-    plane = 3 * ny * 2 * f(Mz) + 3 * Mz * 2 * f(My) + 72.0 * My * Mz
+    if y_first:
+        plane = 3 * nz * 2 * f(My) + 3 * My * 2 * f(Mz) + 72.0 * My * Mz
+    else:
+        plane = 3 * ny * 2 * f(Mz) + 3 * Mz * 2 * f(My) + 72.0 * My * Mz
     return x_part + Mx * plane
 
 
@@ -320,6 +324,8 @@ def gpu_arm(args):
         result["time_to_1e-6"] = solve_section(plan, wl, absorbers, args)
     if not args.no_batch:
         result["batch48"] = batch_section(args)
+    if args.microring:
+        result["microring"] = microring_section(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -343,6 +349,59 @@ def _timed_solve(plan, b, mode, restart, use_pc):
     return {"ms": wall, "device_ms": info["time_ms"], "iterations": info["iterations"], "cycles": info["outer"],
             "matvecs_c128": info["matvecs64"], "matvecs_c64": info["matvecs32"], "converged": info["converged"],
             "true_residual": info["residual"], "preconditioner_dropped": info["fallback"], "restart": restart}
+
+
+def microring_section(args, reps=40, reps64=8):
+    """Operator on the 800 x 600 x 11 ring resonator (circulant 1600 x 1200 x
+    24, pass B on CTA clusters): plan setup, complex64 and complex128
+    applications timed with CUDA events on two input/output pairs of 127 MB
+    each (larger than L2)."""
+    import torch
+
+    from paper_1803_06237_gb300 import vie, workloads
+    wl = workloads.microring()
+    absorbers = []
+    for ab in wl.absorbers:
+        e2 = vie.vie_eps2_from_round_trip(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+        absorbers.append(dict(x0=ab.x0, length=ab.length, degree=ab.degree, direction=ab.direction, eps2_max=e2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    setup_host_ms = (time.perf_counter() - t0) * 1e3
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    info = plan.info()
+    n3 = 3 * wl.n_voxels
+    stream = torch.cuda.current_stream()
+    out = {"grid": list(wl.grid), "circulant": list(info["m"]), "setup_ms": round(setup_host_ms, 1),
+           "device_bytes": info["device_bytes"]}
+    for dtype, name, r in ((torch.complex64, "c64", reps), (torch.complex128, "c128", reps64)):
+        xs = torch.randn((2, n3), dtype=dtype, device="cuda")
+        ys = torch.empty_like(xs)
+        for i in range(3):
+            vie.vie_matvec(plan, xs[i % 2], ys[i % 2], stream)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for i in range(r):
+            vie.vie_matvec(plan, xs[i % 2], ys[i % 2], stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / r
+        es = xs.element_size()
+        Kx, Ky, Kz = (m // 2 + 1 for m in info["m"])
+        alg_bytes = (3 * wl.n_voxels * 2 + wl.n_voxels) * es + 6 * Kx * Ky * Kz * es
+        hbm_peak, peak_kind = _peaks()
+        entry = {"ms_per_matvec": ms, "matvecs_per_s": 1e3 / ms,
+                 "hbm": {"algorithmic_bytes": alg_bytes, "achieved": alg_bytes / ms / 1e6, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": alg_bytes / ms / 1e6 / hbm_peak, "peak_source": peak_kind}}
+        if dtype == torch.complex64:
+            fl = operator_flops(wl.grid, info["m"], y_first=True)
+            entry["alu"] = {"algorithmic_flops": fl, "achieved": fl / ms / 1e9, "peak": FP32_TFLOPS,
+                            "unit": "TFLOP/s", "frac": fl / ms / 1e9 / FP32_TFLOPS}
+        out[name] = entry
+        del xs, ys
+    plan.close()
+    return out
 
 
 def solve_section(plan, wl, absorbers, args):
@@ -608,6 +667,26 @@ def profile_net(reps: int):
     print(json.dumps({"profile_net": reps, **out}))
 
 
+def profile_microring(reps: int):
+    """The ring resonator's plan and `reps` complex64 operator applications: a
+    short launch sequence for kernel launch lists."""
+    import torch
+
+    from paper_1803_06237_gb300 import build, vie, workloads
+    build.build_library()
+    vie.load()
+    wl = workloads.microring()
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps)
+    x = torch.randn(3 * wl.n_voxels, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(reps):
+        vie.vie_matvec(plan, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_microring": reps, "circulant": list(plan.info()["m"])}))
+    plan.close()
+
+
 def profile_circulant(reps: int):
     """Block-circulant builds (complex64 factors, then complex-half factors)
     and `reps` applications of each on the benchmark guide: a short, fixed
@@ -651,9 +730,13 @@ def main():
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--profile-circulant", type=int, default=0,
                     help="only build the block-circulant preconditioner and apply it (for kernel launch lists)")
+    ap.add_argument("--profile-microring", type=int, default=0,
+                    help="only build the ring resonator's plan and apply the operator (for kernel launch lists)")
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
+    ap.add_argument("--no-microring", dest="microring", action="store_false",
+                    help="skip the 800 x 600 x 11 ring-resonator operator section")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="create the guide's plan without VIE_PLAN_AUTOTUNE (circulant sizes, x-pass shape)")
     ap.add_argument("--no-circulant", dest="circulant", action="store_false",
@@ -669,6 +752,9 @@ def main():
         return
     if args.profile_circulant:
         profile_circulant(args.profile_circulant)
+        return
+    if args.profile_microring:
+        profile_microring(args.profile_microring)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -264,7 +264,15 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&M, N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&x, 3 * N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&y, 3 * N * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&work, NL * cand[0][2] * sizeof(float2));
+  size_t split = 0;
+  for (int cx = 0; cx < 3; ++cx)
+    for (int cy = 0; cy < 3; ++cy)
+      for (int cz = 0; cz < 3; ++cz) {
+        const size_t e2 = pass_b_split_elems(p->n[1], p->n[2], cand[0][cx], cand[1][cy], cand[2][cz]);
+        if (e2 > split) split = e2;
+      }
+  const size_t work_bytes = (NL * cand[0][2] + split) * sizeof(float2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&work, work_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(ghat, 0, G * sizeof(float2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(M, 0, N * sizeof(float2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, 3 * N * sizeof(float2), s);
@@ -298,9 +306,9 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
         for (int li = 0; li < (l1 ? 2 : 1); ++li) {
           p->x_lpb = l1 ? lpbs[li] : 0;
           vie_status ms = VIE_OK;
-          for (int r = 0; r < 3 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, s);
+          for (int r = 0; r < 3 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
           cudaEventRecord(e0, s);
-          for (int r = 0; r < 10 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, s);
+          for (int r = 0; r < 10 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
           cudaEventRecord(e1, s);
           const cudaError_t se = cudaStreamSynchronize(s);
           if (se != cudaSuccess) {
@@ -374,7 +382,7 @@ vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0, 
   const size_t N = (size_t)n[0] * n[1] * n[2];
   const size_t G = (size_t)p->kf[0] * 6 * p->kf[1] * p->kf[2];
   const size_t NL = (size_t)3 * n[1] * n[2];
-  p->work_bytes = NL * p->m[0] * sizeof(double2);
+  p->work_bytes = (NL * p->m[0] + pass_b_split_elems(n[1], n[2], p->m[0], p->m[1], p->m[2])) * sizeof(double2);
   struct { void** ptr; size_t sz; } allocs[] = {
       {(void**)&p->toeplitz, 6 * N * sizeof(double2)}, {(void**)&p->ghat64, G * sizeof(double2)},
       {(void**)&p->ghat32, G * sizeof(float2)},        {(void**)&p->M64, N * sizeof(double2)},
@@ -560,14 +568,14 @@ vie_status vie_matvec(vie_plan* p, const void* x, void* y, int dtype, void* stre
   clear_error();
   vie_status st = check_vec_args(p, x, y, dtype);
   if (st != VIE_OK) return st;
-  return matvec_impl(p, x, y, dtype, MODE_OPERATOR, p->work, (cudaStream_t)stream);
+  return matvec_impl(p, x, y, dtype, MODE_OPERATOR, p->work, p->work_bytes, (cudaStream_t)stream);
 }
 
 vie_status vie_rhs_from_source(vie_plan* p, const void* src, void* b, int dtype, void* stream) {
   clear_error();
   vie_status st = check_vec_args(p, src, b, dtype);
   if (st != VIE_OK) return st;
-  return matvec_impl(p, src, b, dtype, MODE_RHS, p->work, (cudaStream_t)stream);
+  return matvec_impl(p, src, b, dtype, MODE_RHS, p->work, p->work_bytes, (cudaStream_t)stream);
 }
 
 vie_status vie_get_toeplitz(const vie_plan* p, double* out) {

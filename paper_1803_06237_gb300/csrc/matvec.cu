@@ -12,7 +12,11 @@
 //      written back in place.
 //   C  per group of x-lines: inverse FFT along x, crop to nx, and
 //      y = w - M u (operator) or y = M (u - w) (right-hand side of a source).
+// Planes too large for one CTA's shared memory (My Mz beyond a few thousand,
+// e.g. 1200 x 24) run pass B on a cluster of CTAs per kx that share the plane
+// through distributed shared memory (pass_b_cluster_kernel).
 // The spectrum is pre-scaled by 1/(Mx My Mz), so no separate normalisation.
+#include <cooperative_groups.h>
 #include <cuda_pipeline.h>
 #include <stdio.h>
 #include <string.h>
@@ -37,6 +41,7 @@ struct PassPtrs {
   V* work[kMaxBatch];
   const V* ghat[kMaxBatch];
   const V* M[kMaxBatch];
+  V* work2[kMaxBatch];        // y-pass buffer of the split pass B (or null)
 };
 
 // ---------------------------------------------------------------------------
@@ -44,7 +49,8 @@ struct PassPtrs {
 // ---------------------------------------------------------------------------
 template <typename V>
 __global__ void __launch_bounds__(256) pass_a_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int NL,
-                                                     Radices rx, const V* __restrict__ twg, int lines_per_block) {
+                                                     Radices rx, const V* __restrict__ twg, int lines_per_block,
+                                                     int gsz) {
   pdl_wait();
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
@@ -66,7 +72,8 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const __grid_constant__ Pas
   V* res = fft_lines<V, false>(A, B, rx, pitch, nl, tw, tid, nth);
   for (int e = tid; e < nl * Mx; e += nth) {
     const int kx = e / nl, l = e - kx * nl;
-    work[(size_t)kx * NL + l0 + l] = res[l * pitch + kx];
+    const int line = l0 + l, grp = line / gsz;
+    work[((size_t)grp * Mx + kx) * gsz + (line - grp * gsz)] = res[l * pitch + kx];
   }
 }
 
@@ -157,6 +164,348 @@ __global__ void __launch_bounds__(256) pass_b_kernel(const __grid_constant__ Pas
     const int z = cz % nz, c = cz / nz;
     slab[e] = zi[(c * ny + y) * pz + z];
   }
+}
+
+// ---------------------------------------------------------------------------
+// pass B for y-z planes larger than one CTA's shared memory: a cluster of CS
+// CTAs per kx holds the plane in distributed shared memory.
+//   1. CTA r loads the y-lines l = c nz + z, l in [r nl, (r + 1) nl), pads
+//      them with zeros to My and transforms them along y.
+//   2. Cluster barrier.  CTA r takes ky in [r nk, (r + 1) nk), kc at a time:
+//      it gathers the 3 nz values of each ky from the owners' shared memory,
+//      pads along z, transforms along z, multiplies by the folded 3x3
+//      spectrum, transforms back along z and scatters z < nz to the owners.
+//   3. Cluster barrier.  Each CTA transforms its own lines back along y and
+//      writes y < ny to the workspace slab.
+// y goes first because only the 3 nz non-zero lines need it: 3 nz My log My
+// + 3 My Mz log Mz operations, against 3 ny Mz log Mz + 3 Mz My log My for z
+// first, fewer when ny >> nz (the 600 x 11 cross-section of a ring
+// resonator).  Remote accesses walk ky, which is contiguous in the owner's
+// rows.  No CTA touches another's shared memory after the last barrier.
+// ---------------------------------------------------------------------------
+struct ClusterGeom {
+  int cs;       // CTAs per cluster (one cluster per kx)
+  int nl;       // y-lines per CTA
+  int nk;       // ky values per CTA in the z stage
+  int kc;       // ky values per chunk of the z stage
+  int py, pz;   // shared row pitches (odd)
+};
+
+template <typename V>
+__global__ void __launch_bounds__(256) pass_b_cluster_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
+                                                             ClusterGeom q, Radices ry, Radices rz,
+                                                             const V* __restrict__ twyg,
+                                                             const V* __restrict__ twzg) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int kx = blockIdx.x / q.cs;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ny = g.ny, nz = g.nz, My = g.My, Mz = g.Mz;
+  const int nly = 3 * nz;
+  const int py = q.py, pz = q.pz, nl = q.nl, kc = q.kc;
+  const int l0 = rank * nl;
+  const int nown = max(0, min(nly - l0, nl));
+  extern __shared__ unsigned char smem_raw[];
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + My;
+  V* A = twz + Mz;
+  V* B = A + (size_t)nl * py;
+  V* Z0 = B + (size_t)nl * py;
+  V* Z1 = Z0 + (size_t)3 * kc * pz;
+  pdl_launch_dependents();
+  for (int i = tid; i < My; i += nth) twy[i] = twyg[i];
+  for (int i = tid; i < Mz; i += nth) twz[i] = twzg[i];
+  pdl_wait();
+  V* __restrict__ slab = pp.work[blockIdx.y] + (size_t)kx * g.NL;
+  const V* __restrict__ ghat = pp.ghat[blockIdx.y];
+  for (int e = tid; e < nown * My; e += nth) {
+    const int row = e / My, y = e - row * My;
+    A[row * py + y] = (y < ny) ? slab[(size_t)(l0 + row) * ny + y] : zero_c<V>();
+  }
+  __syncthreads();
+  V* Y = fft_lines<V, false>(A, B, ry, py, nown, twy, tid, nth);   // same buffer in every CTA
+  V* spare = (Y == A) ? B : A;
+  cluster.sync();
+
+  const bool fx = kx > g.Mx - kx;
+  const int kxf = fx ? g.Mx - kx : kx;
+  const V* G = ghat + (size_t)kxf * 6 * g.Kz * g.Ky;
+  const size_t gcs = (size_t)g.Kz * g.Ky;
+  const int kbeg = rank * q.nk, kend = min(My, kbeg + q.nk);
+  for (int kb = kbeg; kb < kend; kb += kc) {
+    const int kn = min(kc, kend - kb);
+    // rows (c, j) of Z0: z < nz from the owners of lines c nz + z, then zeros
+    for (int e = tid; e < nly * kn; e += nth) {
+      const int l = e / kn, j = e - l * kn;
+      const int owner = l / nl;
+      const V* src = cluster.map_shared_rank(Y, owner);
+      const int c = l / nz, z = l - c * nz;
+      Z0[(c * kn + j) * pz + z] = src[(size_t)(l - owner * nl) * py + kb + j];
+    }
+    for (int e = tid; e < 3 * kn * (Mz - nz); e += nth) {
+      const int row = e / (Mz - nz), z = nz + (e - row * (Mz - nz));
+      Z0[row * pz + z] = zero_c<V>();
+    }
+    __syncthreads();
+    V* Zf = fft_lines<V, false>(Z0, Z1, rz, pz, 3 * kn, twz, tid, nth);
+    for (int e = tid; e < Mz * kn; e += nth) {
+      const int kz = e / kn, j = e - kz * kn;
+      const int ky = kb + j;
+      const bool fy = ky > My - ky, fz = kz > Mz - kz;
+      const int kyf = fy ? My - ky : ky, kzf = fz ? Mz - kz : kz;
+      const size_t o = (size_t)kzf * g.Ky + kyf;
+      V gxx = G[o], gyy = G[gcs + o], gzz = G[2 * gcs + o];
+      V gxy = G[3 * gcs + o], gxz = G[4 * gcs + o], gyz = G[5 * gcs + o];
+      if (fx ^ fy) gxy = scale(gxy, -1.0f);
+      if (fx ^ fz) gxz = scale(gxz, -1.0f);
+      if (fy ^ fz) gyz = scale(gyz, -1.0f);
+      V* px = Zf + (0 * kn + j) * pz + kz;
+      V* pyv = Zf + (1 * kn + j) * pz + kz;
+      V* pzv = Zf + (2 * kn + j) * pz + kz;
+      const V wx = *px, wy = *pyv, wz = *pzv;
+      *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
+      *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
+      *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+    }
+    __syncthreads();
+    V* Zi = fft_lines<V, true>(Zf, (Zf == Z0) ? Z1 : Z0, rz, pz, 3 * kn, twz, tid, nth);
+    for (int e = tid; e < nly * kn; e += nth) {
+      const int l = e / kn, j = e - l * kn;
+      const int owner = l / nl;
+      V* dst = cluster.map_shared_rank(Y, owner);
+      const int c = l / nz, z = l - c * nz;
+      dst[(size_t)(l - owner * nl) * py + kb + j] = Zi[(c * kn + j) * pz + z];
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  V* Yi = fft_lines<V, true>(Y, spare, ry, py, nown, twy, tid, nth);
+  for (int e = tid; e < nown * ny; e += nth) {
+    const int row = e / ny, y = e - row * ny;
+    slab[(size_t)(l0 + row) * ny + y] = Yi[row * py + y];
+  }
+}
+
+// Cluster shape: the smallest cluster whose CTAs fit a shared-memory budget
+// with at least 16 ky per z-stage chunk, trying first a budget that leaves
+// room for two CTAs per SM, then one CTA per SM, then chunks of any size;
+// false when even eight CTAs do not fit.
+static bool pass_b_cluster_geom(int nz, int My, int Mz, size_t vbytes, ClusterGeom* out) {
+  const long budgets[2] = {(long)(110 * 1024 / vbytes), (long)(220 * 1024 / vbytes)};
+  const int py = My | 1, pz = Mz | 1;
+  const int nly = 3 * nz;
+  for (int want = 16; want >= 1; want -= 15)
+    for (int b = 0; b < 2; ++b)
+      for (int cs = 2; cs <= 8; ++cs) {
+        const int nl = (nly + cs - 1) / cs;
+        const int nk = (My + cs - 1) / cs;
+        const long base = (long)My + Mz + 2L * nl * py;
+        const long kmin = want < nk ? want : nk;
+        if (base + 6L * pz * kmin > budgets[b]) continue;
+        long kc = (budgets[b] - base) / (6L * pz);
+        if (kc > nk) kc = nk;
+        if (kc > 64) kc = 64;
+        *out = ClusterGeom{cs, nl, nk, (int)kc, py, pz};
+        return true;
+      }
+  return false;
+}
+
+static size_t pass_b_cluster_smem(const PassBGeom& g, const ClusterGeom& q, size_t vbytes) {
+  return ((size_t)g.My + g.Mz + 2 * (size_t)q.nl * q.py + 6 * (size_t)q.kc * q.pz) * vbytes;
+}
+
+template <typename V>
+static vie_status launch_pass_b_cluster(const PassPtrs<V>& pp, int count, const PassBGeom& g, Radices ry,
+                                        Radices rz, const V* twy, const V* twz, cudaStream_t s) {
+  ClusterGeom q;
+  if (!pass_b_cluster_geom(g.nz, g.My, g.Mz, sizeof(V), &q)) {
+    set_error("y-z plane %d x %d too large for pass B (eight-CTA cluster)", g.My, g.Mz);
+    return VIE_ERR_INVALID;
+  }
+  const size_t smem = pass_b_cluster_smem(g, q, sizeof(V));
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_cluster_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(g.Mx * q.cs), (unsigned)count);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)q.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  VIE_CUDA_TRY(cudaLaunchKernelEx(&cfg, pass_b_cluster_kernel<V>, pp, g, q, ry, rz, twy, twz));
+  return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Split pass B for planes too large for one CTA (y first, three launches):
+//   B1 the x-pass kernel run along y: lines (kx, l), l = c nz + z, of ny
+//      values, zero-padded to My, forward FFT; output Y[kx][ky][l] (the
+//      x-pass kernels' transposed store, grouped by kx: gsz = 3 nz);
+//   B2 pass_bz_kernel: per (kx, ky) the 3 nz values of the three components,
+//      forward FFT along z in registers, folded 3x3 spectral multiply,
+//      inverse FFT along z, z < nz back in place;
+//   B3 the inverse x-pass kernel run along y with a plain epilogue: inverse
+//      FFT, crop to ny, back into the workspace slab work[kx][l ny + y].
+// A B2 block takes one folded kxf, kBzCells consecutive folded kyf and all
+// their images (kx, Mx - kx) x (ky, My - ky): four contiguous runs of Y,
+// and each folded spectrum entry is read from memory once per block and
+// serves up to 8 spectral cells (kz and Mz - kz lie in the same thread's
+// line).  Threads (c, cell) transform one
+// component's z-line; the multiply exchanges them through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kBzCells = 16;
+constexpr int kBzThreads = 3 * 4 * kBzCells;
+
+// NZ > 0 fixes nz at compile time (the zero padding and the cropped outputs
+// then drop out of the register FFTs); NZ = 0 reads it from g.
+template <typename V, int MZ, int NZ>
+__global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 1)
+    pass_bz_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g, int tiles, const V* __restrict__ twzg) {
+  constexpr int C4 = 4 * kBzCells;
+  const int nz = NZ > 0 ? NZ : g.nz, nl3 = 3 * nz;
+  const int pio = nl3 | 1;
+  extern __shared__ unsigned char smem_raw[];
+  V* twz = reinterpret_cast<V*>(smem_raw);
+  V* Gs = twz + MZ;                          // [comp][kzf][j]: 6 Kz kBzCells
+  V* S = Gs + (size_t)6 * g.Kz * kBzCells;   // [c][kz][cell]
+  V* IO = S + 3 * MZ * C4;                   // [cell][pio]
+  const int kxf = blockIdx.x / tiles;
+  const int kyf0 = (blockIdx.x - kxf * tiles) * kBzCells;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  // cell = image * kBzCells + j; false for images that repeat another
+  // (kxf = 0 or Mx / 2, same for y) and for kyf past the folded range
+  auto cell_k = [&](int cell, int* kx, int* ky) -> bool {
+    const int img = cell / kBzCells, j = cell - img * kBzCells;
+    const int kyf = kyf0 + j;
+    if (kyf >= g.Ky) return false;
+    if ((img & 1) && (kxf == 0 || 2 * kxf == g.Mx)) return false;
+    if ((img & 2) && (kyf == 0 || 2 * kyf == g.My)) return false;
+    *kx = (img & 1) ? g.Mx - kxf : kxf;
+    *ky = (img & 2) ? g.My - kyf : kyf;
+    return true;
+  };
+  pdl_launch_dependents();
+  // plan constants before the dependency wait: twiddles and the spectrum tile
+  for (int i = tid; i < MZ; i += nth) __pipeline_memcpy_async(twz + i, twzg + i, sizeof(V));
+  {
+    const V* G = pp.ghat[blockIdx.y] + (size_t)kxf * 6 * g.Kz * g.Ky;
+    const int nj = min(kBzCells, g.Ky - kyf0);
+    for (int e = tid; e < 6 * g.Kz * kBzCells; e += nth) {
+      const int row = e / kBzCells, j = e - row * kBzCells;   // row = comp Kz + kzf
+      if (j < nj) __pipeline_memcpy_async(Gs + e, G + (size_t)row * g.Ky + kyf0 + j, sizeof(V));
+    }
+  }
+  __pipeline_commit();
+  pdl_wait();
+  V* __restrict__ Y = pp.work2[blockIdx.y];
+  for (int e = tid; e < C4 * nl3; e += nth) {   // all loads in flight at once
+    const int cell = e / nl3, l = e - cell * nl3;
+    int kx, ky;
+    if (cell_k(cell, &kx, &ky))
+      __pipeline_memcpy_async(IO + cell * pio + l, Y + ((size_t)kx * g.My + ky) * nl3 + l, sizeof(V));
+  }
+  __pipeline_commit();
+  __pipeline_wait_prior(0);
+  __syncthreads();
+  const int c = tid / C4, cell = tid - c * C4;
+  int kx0 = 0, ky0 = 0;
+  const bool valid = cell_k(cell, &kx0, &ky0);
+  {
+    V a[MZ];
+#pragma unroll
+    for (int z = 0; z < MZ; ++z) a[z] = (valid && z < nz) ? IO[cell * pio + c * nz + z] : zero_c<V>();
+    reg_fft<V, false, MZ>(a, twz);
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) S[(c * MZ + kz) * C4 + cell] = a[kz];
+  }
+  __syncthreads();
+  const int gcs = g.Kz * kBzCells;
+  for (int e = tid; e < MZ * C4; e += nth) {
+    const int kz = e / C4, cl = e - kz * C4;
+    int kx, ky;
+    if (!cell_k(cl, &kx, &ky)) continue;
+    const bool fx = kx > g.Mx - kx, fy = ky > g.My - ky, fz = kz > MZ - kz;
+    const int kzf = fz ? MZ - kz : kz;
+    const V* Gc = Gs + kzf * kBzCells + (cl % kBzCells);
+    V gxx = Gc[0], gyy = Gc[gcs], gzz = Gc[2 * gcs];
+    V gxy = Gc[3 * gcs], gxz = Gc[4 * gcs], gyz = Gc[5 * gcs];
+    if (fx ^ fy) gxy = scale(gxy, -1.0f);
+    if (fx ^ fz) gxz = scale(gxz, -1.0f);
+    if (fy ^ fz) gyz = scale(gyz, -1.0f);
+    V* px = S + (0 * MZ + kz) * C4 + cl;
+    V* pyv = S + (1 * MZ + kz) * C4 + cl;
+    V* pzv = S + (2 * MZ + kz) * C4 + cl;
+    const V wx = *px, wy = *pyv, wz = *pzv;
+    *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
+    *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
+    *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+  }
+  __syncthreads();
+  {
+    V a[MZ];
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) a[kz] = S[(c * MZ + kz) * C4 + cell];
+    reg_fft<V, true, MZ>(a, twz);
+#pragma unroll
+    for (int z = 0; z < MZ; ++z)
+      if (z < nz) IO[cell * pio + c * nz + z] = a[z];
+  }
+  __syncthreads();
+  for (int e = tid; e < C4 * nl3; e += nth) {
+    const int cell2 = e / nl3, l = e - cell2 * nl3;
+    int kx, ky;
+    if (cell_k(cell2, &kx, &ky)) Y[((size_t)kx * g.My + ky) * nl3 + l] = IO[cell2 * pio + l];
+  }
+}
+
+// z lengths with a compiled B2 kernel; other lengths use the cluster pass.
+// (MZ, NZ) pairs with nz fixed at compile time: 220 nm layers at 20 nm.
+#define VIE_PASS_BZ_SIZES(X) \
+  X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32)
+#define VIE_PASS_BZ_FIXED(X) X(24, 11) X(24, 12)
+
+static bool pass_bz_available(int mz) {
+#define VIE_X(a) if (mz == a) return true;
+  VIE_PASS_BZ_SIZES(VIE_X)
+#undef VIE_X
+  return false;
+}
+
+template <typename V, int MZ, int NZ>
+static vie_status launch_pass_bz(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twz,
+                                 cudaStream_t s) {
+  constexpr int C4 = 4 * kBzCells;
+  const int pio = (3 * g.nz) | 1;
+  const size_t smem = ((size_t)MZ + 6 * (size_t)g.Kz * kBzCells + 3 * MZ * C4 + (size_t)C4 * pio) * sizeof(V);
+  if (smem > 220 * 1024) { set_error("pass B2 shared memory %zu too large", smem); return VIE_ERR_INVALID; }
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_bz_kernel<V, MZ, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  const int tiles = (g.Ky + kBzCells - 1) / kBzCells;
+  const int Kx = g.Mx / 2 + 1;
+  VIE_CUDA_TRY(launch_pdl(pass_bz_kernel<V, MZ, NZ>, dim3((unsigned)(Kx * tiles), (unsigned)count), dim3(kBzThreads),
+                          smem, s, pp, g, tiles, twz));
+  return VIE_OK;
+}
+
+template <typename V>
+static vie_status dispatch_pass_bz(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twz,
+                                   cudaStream_t s) {
+#define VIE_Y(a, b) if (g.Mz == a && g.nz == b) return launch_pass_bz<V, a, b>(pp, count, g, twz, s);
+  VIE_PASS_BZ_FIXED(VIE_Y)
+#undef VIE_Y
+#define VIE_X(a) if (g.Mz == a) return launch_pass_bz<V, a, 0>(pp, count, g, twz, s);
+  VIE_PASS_BZ_SIZES(VIE_X)
+#undef VIE_X
+  set_error("no z-stage kernel for Mz = %d", g.Mz);
+  return VIE_ERR_INVALID;
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +676,7 @@ static vie_status dispatch_pass_b_reg(const PassPtrs<V>& pp, int count, const Pa
 template <typename V>
 __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int nyz,
                                                      int NL, Radices rx, const V* __restrict__ twg,
-                                                     int lines_per_block, int mode) {
+                                                     int lines_per_block, int mode, int gsz) {
   pdl_wait();
   const V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ x = pp.x[blockIdx.y];
@@ -345,7 +694,8 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ Pas
   for (int i = tid; i < Mx; i += nth) tw[i] = twg[i];
   for (int e = tid; e < nl * Mx; e += nth) {
     const int kx = e / nl, l = e - kx * nl;
-    A[l * pitch + kx] = work[(size_t)kx * NL + l0 + l];
+    const int line = l0 + l, grp = line / gsz;
+    A[l * pitch + kx] = work[((size_t)grp * Mx + kx) * gsz + (line - grp * gsz)];
   }
   __syncthreads();
   V* res = fft_lines<V, true>(A, B, rx, pitch, nl, tw, tid, nth);
@@ -355,6 +705,7 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ Pas
     const size_t gi = (size_t)line * nx + ix;
     const size_t vox = (size_t)(line % nyz) * nx + ix;
     const V u = res[l * pitch + ix];
+    if (mode == MODE_PLAIN) { y[gi] = u; continue; }
     const V w = x[gi];
     const V m = Mc[vox];
     y[gi] = (mode == MODE_OPERATOR) ? sub(w, mul(m, u)) : mul(m, sub(u, w));
@@ -367,7 +718,9 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ Pas
 //   step 1: thread (l, n1) transforms the L2 values n1 + L1 n2 and multiplies by
 //           w_Mx^(n1 k2);  step 2: thread (l, k2) transforms the L1 values.
 // Lanes run fastest over the LPB lines of the block, so the transposed
-// workspace accesses work[k][line] are contiguous across a warp.  Shared rows
+// workspace accesses work[k][line] are contiguous across a warp.  Lines may
+// be grouped (gsz lines per group, work[group][k][line in group]); the x
+// passes use one group (gsz = NL).  Shared rows
 // are padded to a pitch congruent to LPB mod 16 (no bank conflicts for 8-byte
 // elements).
 // ---------------------------------------------------------------------------
@@ -375,7 +728,7 @@ __host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb
 
 template <typename V, int L1, int L2, int LPB>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
-    const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg) {
+    const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
   constexpr int MX = L1 * L2;
@@ -426,15 +779,18 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
     for (int n1 = 0; n1 < L1; ++n1) a[n1] = T[k2 * R + n1 * LPB + l];
     reg_fft<V, false, L1>(a, tw1);
     if (l < nl) {
+      const int line = l0 + l, grp = line / gsz;
+      V* dst = work + (size_t)grp * MX * gsz + (line - grp * gsz);
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1) work[(size_t)(k2 + L2 * k1) * NL + l0 + l] = a[k1];
+      for (int k1 = 0; k1 < L1; ++k1) dst[(size_t)(k2 + L2 * k1) * gsz] = a[k1];
     }
   }
 }
 
 template <typename V, int L1, int L2, int LPB>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
-    const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode) {
+    const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode,
+    int gsz) {
   const V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ x = pp.x[blockIdx.y];
   const V* __restrict__ Mc = pp.M[blockIdx.y];
@@ -459,13 +815,17 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     // FFTs; the contrast rows are plan data, x only after the dependency wait
     for (int i = tid; i < MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
     __pipeline_commit();
-    for (int l = 0; l < nl; ++l) {
-      const V* msrc = Mc + (size_t)((l0 + l) % nyz) * nx;
-      for (int i = tid; i < nx; i += nth) __pipeline_memcpy_async(Ms + l * nx + i, msrc + i, sizeof(V));
+    if (mode != MODE_PLAIN) {
+      for (int l = 0; l < nl; ++l) {
+        const V* msrc = Mc + (size_t)((l0 + l) % nyz) * nx;
+        for (int i = tid; i < nx; i += nth) __pipeline_memcpy_async(Ms + l * nx + i, msrc + i, sizeof(V));
+      }
     }
     pdl_wait();
-    const V* xsrc = x + (size_t)l0 * nx;
-    for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
+    if (mode != MODE_PLAIN) {
+      const V* xsrc = x + (size_t)l0 * nx;
+      for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
+    }
     __pipeline_commit();
     __pipeline_wait_prior(1);      // twiddles only
   }
@@ -477,10 +837,11 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
   // input a = a1 + L1 a2 (a spectrum index kx), output b = b2 + L2 b1 (x)
   if (tid < LPB * L1) {
     const int l = tid % LPB, a1 = tid / LPB;
+    const int line = l0 + (l < nl ? l : 0), grp = line / gsz;
+    const V* src = work + (size_t)grp * MX * gsz + (line - grp * gsz);
     V a[L2];
 #pragma unroll
-    for (int a2 = 0; a2 < L2; ++a2)
-      a[a2] = (l < nl) ? work[(size_t)(a1 + L1 * a2) * NL + l0 + l] : zero_c<V>();
+    for (int a2 = 0; a2 < L2; ++a2) a[a2] = (l < nl) ? src[(size_t)(a1 + L1 * a2) * gsz] : zero_c<V>();
     reg_fft<V, true, L2>(a, tw2);
 #pragma unroll
     for (int b2 = 0; b2 < L2; ++b2) T[b2 * R + a1 * LPB + l] = (b2 == 0) ? a[0] : mulc(a[b2], twx[a1 * b2]);
@@ -508,6 +869,7 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     for (int e = tid; e < total; e += nth) {
       const int l = e / nx, ix = e - l * nx;
       const V uu = Ys[l * P + ix];
+      if (mode == MODE_PLAIN) { y[g0 + e] = uu; continue; }
       const V wv = Xs[e], mv = Ms[e];
       y[g0 + e] = (mode == MODE_OPERATOR) ? sub(wv, mul(mv, uu)) : mul(mv, sub(uu, wv));
     }
@@ -520,22 +882,24 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
 
 template <typename V, int L1, int L2, int LPB>
 static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
-                                const V* twx, int mode, cudaStream_t s, bool* done) {
+                                const V* twx, int mode, cudaStream_t s, bool* done, int gsz) {
   {
     constexpr int R = pitch_mod16(L1 * LPB, LPB);
     constexpr int NT = LPB * (L1 > L2 ? L1 : L2);
     const int P = pitch_mod16(nx, LPB);
-    const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P + (forward ? 0 : 2 * LPB * nx)) * sizeof(V);
+    const bool operands = !forward && mode != MODE_PLAIN;   // epilogue rows of x and M
+    const size_t smem = (size_t)(L1 * L2 + L1 + L2 + L2 * R + LPB * P + (operands ? 2 * LPB * nx : 0)) * sizeof(V);
     if (smem > 200 * 1024) { *done = false; return VIE_OK; }
     const dim3 blocks((unsigned)((NL + LPB - 1) / LPB), (unsigned)count);
     if (forward) {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      VIE_CUDA_TRY(launch_pdl(pass_a4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, NL, twx));
+      VIE_CUDA_TRY(launch_pdl(pass_a4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, NL, twx, gsz));
     } else {
       VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      VIE_CUDA_TRY(launch_pdl(pass_c4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, nyz, NL, twx, mode));
+      VIE_CUDA_TRY(
+          launch_pdl(pass_c4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, nyz, NL, twx, mode, gsz));
     }
     VIE_LAUNCH_CHECK();
     *done = true;
@@ -545,17 +909,27 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
 
 // Four lines per block, or two when four would leave fewer than two blocks
 // per SM (more blocks hide the latency of the small per-line work), unless
-// the plan's tuner chose (lpb = 2 or 4).
+// the plan's tuner chose (lpb = 2 or 4).  Inverse passes with at least four
+// blocks of eight lines per SM (complex64) take eight lines when they fit:
+// each transposed row read is then 64 contiguous bytes, which matters once
+// the workspace no longer fits in L2 (forward passes measured slower so).
 template <typename V, int L1, int L2>
 static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
-                            const V* twx, int mode, cudaStream_t s, bool* done, int lpb) {
+                            const V* twx, int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
   if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
+    if constexpr (sizeof(V) == sizeof(float2)) {
+      const long blocks8 = (long)((NL + 7) / 8) * count;
+      if (lpb == 8 || (lpb == 0 && !forward && blocks8 >= 4L * 152)) {
+        vie_status st = launch_x4_lpb<V, L1, L2, 8>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+        if (st != VIE_OK || *done) return st;
+      }
+    }
     const long blocks4 = (long)((NL + 3) / 4) * count;
-    if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
-    if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
+    if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     if (blocks4 < 2L * 152)
-      return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
-    return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done);
+      return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
   } else {
     *done = false;
     return VIE_OK;
@@ -573,10 +947,10 @@ void x4_factors(int mx, int* l1, int* l2) {
 
 template <typename V>
 static vie_status dispatch_x4(bool forward, int l1, int l2, const PassPtrs<V>& pp, int count, int nx, int nyz,
-                              int NL, const V* twx, int mode, cudaStream_t s, bool* done, int lpb) {
+                              int NL, const V* twx, int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
   *done = false;
 #define VIE_X(a, b) \
-  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb);
+  if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb, gsz);
   VIE_PASS_X4_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
@@ -585,6 +959,74 @@ static vie_status dispatch_x4(bool forward, int l1, int l2, const PassPtrs<V>& p
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
+// Planes that neither the register pass B nor the one-CTA generic pass B can
+// hold take the split pass B when a z-stage kernel exists for Mz.
+static bool pass_b_needs_more_than_one_cta(int My, int Mz, size_t vbytes) {
+  return (size_t)(My + Mz + 2 * 3 * Mz * (My + 1)) * vbytes > 220 * 1024;
+}
+
+size_t pass_b_split_elems(int ny, int nz, int Mx, int My, int Mz) {
+  (void)ny;
+  if (!pass_b_needs_more_than_one_cta(My, Mz, sizeof(double2)) || !pass_bz_available(Mz)) return 0;
+  return (size_t)Mx * My * 3 * nz;
+}
+
+// Generic (shared-memory Stockham) x-pass kernels for `n`-value lines
+// transformed at length rd.len: pass_a_kernel forward, pass_c_kernel inverse.
+template <typename V>
+static vie_status launch_x_generic(bool forward, const PassPtrs<V>& pp, int count, int n, int nyz, int NL,
+                                   const Radices& rd, const V* tw, int mode, cudaStream_t s, int gsz) {
+  const size_t line_bytes = (size_t)2 * (rd.len + 1) * sizeof(V);
+  const size_t tw_bytes = (size_t)rd.len * sizeof(V);
+  int lpb = 4;
+  while (lpb > 1 && tw_bytes + lpb * line_bytes > 200 * 1024) lpb >>= 1;
+  const size_t smem = tw_bytes + lpb * line_bytes;
+  if (smem > 220 * 1024) {
+    set_error("FFT length %d too large for the line-pass shared memory", rd.len);
+    return VIE_ERR_INVALID;
+  }
+  const dim3 blocks((unsigned)((NL + lpb - 1) / lpb), (unsigned)count);
+  if (forward) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    pass_a_kernel<V><<<blocks, 256, smem, s>>>(pp, n, NL, rd, tw, lpb, gsz);
+  } else {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    pass_c_kernel<V><<<blocks, 256, smem, s>>>(pp, n, nyz, NL, rd, tw, lpb, mode, gsz);
+  }
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
+// Split pass B (B1, B2, B3 above) on the workspaces pp.work / pp.work2.
+template <typename V>
+static vie_status run_split_b(const vie_plan* p, const PassPtrs<V>& pp, int count, const PassBGeom& g,
+                              const V* twy, const V* twz, cudaStream_t s) {
+  const int NLy = g.Mx * 3 * g.nz;
+  int l1 = 0, l2 = 0;
+  x4_factors(g.My, &l1, &l2);
+  PassPtrs<V> p1 = pp;   // B1: lines of the slab -> Y
+  PassPtrs<V> p3 = pp;   // B3: Y -> lines of the slab
+  for (int k = 0; k < count; ++k) {
+    p1.x[k] = pp.work[k];
+    p1.work[k] = pp.work2[k];
+    p3.work[k] = pp.work2[k];
+    p3.y[k] = pp.work[k];
+  }
+  bool done = false;
+  vie_status st = VIE_OK;
+  const int gsz = 3 * g.nz;   // one group of lines per kx: Y[kx][ky][l]
+  if (l1) st = dispatch_x4<V>(true, l1, l2, p1, count, g.ny, 1, NLy, twy, MODE_PLAIN, s, &done, 0, gsz);
+  if (st == VIE_OK && !done)
+    st = launch_x_generic<V>(true, p1, count, g.ny, 1, NLy, radices_of(p->ax[1]), twy, MODE_PLAIN, s, gsz);
+  if (st == VIE_OK) st = dispatch_pass_bz<V>(pp, count, g, twz, s);
+  done = false;
+  if (st == VIE_OK && l1)
+    st = dispatch_x4<V>(false, l1, l2, p3, count, g.ny, 1, NLy, twy, MODE_PLAIN, s, &done, 0, gsz);
+  if (st == VIE_OK && !done)
+    st = launch_x_generic<V>(false, p3, count, g.ny, 1, NLy, radices_of(p->ax[1]), twy, MODE_PLAIN, s, gsz);
+  return st;
+}
+
 // The three passes for `count` problems of one shape (count <= kMaxBatch).
 template <typename V>
 static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count, const V* twx, const V* twy,
@@ -604,27 +1046,33 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
     return VIE_ERR_INVALID;
   }
   const size_t smem_b = (size_t)(My + Mz + 2 * 3 * Mz * (My + 1)) * sizeof(V);
-  if (smem_b > 220 * 1024) {
-    set_error("y-z plane %d x %d too large for the per-kx pass", My, Mz);
-    return VIE_ERR_INVALID;
-  }
   const dim3 blocks_ac((unsigned)((NL + lpb - 1) / lpb), (unsigned)count);
   int l1 = 0, l2 = 0;
   x4_factors(Mx, &l1, &l2);
   bool done = false;
   vie_status st = VIE_OK;
   if (l1) {
-    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb);
+    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb, NL);
     if (st != VIE_OK) return st;
   }
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-    pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, NL, radices_of(p->ax[0]), twx, lpb);
+    pass_a_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, NL, radices_of(p->ax[0]), twx, lpb, NL);
     VIE_LAUNCH_CHECK();
   }
   PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
   st = dispatch_pass_b_reg<V>(pp, count, g, twy, twz, s, &done);
   if (st != VIE_OK) return st;
+  if (!done && smem_b > 220 * 1024 && pp.work2[0] && pass_bz_available(Mz)) {
+    st = run_split_b<V>(p, pp, count, g, twy, twz, s);
+    if (st != VIE_OK) return st;
+    done = true;
+  }
+  if (!done && smem_b > 220 * 1024) {
+    st = launch_pass_b_cluster<V>(pp, count, g, radices_of(p->ax[1]), radices_of(p->ax[2]), twy, twz, s);
+    if (st != VIE_OK) return st;
+    done = true;
+  }
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
     pass_b_kernel<V><<<dim3((unsigned)Mx, (unsigned)count), threads, smem_b, s>>>(pp, g, radices_of(p->ax[1]),
@@ -633,25 +1081,37 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   }
   done = false;
   if (l1) {
-    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb);
+    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb, NL);
     if (st != VIE_OK) return st;
   }
   if (!done) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-    pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, ny * nz, NL, radices_of(p->ax[0]), twx, lpb, mode);
+    pass_c_kernel<V><<<blocks_ac, threads, smem_ac, s>>>(pp, nx, ny * nz, NL, radices_of(p->ax[0]), twx, lpb, mode,
+                                                        NL);
     VIE_LAUNCH_CHECK();
   }
   return VIE_OK;
 }
 
+// The split pass B's buffer behind the x-pass spectra of a workspace of
+// work_bytes, or null (that pass B is not needed or does not fit).
+template <typename V>
+static V* split_buffer(const vie_plan* p, V* work, size_t work_bytes) {
+  const size_t xs = (size_t)3 * p->n[1] * p->n[2] * p->m[0];
+  const size_t e = pass_b_split_elems(p->n[1], p->n[2], p->m[0], p->m[1], p->m[2]);
+  if (e == 0 || (xs + e) * sizeof(V) > work_bytes) return nullptr;
+  return work + xs;
+}
+
 template <typename V>
 static vie_status run_one(vie_plan* p, const V* x, V* y, const V* ghat, const V* Mc, const V* twx, const V* twy,
-                          const V* twz, int mode, V* work, cudaStream_t s) {
+                          const V* twz, int mode, V* work, size_t work_bytes, cudaStream_t s) {
   PassPtrs<V> pp;
   memset(&pp, 0, sizeof(pp));
   pp.x[0] = x;
   pp.y[0] = y;
   pp.work[0] = work;
+  pp.work2[0] = split_buffer<V>(p, work, work_bytes);
   pp.ghat[0] = ghat;
   pp.M[0] = Mc;
   return run_passes<V>(p, pp, 1, twx, twy, twz, mode, s);
@@ -674,6 +1134,7 @@ static vie_status group_passes(vie_plan* const* plans, int count, const void* co
       pp.x[k] = (const V*)x[i0 + k];
       pp.y[k] = (V*)y[i0 + k];
       pp.work[k] = (V*)q->work;
+      pp.work2[k] = split_buffer<V>(q, (V*)q->work, q->work_bytes);
       pp.ghat[k] = f32 ? (const V*)q->ghat32 : (const V*)q->ghat64;
       pp.M[k] = f32 ? (const V*)q->M32 : (const V*)q->M64;
     }
@@ -691,13 +1152,14 @@ vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x,
   return VIE_ERR_INVALID;
 }
 
-vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, void* work, cudaStream_t s) {
+vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, void* work, size_t work_bytes,
+                       cudaStream_t s) {
   if (dtype == VIE_C64)
     return run_one<float2>(p, (const float2*)x, (float2*)y, p->ghat32, p->M32, p->ax[0].tw32, p->ax[1].tw32,
-                           p->ax[2].tw32, mode, (float2*)work, s);
+                           p->ax[2].tw32, mode, (float2*)work, work_bytes, s);
   if (dtype == VIE_C128)
     return run_one<double2>(p, (const double2*)x, (double2*)y, p->ghat64, p->M64, p->ax[0].tw64, p->ax[1].tw64,
-                            p->ax[2].tw64, mode, (double2*)work, s);
+                            p->ax[2].tw64, mode, (double2*)work, work_bytes, s);
   set_error("unknown dtype %d", dtype);
   return VIE_ERR_INVALID;
 }
@@ -774,5 +1236,6 @@ extern "C" vie_status vie_matvec_static_scratch(const vie_plan* plan, const void
   void* work = nullptr;
   vie_status st = static_scratch_address(&work);
   if (st != VIE_OK) return st;
-  return matvec_impl(const_cast<vie_plan*>(plan), x_dev, y_dev, dtype, MODE_OPERATOR, work, (cudaStream_t)stream);
+  return matvec_impl(const_cast<vie_plan*>(plan), x_dev, y_dev, dtype, MODE_OPERATOR, work, kStaticScratchBytes,
+                     (cudaStream_t)stream);
 }

@@ -158,10 +158,17 @@ namespace vie {
 
 vie_status compute_toeplitz(vie_plan* p, cudaStream_t s);
 vie_status compute_spectrum(vie_plan* p, cudaStream_t s);
+// `work` holds work_bytes; beyond the 3 ny nz Mx spectra of the x passes it
+// may hold the y-pass buffer of the split pass B (pass_b_split_elems).
 vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode,
-                       void* work, cudaStream_t s);
+                       void* work, size_t work_bytes, cudaStream_t s);
+// Complex values of the split pass B's buffer (Mx My 3 nz) when a plane of
+// this shape takes it, else 0.
+size_t pass_b_split_elems(int ny, int nz, int Mx, int My, int Mz);
 
-enum { MODE_OPERATOR = 0, MODE_RHS = 1 };
+// MODE_PLAIN (x-pass kernels run along y inside pass B): inverse FFT and
+// crop only, no contrast epilogue.
+enum { MODE_OPERATOR = 0, MODE_RHS = 1, MODE_PLAIN = 2 };
 
 // Right preconditioner z = P(v) on vectors of type dtype (3 N complex).
 typedef vie_status (*vie_precond_fn)(void* ctx, int dtype, const void* v, void* z, cudaStream_t s);

@@ -20,6 +20,11 @@ Workloads (sizes in units of the voxel size h unless stated):
 * ``batch48``    48 guides of the same cross-section: absorber length
                  {1,2,4,6,8,10} um x degree {0,1,2,3} x eps''_max {0.5, 2};
                  nx = 250 + 50 L[um] (a 5 um body plus the absorber).
+* ``microring``  ring resonator, R = 5 um, 450 x 220 nm strips, 200 nm gap
+                 to a straight bus along x, h = 20 nm, 800 x 600 x 11 voxels,
+                 cubic absorbers over the first and last 4 um in x, y-sheet
+                 on the bus 1 um inside the left absorber's end; 16
+                 wavelengths in [1.54, 1.56] um (``microring_wavelengths``).
 """
 from __future__ import annotations
 
@@ -181,3 +186,40 @@ def random_guide(seed: int, nx: int = 160, ny: int = 40, nz: int = 11, h_um: flo
     prof = np.exp(-(zz[:, None] ** 2 + (y[None, :] - yc) ** 2) / (0.2 / h_um) ** 2)
     src[1, :, :, ix] = prof
     return Workload(f"guide_{seed}", (nx, ny, nz), h_um, _k0(), eps_bg, eps, [ab], "sheet", src, eps_core=eps_core)
+
+
+def microring(nx: int = 800, ny: int = 600, nz: int = 11, h_um: float = 0.02, radius_um: float = 5.0,
+              width_um: float = 0.45, gap_um: float = 0.2, absorber_len_um: float = 4.0, degree: int = 3,
+              r_rt: float = 1e-10, eps_core: float = 12.11, eps_bg: float = 2.085,
+              lambda_um: float = LAMBDA0_UM) -> Workload:
+    """Ring resonator beside a straight bus (all nz layers core).  The bus
+    runs along x with its centre 20 voxels from the low-y edge; the ring is
+    centred in x, its centre-line radius ``radius_um``, with ``gap_um``
+    between the bus and the ring edges.  The absorbers span the full
+    cross-section over their x range, so at this grid size they also reach
+    the ring's outermost x sides."""
+    w = width_um / h_um
+    R = radius_um / h_um
+    yb = 20.0
+    yc = yb + w + gap_um / h_um + R
+    xc = nx / 2.0
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    X, Y = np.meshgrid(x, y)                               # (ny, nx)
+    inside = (np.abs(Y - yb) <= w / 2) | (np.abs(np.hypot(X - xc, Y - yc) - R) <= w / 2)
+    eps = np.full((nz, ny, nx), eps_bg + 0j)
+    eps[:, inside] = eps_core
+    L = absorber_len_um / h_um
+    abs_ = [Absorber(x0=L, length=L, degree=degree, r_rt=r_rt, direction=-1),
+            Absorber(x0=nx - L, length=L, degree=degree, r_rt=r_rt, direction=+1)]
+    src = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+    ix = int(round(L + 1.0 / h_um))
+    zz = np.arange(nz) + 0.5 - nz / 2.0
+    src[1, :, :, ix] = np.exp(-(zz[:, None] ** 2 + (y[None, :] - yb) ** 2) / (0.2 / h_um) ** 2)
+    return Workload("microring", (nx, ny, nz), h_um, 2.0 * math.pi / lambda_um, eps_bg, eps, abs_, "sheet",
+                    src, eps_core=eps_core)
+
+
+def microring_wavelengths(count: int = 16, lo_um: float = 1.54, hi_um: float = 1.56) -> list:
+    """``count`` equally spaced wavelengths in [lo, hi] (um)."""
+    return [lo_um + (hi_um - lo_um) * i / (count - 1) for i in range(count)]

@@ -238,3 +238,85 @@ def test_autotuned_plan_matches_oracle(grid):
     assert clone.info()["m"] == info["m"] and clone.info()["x_lines_per_block"] == info["x_lines_per_block"]
     vie.vie_set_permittivity(clone, eps)
     assert rel_l2(_apply(clone, x, torch.complex64), y_ref) <= TOL32
+
+
+@pytest.mark.parametrize("grid", [(4, 200, 12), (3, 300, 6), (5, 97, 13), (4, 100, 7), (2, 150, 20),
+                                  (3, 200, 23)])
+def test_large_plane_pass_b_grids(grid):
+    """y-z planes larger than one CTA's shared memory (complex64 from My Mz
+    ~ 4.7e3, complex128 from ~2.3e3; (4, 100, 7) only in complex128): the
+    split pass B (y along lines, z-stage kernel, inverse y) where Mz has a
+    z-stage kernel, else (Mz = 40, 45) the pass on a cluster of 2-8 CTAs
+    sharing the plane in distributed shared memory.  Ragged tiles, folded
+    images at kxf = 0 and Mx / 2."""
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    eps = workloads.random_permittivity(grid, seed=61)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=62)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
+    assert rel_l2(_apply(plan, x, torch.complex128), y_ref) <= TOL64
+    assert rel_l2(_apply(plan, x, torch.complex64), y_ref) <= TOL32
+
+
+def _absorber_dicts(wl):
+    out = []
+    for ab in wl.absorbers:
+        e2 = op.eps2_max_from_rrt(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core)
+        out.append(dict(x0=ab.x0, length=ab.length, degree=ab.degree, direction=ab.direction, eps2_max=e2))
+    return out
+
+
+@pytest.fixture(scope="module")
+def microring_plan():
+    wl = workloads.microring()
+    absorbers = _absorber_dicts(wl)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    assert plan.info()["m"] == (1600, 1200, 24)
+    vie.vie_set_permittivity(plan, wl.eps, absorbers)
+    M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, absorbers))
+    return wl, plan, M
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, TOL64), (torch.complex64, 1e-5)])
+def test_full_size_microring_sampled(microring_plan, dtype, tol):
+    """800 x 600 x 11 ring resonator (circulant 1600 x 1200 x 24, pass B on
+    CTA clusters): sparse input, sampled outputs summed directly by the
+    oracle, including the neighbours of every source entry."""
+    wl, plan, M = microring_plan
+    x = workloads.sparse_currents(wl.grid, seed=71, nnz=16)
+    y = _apply(plan, x, dtype)
+    idx = workloads.sample_indices(wl.grid, seed=72, count=200)
+    nzv = np.flatnonzero(x.ravel())
+    nx, ny = wl.grid[0], wl.grid[1]
+    idx = np.unique(np.concatenate([idx, nzv, nzv + 1, nzv + nx, nzv + nx * ny]))
+    idx = idx[idx < 3 * wl.n_voxels]
+    ref = oracle_sparse_apply(wl.kappa, wl.grid, M, x, idx)
+    assert np.abs(y[idx] - ref).max() <= tol * np.abs(ref).max()
+    assert np.isfinite(y).all()
+
+
+def _apply_static(plan, x, dtype):
+    xd = torch.from_numpy(np.ascontiguousarray(x.ravel())).to(dtype).cuda()
+    yd = torch.empty_like(xd)
+    vie.vie_matvec_static_scratch(plan, xd, yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.complex128)
+
+
+def test_static_workspace_large_plane():
+    """16 x 600 x 11 (circulant 32 x 1200 x 24): the plan's workspace holds the
+    split pass B's buffer; the 16 MiB static workspace holds it in complex64
+    but not in complex128, where the same plan falls back to the cluster
+    pass.  All four routes agree with the oracle."""
+    grid = (16, 600, 11)
+    plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    assert plan.info()["m"] == (32, 1200, 24)
+    eps = workloads.random_permittivity(grid, seed=81)
+    vie.vie_set_permittivity(plan, eps)
+    x = workloads.random_currents(grid, seed=82)
+    M = op.contrast_M(op.chi_from_permittivity(eps, 2.085))
+    y_ref = oracle_matvec(grid, plan.info()["kappa"], M, x).ravel()
+    for dtype, tol in ((torch.complex128, TOL64), (torch.complex64, TOL32)):
+        assert rel_l2(_apply(plan, x, dtype), y_ref) <= tol
+        assert rel_l2(_apply_static(plan, x, dtype), y_ref) <= tol
