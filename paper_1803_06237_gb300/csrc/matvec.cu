@@ -370,54 +370,57 @@ template <typename V, int MZ, int NZ>
 __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 1)
     pass_bz_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g, int tiles, const V* __restrict__ twzg) {
   constexpr int C4 = 4 * kBzCells;
+  constexpr int KZ = MZ / 2 + 1;
   const int nz = NZ > 0 ? NZ : g.nz, nl3 = 3 * nz;
   const int pio = nl3 | 1;
   extern __shared__ unsigned char smem_raw[];
-  V* twz = reinterpret_cast<V*>(smem_raw);
-  V* Gs = twz + MZ;                          // [comp][kzf][j]: 6 Kz kBzCells
-  V* S = Gs + (size_t)6 * g.Kz * kBzCells;   // [c][kz][cell]
+  long long* base = reinterpret_cast<long long*>(smem_raw);   // Y offset of each cell, -1: no cell
+  int* flip = reinterpret_cast<int*>(base + C4);              // bit 0: kx > Mx - kx, bit 1: ky > My - ky
+  V* twz = reinterpret_cast<V*>(flip + C4);
+  V* Gs = twz + MZ;                          // [comp][kzf][j]: 6 KZ kBzCells
+  V* S = Gs + (size_t)6 * KZ * kBzCells;     // [c][kz][cell]
   V* IO = S + 3 * MZ * C4;                   // [cell][pio]
   const int kxf = blockIdx.x / tiles;
   const int kyf0 = (blockIdx.x - kxf * tiles) * kBzCells;
   const int tid = threadIdx.x, nth = blockDim.x;
-  // cell = image * kBzCells + j; false for images that repeat another
-  // (kxf = 0 or Mx / 2, same for y) and for kyf past the folded range
-  auto cell_k = [&](int cell, int* kx, int* ky) -> bool {
-    const int img = cell / kBzCells, j = cell - img * kBzCells;
-    const int kyf = kyf0 + j;
-    if (kyf >= g.Ky) return false;
-    if ((img & 1) && (kxf == 0 || 2 * kxf == g.Mx)) return false;
-    if ((img & 2) && (kyf == 0 || 2 * kyf == g.My)) return false;
-    *kx = (img & 1) ? g.Mx - kxf : kxf;
-    *ky = (img & 2) ? g.My - kyf : kyf;
-    return true;
-  };
   pdl_launch_dependents();
   // plan constants before the dependency wait: twiddles and the spectrum tile
   for (int i = tid; i < MZ; i += nth) __pipeline_memcpy_async(twz + i, twzg + i, sizeof(V));
   {
-    const V* G = pp.ghat[blockIdx.y] + (size_t)kxf * 6 * g.Kz * g.Ky;
+    const V* G = pp.ghat[blockIdx.y] + (size_t)kxf * 6 * KZ * g.Ky;
     const int nj = min(kBzCells, g.Ky - kyf0);
-    for (int e = tid; e < 6 * g.Kz * kBzCells; e += nth) {
-      const int row = e / kBzCells, j = e - row * kBzCells;   // row = comp Kz + kzf
+    for (int e = tid; e < 6 * KZ * kBzCells; e += nth) {
+      const int row = e / kBzCells, j = e - row * kBzCells;   // row = comp KZ + kzf
       if (j < nj) __pipeline_memcpy_async(Gs + e, G + (size_t)row * g.Ky + kyf0 + j, sizeof(V));
     }
   }
   __pipeline_commit();
+  // cell = image * kBzCells + j: (kx, ky) = (kxf or Mx - kxf, kyf or My - kyf);
+  // no cell where an image repeats another (kxf = 0 or Mx / 2, same for y)
+  // or kyf lies past the folded range
+  if (tid < C4) {
+    const int img = tid / kBzCells, kyf = kyf0 + (tid - img * kBzCells);
+    bool ok = kyf < g.Ky;
+    if ((img & 1) && (kxf == 0 || 2 * kxf == g.Mx)) ok = false;
+    if ((img & 2) && (kyf == 0 || 2 * kyf == g.My)) ok = false;
+    const int kx = (img & 1) ? g.Mx - kxf : kxf;
+    const int ky = (img & 2) ? g.My - kyf : kyf;
+    base[tid] = ok ? ((long long)kx * g.My + ky) * nl3 : -1;
+    flip[tid] = (kx > g.Mx - kx ? 1 : 0) | (ky > g.My - ky ? 2 : 0);
+  }
+  __syncthreads();
   pdl_wait();
   V* __restrict__ Y = pp.work2[blockIdx.y];
   for (int e = tid; e < C4 * nl3; e += nth) {   // all loads in flight at once
     const int cell = e / nl3, l = e - cell * nl3;
-    int kx, ky;
-    if (cell_k(cell, &kx, &ky))
-      __pipeline_memcpy_async(IO + cell * pio + l, Y + ((size_t)kx * g.My + ky) * nl3 + l, sizeof(V));
+    const long long b = base[cell];
+    if (b >= 0) __pipeline_memcpy_async(IO + cell * pio + l, Y + b + l, sizeof(V));
   }
   __pipeline_commit();
   __pipeline_wait_prior(0);
   __syncthreads();
   const int c = tid / C4, cell = tid - c * C4;
-  int kx0 = 0, ky0 = 0;
-  const bool valid = cell_k(cell, &kx0, &ky0);
+  const bool valid = base[cell] >= 0;
   {
     V a[MZ];
 #pragma unroll
@@ -427,26 +430,33 @@ __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 
     for (int kz = 0; kz < MZ; ++kz) S[(c * MZ + kz) * C4 + cell] = a[kz];
   }
   __syncthreads();
-  const int gcs = g.Kz * kBzCells;
-  for (int e = tid; e < MZ * C4; e += nth) {
-    const int kz = e / C4, cl = e - kz * C4;
-    int kx, ky;
-    if (!cell_k(cl, &kx, &ky)) continue;
-    const bool fx = kx > g.Mx - kx, fy = ky > g.My - ky, fz = kz > MZ - kz;
-    const int kzf = fz ? MZ - kz : kz;
-    const V* Gc = Gs + kzf * kBzCells + (cl % kBzCells);
-    V gxx = Gc[0], gyy = Gc[gcs], gzz = Gc[2 * gcs];
-    V gxy = Gc[3 * gcs], gxz = Gc[4 * gcs], gyz = Gc[5 * gcs];
-    if (fx ^ fy) gxy = scale(gxy, -1.0f);
-    if (fx ^ fz) gxz = scale(gxz, -1.0f);
-    if (fy ^ fz) gyz = scale(gyz, -1.0f);
-    V* px = S + (0 * MZ + kz) * C4 + cl;
-    V* pyv = S + (1 * MZ + kz) * C4 + cl;
-    V* pzv = S + (2 * MZ + kz) * C4 + cl;
-    const V wx = *px, wy = *pyv, wz = *pzv;
-    *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
-    *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
-    *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+  // u_p = sum_q G_pq w_q: item (image, kzf, j) serves kz = kzf and Mz - kzf
+  const int gcs = KZ * kBzCells;
+  for (int e = tid; e < 4 * KZ * kBzCells; e += nth) {
+    const int j = e % kBzCells, r = e / kBzCells;
+    const int kzf = r % KZ, img = r / KZ;
+    const int cl = img * kBzCells + j;
+    if (base[cl] < 0) continue;
+    const int fl = flip[cl];
+    const bool fx = fl & 1, fy = fl & 2;
+    const V* Gc = Gs + kzf * kBzCells + j;
+    const V gxx = Gc[0], gyy = Gc[gcs], gzz = Gc[2 * gcs];
+    const V gxy0 = Gc[3 * gcs], gxz0 = Gc[4 * gcs], gyz0 = Gc[5 * gcs];
+    const int nkz = (kzf == 0 || 2 * kzf == MZ) ? 1 : 2;
+    for (int t = 0; t < nkz; ++t) {
+      const int kz = t ? MZ - kzf : kzf;
+      const bool fz = t == 1;
+      const V gxy = (fx ^ fy) ? scale(gxy0, -1.0f) : gxy0;
+      const V gxz = (fx ^ fz) ? scale(gxz0, -1.0f) : gxz0;
+      const V gyz = (fy ^ fz) ? scale(gyz0, -1.0f) : gyz0;
+      V* px = S + (0 * MZ + kz) * C4 + cl;
+      V* pyv = S + (1 * MZ + kz) * C4 + cl;
+      V* pzv = S + (2 * MZ + kz) * C4 + cl;
+      const V wx = *px, wy = *pyv, wz = *pzv;
+      *px = add(add(mul(gxx, wx), mul(gxy, wy)), mul(gxz, wz));
+      *pyv = add(add(mul(gxy, wx), mul(gyy, wy)), mul(gyz, wz));
+      *pzv = add(add(mul(gxz, wx), mul(gyz, wy)), mul(gzz, wz));
+    }
   }
   __syncthreads();
   {
@@ -461,8 +471,8 @@ __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 
   __syncthreads();
   for (int e = tid; e < C4 * nl3; e += nth) {
     const int cell2 = e / nl3, l = e - cell2 * nl3;
-    int kx, ky;
-    if (cell_k(cell2, &kx, &ky)) Y[((size_t)kx * g.My + ky) * nl3 + l] = IO[cell2 * pio + l];
+    const long long b = base[cell2];
+    if (b >= 0) Y[b + l] = IO[cell2 * pio + l];
   }
 }
 
@@ -484,7 +494,8 @@ static vie_status launch_pass_bz(const PassPtrs<V>& pp, int count, const PassBGe
                                  cudaStream_t s) {
   constexpr int C4 = 4 * kBzCells;
   const int pio = (3 * g.nz) | 1;
-  const size_t smem = ((size_t)MZ + 6 * (size_t)g.Kz * kBzCells + 3 * MZ * C4 + (size_t)C4 * pio) * sizeof(V);
+  const size_t smem = (size_t)C4 * (sizeof(long long) + sizeof(int)) +
+                      ((size_t)MZ + 6 * (size_t)(MZ / 2 + 1) * kBzCells + 3 * MZ * C4 + (size_t)C4 * pio) * sizeof(V);
   if (smem > 220 * 1024) { set_error("pass B2 shared memory %zu too large", smem); return VIE_ERR_INVALID; }
   VIE_CUDA_TRY(cudaFuncSetAttribute(pass_bz_kernel<V, MZ, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
