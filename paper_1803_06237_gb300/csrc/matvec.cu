@@ -525,7 +525,9 @@ static vie_status dispatch_pass_bz(const PassPtrs<V>& pp, int count, const PassB
 // threads walking their own rows hit distinct banks.
 //   S1: (c, kz) y-lines, pitch PY;  S2: (c, y) z-lines, pitch PZ.
 // ---------------------------------------------------------------------------
-template <typename V, int MY, int MZ>
+// NY, NZ > 0 fix the cross-section at compile time: the zero padding and the
+// cropped outputs then drop out of the register butterflies.
+template <typename V, int MY, int MZ, int NY, int NZ>
 __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                          const V* __restrict__ twyg, const V* __restrict__ twzg) {
   V* __restrict__ work = pp.work[blockIdx.y];
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__
   V* Gs = S2 + 3 * g.ny * PZ;          // folded spectrum chunk of this kx, 6 Kz Ky
   const int kx = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int ny = g.ny, nz = g.nz;
+  const int ny = NY > 0 ? NY : g.ny, nz = NZ > 0 ? NZ : g.nz;
   const bool fx = kx > g.Mx - kx;
   const int kxf = fx ? g.Mx - kx : kx;
   pdl_launch_dependents();
@@ -632,6 +634,9 @@ __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__
 // (MY, MZ) pairs with a register-FFT pass B; other sizes use pass_b_kernel.
 #define VIE_PASS_B_REG_SIZES(X) \
   X(24, 24) X(45, 24) X(48, 24) X(50, 24) X(30, 24) X(40, 24) X(25, 24) X(45, 25) X(48, 25) X(24, 25)
+// (MY, MZ, NY, NZ) with the cross-section compiled in: the 460 x 220 nm strip
+// at 20 nm (23 x 11 voxels) in its smallest 5-smooth embeddings.
+#define VIE_PASS_B_REG_FIXED(X) X(45, 24, 23, 11) X(48, 24, 23, 11)
 
 bool pass_b_reg_available(int my, int mz) {
 #define VIE_X(a, b) if (my == a && mz == b) return true;
@@ -640,30 +645,30 @@ bool pass_b_reg_available(int my, int mz) {
   return false;
 }
 
-template <typename V, int MY, int MZ>
+template <typename V, int MY, int MZ, int NY, int NZ>
 static vie_status launch_pass_b_reg(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twy,
                                     const V* twz, cudaStream_t s) {
   constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
   constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
   const size_t smem = (size_t)(MY + MZ + 3 * MZ * PY + 3 * g.ny * PZ + 6 * g.Kz * g.Ky) * sizeof(V);
   if (smem > 220 * 1024) { set_error("pass B shared memory %zu too large", smem); return VIE_ERR_INVALID; }
-  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_reg_kernel<V, MY, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_reg_kernel<V, MY, MZ, NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int lines = 3 * (g.ny > MZ ? g.ny : MZ);
   int threads = ((lines + 31) / 32) * 32;
   if (threads > 256) threads = 256;
-  VIE_CUDA_TRY(launch_pdl(pass_b_reg_kernel<V, MY, MZ>, dim3((unsigned)g.Mx, (unsigned)count), dim3(threads), smem,
+  VIE_CUDA_TRY(launch_pdl(pass_b_reg_kernel<V, MY, MZ, NY, NZ>, dim3((unsigned)g.Mx, (unsigned)count), dim3(threads), smem,
                           s, pp, g, twy, twz));
   return VIE_OK;
 }
 
 // complex128 lines longer than 30 would spill registers: those keep the generic pass
-template <typename V, int MY, int MZ>
+template <typename V, int MY, int MZ, int NY = 0, int NZ = 0>
 static vie_status try_pass_b_reg(const PassPtrs<V>& pp, int count, const PassBGeom& g, const V* twy,
                                  const V* twz, cudaStream_t s, bool* done) {
   if constexpr (sizeof(V) == sizeof(float2) || (MY <= 30 && MZ <= 30)) {
     *done = true;
-    return launch_pass_b_reg<V, MY, MZ>(pp, count, g, twy, twz, s);
+    return launch_pass_b_reg<V, MY, MZ, NY, NZ>(pp, count, g, twy, twz, s);
   } else {
     *done = false;
     return VIE_OK;
@@ -676,6 +681,11 @@ static vie_status dispatch_pass_b_reg(const PassPtrs<V>& pp, int count, const Pa
   *done = false;
 #define VIE_X(a, b) \
   if (g.My == a && g.Mz == b) return try_pass_b_reg<V, a, b>(pp, count, g, twy, twz, s, done);
+#define VIE_Y(a, b, c, d)                       \
+  if (g.My == a && g.Mz == b && g.ny == c && g.nz == d) \
+    return try_pass_b_reg<V, a, b, c, d>(pp, count, g, twy, twz, s, done);
+  VIE_PASS_B_REG_FIXED(VIE_Y)
+#undef VIE_Y
   VIE_PASS_B_REG_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
@@ -737,9 +747,13 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ Pas
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb - n % 16) % 16 + 16) % 16; }
 
-template <typename V, int L1, int L2, int LPB>
+// NX > 0 (a multiple of L1 for pass A, of L2 for pass C) fixes the line
+// length at compile time: the zero padding of the forward transform and the
+// cropped outputs of the inverse drop out of the register butterflies.
+template <typename V, int L1, int L2, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
+  static_assert(NX == 0 || (NX % L1 == 0 && NX % L2 == 0), "compiled line length must divide by L1 and L2");
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
   constexpr int MX = L1 * L2;
@@ -776,7 +790,8 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
 #pragma unroll
     for (int n2 = 0; n2 < L2; ++n2) {
       const int n = n1 + L1 * n2;
-      a[n2] = (l < nl && n < nx) ? Xs[l * P + n] : zero_c<V>();
+      const bool in = NX > 0 ? (n2 < NX / L1) : (n < nx);
+      a[n2] = (l < nl && in) ? Xs[l * P + n] : zero_c<V>();
     }
     reg_fft<V, false, L2>(a, tw2);
 #pragma unroll
@@ -798,7 +813,7 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
   }
 }
 
-template <typename V, int L1, int L2, int LPB>
+template <typename V, int L1, int L2, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode,
     int gsz) {
@@ -867,7 +882,7 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
 #pragma unroll
     for (int b1 = 0; b1 < L1; ++b1) {
       const int n = b2 + L2 * b1;
-      if (n < nx) Ys[l * P + n] = a[b1];
+      if (NX > 0 ? (b1 < NX / L2) : (n < nx)) Ys[l * P + n] = a[b1];
     }
   }
   __syncthreads();
@@ -890,8 +905,11 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
 // Mx = L1 x L2 factorisations with a four-step register x pass.
 #define VIE_PASS_X4_SIZES(X) \
   X(40, 30) X(24, 25) X(24, 30) X(30, 30) X(45, 25) X(45, 30) X(50, 30) X(40, 40) X(20, 20)
+// (L1, L2, NX) with the line length compiled in: 600 values (12 um at 20 nm
+// along x; the ring resonator's 600 y-voxels) into 1200 = 40 x 30.
+#define VIE_PASS_X4_FIXED(X) X(40, 30, 600)
 
-template <typename V, int L1, int L2, int LPB>
+template <typename V, int L1, int L2, int LPB, int NX>
 static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
                                 const V* twx, int mode, cudaStream_t s, bool* done, int gsz) {
   {
@@ -903,14 +921,14 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
     if (smem > 200 * 1024) { *done = false; return VIE_OK; }
     const dim3 blocks((unsigned)((NL + LPB - 1) / LPB), (unsigned)count);
     if (forward) {
-      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB>,
+      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a4_kernel<V, L1, L2, LPB, NX>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      VIE_CUDA_TRY(launch_pdl(pass_a4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, NL, twx, gsz));
+      VIE_CUDA_TRY(launch_pdl(pass_a4_kernel<V, L1, L2, LPB, NX>, blocks, dim3(NT), smem, s, pp, nx, NL, twx, gsz));
     } else {
-      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB>,
+      VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c4_kernel<V, L1, L2, LPB, NX>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       VIE_CUDA_TRY(
-          launch_pdl(pass_c4_kernel<V, L1, L2, LPB>, blocks, dim3(NT), smem, s, pp, nx, nyz, NL, twx, mode, gsz));
+          launch_pdl(pass_c4_kernel<V, L1, L2, LPB, NX>, blocks, dim3(NT), smem, s, pp, nx, nyz, NL, twx, mode, gsz));
     }
     VIE_LAUNCH_CHECK();
     *done = true;
@@ -924,23 +942,23 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
 // blocks of eight lines per SM (complex64) take eight lines when they fit:
 // each transposed row read is then 64 contiguous bytes, which matters once
 // the workspace no longer fits in L2 (forward passes measured slower so).
-template <typename V, int L1, int L2>
+template <typename V, int L1, int L2, int NX = 0>
 static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
                             const V* twx, int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
   if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
     if constexpr (sizeof(V) == sizeof(float2)) {
       const long blocks8 = (long)((NL + 7) / 8) * count;
       if (lpb == 8 || (lpb == 0 && !forward && blocks8 >= 4L * 152)) {
-        vie_status st = launch_x4_lpb<V, L1, L2, 8>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+        vie_status st = launch_x4_lpb<V, L1, L2, 8, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
         if (st != VIE_OK || *done) return st;
       }
     }
     const long blocks4 = (long)((NL + 3) / 4) * count;
-    if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
-    if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     if (blocks4 < 2L * 152)
-      return launch_x4_lpb<V, L1, L2, 2>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
-    return launch_x4_lpb<V, L1, L2, 4>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+      return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
   } else {
     *done = false;
     return VIE_OK;
@@ -962,6 +980,11 @@ static vie_status dispatch_x4(bool forward, int l1, int l2, const PassPtrs<V>& p
   *done = false;
 #define VIE_X(a, b) \
   if (l1 == a && l2 == b) return launch_x4<V, a, b>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb, gsz);
+#define VIE_Y(a, b, c)                      \
+  if (l1 == a && l2 == b && nx == c)          \
+    return launch_x4<V, a, b, c>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb, gsz);
+  VIE_PASS_X4_FIXED(VIE_Y)
+#undef VIE_Y
   VIE_PASS_X4_SIZES(VIE_X)
 #undef VIE_X
   return VIE_OK;
