@@ -227,9 +227,11 @@ using namespace vie;
 
 // VIE_PLAN_AUTOTUNE: every combination of the three smallest 5-smooth
 // sizes >= 2n - 1 per axis and, where the x passes are four-step kernels, 2
-// or 4 lines per x-pass block is timed over 3 + 10 complex64 operator
-// applications (CUDA events) on a zero spectrum and contrast (the time does
-// not depend on the values); the fastest is kept.  Candidates the passes
+// or 4 lines per x-pass block is timed (3 warm-up applications, then the
+// best of two bursts of 10 complex64 operator applications, CUDA events) on
+// a zero spectrum and contrast (the time does not depend on the values); the
+// fastest is kept.  Under a profiler that serialises kernels the timings,
+// and so the choice, are not those of a plain run.  Candidates the passes
 // reject (shared-memory limits) are skipped.
 static vie_status autotune(vie_plan* p, cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -306,19 +308,25 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
         for (int li = 0; li < (l1 ? 2 : 1); ++li) {
           p->x_lpb = l1 ? lpbs[li] : 0;
           vie_status ms = VIE_OK;
-          for (int r = 0; r < 3 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
-          cudaEventRecord(e0, s);
-          for (int r = 0; r < 10 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
-          cudaEventRecord(e1, s);
-          const cudaError_t se = cudaStreamSynchronize(s);
-          if (se != cudaSuccess) {
-            set_error("autotune: %s", cudaGetErrorString(se));
-            cleanup();
-            return VIE_ERR_CUDA;
+          for (int r = 0; r < 3 && ms == VIE_OK; ++r)
+            ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
+          float t = 1e30f;
+          for (int rep = 0; rep < 2 && ms == VIE_OK; ++rep) {   // best of two bursts
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 10 && ms == VIE_OK; ++r)
+              ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
+            cudaEventRecord(e1, s);
+            const cudaError_t se = cudaStreamSynchronize(s);
+            if (se != cudaSuccess) {
+              set_error("autotune: %s", cudaGetErrorString(se));
+              cleanup();
+              return VIE_ERR_CUDA;
+            }
+            float tr = 0.f;
+            cudaEventElapsedTime(&tr, e0, e1);
+            if (tr < t) t = tr;
           }
           if (ms != VIE_OK) { clear_error(); continue; }
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
           ++count;
           if (t < best) {
             best = t;

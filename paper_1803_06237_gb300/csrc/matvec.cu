@@ -936,7 +936,7 @@ static vie_status launch_x4_lpb(bool forward, const PassPtrs<V>& pp, int count, 
   }
 }
 
-// Four lines per block, or two when four would leave fewer than two blocks
+// Four lines per block, or two when four would leave fewer than one block
 // per SM (more blocks hide the latency of the small per-line work), unless
 // the plan's tuner chose (lpb = 2 or 4).  Inverse passes with at least four
 // blocks of eight lines per SM (complex64) take eight lines when they fit:
@@ -956,7 +956,7 @@ static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int 
     const long blocks4 = (long)((NL + 3) / 4) * count;
     if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
-    if (blocks4 < 2L * 152)
+    if (blocks4 < 152)
       return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
   } else {
