@@ -470,9 +470,16 @@ def circulant_section(plan, b, args, reps=20, fp16=False):
     import torch
 
     from paper_1803_06237_gb300 import vie
+    flags = vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT
+    # the first build in a process also pays one-time library set-up (cuBLAS
+    # handle, module loading): timed separately, then a warm build is timed
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT)
+    vie.vie_circulant_create(plan, flags).close()
+    torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    c = vie.vie_circulant_create(plan, flags)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = vie.vie_circulant_info(c)
@@ -499,7 +506,8 @@ def circulant_section(plan, b, args, reps=20, fp16=False):
     solve = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
     vie.vie_set_circulant_preconditioner(plan, None)
     c.close()
-    return {"setup_ms": setup_ms, "build_ms_library": info["build_ms"], "device_bytes": info["device_bytes"],
+    return {"setup_ms": setup_ms, "setup_first_in_process_ms": first_ms, "build_ms_library": info["build_ms"],
+            "device_bytes": info["device_bytes"],
             "apply_ms": ms,
             "apply_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                                "frac": achieved / hbm_peak, "peak_source": kind,
