@@ -308,7 +308,9 @@ def gpu_arm(args):
         "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(wl.grid), "circulant": list(info["m"]),
                    "autotune": ({"candidates": info["tune_candidates"], "ms": round(info["tune_ms"], 1),
-                                 "x_lines_per_block": info["x_lines_per_block"]} if args.autotune else None),
+                                 "x_lines_per_block": info["x_lines_per_block"],
+                                 "x_lines_per_block_inverse": info["x_lines_per_block_inverse"]}
+                                if args.autotune else None),
                    "input_pool_vectors": pool, "l2": f"inputs+outputs cycle through {2 * pool * vec_bytes / 2**20:.0f} MiB > 129 MB L2",
                    "parallelism": f"{world} independent replicas"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,

@@ -227,7 +227,7 @@ using namespace vie;
 
 // VIE_PLAN_AUTOTUNE: every combination of the three smallest 5-smooth
 // sizes >= 2n - 1 per axis and, where the x passes are four-step kernels, 2
-// or 4 lines per x-pass block is timed (3 warm-up applications, then the
+// or 4 lines per block for the forward and for the inverse x pass is timed (3 warm-up applications, then the
 // best of two bursts of 10 complex64 operator applications, CUDA events) on
 // a zero spectrum and contrast (the time does not depend on the values); the
 // fastest is kept.  Under a profiler that serialises kernels the timings,
@@ -291,7 +291,7 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
   p->ghat32 = ghat;
   p->M32 = M;
   float best = 1e30f;
-  int bm[3] = {p->m[0], p->m[1], p->m[2]}, blpb = 0, count = 0;
+  int bm[3] = {p->m[0], p->m[1], p->m[2]}, blpb = 0, blpbi = 0, count = 0;
   for (int cx = 0; cx < 3; ++cx)
     for (int cy = 0; cy < 3; ++cy)
       for (int cz = 0; cz < 3; ++cz) {
@@ -305,8 +305,9 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
         int l1 = 0, l2 = 0;
         x4_factors(p->m[0], &l1, &l2);
         const int lpbs[2] = {2, 4};
-        for (int li = 0; li < (l1 ? 2 : 1); ++li) {
-          p->x_lpb = l1 ? lpbs[li] : 0;
+        for (int li = 0; li < (l1 ? 4 : 1); ++li) {   // (forward, inverse) lines per block
+          p->x_lpb = l1 ? lpbs[li & 1] : 0;
+          p->x_lpb_inv = l1 ? lpbs[li >> 1] : 0;
           vie_status ms = VIE_OK;
           for (int r = 0; r < 3 && ms == VIE_OK; ++r)
             ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
@@ -332,6 +333,7 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
             best = t;
             bm[0] = p->m[0]; bm[1] = p->m[1]; bm[2] = p->m[2];
             blpb = p->x_lpb;
+            blpbi = p->x_lpb_inv;
           }
         }
       }
@@ -342,6 +344,7 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
     p->kf[a] = bm[a] / 2 + 1;
   }
   p->x_lpb = blpb;
+  p->x_lpb_inv = blpbi;
   p->tune_candidates = count;
   p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return VIE_OK;
@@ -448,6 +451,7 @@ vie_status vie_plan_clone(const vie_plan* base, vie_plan** out) {
     p->n[a] = base->n[a];
     p->m[a] = base->m[a];
     p->x_lpb = base->x_lpb;
+    p->x_lpb_inv = base->x_lpb_inv;
     p->kf[a] = base->kf[a];
     p->ax[a] = base->ax[a];
   }
@@ -549,6 +553,7 @@ vie_status vie_plan_get_info(const vie_plan* p, vie_plan_info* info) {
   info->tune_ms = p->tune_ms;
   info->tune_candidates = p->tune_candidates;
   info->x_lines_per_block = p->x_lpb;
+  info->x_lines_per_block_inverse = p->x_lpb_inv;
   return VIE_OK;
 }
 

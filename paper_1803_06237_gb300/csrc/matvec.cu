@@ -1115,7 +1115,7 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   }
   done = false;
   if (l1) {
-    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb, NL);
+    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb_inv, NL);
     if (st != VIE_OK) return st;
   }
   if (!done) {

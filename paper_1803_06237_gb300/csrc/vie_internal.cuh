@@ -149,7 +149,8 @@ struct vie_plan {
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
   void* precond = nullptr;    // preconditioner state (learned or block-circulant), if set
   int contrast_gen = 0;       // incremented whenever the contrast is set
-  int x_lpb = 0;              // four-step x-pass lines per block (0: heuristic)
+  int x_lpb = 0;              // four-step forward x-pass lines per block (0: heuristic)
+  int x_lpb_inv = 0;          // four-step inverse x-pass lines per block (0: heuristic)
   double tune_ms = 0.0;       // VIE_PLAN_AUTOTUNE host time
   int tune_candidates = 0;
 };

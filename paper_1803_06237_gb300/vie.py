@@ -35,7 +35,8 @@ class vie_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("h", ctypes.c_double),
                 ("k0", ctypes.c_double), ("eps_bg", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double), ("tune_ms", ctypes.c_double),
-                ("tune_candidates", ctypes.c_int), ("x_lines_per_block", ctypes.c_int)]
+                ("tune_candidates", ctypes.c_int), ("x_lines_per_block", ctypes.c_int),
+                ("x_lines_per_block_inverse", ctypes.c_int)]
 
 
 class vie_absorber(ctypes.Structure):
@@ -176,7 +177,8 @@ class Plan:
         return {"n": tuple(inf.n), "m": tuple(inf.m), "h": inf.h, "k0": inf.k0, "eps_bg": inf.eps_bg,
                 "kappa": inf.kappa, "device_bytes": inf.device_bytes, "setup_ms": inf.setup_ms,
                 "tune_ms": inf.tune_ms, "tune_candidates": inf.tune_candidates,
-                "x_lines_per_block": inf.x_lines_per_block}
+                "x_lines_per_block": inf.x_lines_per_block,
+                "x_lines_per_block_inverse": inf.x_lines_per_block_inverse}
 
 
 # ----------------------------------------------------------------------------

@@ -225,7 +225,7 @@ def test_autotuned_plan_matches_oracle(grid):
     info = plan.info()
     assert info["tune_candidates"] >= 1 and info["tune_ms"] > 0
     assert all(mi >= 2 * ni - 1 and _smooth(mi) for mi, ni in zip(info["m"], grid))
-    assert info["x_lines_per_block"] in (0, 2, 4)
+    assert info["x_lines_per_block"] in (0, 2, 4) and info["x_lines_per_block_inverse"] in (0, 2, 4)
     eps = workloads.random_permittivity(grid, seed=41)
     vie.vie_set_permittivity(plan, eps)
     x = workloads.random_currents(grid, seed=42)
@@ -235,7 +235,9 @@ def test_autotuned_plan_matches_oracle(grid):
     assert rel_l2(_apply(plan, x, torch.complex64), y_ref) <= TOL32
     # a clone keeps the tuned shapes
     clone = vie.vie_plan_clone(plan)
-    assert clone.info()["m"] == info["m"] and clone.info()["x_lines_per_block"] == info["x_lines_per_block"]
+    ci = clone.info()
+    assert ci["m"] == info["m"] and ci["x_lines_per_block"] == info["x_lines_per_block"]
+    assert ci["x_lines_per_block_inverse"] == info["x_lines_per_block_inverse"]
     vie.vie_set_permittivity(clone, eps)
     assert rel_l2(_apply(clone, x, torch.complex64), y_ref) <= TOL32
 
