@@ -367,7 +367,7 @@ constexpr int kBzThreads = 3 * 4 * kBzCells;
 // NZ > 0 fixes nz at compile time (the zero padding and the cropped outputs
 // then drop out of the register FFTs); NZ = 0 reads it from g.
 template <typename V, int MZ, int NZ>
-__global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 1)
+__global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 4 : 1)
     pass_bz_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g, int tiles, const V* __restrict__ twzg) {
   constexpr int C4 = 4 * kBzCells;
   constexpr int KZ = MZ / 2 + 1;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 
   V* twz = reinterpret_cast<V*>(flip + C4);
   V* Gs = twz + MZ;                          // [comp][kzf][j]: 6 KZ kBzCells
   V* S = Gs + (size_t)6 * KZ * kBzCells;     // [c][kz][cell]
-  V* IO = S + 3 * MZ * C4;                   // [cell][pio]
+  V* IO = S;                                 // [cell][pio], shares S (pio <= 3 MZ)
   const int kxf = blockIdx.x / tiles;
   const int kyf0 = (blockIdx.x - kxf * tiles) * kBzCells;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 
     V a[MZ];
 #pragma unroll
     for (int z = 0; z < MZ; ++z) a[z] = (valid && z < nz) ? IO[cell * pio + c * nz + z] : zero_c<V>();
+    __syncthreads();   // every thread has its line: S may overwrite IO
     reg_fft<V, false, MZ>(a, twz);
 #pragma unroll
     for (int kz = 0; kz < MZ; ++kz) S[(c * MZ + kz) * C4 + cell] = a[kz];
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 3 : 
     V a[MZ];
 #pragma unroll
     for (int kz = 0; kz < MZ; ++kz) a[kz] = S[(c * MZ + kz) * C4 + cell];
+    __syncthreads();   // every thread has its line: IO may overwrite S
     reg_fft<V, true, MZ>(a, twz);
 #pragma unroll
     for (int z = 0; z < MZ; ++z)
@@ -494,8 +496,9 @@ static vie_status launch_pass_bz(const PassPtrs<V>& pp, int count, const PassBGe
                                  cudaStream_t s) {
   constexpr int C4 = 4 * kBzCells;
   const int pio = (3 * g.nz) | 1;
+  if (pio > 3 * MZ) { set_error("pass B2: nz = %d too large for Mz = %d", g.nz, MZ); return VIE_ERR_INVALID; }
   const size_t smem = (size_t)C4 * (sizeof(long long) + sizeof(int)) +
-                      ((size_t)MZ + 6 * (size_t)(MZ / 2 + 1) * kBzCells + 3 * MZ * C4 + (size_t)C4 * pio) * sizeof(V);
+                      ((size_t)MZ + 6 * (size_t)(MZ / 2 + 1) * kBzCells + 3 * MZ * C4) * sizeof(V);
   if (smem > 220 * 1024) { set_error("pass B2 shared memory %zu too large", smem); return VIE_ERR_INVALID; }
   VIE_CUDA_TRY(cudaFuncSetAttribute(pass_bz_kernel<V, MZ, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));

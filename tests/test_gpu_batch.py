@@ -60,6 +60,33 @@ def test_grouped_operator_equals_single_calls(dtype):
         assert torch.equal(y, y1)
 
 
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_grouped_operator_large_planes(dtype):
+    """Three plans whose y-z plane takes the split pass B (4 x 200 x 12:
+    circulant 8 x 400 x 24), grouped in one launch per pass: equal to single
+    calls bit for bit and to the oracle."""
+    grid = (4, 200, 12)
+    base = vie.vie_plan_create(grid, 0.02, K0, 2.085)
+    plans = [base, vie.vie_plan_clone(base), vie.vie_plan_clone(base)]
+    xs, Ms = [], []
+    for k, p in enumerate(plans):
+        eps = workloads.random_permittivity(grid, seed=90 + k)
+        vie.vie_set_permittivity(p, eps)
+        Ms.append(op.contrast_M(op.chi_from_permittivity(eps, 2.085)))
+        xs.append(torch.from_numpy(workloads.random_currents(grid, seed=95 + k).ravel()).to(dtype).cuda())
+    ys = [torch.empty_like(x) for x in xs]
+    vie.vie_matvec_batch(plans, xs, ys)
+    kappa = base.info()["kappa"]
+    tol = 1e-12 if dtype == torch.complex128 else 2e-6
+    for p, x, y, M in zip(plans, xs, ys, Ms):
+        y1 = torch.empty_like(x)
+        vie.vie_matvec(p, x, y1)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y1)
+        ref = oracle_matvec(grid, kappa, M, x.cpu().numpy().astype(np.complex128).reshape(3, 12, 200, 4)).ravel()
+        assert rel_l2(y.cpu().numpy().astype(np.complex128), ref) <= tol
+
+
 @pytest.mark.parametrize("mode,tol", [(vie.VIE_SOLVE_MIXED, 1e-6), (vie.VIE_SOLVE_FP64, 1e-8)])
 def test_batched_solve_matches_single_solves_and_oracle(mode, tol):
     specs = [(60, 15, 0, 0.5), (80, 20, 2, 2.0), (60, 25, 3, 2.0), (100, 30, 1, 0.5)]
