@@ -94,6 +94,10 @@ typedef struct {
  * in FP64, the Galerkin Toeplitz entries T_pq(Delta) of N (Sec. 3.1,
  * N_ij = <N P_j, P_i>) for Delta in [0,n) and the spectra of their circulant
  * embedding (Sec. 6), stored once in complex128 and once in complex64.
+ * The plan's workspace holds 3*ny*nz*Mx complex128 values, plus Mx*My*3*nz
+ * when the y-z plane is too large for one thread block (e.g. 1200 x 24: a
+ * ring resonator's 600 x 11 cross-section), where the operator transforms y,
+ * then z, then y back in separate passes; device_bytes reports the total.
  * Synchronises the device before returning.  The contrast starts at zero
  * (operator = identity).  Errors: VIE_ERR_INVALID (n < 1, h <= 0, k0 < 0,
  * eps_bg <= 0), VIE_ERR_OOM, VIE_ERR_CUDA.  *out is NULL on error. */
@@ -363,7 +367,11 @@ vie_status vie_reflection(const void* eref_dev, const void* e_dev, int count,
  * process exits) instead of the plan's workspace, so it may run on another
  * stream while vie_matvec runs on the same plan.  The plan is only read.
  * Limit: 3*ny*nz*Mx complex values of `dtype` (Mx from vie_plan_get_info) must
- * fit in 16 MiB; larger plans are rejected with VIE_ERR_INVALID.  The plan's
+ * fit in 16 MiB; larger plans are rejected with VIE_ERR_INVALID.  Where the
+ * y-z plane is too large for one thread block and the y-pass buffer
+ * (Mx*My*3*nz values) does not fit behind it in the 16 MiB, the plane is
+ * transformed by clusters of thread blocks sharing it in distributed shared
+ * memory (same result, slower).  The plan's
  * device must be current.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Every call shares the one array and it keeps the previous
