@@ -191,6 +191,24 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """The slowest rank's time (every rank gets it); `device` is where the
+    process group's collectives run ("cuda" for NCCL, "cpu" for gloo)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, ms: float) -> float:
+    """Units per second for the whole job: every rank did `steps` units in
+    at most `ms` milliseconds (weak scaling)."""
+    return world * steps / (ms / 1e3)
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -241,13 +259,9 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev[0].elapsed_time(ev[1])
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]), world, "cuda")
     per_step_ms = ms / K
-    value = world * K / (ms / 1e3)
+    value = whole_job_rate(world, K, ms)
 
     # end to end through the public API with host buffers (pinned), copies timed
     Ke = min(K, args.e2e_steps)
@@ -270,12 +284,8 @@ def gpu_arm(args):
         hy.copy_(dy, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * Ke / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    e2e_value = whole_job_rate(world, Ke, e2e_ms)
 
     # roofline of the operator application (its three launches are the unit)
     nx, ny, nz = wl.grid
