@@ -13,8 +13,11 @@
 //   C  per group of x-lines: inverse FFT along x, crop to nx, and
 //      y = w - M u (operator) or y = M (u - w) (right-hand side of a source).
 // Planes too large for one CTA's shared memory (My Mz beyond a few thousand,
-// e.g. 1200 x 24) run pass B on a cluster of CTAs per kx that share the plane
-// through distributed shared memory (pass_b_cluster_kernel).
+// e.g. 1200 x 24) split pass B in three launches through a y-pass buffer in
+// the plan's workspace (run_split_b: y lines, z stage, inverse y); without
+// that buffer (the static workspace) or a z-stage kernel for Mz, pass B runs
+// on a cluster of CTAs per kx sharing the plane through distributed shared
+// memory (pass_b_cluster_kernel).
 // The spectrum is pre-scaled by 1/(Mx My Mz), so no separate normalisation.
 #include <cooperative_groups.h>
 #include <cuda_pipeline.h>
