@@ -62,3 +62,36 @@ def test_round_trip_helper_matches_oracle(lib):
         a = vie.vie_eps2_from_round_trip(1e-10, d, 4.0, k0, 12.11)
         b = op.eps2_max_from_rrt(1e-10, d, 4.0, k0, 12.11)
         assert abs(a - b) <= 1e-14 * abs(b)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding mirrors, from a C
+    program compiled against include/vie.h, equal those of the ctypes
+    structures."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"vie_plan_info": vie.vie_plan_info, "vie_absorber": vie.vie_absorber,
+               "vie_solve_opts": vie.vie_solve_opts, "vie_solve_info": vie.vie_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vie.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
