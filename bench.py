@@ -184,6 +184,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clock_snapshot(index: int) -> dict:
+    """One nvidia-smi read of the SM clock, its maximum and the throttle
+    reasons (before and after the timed region, which can be shorter than the
+    sampler's 200 ms period)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), f"--query-gpu={ClockSampler.FIELDS}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20).stdout
+    except (OSError, subprocess.TimeoutExpired):
+        return {}
+    parts = [x.strip() for x in out.strip().split(",")]
+    if len(parts) < 8:
+        return {}
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        return {"sm_mhz": float(parts[0]), "sm_max_mhz": float(parts[1]), "power_w": float(parts[2]),
+                "reasons": [n for n, v in zip(names, parts[4:8]) if v.lower().startswith("active")]}
+    except ValueError:
+        return {}
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,6 +268,8 @@ def gpu_arm(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.25)                      # the sampler's first line
+    clk_before = clock_snapshot(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -256,9 +278,20 @@ def gpu_arm(args):
         vie.vie_matvec(plan, xs[i % pool], ys[i % pool], stream)
     ev[1].record(stream)
     torch.cuda.synchronize()
+    clk_after = clock_snapshot(local)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    clk["before"] = clk_before
+    clk["after"] = clk_after
+    if clk.get("sm_mhz") is None:
+        reads = [c["sm_mhz"] for c in (clk_before, clk_after) if c.get("sm_mhz")]
+        clk["sm_mhz"] = statistics.median(reads) if reads else None
+        clk["sm_max_mhz"] = max([c["sm_max_mhz"] for c in (clk_before, clk_after) if c.get("sm_max_mhz")],
+                                default=None)
+        clk["reasons"] = sorted(set(clk.get("reasons", [])) | set(clk_before.get("reasons", []))
+                                | set(clk_after.get("reasons", [])))
+        clk["source"] = "nvidia-smi reads just before and after the timed region (shorter than the 200 ms sampler)"
     ms = max_over_ranks(ev[0].elapsed_time(ev[1]), world, "cuda")
     per_step_ms = ms / K
     value = whole_job_rate(world, K, ms)
@@ -287,6 +320,10 @@ def gpu_arm(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     e2e_value = whole_job_rate(world, Ke, e2e_ms)
 
+    # measured FP32 / FP64 FMA rates (the ALU roofline), outside the timed region
+    fp32_peak = vie.vie_probe_fma_tflops(vie.VIE_C64)
+    fp64_peak = vie.vie_probe_fma_tflops(vie.VIE_C128)
+
     # roofline of the operator application (its three launches are the unit)
     nx, ny, nz = wl.grid
     Mx, My, Mz = info["m"]
@@ -296,7 +333,7 @@ def gpu_arm(args):
     alg_flops = operator_flops(wl.grid, info["m"])
     t_s = per_step_ms * 1e-3
     hbm_peak, peak_kind = _peaks()
-    alu_peak = FP32_TFLOPS
+    alu_peak = fp32_peak
     achieved_tf = alg_flops / t_s / 1e12
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
@@ -309,7 +346,8 @@ def gpu_arm(args):
                 "frac": achieved_tf / alu_peak, "traffic": traffic,
                 "kernel": "complex64 operator application (passes A, B, C)",
                 "algorithmic_flops_per_launch": alg_flops, "algorithmic_bytes_per_launch": alg_bytes,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "peak_source": "measured FP32 FMA throughput (vie_probe_fma_tflops); nominal %.1f = "
+                               "152 SMs x 128 lanes x 2 flop x 2.07 GHz" % FP32_TFLOPS,
                 "hbm": {"achieved": alg_bytes / t_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": alg_bytes / t_s / 1e9 / hbm_peak, "peak_source": peak_kind}}
     result = {
@@ -329,6 +367,9 @@ def gpu_arm(args):
         "roofline": roofline,
         "clocks": clk,
         "setup_ms": info["setup_ms"],
+        "alu_peaks_measured": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
+                               "how": "FMA chains on every SM, CUDA events (vie_probe_fma_tflops)"},
+        "c128_operator": c128_section(plan, wl, info, fp64_peak, alg_flops),
     }
     if not args.no_net:
         result["net_inference"] = net_section(plan, wl.grid)
@@ -347,11 +388,46 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
-def _timed_solve(plan, b, mode, restart, use_pc):
+def c128_section(plan, wl, info, fp64_peak, alg_flops, reps=100):
+    """The complex128 operator (the refinement's outer residual) on the same
+    guide: applications per second, against the measured FP64 FMA rate (same
+    algorithmic flop count as complex64) and the HBM roofline."""
+    import torch
+
+    from paper_1803_06237_gb300 import vie
+    n3 = 3 * wl.n_voxels
+    pool = max(2, int(np.ceil(1.5 * L2_BYTES / (2 * n3 * 16))))
+    xs = torch.randn((pool, n3), dtype=torch.complex128, device="cuda")
+    ys = torch.empty_like(xs)
+    stream = torch.cuda.current_stream()
+    for i in range(3):
+        vie.vie_matvec(plan, xs[i % pool], ys[i % pool], stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        vie.vie_matvec(plan, xs[i % pool], ys[i % pool], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    Kx, Ky, Kz = (m // 2 + 1 for m in info["m"])
+    alg_bytes = (3 * wl.n_voxels * 2 + wl.n_voxels) * 16 + 6 * Kx * Ky * Kz * 16
+    hbm_peak, kind = _peaks()
+    tf = alg_flops / (ms * 1e-3) / 1e12
+    return {"ms_per_matvec": ms, "matvecs_per_s": 1e3 / ms, "input_pool_vectors": pool,
+            "alu": {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                    "peak_source": "measured FP64 FMA throughput"},
+            "hbm": {"achieved": alg_bytes / ms / 1e6, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": alg_bytes / ms / 1e6 / hbm_peak, "algorithmic_bytes": alg_bytes, "peak_source": kind}}
+
+
+def _timed_solve(plan, b, mode, restart, use_pc, keep=None):
     import torch
 
     from paper_1803_06237_gb300 import vie
     x = torch.zeros_like(b)
+    if keep is not None:
+        keep.append(x)
     torch.cuda.synchronize()
     t = time.perf_counter()
     info = vie.vie_solve(plan, b, x, 1e-6, mode=mode, restart=restart, use_preconditioner=use_pc,
@@ -428,8 +504,13 @@ def solve_section(plan, wl, absorbers, args):
     b = torch.empty_like(src)
     vie.vie_rhs_from_source(plan, src, b)
     _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, False)      # warm-up (workspaces)
-    out = {"fp64": _timed_solve(plan, b, vie.VIE_SOLVE_FP64, args.restart_fp64, False),
-           "mixed": _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, False)}
+    sols = {}
+    out = {}
+    for name, mode, restart in (("fp64", vie.VIE_SOLVE_FP64, args.restart_fp64),
+                                ("mixed", vie.VIE_SOLVE_MIXED, args.restart_mixed)):
+        keep = []
+        out[name] = _timed_solve(plan, b, mode, restart, False, keep)
+        sols[name] = keep[0]
     if args.train_steps > 0:
         t0 = time.perf_counter()
         pairs = learned.make_pairs(range(args.train_problems), grid=(160, 40, 11), restart=20, cycles=10)
@@ -450,20 +531,25 @@ def solve_section(plan, wl, absorbers, args):
         ev1.record()
         torch.cuda.synchronize()
         net_ms = ev0.elapsed_time(ev1) / 20
-        vie.vie_set_preconditioner(plan, net)
+        vie.vie_set_preconditioner_net(plan, net)
         _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)   # warm-up
-        out["mixed_learned"] = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
+        keep = []
+        out["mixed_learned"] = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True, keep)
+        sols["mixed_learned"] = keep[0]
         out["training"] = {"pairs": len(pairs), "problems": args.train_problems, "steps": args.train_steps,
                            "identity_loss": learned.identity_loss(pairs),
                            "pair_generation_s": t1 - t0, "train_s": t2 - t1,
                            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
                            "net_apply_ms": net_ms}
-        vie.vie_set_preconditioner(plan, None)
+        vie.vie_set_preconditioner_net(plan, None)
     if args.circulant:
         out["circulant"] = circulant_section(plan, b, args)
         out["mixed_circulant"] = out["circulant"].pop("solve")
+        sols["mixed_circulant"] = out["circulant"].pop("x")
         out["circulant_fp16"] = circulant_section(plan, b, args, fp16=True)
         out["mixed_circulant_fp16"] = out["circulant_fp16"].pop("solve")
+        sols["mixed_circulant_fp16"] = out["circulant_fp16"].pop("x")
+        out["accuracy"] = accuracy_section(plan, wl, b, sols, args)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     if "mixed_learned" in out:
         out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms"] / out["mixed_learned"]["ms"]
@@ -474,7 +560,7 @@ def solve_section(plan, wl, absorbers, args):
 
 
 def circulant_section(plan, b, args, reps=20, fp16=False):
-    """The block-circulant preconditioner (Sec. 6) on the benchmark guide:
+    """The block-circulant preconditioner (Sec. 5.4) on the benchmark guide:
     setup (blocks, DFT along x, batched LU) timed on the host clock, the
     application timed with CUDA events against the HBM roofline (it streams
     the nx (3 ny nz)^2 complex64 factors once), and the preconditioned mixed
@@ -515,7 +601,8 @@ def circulant_section(plan, b, args, reps=20, fp16=False):
     achieved = factor_bytes / (ms * 1e-3) / 1e9
     vie.vie_set_circulant_preconditioner(plan, c)
     _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)      # warm-up
-    solve = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True)
+    keep = []
+    solve = _timed_solve(plan, b, vie.VIE_SOLVE_MIXED, args.restart_mixed, True, keep)
     vie.vie_set_circulant_preconditioner(plan, None)
     c.close()
     return {"setup_ms": setup_ms, "setup_first_in_process_ms": first_ms, "build_ms_library": info["build_ms"],
@@ -526,7 +613,55 @@ def circulant_section(plan, b, args, reps=20, fp16=False):
                                "algorithmic_bytes": factor_bytes,
                                "note": "LU factors of the nx blocks (%s) read once per application"
                                        % ("complex half" if fp16 else "complex64")},
-            "solve": solve}
+            "solve": solve, "x": keep[0]}
+
+
+def accuracy_section(plan, wl, b, sols, args):
+    """Accuracy of the timed solves (Sec. 5.1 R, Sec. 3 fields): the field
+    error of each timed solution against a tight solve of the same guide
+    (complex128 flexible GMRES with the block-circulant preconditioner to a
+    true residual of 1e-10), and the reflection coefficient of the 4 um
+    absorber: R = sum |E_ref - E|^2 / sum |E_ref|^2 on the axis before the
+    absorber, E_ref from the same guide with a 12 um absorber (same R_rt)."""
+    import torch
+
+    from paper_1803_06237_gb300 import vie, workloads
+
+    def tight(p, rhs, tol):
+        c = vie.vie_circulant_create(p, vie.VIE_CIRC_DEFAULT)
+        vie.vie_set_circulant_preconditioner(p, c)
+        x = torch.zeros_like(rhs)
+        inf = vie.vie_solve(p, rhs, x, tol, mode=vie.VIE_SOLVE_FP64, restart=args.restart_mixed,
+                            use_preconditioner=True, raise_on_not_converged=False)
+        vie.vie_set_circulant_preconditioner(p, None)
+        c.close()
+        return x, inf
+
+    x_ref, inf = tight(plan, b, 1e-10)
+    out = {"reference_solve": {"mode": "complex128 flexible GMRES + block-circulant", "true_residual": inf["residual"],
+                               "converged": inf["converged"]},
+           "field_rel_l2": {k: float((torch.linalg.vector_norm(v - x_ref) / torch.linalg.vector_norm(x_ref)).item())
+                            for k, v in sols.items()}}
+    body = int(round(wl.absorbers[0].x0))
+    L_ref = 12.0
+    wl2 = workloads.waveguide(nx=body + int(round(L_ref / wl.h_um)), absorber_len_um=L_ref)
+    ab2 = wl2.absorbers[0]
+    e2 = vie.vie_eps2_from_round_trip(ab2.r_rt, ab2.degree, ab2.length * wl2.h_um, wl2.k0_per_um, wl2.eps_core)
+    plan2 = vie.vie_plan_create(wl2.grid, wl2.h_um, wl2.k0_per_um, wl2.eps_bg)
+    vie.vie_set_permittivity(plan2, wl2.eps, [dict(x0=ab2.x0, length=ab2.length, degree=ab2.degree, eps2_max=e2)])
+    src2 = torch.from_numpy(np.ascontiguousarray(wl2.src.ravel())).cuda()
+    b2 = torch.empty_like(src2)
+    vie.vie_rhs_from_source(plan2, src2, b2)
+    x2, inf2 = tight(plan2, b2, 1e-10)
+    e_ref = vie.vie_axis_field(plan2, x2, body)
+    R = {"tight": vie.vie_reflection(e_ref, vie.vie_axis_field(plan, x_ref, body))}
+    for k, v in sols.items():
+        R[k] = vie.vie_reflection(e_ref, vie.vie_axis_field(plan, v, body))
+    plan2.close()
+    out["reflection"] = {"R": R, "absorber_um": wl.absorbers[0].length * wl.h_um, "reference_absorber_um": L_ref,
+                         "axis_voxels": body, "reference_true_residual": inf2["residual"],
+                         "note": "R of each timed solve's field and of the tight solve"}
+    return out
 
 
 def batch_section(args):

@@ -3,11 +3,11 @@
  * "Adiabatic absorbers in photonics simulations with the volume integral
  * equation method" (arXiv:1803.06237) on one NVIDIA GB300 (sm_103a).
  *
- * The library solves the discrete J-VIE of Sec. 6,
+ * The library solves the discrete J-VIE of Sec. 3.1,
  *     (I - M_eps N) w = c_e M_eps e_inc,
  * on a uniform voxel grid with piecewise-constant currents and materials
  * (Sec. 3.1).  N is block-Toeplitz with six unique tensor components and is
- * applied with FFTs (Sec. 6); M_eps = (eps_r - 1)/eps_r per voxel (Sec. 3)
+ * applied with FFTs (Sec. 5.4); M_eps = (eps_r - 1)/eps_r per voxel (Sec. 3)
  * carries the material and the graded absorber loss (Sec. 4.1-4.2).
  *
  * Conventions shared by every entry point
@@ -93,7 +93,7 @@ typedef struct {
  * background permittivity eps_bg (Sec. 2 scaling).  Computes on the device,
  * in FP64, the Galerkin Toeplitz entries T_pq(Delta) of N (Sec. 3.1,
  * N_ij = <N P_j, P_i>) for Delta in [0,n) and the spectra of their circulant
- * embedding (Sec. 6), stored once in complex128 and once in complex64.
+ * embedding (Sec. 5.4), stored once in complex128 and once in complex64.
  * The plan's workspace holds 3*ny*nz*Mx complex128 values, plus Mx*My*3*nz
  * when the y-z plane is too large for one thread block (e.g. 1200 x 24: a
  * ring resonator's 600 x 11 cross-section), where the operator transforms y,
@@ -124,7 +124,7 @@ vie_status vie_set_permittivity(vie_plan* plan, const double* eps_host,
 vie_status vie_set_contrast(vie_plan* plan, const double* chi_host);
 
 /* y = w - M (N w): one application of the J-VIE operator I - M_eps N
- * (Sec. 6 MVP): pad to the circulant, 3-D FFT, symmetric 3x3 spectral
+ * (Sec. 5.4 MVP): pad to the circulant, 3-D FFT, symmetric 3x3 spectral
  * multiply, inverse FFT, crop, contrast.  x_dev and y_dev are device vectors
  * of 3*nx*ny*nz complex numbers of type `dtype`; they must not overlap.
  * Asynchronous on `stream`.  Uses the plan's workspace, so calls on one plan
@@ -153,7 +153,7 @@ vie_status vie_eps2_from_round_trip(double r_rt, int degree, double length,
                                     double* eps2_max);
 
 /* ------------------------------------------------------------------------ */
-/* Iterative solution of (I - M_eps N) w = b (Sec. 6 discrete J-VIE; the paper
+/* Iterative solution of (I - M_eps N) w = b (Sec. 3.1 discrete J-VIE; the paper
  * uses GMRES at relative tolerance 1e-8, Sec. 5).                            */
 /* ------------------------------------------------------------------------ */
 enum {
@@ -176,6 +176,10 @@ typedef struct {
                              set by vie_set_preconditioner (flexible GMRES) */
   int check_every;        /* host reads the device status every k steps (0 -> 4) */
   double timeout_s;       /* host wall-clock limit (0 -> 600 s) */
+  int host_buffers;       /* 0: b and x are device pointers; 1: host pointers
+                             (pageable or pinned), staged through device
+                             buffers of 2 x 3N complex128 that the plan
+                             allocates on first use and keeps */
 } vie_solve_opts;
 
 typedef struct {
@@ -194,15 +198,18 @@ typedef struct {
   double history[64];     /* true relative residual at the start of each cycle */
 } vie_solve_info;
 
-/* Solve (I - M N) x = b on the device.  b_dev and x_dev are complex128 device
- * vectors of 3*nx*ny*nz entries (x_dev: initial guess if opts->x0_given, the
- * solution on return; b_dev is not modified).  Convergence is judged on the
- * true FP64 residual.  The solver workspace is allocated on the first call
- * for a given (restart, mode) and kept by the plan.  Synchronises `stream`
- * before returning.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA,
+/* Solve (I - M N) x = b on the device (the paper's system of Sec. 3.1,
+ * solved with GMRES as in Sec. 5).  b and x are complex128 vectors of
+ * 3*nx*ny*nz entries, device pointers, or host pointers when
+ * opts->host_buffers = 1 (b is copied in, x copied in if opts->x0_given and
+ * copied out after the solve).  x: initial guess if opts->x0_given, the
+ * solution on return; b is not modified.  Convergence is judged on the true
+ * FP64 residual.  The solver workspace is allocated on the first call for a
+ * given (restart, mode) and kept by the plan.  Synchronises `stream` before
+ * returning.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA,
  * VIE_ERR_NONFINITE, VIE_ERR_TIMEOUT (x holds the best iterate),
  * VIE_ERR_NOT_CONVERGED (caps reached; x and info hold the last iterate). */
-vie_status vie_solve(vie_plan* plan, const void* b_dev, void* x_dev, double tol,
+vie_status vie_solve(vie_plan* plan, const void* b, void* x, double tol,
                      const vie_solve_opts* opts, vie_solve_info* info, void* stream);
 
 /* ------------------------------------------------------------------------ */
@@ -226,17 +233,18 @@ vie_status vie_matvec_batch(vie_plan* const* plans, int count, const void* const
 /* vie_solve for count problems at once: every step advances all open
  * problems with one launch per kernel (the operator per group of equal
  * shape); each problem stops when its own true FP64 residual reaches tol.
- * b_dev[i], x_dev[i]: complex128 device vectors of plan i; infos[i] its
+ * b[i], x[i]: complex128 vectors of plan i (device pointers, or host pointers
+ * with opts->host_buffers = 1, staged as in vie_solve); infos[i] its
  * report.  Synchronises `stream`.  Returns the first non-OK status of any
- * problem (VIE_ERR_NOT_CONVERGED etc.; every x_dev[i] then holds its last
+ * problem (VIE_ERR_NOT_CONVERGED etc.; every x[i] then holds its last
  * iterate).  Errors: as vie_solve. */
-vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const* b_dev,
-                           void* const* x_dev, double tol, const vie_solve_opts* opts,
+vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const* b,
+                           void* const* x, double tol, const vie_solve_opts* opts,
                            vie_solve_info* infos, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Learned right preconditioner (not in the paper, whose preconditioner is   */
-/* block-circulant, Sec. 6): a 3-D convolutional network z = Net(v, chi)     */
+/* block-circulant, Sec. 5.4): a 3-D convolutional network z = Net(v, chi)     */
 /* trained on the device.  8 input channels (re/im of the three components  */
 /* of v scaled to unit RMS, re/im of chi), 4 levels (2x2 average pooling in  */
 /* x and y), 32 channels, 3x3x3 convolutions with zero padding, ReLU,        */
@@ -291,7 +299,7 @@ vie_status vie_net_adam_step(vie_net* net, float lr, float grad_scale, void* str
 vie_status vie_net_status(vie_net* net, int* flag, int clear);
 
 /* ------------------------------------------------------------------------ */
-/* Block-circulant preconditioner (Sec. 6): W, the matrix nearest to        */
+/* Block-circulant preconditioner (Sec. 5.4): W, the matrix nearest to        */
 /* A = I - M N in the Frobenius norm among those that are circulant along x */
 /* (dense (3 ny nz)^2 blocks, rows and columns ordered (component, z, y)):   */
 /* W = circ(c_0 .. c_{nx-1}), c_k = (1/nx) sum_i A[i][(i - k) mod nx].  The  */
@@ -334,11 +342,21 @@ vie_status vie_circulant_destroy(vie_circulant* c);
  * vie_set_preconditioner.  `c` must have been built for this plan. */
 vie_status vie_set_circulant_preconditioner(vie_plan* plan, vie_circulant* c);
 
-/* Use `net` (NULL: none) as the right preconditioner of this plan's solves
- * with opts->use_preconditioner = 1 (flexible GMRES).  The plan keeps a
- * reference; the caller keeps ownership and must not destroy the network
- * while it is set. */
-vie_status vie_set_preconditioner(vie_plan* plan, vie_net* net);
+/* Use the learned network with the given FP32 parameters as the right
+ * preconditioner of this plan's solves with opts->use_preconditioner = 1
+ * (flexible GMRES).  weights: host array of vie_net_param_count() floats in
+ * the parameter layout above (e.g. from vie_net_get_params after training);
+ * bytes must be 4 * vie_net_param_count().  The plan builds and owns a
+ * network from a copy (the caller's array is not kept) and releases it when
+ * the preconditioner is replaced or the plan destroyed.  weights = NULL:
+ * unpreconditioned (any preconditioner set before is removed).  Errors:
+ * VIE_ERR_INVALID (bytes), VIE_ERR_OOM, VIE_ERR_CUDA. */
+vie_status vie_set_preconditioner(vie_plan* plan, const void* weights, size_t bytes);
+
+/* Same, with a network object the caller keeps (e.g. while training it):
+ * `net` (NULL: none) becomes the right preconditioner; the plan keeps a
+ * reference, and the caller must not destroy the network while it is set. */
+vie_status vie_set_preconditioner_net(vie_plan* plan, vie_net* net);
 
 /* Field on the centre axis (step a12; Sec. 3 equivalent currents J =
  * c_e chi E, so E = J/(c_e chi); the factor c_e h^(3/2) common to every
@@ -360,7 +378,7 @@ vie_status vie_reflection(const void* eref_dev, const void* e_dev, int count,
  * device memory where they apply the operator (their memory is owned by
  * another allocator or held to a fixed budget after start-up, so they cannot
  * make a second plan or a second workspace).  The paper has no counterpart:
- * this is a deployment variant of the Sec. 6 product.
+ * this is a deployment variant of the Sec. 5.4 product.
  *
  * It allocates nothing.  Its workspace is a static device array of 16 MiB
  * inside the library (every GPU that loads the library holds it until the
@@ -372,15 +390,26 @@ vie_status vie_reflection(const void* eref_dev, const void* e_dev, int count,
  * (Mx*My*3*nz values) does not fit behind it in the 16 MiB, the plane is
  * transformed by clusters of thread blocks sharing it in distributed shared
  * memory (same result, slower).  The plan's
- * device must be current.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call shares the one array and it keeps the previous
+ * device must be current.  vie_plan_create and vie_plan_clone look up the
+ * array's device address (cudaGetSymbolAddress) on the plan's device, which
+ * also makes the CUDA runtime load the part of the library that holds the
+ * array; so under lazy module loading (the CUDA default) the memory is
+ * reserved when a plan is made, not by the first call here, and the calls
+ * only read the cached address.  Every call shares the one array and it keeps the previous
  * call's contents; nothing in it needs to start at zero (the first pass writes
  * every element the later passes read).  Calls whose execution overlaps on the
  * GPU race on the array: order them on one stream or with events.
  * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID, VIE_ERR_CUDA. */
 vie_status vie_matvec_static_scratch(const vie_plan* plan, const void* x_dev,
                                      void* y_dev, int dtype, void* stream);
+
+/* Measured fused multiply-add throughput of the current GPU in TFLOP/s
+ * (2 flops per FMA): FP32 for dtype VIE_C64, FP64 for VIE_C128.  Runs two
+ * short FMA-chain kernels (a few ms) on `stream` and synchronises it.  The
+ * paper has no counterpart: this is the ALU roofline against which the
+ * operator's FP32 (complex64) and FP64 (complex128) passes are reported.
+ * Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA. */
+vie_status vie_probe_fma_tflops(int dtype, double* tflops, void* stream);
 
 /* Thread-local description of the last error ("" if none). */
 const char* vie_last_error(void);

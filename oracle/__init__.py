@@ -12,10 +12,10 @@ Modules
 greens     Galerkin entries T_pq(Delta) of the discrete operator N (Sec. 3.1,
            Eq. for N_ij = <N P_j, P_i>) by singularity-aware quadrature.
 operator   dense assembly of I - M_eps N on tiny grids, the circulant-embedded
-           FFT matvec (Sec. 6, "Numerical aspects"), contrast and absorber
+           FFT matvec (Sec. 5.4, "Numerical aspects"), contrast and absorber
            (Sec. 4.1-4.2), and the right-hand side of the J-VIE.
 gmres      restarted GMRES / flexible GMRES with MGS Arnoldi and Givens
-           rotations in FP64 (Sec. 5 solver, Sec. 6 discussion).
+           rotations in FP64 (Sec. 5 solver, Sec. 5.4 discussion).
 metrics    field on the centre axis and the reflection coefficient R (Sec. 5.1).
 
 Everything is written for clarity: plain NumPy/SciPy in float64/complex128,

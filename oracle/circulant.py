@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-Paper (arXiv:1803.06237), Sec. 6: a block-circulant matrix W closest to
+Paper (arXiv:1803.06237), Sec. 5.4: a block-circulant matrix W closest to
 A = I - M_eps N in the Frobenius norm (after Chan and Olkin), inverted with
 FFTs, preconditions GMRES.  The paper leaves the details to a later article;
 the reading used here:

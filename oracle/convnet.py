@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-The paper preconditions GMRES with a block-circulant approximation (Sec. 6);
+The paper preconditions GMRES with a block-circulant approximation (Sec. 5.4);
 the learned preconditioner is this project's addition: a small 3-D
 convolutional network z = Net(v, chi) used as the right preconditioner of
 flexible GMRES.  The network (our reading of "4 levels, 32 channels, 3x3x3"):
@@ -122,14 +122,8 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(p, x, keep=False, act_round=None, store_round=None):
-    """Net(x); with keep=True also returns the intermediate tensors.
-    ``act_round``, if given, is applied to the input of every convolution
-    (e.g. rounding to BF16, as a tensor-core convolution does);
-    ``store_round`` to every hidden activation after its ReLU (h_l and u_l),
-    for an implementation that stores them in a narrower type."""
-    rnd = act_round if act_round is not None else (lambda t: t)
-    sto = store_round if store_round is not None else (lambda t: t)
+def forward(p, x, keep=False):
+    """Net(x) in FP64; with keep=True also returns the intermediate tensors."""
     cache = {"x": x}
     a = x
     hs = []
@@ -137,19 +131,19 @@ def forward(p, x, keep=False, act_round=None, store_round=None):
         if lvl > 0:
             a = pool(hs[-1])
             cache[f"a{lvl}"] = a
-        z = conv3d(rnd(a), p[f"enc{lvl}.w"], p[f"enc{lvl}.b"])
-        h = sto(relu(z))
+        z = conv3d(a, p[f"enc{lvl}.w"], p[f"enc{lvl}.b"])
+        h = relu(z)
         cache[f"encz{lvl}"] = z
         hs.append(h)
     u = hs[3]
     for lvl in (2, 1, 0):
         s = up(u, hs[lvl].shape[2], hs[lvl].shape[3]) + hs[lvl]
-        z = conv3d(rnd(s), p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])
+        z = conv3d(s, p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])
         cache[f"decin{lvl}"] = s
         cache[f"decz{lvl}"] = z
-        u = sto(relu(z))
+        u = relu(z)
         cache[f"u{lvl}"] = u
-    y = conv3d(rnd(u), p["out.w"], p["out.b"])
+    y = conv3d(u, p["out.w"], p["out.b"])
     cache["hs"] = hs
     return (y, cache) if keep else y
 

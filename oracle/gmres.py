@@ -3,7 +3,7 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 The paper solves the discrete J-VIE with GMRES at relative tolerance 1e-8
-(Sec. 5 opening; Sec. 6 "Numerical aspects", which also shows unrestarted
+(Sec. 5 opening; Sec. 5.4 "Numerical aspects", which also shows unrestarted
 GMRES histories).  The oracle is the textbook algorithm: Arnoldi with modified
 Gram-Schmidt, Givens rotations on the Hessenberg matrix, the small
 least-squares problem solved by back substitution, restart after ``restart``

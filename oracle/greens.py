@@ -10,7 +10,7 @@ What the paper fixes (arXiv:1803.06237)
 * Sec. 3.1 (Discretization): piecewise-constant basis P_i = (Delta V)^(-1/2) on
   voxel V_i, <P_i, P_j> = delta_ij, and N_ij = <N P_j, P_i> per Cartesian
   component pair (p, q).  On a uniform grid N is block-Toeplitz (Sec. 3.1 end)
-  with six unique tensor components (Sec. 6).
+  with six unique tensor components (Sec. 5.4).
 * Sec. 2 (setup): an exterior medium eps_bg is handled by scaling, so the
   wavenumber inside the operator is k = k0 sqrt(eps_bg).
 
@@ -62,7 +62,7 @@ import itertools
 import numpy as np
 
 # Component order used everywhere in this package (symmetric tensor, six
-# unique components, Sec. 6): xx, yy, zz, xy, xz, yz.
+# unique components, Sec. 5.4): xx, yy, zz, xy, xz, yz.
 COMPONENTS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 
 

@@ -17,7 +17,10 @@ Reading: the axis is the voxel row at (ny // 2, nz // 2); all three field
 components enter the norm.
 
 Pins (tests/test_oracle_metrics.py): R = 0 for identical fields, R = 1 for a
-zero field, R of a known perturbation, and invariance under a common scale.
+zero field, R = |r|^2 for a mode plus a reflected wave r exp(+j beta x) over
+whole half-periods, R = |1 - a exp(j phi)|^2 for a scaled and phase-shifted
+field; the GPU solves' R is compared with R from oracle solves
+(tests/test_gpu_reflection.py).
 """
 from __future__ import annotations
 

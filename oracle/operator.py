@@ -4,12 +4,12 @@ Test infrastructure only (see ``oracle/__init__``).
 
 Paper (arXiv:1803.06237):
 * Sec. 3, boxed J-VIE: (I - M_eps N) J = c_e M_eps E_inc with
-  M_eps = (eps_r - 1) / eps_r; discrete form Sec. 6:
+  M_eps = (eps_r - 1) / eps_r; discrete form Sec. 3.1:
   (I - M_eps N) w_e = c_e M_eps e_inc.
 * Sec. 3.1: material constant per voxel (value at the voxel centre), pulled out
   of the inner products, so A = I - diag(M) T with the Toeplitz T of
   ``oracle.greens``.
-* Sec. 6: the block-Toeplitz N is applied with FFTs (circulant embedding).
+* Sec. 5.4: the block-Toeplitz N is applied with FFTs (circulant embedding).
 * Sec. 2: a background eps_bg is scaled out (eps -> eps / eps_bg, k0 -> k0 sqrt(eps_bg)).
 * Sec. 4.1: sigma(x) = sigma_0 s(x / L), s(u) = u^d for 0 <= u <= 1, d = 0..3.
 * Sec. 4.2: eps_r = eps' - j eps'' inside the absorber.  Reading: eps'' = sigma / (w eps_0)
@@ -25,6 +25,13 @@ Pins (tests/test_oracle_operator.py): dense per-pair assembly vs FFT matvec on
 chi = 0 gives A = I exactly, complex symmetry of the dense matrix
 (reciprocity), -Im(T) positive semidefinite (radiated power), the absorber
 profile against hand-evaluated monomials and the round-trip closed form.
+tests/test_oracle_physics.py: the right-hand side b = M((T - I) w_src)
+against a direct quadrature of the closed-form dyadic Green function away
+from the source and against the static depolarisation (-1/3) of a uniformly
+polarised cube in the source voxel; -Im(T) against the far-field
+(plane-wave) expansion of the radiated power; a voxelised sphere at k0 a = 1
+against the Mie series (lossy and lossless, error shrinking with h); energy
+balance (extinction = radiated power) in the lossless case.
 """
 from __future__ import annotations
 
@@ -107,7 +114,7 @@ def dense_T(n, kappa: float) -> np.ndarray:
 
 
 def dense_A(n, kappa: float, Mvox: np.ndarray) -> np.ndarray:
-    """A = I - diag(M) T (Sec. 6 discrete J-VIE), M repeated for 3 components."""
+    """A = I - diag(M) T (Sec. 3.1 discrete J-VIE), M repeated for 3 components."""
     T = dense_T(n, kappa)
     m = np.tile(np.asarray(Mvox, dtype=np.complex128).ravel(), 3)
     return np.eye(T.shape[0], dtype=np.complex128) - m[:, None] * T
@@ -165,7 +172,7 @@ def apply_T(Ghat: np.ndarray, n, w: np.ndarray) -> np.ndarray:
 
 
 def matvec(Ghat: np.ndarray, n, Mvox: np.ndarray, w: np.ndarray) -> np.ndarray:
-    """y = w - M (T w) (Sec. 6 MVP of I - M_eps N)."""
+    """y = w - M (T w) (Sec. 5.4 MVP of I - M_eps N)."""
     w = np.asarray(w, dtype=np.complex128).reshape(3, *np.asarray(Mvox).shape)
     return w - np.asarray(Mvox)[None] * apply_T(Ghat, n, w)
 

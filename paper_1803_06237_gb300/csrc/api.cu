@@ -218,6 +218,7 @@ static void free_plan(vie_plan* p) {
   cudaFree(p->M32);
   cudaFree(p->chi64);
   cudaFree(p->work);
+  cudaFree(p->host_stage);
   delete p;
 }
 
@@ -436,6 +437,7 @@ vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(s);
+  if (st == VIE_OK) st = static_scratch_prepare();
   if (st != VIE_OK) { free_plan(p); return st; }
   *out = p;
   return VIE_OK;
@@ -492,6 +494,8 @@ vie_status vie_plan_clone(const vie_plan* base, vie_plan** out) {
     free_plan(p);
     return VIE_ERR_CUDA;
   }
+  vie_status st = static_scratch_prepare();
+  if (st != VIE_OK) { free_plan(p); return st; }
   *out = p;
   return VIE_OK;
 }

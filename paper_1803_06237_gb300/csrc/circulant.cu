@@ -1,4 +1,4 @@
-// Block-circulant preconditioner of Sec. 6: the Frobenius-nearest matrix W
+// Block-circulant preconditioner of Sec. 5.4: the Frobenius-nearest matrix W
 // to A = I - M N that is circulant in x, with dense (3 ny nz)^2 blocks.
 //
 // View A as nx x nx blocks A[i][j] (rows and columns ordered (p, z, y)):

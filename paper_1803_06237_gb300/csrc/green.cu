@@ -4,7 +4,7 @@
 // Paper (arXiv:1803.06237): N f = curl curl S f with G = exp(-j k r)/(4 pi r)
 // (Sec. 3); N_ij = <N P_j, P_i> with P_i = h^(-3/2) on voxel i (Sec. 3.1);
 // N is block-Toeplitz with six unique tensor components and its product is
-// computed with FFTs (Sec. 6).
+// computed with FFTs (Sec. 5.4).
 //
 // With h as the unit of length and kappa = k h, (lap + k^2) G = -delta gives
 // N = k^2 S + grad div S + I, and the entry for offset D and components p, q is

@@ -1,4 +1,4 @@
-// Krylov solvers for the discrete J-VIE (I - M_eps N) w = b (Sec. 6 of
+// Krylov solvers for the discrete J-VIE (I - M_eps N) w = b (Sec. 5.4 of
 // arXiv:1803.06237; the paper solves it with GMRES at tolerance 1e-8, Sec. 5),
 // for one problem or a batch of problems of uneven sizes.
 //
@@ -945,6 +945,56 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
 
 using namespace vie;
 
+namespace vie {
+
+// Device copies of b and x for a solve on host buffers: 2 x 3N complex128,
+// allocated on the plan's first such solve and kept.
+static vie_status host_stage(vie_plan* p, double2** b, double2** x) {
+  const size_t n3 = (size_t)3 * p->n[0] * p->n[1] * p->n[2];
+  if (!p->host_stage) {
+    cudaError_t e = cudaMalloc(&p->host_stage, 2 * n3 * sizeof(double2));
+    if (e != cudaSuccess) {
+      p->host_stage = nullptr;
+      set_error("staging buffers for host vectors: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+    }
+  }
+  *b = (double2*)p->host_stage;
+  *x = *b + n3;
+  return VIE_OK;
+}
+
+// Solve on host buffers: copy b (and x when it is an initial guess) to the
+// plans' staging buffers, solve there, copy every x back (also when the solve
+// reports an error status: x then holds the last or best iterate).
+static vie_status solve_host(vie_plan* const* plans, int count, const void* const* b_host, void* const* x_host,
+                             double tol, const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn fn,
+                             void* const* ctx, cudaStream_t s) {
+  std::vector<const double2*> bd(count);
+  std::vector<double2*> xd(count);
+  for (int i = 0; i < count; ++i) {
+    double2* b = nullptr;
+    double2* x = nullptr;
+    vie_status st = host_stage(plans[i], &b, &x);
+    if (st != VIE_OK) return st;
+    const size_t bytes = (size_t)3 * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
+    VIE_CUDA_TRY(cudaMemcpyAsync(b, b_host[i], bytes, cudaMemcpyHostToDevice, s));
+    if (o->x0_given) VIE_CUDA_TRY(cudaMemcpyAsync(x, x_host[i], bytes, cudaMemcpyHostToDevice, s));
+    bd[i] = b;
+    xd[i] = x;
+  }
+  vie_status st = solve_batch_impl(plans, count, bd.data(), xd.data(), tol, o, infos, fn, ctx, s);
+  if (st == VIE_ERR_INVALID || st == VIE_ERR_OOM || st == VIE_ERR_CUDA) return st;
+  for (int i = 0; i < count; ++i) {
+    const size_t bytes = (size_t)3 * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
+    VIE_CUDA_TRY(cudaMemcpyAsync(x_host[i], xd[i], bytes, cudaMemcpyDeviceToHost, s));
+  }
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+}  // namespace vie
+
 extern "C" vie_status vie_solve(vie_plan* p, const void* b_dev, void* x_dev, double tol, const vie_solve_opts* opts,
                                 vie_solve_info* info, void* stream) {
   clear_error();
@@ -958,6 +1008,8 @@ extern "C" vie_status vie_solve(vie_plan* p, const void* b_dev, void* x_dev, dou
     vie_status st = precond_get(p, &fn, &ctx);
     if (st != VIE_OK) return st;
   }
+  if (opts->host_buffers)
+    return solve_host(&p, 1, &b_dev, &x_dev, tol, opts, info, fn, &ctx, (cudaStream_t)stream);
   const double2* b = (const double2*)b_dev;
   double2* x = (double2*)x_dev;
   return solve_batch_impl(&p, 1, &b, &x, tol, opts, info, fn, &ctx, (cudaStream_t)stream);
@@ -989,6 +1041,8 @@ extern "C" vie_status vie_solve_batch(vie_plan* const* plans, int count, const v
       fn = f;
     }
   }
+  if (opts->host_buffers)
+    return solve_host(plans, count, b_dev, x_dev, tol, opts, infos, fn, ctx.data(), (cudaStream_t)stream);
   return solve_batch_impl(plans, count, (const double2* const*)b_dev, (double2* const*)x_dev, tol, opts, infos, fn,
                           ctx.data(), (cudaStream_t)stream);
 }

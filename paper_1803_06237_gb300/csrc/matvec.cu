@@ -1,4 +1,4 @@
-// The J-VIE operator application y = w - M (N w) (Sec. 6 of arXiv:1803.06237:
+// The J-VIE operator application y = w - M (N w) (Sec. 5.4 of arXiv:1803.06237:
 // the block-Toeplitz N, six unique tensor components, applied with FFTs; the
 // diagonal multiplier M_eps of Sec. 3 carries material and absorber).
 //
@@ -1248,6 +1248,15 @@ static vie_status static_scratch_address(void** out) {
   }
   *out = g_static_scratch_addr[dev];
   return VIE_OK;
+}
+
+// Called by vie_plan_create and vie_plan_clone, where allocating is allowed:
+// the lookup makes the runtime load this file's module (and with it the
+// static array) on the current device, so that under lazy module loading the
+// first vie_matvec_static_scratch call does not load it and reserve memory.
+vie_status static_scratch_prepare() {
+  void* unused = nullptr;
+  return static_scratch_address(&unused);
 }
 
 }  // namespace vie

@@ -1,7 +1,7 @@
 // Learned right preconditioner z = Net(v, chi): a 3-D convolutional network
 // trained on the device by the kernels in this file.
 //
-// The paper preconditions GMRES with a block-circulant matrix (Sec. 6); the
+// The paper preconditions GMRES with a block-circulant matrix (Sec. 5.4); the
 // network is this project's addition.  Architecture (same as the oracle's):
 // 8 input channels (re/im of the three components of v, re/im of chi), four
 // levels (average pooling 2 x 2 in x and y, z kept), 32 channels, 3x3x3 convs
@@ -763,11 +763,12 @@ static vie_status net_apply_t(vie_net* net, const vie_plan* p, const V* v, V* z,
 }
 
 // The preconditioner set on a plan: a network (learned) or a block-circulant
-// matrix (Sec. 6); exactly one of net and circ is set.
+// matrix (Sec. 5.4); exactly one of net and circ is set.
 struct PrecondCtx {
   vie_net* net;
   const vie_plan* plan;
   vie_circulant* circ;
+  bool owns_net;              // the network was built by vie_set_preconditioner from caller weights
 };
 
 static vie_status precond_apply(void* ctx, int dtype, const void* v, void* z, cudaStream_t s) {
@@ -779,7 +780,9 @@ static vie_status precond_apply(void* ctx, int dtype, const void* v, void* z, cu
 
 void free_precond(vie_plan* p) {
   if (p && p->precond) {
-    delete (PrecondCtx*)p->precond;
+    PrecondCtx* c = (PrecondCtx*)p->precond;
+    if (c->owns_net) vie_net_destroy(c->net);
+    delete c;
     p->precond = nullptr;
   }
 }
@@ -906,7 +909,7 @@ vie_status vie_net_apply(vie_net* n, const vie_plan* p, const void* v_dev, void*
   clear_error();
   if (!n || !p || !v_dev || !z_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
   if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
-  PrecondCtx c{n, p, nullptr};
+  PrecondCtx c{n, p, nullptr, false};
   return precond_apply(&c, dtype, v_dev, z_dev, (cudaStream_t)stream);
 }
 
@@ -971,11 +974,34 @@ vie_status vie_net_status(vie_net* n, int* flag, int clear) {
   return VIE_OK;
 }
 
-vie_status vie_set_preconditioner(vie_plan* p, vie_net* n) {
+vie_status vie_set_preconditioner_net(vie_plan* p, vie_net* n) {
   clear_error();
   if (!p) { set_error("null plan"); return VIE_ERR_INVALID; }
   free_precond(p);
-  if (n) p->precond = new PrecondCtx{n, p, nullptr};
+  if (n) p->precond = new PrecondCtx{n, p, nullptr, false};
+  return VIE_OK;
+}
+
+vie_status vie_set_preconditioner(vie_plan* p, const void* weights, size_t bytes) {
+  clear_error();
+  if (!p) { set_error("null plan"); return VIE_ERR_INVALID; }
+  if (!weights) {
+    free_precond(p);
+    return VIE_OK;
+  }
+  const size_t np = total_params();
+  if (bytes != np * sizeof(float)) {
+    set_error("weights must hold %zu bytes (%zu FP32 parameters), got %zu", np * sizeof(float), np, bytes);
+    return VIE_ERR_INVALID;
+  }
+  int cur = -1;
+  VIE_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != p->device) { set_error("the plan's device (%d) must be current", p->device); return VIE_ERR_INVALID; }
+  vie_net* n = nullptr;
+  vie_status st = vie_net_create(&n, (const float*)weights, np, 0);
+  if (st != VIE_OK) return st;
+  free_precond(p);
+  p->precond = new PrecondCtx{n, p, nullptr, true};
   return VIE_OK;
 }
 
@@ -988,7 +1014,7 @@ vie_status vie_set_circulant_preconditioner(vie_plan* p, vie_circulant* c) {
     return VIE_ERR_INVALID;
   }
   free_precond(p);
-  if (c) p->precond = new PrecondCtx{nullptr, p, c};
+  if (c) p->precond = new PrecondCtx{nullptr, p, c, false};
   return VIE_OK;
 }
 

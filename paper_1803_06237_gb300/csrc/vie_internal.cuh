@@ -148,6 +148,7 @@ struct vie_plan {
   int* shared_refs = nullptr; // plans made by vie_plan_clone share entries, spectra and twiddles
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
   void* precond = nullptr;    // preconditioner state (learned or block-circulant), if set
+  void* host_stage = nullptr; // device copies of b and x for solves on host buffers (2 x 3N complex128)
   int contrast_gen = 0;       // incremented whenever the contrast is set
   int x_lpb = 0;              // four-step forward x-pass lines per block (0: heuristic)
   int x_lpb_inv = 0;          // four-step inverse x-pass lines per block (0: heuristic)
@@ -166,6 +167,9 @@ vie_status matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode,
 // Complex values of the split pass B's buffer (Mx My 3 nz) when a plane of
 // this shape takes it, else 0.
 size_t pass_b_split_elems(int ny, int nz, int Mx, int My, int Mz);
+// Looks up the static workspace of vie_matvec_static_scratch on the current
+// device (loads its module there); plan creation calls it.
+vie_status static_scratch_prepare();
 
 // MODE_PLAIN (x-pass kernels run along y inside pass B): inverse FFT and
 // crop only, no contrast epilogue.

@@ -48,7 +48,7 @@ class vie_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("x0_given", ctypes.c_int),
                 ("use_preconditioner", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("host_buffers", ctypes.c_int)]
 
 
 class vie_solve_info(ctypes.Structure):
@@ -93,13 +93,15 @@ _SIGNATURES = {
     "vie_circulant_info": ([_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)], _I),
     "vie_circulant_destroy": ([_P], _I),
     "vie_set_circulant_preconditioner": ([_P, _P], _I),
-    "vie_set_preconditioner": ([_P, _P], _I),
+    "vie_set_preconditioner": ([_P, _P, ctypes.c_size_t], _I),
+    "vie_set_preconditioner_net": ([_P, _P], _I),
     "vie_plan_clone": ([_P, ctypes.POINTER(_P)], _I),
     "vie_matvec_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P], _I),
     "vie_solve_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D,
                          ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_reflection": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
+    "vie_probe_fma_tflops": ([_I, ctypes.POINTER(_D), _P], _I),
     "vie_last_error": ([], ctypes.c_char_p),
 }
 
@@ -270,15 +272,16 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
               max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
               use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
               stream=None, raise_on_not_converged: bool = True) -> dict:
-    """Solve (I - M N) x = b on the device; b, x complex128 CUDA tensors."""
-    import torch
-    for t in (b, x):
-        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128 and t.numel() == 3 * plan.n_vox):
-            raise ValueError("b and x must be contiguous complex128 CUDA vectors of 3*nx*ny*nz entries")
+    """Solve (I - M N) x = b on the device.  b, x: complex128 CUDA tensors, or
+    (both) C-contiguous complex128 NumPy arrays on the host, which the library
+    stages through device buffers (opts.host_buffers = 1); x is written in
+    place either way."""
+    host = _vectors_kind([(b, x)], [plan])
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
-                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s))
+                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s),
+                          int(host))
     info = vie_solve_info()
-    st = load().vie_solve(plan.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+    st = load().vie_solve(plan.handle, _vec_ptr(b), _vec_ptr(x), float(tol),
                           ctypes.byref(opts), ctypes.byref(info), _stream_handle(stream))
     out = {"status": st, "iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
            "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
@@ -287,6 +290,31 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
     if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
         _check(st, "vie_solve")
     return out
+
+
+def _vectors_kind(pairs, plans) -> bool:
+    """True for host NumPy vectors, False for CUDA tensors; checks type, size
+    and contiguity of every (b, x) pair."""
+    import torch
+    host = isinstance(pairs[0][0], np.ndarray)
+    for (b, x), p in zip(pairs, plans):
+        for t in (b, x):
+            if host:
+                ok = (isinstance(t, np.ndarray) and t.dtype == np.complex128 and t.flags.c_contiguous
+                      and t.size == 3 * p.n_vox)
+                if t is x and not t.flags.writeable:
+                    ok = False
+            else:
+                ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+                      and t.dtype == torch.complex128 and t.numel() == 3 * p.n_vox)
+            if not ok:
+                raise ValueError("b and x must both be contiguous complex128 vectors of 3*nx*ny*nz entries: "
+                                 "CUDA tensors, or writable NumPy arrays on the host")
+    return host
+
+
+def _vec_ptr(t):
+    return ctypes.c_void_p(t.ctypes.data if isinstance(t, np.ndarray) else t.data_ptr())
 
 
 def vie_plan_clone(base: Plan) -> Plan:
@@ -318,20 +346,20 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
                     max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
                     use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
                     stream=None, raise_on_not_converged: bool = True):
-    """Solve every (plan, b, x) together; returns (status, [info dict per problem])."""
-    import torch
+    """Solve every (plan, b, x) together (CUDA tensors, or host NumPy arrays
+    as in vie_solve); returns (status, [info dict per problem])."""
     n = len(plans)
     if not (n == len(bs) == len(xs)) or n == 0:
         raise ValueError("plans, bs and xs must have the same non-zero length")
-    for p, b, x in zip(plans, bs, xs):
-        for t in (b, x):
-            if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128 and t.numel() == 3 * p.n_vox):
-                raise ValueError("b and x must be contiguous complex128 CUDA vectors of 3*nx*ny*nz entries")
+    host = _vectors_kind(list(zip(bs, xs)), plans)
+    if any(isinstance(t, np.ndarray) != host for t in list(bs) + list(xs)):
+        raise ValueError("every b and x must be of one kind: all CUDA tensors or all host arrays")
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
-                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s))
+                          int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s),
+                          int(host))
     infos = (vie_solve_info * n)()
     st = load().vie_solve_batch(_ptr_array([p.handle.value for p in plans]), n,
-                                _ptr_array([b.data_ptr() for b in bs]), _ptr_array([x.data_ptr() for x in xs]),
+                                _ptr_array([_vec_ptr(b).value for b in bs]), _ptr_array([_vec_ptr(x).value for x in xs]),
                                 float(tol), ctypes.byref(opts), infos, _stream_handle(stream))
     out = []
     for info in infos:
@@ -485,9 +513,23 @@ def vie_net_adam_step(net: Net, lr: float, grad_scale: float = 1.0, stream=None)
            "vie_net_adam_step")
 
 
-def vie_set_preconditioner(plan: Plan, net):
-    _check(load().vie_set_preconditioner(plan.handle, net.handle if net is not None else None),
-           "vie_set_preconditioner")
+def vie_set_preconditioner(plan: Plan, weights):
+    """Learned right preconditioner from FP32 parameters (host array of
+    vie_net_param_count() floats); None removes any preconditioner.  The plan
+    keeps its own copy."""
+    if weights is None:
+        _check(load().vie_set_preconditioner(plan.handle, None, 0), "vie_set_preconditioner")
+    else:
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(load().vie_set_preconditioner(plan.handle, ctypes.c_void_p(w.ctypes.data), w.nbytes),
+               "vie_set_preconditioner")
+    plan._net = None
+
+
+def vie_set_preconditioner_net(plan: Plan, net):
+    """A network object (kept by the caller) as the right preconditioner."""
+    _check(load().vie_set_preconditioner_net(plan.handle, net.handle if net is not None else None),
+           "vie_set_preconditioner_net")
     plan._net = net      # keep the network alive while it is set
 
 
@@ -513,6 +555,14 @@ def vie_reflection(e_ref, e, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().vie_reflection(ctypes.c_void_p(e_ref.data_ptr()), ctypes.c_void_p(e.data_ptr()), e.numel(),
                                  ctypes.byref(out), _stream_handle(stream)), "vie_reflection")
+    return out.value
+
+
+def vie_probe_fma_tflops(dtype_code: int, stream=None) -> float:
+    """Measured FP32 (VIE_C64) or FP64 (VIE_C128) FMA throughput, TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load().vie_probe_fma_tflops(int(dtype_code), ctypes.byref(out), _stream_handle(stream)),
+           "vie_probe_fma_tflops")
     return out.value
 
 

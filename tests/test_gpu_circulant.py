@@ -1,4 +1,4 @@
-"""GPU block-circulant preconditioner (Sec. 6) against the FP64 oracle
+"""GPU block-circulant preconditioner (Sec. 5.4) against the FP64 oracle
 (oracle/circulant.py): z = W^{-1} v on grids with one and several LU panels,
 ragged solve blocks and x lengths that are not 5-smooth; solves with it."""
 import math

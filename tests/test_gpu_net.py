@@ -28,6 +28,23 @@ def _bf16(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _forward_bf16(p, x):
+    """The network as the tensor-core inference path rounds it, assembled here
+    from the oracle's FP64 primitives: every convolution input and every stored
+    hidden activation (after its ReLU) rounded to BF16, FP64 arithmetic
+    otherwise.  Test-side emulation; the oracle's own forward is plain FP64."""
+    hs, a = [], x
+    for lvl in range(4):
+        if lvl > 0:
+            a = cn.pool(hs[-1])
+        hs.append(_bf16(cn.relu(cn.conv3d(_bf16(a), p[f"enc{lvl}.w"], p[f"enc{lvl}.b"]))))
+    u = hs[3]
+    for lvl in (2, 1, 0):
+        s = cn.up(u, hs[lvl].shape[2], hs[lvl].shape[3]) + hs[lvl]
+        u = _bf16(cn.relu(cn.conv3d(_bf16(s), p[f"dec{lvl}.w"], p[f"dec{lvl}.b"])))
+    return cn.conv3d(_bf16(u), p["out.w"], p["out.b"])
+
+
 def _oracle_params(flat):
     p, off = {}, 0
     for name, ci, co in cn.LAYERS:
@@ -81,12 +98,14 @@ def test_param_layout_and_identity_at_start():
                                         ((160, 40, 11), np.complex64), ((600, 23, 11), np.complex64)])
 def test_forward_matches_oracle(grid, dtype):
     """Inference (tcgen05 convolutions, BF16 weights, channels-last BF16
-    activations, FP32 accumulation) against the FP64 oracle with the same
-    roundings (convolution inputs and stored activations rounded to BF16);
-    the tolerance covers values that land on the other side of a BF16
-    rounding boundary in FP32 and FP64.  The two largest grids give every
-    persistent CTA several tiles (the 600 x 23 x 11 guide is the benchmark
-    workload's grid)."""
+    activations, FP32 accumulation) against the plain FP64 oracle forward
+    (same BF16 weights): the 16 BF16 roundings of activations (relative
+    <= 2^-9 each) move the network's correction by ~0.25% on these inputs
+    (sqrt(16) 2^-9 = 0.8% if independent), so 2e-2 bounds it with margin.
+    Also against a test-side emulation of the same roundings, whose residual
+    gap is values landing on the other side of a BF16 rounding boundary in
+    FP32 and FP64.  The two largest grids give every persistent CTA several
+    tiles (the 600 x 23 x 11 guide is the benchmark workload's grid)."""
     plan, chi, net = _setup(grid, 5)
     p = _oracle_params(vie.vie_net_get_params(net))
     nx, ny, nz = grid
@@ -99,13 +118,14 @@ def test_forward_matches_oracle(grid, dtype):
     vr = v.astype(np.complex128)
     s = _scale(v) if dtype == np.complex64 else math.sqrt(vr.size / np.sum(np.abs(vr) ** 2))
     X = cn.pack_input(vr * s, chi)
-    z_ref = vr + cn.unpack_output(cn.forward(p, X, act_round=_bf16, store_round=_bf16)) / s
     z = zd.cpu().numpy().reshape(3, nz, ny, nx)
-    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 3e-3
-    # the correction alone, against the oracle's correction
     dz = (z - vr).ravel()
-    dz_ref = (z_ref - vr).ravel()
-    assert np.linalg.norm(dz - dz_ref) / np.linalg.norm(dz_ref) < 2e-2
+    for y_ref in (cn.forward(p, X), _forward_bf16(p, X)):
+        z_ref = vr + cn.unpack_output(y_ref) / s
+        assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 3e-3
+        # the correction alone, against the reference's correction
+        dz_ref = (z_ref - vr).ravel()
+        assert np.linalg.norm(dz - dz_ref) / np.linalg.norm(dz_ref) < 2e-2
 
 
 def test_gradients_match_oracle():
@@ -156,7 +176,7 @@ def test_flexible_gmres_with_network_converges():
     plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
     vie.vie_set_permittivity(plan, wl.eps, ab)
     net = vie.vie_net_create(seed=3)
-    vie.vie_set_preconditioner(plan, net)
+    vie.vie_set_preconditioner_net(plan, net)
     src = torch.from_numpy(wl.src.ravel()).cuda()
     b = torch.empty_like(src)
     vie.vie_rhs_from_source(plan, src, b)

@@ -106,7 +106,7 @@ def test_inverse_undoes_block_circular_convolution():
 
 
 def test_preconditioned_gmres_needs_far_fewer_steps():
-    """Sec. 6: on a strip guide with an absorber the circulant preconditioner
+    """Sec. 5.4: on a strip guide with an absorber the circulant preconditioner
     cuts the GMRES step count several-fold (here 60 x 6 x 3 voxels of 80 nm)."""
     from oracle import gmres as gm
     from oracle import greens
