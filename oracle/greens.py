@@ -254,6 +254,50 @@ def toeplitz_entries(kappa: float, offsets, q_override: int | None = None,
     return out
 
 
+def curl_entries(kappa: float, offsets, q_override: int | None = None,
+                 q_duffy: int = Q_DUFFY) -> np.ndarray:
+    """Galerkin entries of the scalar derivatives of S, in units of h:
+    C_a(Delta) = <P_i, d_a S P_j> / h = int (d_a g)(u) L_Delta(u) du, shape (K, 3)
+    for a = x, y, z.  By parts on the tent (no boundary terms: L_Delta vanishes
+    on the edge of its support, d_a g ~ 1/|u|^2 is integrable)
+
+        C_a(Delta) = int g(u) s(u_a - Delta_a) L(u_b - Delta_b) L(u_c - Delta_c) du,
+
+    s(t) = sign(t) on |t| < 1, integrated with the same unit-cell rules as the
+    entries of T.  The curl operator K = curl S (Sec. 3) has the entries
+    K_pq(Delta) = h eps_paq C_a(Delta) (eps the Levi-Civita symbol), i.e.
+    (K f) = C * f as a cross product C x f."""
+    offsets = np.asarray(offsets, dtype=np.int64).reshape(-1, 3)
+    out = np.zeros((offsets.shape[0], 3), dtype=np.complex128)
+    cheb = np.abs(offsets).max(axis=1)
+    for n, D in enumerate(offsets):
+        q = q_override or gl_order(int(cheb[n]))
+        pts, wts = [], []
+        for m in itertools.product((-1, 0), repeat=3):
+            P, W = _cell_rule_3d(D + np.array(m), q, q_duffy)
+            pts.append(P)
+            wts.append(W)
+        P = np.concatenate(pts)
+        W = np.concatenate(wts)
+        rel = P - D
+        gw = _g(np.linalg.norm(P, axis=1), kappa) * W
+        L = [_tent(rel[:, a]) for a in range(3)]
+        S = [_sgn(rel[:, a]) for a in range(3)]
+        out[n, 0] = np.sum(gw * S[0] * L[1] * L[2])
+        out[n, 1] = np.sum(gw * L[0] * S[1] * L[2])
+        out[n, 2] = np.sum(gw * L[0] * L[1] * S[2])
+    return out
+
+
+def curl_octant_table(kappa: float, n) -> np.ndarray:
+    """C_a for Delta in [0, n0) x [0, n1) x [0, n2); shape (3, n2, n1, n0).
+    C_a is odd in Delta_a and even in the other two components."""
+    n0, n1, n2 = (int(v) for v in n)
+    zz, yy, xx = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    offs = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    return curl_entries(kappa, offs).T.reshape(3, n2, n1, n0)
+
+
 def volume_integral(kappa: float, offset, q: int = 16, q_duffy: int = Q_DUFFY):
     """V(Delta) alone (used by the trace-identity and closed-form pins)."""
     D = np.asarray(offset, dtype=np.int64)
