@@ -191,7 +191,9 @@ typedef struct {
   int matvecs64;          /* complex128 operator applications */
   int matvecs32;          /* complex64 operator applications */
   int converged;          /* 1 if ||b - A x|| <= tol ||b|| (true FP64 residual) */
-  int fallback;           /* 1 if the preconditioner was dropped during the solve */
+  int fallback;           /* 1 if the preconditioner was dropped during the solve
+                             (a cycle it did not help, or network outputs that
+                             were not finite and were replaced by the input) */
   double residual;        /* final true relative residual ||b - A x|| / ||b|| */
   double time_ms;         /* device time of the solve */
   int history_len;        /* entries used in history */
@@ -315,8 +317,7 @@ typedef struct vie_circulant vie_circulant;
 /* Flags of vie_circulant_create. */
 #define VIE_CIRC_DEFAULT 0
 #define VIE_CIRC_FP16_FACTORS 1   /* keep the LU factors in complex half precision (half the memory and
-                                     half the bytes per application); the factorisation runs in complex64
-                                     with its trailing updates on TF32 tensor cores */
+                                     half the bytes per application); the factorisation runs in complex64 */
 
 /* Build W from the plan's current Toeplitz entries and contrast (the plan's
  * contrast must have been set) and factor it; synchronises `stream`.  The
@@ -358,6 +359,54 @@ vie_status vie_set_preconditioner(vie_plan* plan, const void* weights, size_t by
  * reference, and the caller must not destroy the network while it is set. */
 vie_status vie_set_preconditioner_net(vie_plan* plan, vie_net* net);
 
+/* ------------------------------------------------------------------------ */
+/* JM-VIE (Sec. 3, discrete form Sec. 3.1): electric and magnetic currents,  */
+/* for magnetic loss matched to the electric absorber (Sec. 4.2).  With      */
+/* u_e = J/c_e and u_m = eta M/c_m (both in units of the electric field,   */
+/* eta the background impedance) the system (I - M T)(J, M) = C M (E, H)    */
+/* reads                                                                     */
+/*   u_e - M_eps (N u_e) + j kappa M_eps (C x u_m) = M_eps e_inc             */
+/*   u_m - M_mu  (N u_m) - j kappa M_mu  (C x u_e) = M_mu  eta h_inc         */
+/* with K = curl S = h C x (the curl Toeplitz operator, three unique odd     */
+/* components C_a = <P_i, d_a S P_j>/h), kappa = k h, M_mu = (mu_r-1)/mu_r.  */
+/* A JM vector holds 6 components per voxel, [c][z][y][x] with c = 0..2     */
+/* the electric and c = 3..5 the magnetic current, 6*nx*ny*nz complex       */
+/* numbers.  The plane of one kx (6 x My x Mz values) must fit in one       */
+/* thread block's shared memory (e.g. the 23 x 11 guide cross-section).     */
+/* ------------------------------------------------------------------------ */
+
+/* Permeability of the plan's voxels for the JM-VIE: mu_host holds
+ * nx*ny*nz complex128 mu_r = mu' - j mu'' in [z][y][x] order, or NULL for
+ * the impedance-matched permeability of Sec. 4.2, mu'' = eps''/eps' with
+ * eps' - j eps'' the plan's current permittivity (mu_r = 1 where it is
+ * lossless, i.e. outside the absorbers).  The first call computes, in FP64,
+ * the curl entries C_a(Delta) and their folded spectra and allocates the
+ * JM workspace (6 ny nz Mx complex128).  Call it again after the
+ * permittivity changes.  Synchronous.  Errors: VIE_ERR_INVALID,
+ * VIE_ERR_NONFINITE (mu = 0 or non-finite), VIE_ERR_OOM, VIE_ERR_CUDA. */
+vie_status vie_set_permeability(vie_plan* plan, const double* mu_host);
+
+/* y = u - M (T u) for 6N device vectors x = u and y of type dtype (not
+ * overlapping).  Asynchronous on `stream`; uses the plan's JM workspace.
+ * Errors: VIE_ERR_INVALID (no permeability set, stale, overlap),
+ * VIE_ERR_CUDA. */
+vie_status vie_jm_matvec(vie_plan* plan, const void* x_dev, void* y_dev, int dtype, void* stream);
+
+/* Right-hand side for impressed currents (w_e, w_m) (6N, scaled like u)
+ * radiating in the background: e_inc = (N - I) w_e - j kappa C x w_m,
+ * eta h_inc = (N - I) w_m + j kappa C x w_e, b = (M_eps e_inc, M_mu eta h_inc).
+ * Same rules as vie_jm_matvec. */
+vie_status vie_jm_rhs_from_source(vie_plan* plan, const void* src_dev, void* b_dev, int dtype, void* stream);
+
+/* Solve the JM-VIE for 6N complex128 vectors b and x (device pointers, or
+ * host pointers with opts->host_buffers = 1), as vie_solve does for the
+ * J-VIE: restarted GMRES on the complex128 operator or mixed-precision
+ * refinement; no preconditioner (opts->use_preconditioner must be 0).
+ * The field on the axis is vie_axis_field of the electric half (E =
+ * u_e / chi_e).  Errors: as vie_solve. */
+vie_status vie_jm_solve(vie_plan* plan, const void* b, void* x, double tol, const vie_solve_opts* opts,
+                        vie_solve_info* info, void* stream);
+
 /* Field on the centre axis (step a12; Sec. 3 equivalent currents J =
  * c_e chi E, so E = J/(c_e chi); the factor c_e h^(3/2) common to every
  * field is not applied).  w_dev: complex128 solution (3*nx*ny*nz); e_dev:
@@ -373,6 +422,13 @@ vie_status vie_axis_field(const vie_plan* plan, const void* w_dev, int n_keep,
  * VIE_ERR_INVALID, VIE_ERR_NONFINITE (zero reference), VIE_ERR_CUDA. */
 vie_status vie_reflection(const void* eref_dev, const void* e_dev, int count,
                           double* r_out, void* stream);
+
+/* Transmission through the voxel plane ix (Sec. 5.2): T = sum of |E|^2 over
+ * the plane's voxels with chi != 0 (the structure's cross-section), E =
+ * w / chi per component (the common factor |c_e|^2 h^3 is not applied).
+ * w_dev: complex128 solution (3*nx*ny*nz).  FP64 sums.  Synchronous.
+ * Errors: VIE_ERR_INVALID, VIE_ERR_CUDA. */
+vie_status vie_slice_power(const vie_plan* plan, const void* w_dev, int ix, double* t_out, void* stream);
 
 /* Same operator application as vie_matvec, for callers that cannot allocate
  * device memory where they apply the operator (their memory is owned by

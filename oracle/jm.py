@@ -56,19 +56,13 @@ def mu_contrast(mu: np.ndarray) -> np.ndarray:
     return (mu - 1.0) / mu
 
 
-def matched_permeability(eps: np.ndarray, eps_bg: float, absorbers=()) -> np.ndarray:
-    """mu_r = 1 - j mu'' with mu'' = eps''/eps' (Sec. 4.2) on the voxels the
-    absorbers act on (core voxels, eps != eps_bg), 1 elsewhere; eps'' is the
-    absorbers' graded loss, eps' the voxel's real permittivity (the ratio is
-    the same before and after scaling by eps_bg)."""
-    eps = np.asarray(eps, dtype=np.complex128)
-    nx = eps.shape[-1]
-    core = np.abs(eps - eps_bg) > 0
-    e2 = np.zeros(eps.shape)
-    for ab in absorbers:
-        e2 = e2 + core * op.absorber_eps2(nx, ab["x0"], ab["length"], ab["degree"], ab["eps2_max"],
-                                          ab.get("direction", +1))[None, None, :]
-    return 1.0 - 1j * e2 / eps.real
+def matched_permeability(chi: np.ndarray) -> np.ndarray:
+    """mu_r = 1 - j mu'' with mu'' = eps''/eps' (Sec. 4.2) from the contrast
+    chi = eps_r/eps_bg - 1 (eps' - j eps'' = eps_bg (1 + chi); the ratio does
+    not depend on eps_bg): non-zero where the permittivity is lossy, i.e. in
+    the absorbers."""
+    chi = np.asarray(chi, dtype=np.complex128)
+    return 1.0 - 1j * (-chi.imag) / (1.0 + chi.real)
 
 
 # ----------------------------------------------------------------------------

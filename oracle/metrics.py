@@ -16,6 +16,9 @@ Paper (arXiv:1803.06237):
 Reading: the axis is the voxel row at (ny // 2, nz // 2); all three field
 components enter the norm.
 
+The transmission through a plane (Sec. 5.2), T = sum |E|^2 over the plane's
+voxels inside the structure (chi != 0), with the same E.
+
 Pins (tests/test_oracle_metrics.py): R = 0 for identical fields, R = 1 for a
 zero field, R = |r|^2 for a mode plus a reflected wave r exp(+j beta x) over
 whole half-periods, R = |1 - a exp(j phi)|^2 for a scaled and phase-shifted
@@ -40,3 +43,13 @@ def reflection_coefficient(E_ref: np.ndarray, E_L: np.ndarray) -> float:
     E_ref = np.asarray(E_ref)
     E_L = np.asarray(E_L)
     return float(np.sum(np.abs(E_ref - E_L) ** 2) / np.sum(np.abs(E_ref) ** 2))
+
+
+def slice_power(w: np.ndarray, chi: np.ndarray, ix: int) -> float:
+    """Transmission through the voxel plane ix (Sec. 5.2): sum of |E|^2 over
+    the plane's voxels with chi != 0, E = w / chi (up to c_e h^{3/2})."""
+    nz, ny, nx = chi.shape
+    w = np.asarray(w).reshape(3, nz, ny, nx)[:, :, :, ix]
+    c = chi[:, :, ix]
+    inside = c != 0
+    return float(np.sum(np.abs(w[:, inside] / c[inside][None]) ** 2))

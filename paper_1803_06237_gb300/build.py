@@ -67,7 +67,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=()) ->
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + ".tmp"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(exe)), "lib64")
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas",
+    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart",
            "-Xlinker", "-rpath", "-Xlinker", cudalib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -51,6 +51,33 @@ bool factor_length(int len, AxisPlan* out) {
   return r == 1;
 }
 
+// Radices for lengths with any prime factors: 4, 2, 3, 5 first, then every
+// larger prime factor in increasing order (a generic Stockham stage sums
+// those directly).  Used by the FFTs along x of the block-circulant
+// preconditioner, whose length is the grid's nx.
+bool factor_length_any(int len, AxisPlan* out) {
+  if (len < 1) return false;
+  out->len = len;
+  out->nstages = 0;
+  int r = len;
+  for (int f : {4, 2, 3, 5}) {
+    while (r % f == 0) {
+      if (out->nstages >= kMaxStages) return false;
+      out->radix[out->nstages++] = f;
+      r /= f;
+    }
+  }
+  for (int f = 7; r > 1; f += 2) {
+    if ((long long)f * f > r) f = r;       // what is left is prime
+    while (r % f == 0) {
+      if (out->nstages >= kMaxStages) return false;
+      out->radix[out->nstages++] = f;
+      r /= f;
+    }
+  }
+  return true;
+}
+
 // Twiddles exp(-2 pi i k / len) in FP64 on the host (libm cos/sin), the
 // argument reduced to the first octant through the symmetries of the circle.
 static void twiddle_host(int len, std::vector<double>& re, std::vector<double>& im) {
@@ -196,6 +223,40 @@ static vie_status set_contrast_common(vie_plan* p, const double* host, const vie
   return st;
 }
 
+// JM-VIE contrast (Sec. 3): mu_r per voxel from the caller, or matched to
+// the permittivity's loss (Sec. 4.2, mu'' = eps''/eps' with eps' - j eps'' =
+// eps_bg (1 + chi)); M_mu = (mu_r - 1)/mu_r.  The 6N contrast holds M_eps for
+// the three electric and M_mu for the three magnetic components.
+__global__ void jm_contrast_kernel(const double2* __restrict__ mu_in, const double2* __restrict__ chi,
+                                   const double2* __restrict__ Me, double2* __restrict__ chimu,
+                                   double2* __restrict__ M64, float2* __restrict__ M32, size_t N, int* bad) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    double2 mu;
+    if (mu_in) {
+      mu = mu_in[v];
+    } else {
+      const double2 c = chi[v];
+      mu = make_double2(1.0, c.y < 0.0 ? c.y / (1.0 + c.x) : 0.0);   // 1 - j (-Im chi)/(1 + Re chi)
+    }
+    const double den = mu.x * mu.x + mu.y * mu.y;
+    // (mu - 1)/mu = 1 - conj(mu)/|mu|^2
+    double mr = 1.0 - mu.x / den, mi = mu.y / den;
+    if (!(isfinite(mr) && isfinite(mi)) || den == 0.0) {
+      atomicExch(bad, 1);
+      mr = 0.0;
+      mi = 0.0;
+    }
+    chimu[v] = make_double2(mu.x - 1.0, mu.y);
+    const double2 me = Me[v];
+    for (int c = 0; c < 3; ++c) {
+      M64[c * N + v] = me;
+      M32[c * N + v] = make_float2((float)me.x, (float)me.y);
+      M64[(3 + c) * N + v] = make_double2(mr, mi);
+      M32[(3 + c) * N + v] = make_float2((float)mr, (float)mi);
+    }
+  }
+}
+
 static void free_plan(vie_plan* p) {
   if (!p) return;
   free_krylov(p);
@@ -219,6 +280,13 @@ static void free_plan(vie_plan* p) {
   cudaFree(p->chi64);
   cudaFree(p->work);
   cudaFree(p->host_stage);
+  cudaFree(p->curl);
+  cudaFree(p->chat64);
+  cudaFree(p->chat32);
+  cudaFree(p->Mjm64);
+  cudaFree(p->Mjm32);
+  cudaFree(p->chimu64);
+  cudaFree(p->jm_work);
   delete p;
 }
 
@@ -602,6 +670,98 @@ vie_status vie_get_toeplitz(const vie_plan* p, double* out) {
   VIE_CUDA_TRY(cudaSetDevice(p->device));
   VIE_CUDA_TRY(cudaMemcpy(out, p->toeplitz, 6 * N * sizeof(double2), cudaMemcpyDeviceToHost));
   return VIE_OK;
+}
+
+vie_status vie_set_permeability(vie_plan* p, const double* mu_host) {
+  clear_error();
+  if (!p) { set_error("null plan"); return VIE_ERR_INVALID; }
+  VIE_CUDA_TRY(cudaSetDevice(p->device));
+  const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  if (!p->curl) {
+    // first call: the curl entries, their spectra, the 6N contrast and the workspace
+    const size_t C = (size_t)p->kf[0] * 3 * p->kf[1] * p->kf[2];
+    const size_t W = (size_t)6 * p->n[1] * p->n[2] * p->m[0];
+    struct { void** ptr; size_t sz; } allocs[] = {
+        {(void**)&p->curl, 3 * N * sizeof(double2)}, {(void**)&p->chat64, C * sizeof(double2)},
+        {(void**)&p->chat32, C * sizeof(float2)},    {(void**)&p->Mjm64, 6 * N * sizeof(double2)},
+        {(void**)&p->Mjm32, 6 * N * sizeof(float2)}, {(void**)&p->chimu64, N * sizeof(double2)},
+        {(void**)&p->jm_work, W * sizeof(double2)}};
+    for (auto& a : allocs) {
+      cudaError_t e = cudaMalloc(a.ptr, a.sz);
+      if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu) for the JM-VIE: %s", a.sz, cudaGetErrorString(e));
+        for (auto& b : allocs) { cudaFree(*b.ptr); *b.ptr = nullptr; }
+        return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
+      }
+      p->device_bytes += a.sz;
+    }
+    vie_status st = compute_curl(p, 0);
+    if (st == VIE_OK) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) { set_error("curl spectrum: %s", cudaGetErrorString(e)); st = VIE_ERR_CUDA; }
+    }
+    if (st != VIE_OK) {
+      cudaFree(p->curl);
+      p->curl = nullptr;
+      return st;
+    }
+  }
+  double2* mu_dev = nullptr;
+  int* bad = nullptr;
+  VIE_CUDA_TRY(cudaMalloc((void**)&bad, sizeof(int)));
+  cudaError_t e = cudaMemset(bad, 0, sizeof(int));
+  if (e == cudaSuccess && mu_host) {
+    e = cudaMalloc((void**)&mu_dev, N * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpy(mu_dev, mu_host, N * sizeof(double2), cudaMemcpyHostToDevice);
+  }
+  int hbad = 0;
+  if (e == cudaSuccess) {
+    const unsigned blocks = (unsigned)((N + 255) / 256 < 152 * 16 ? (N + 255) / 256 : 152 * 16);
+    jm_contrast_kernel<<<blocks, 256>>>(mu_dev, p->chi64, p->M64, p->chimu64, p->Mjm64, p->Mjm32, N, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  cudaFree(mu_dev);
+  if (e != cudaSuccess) {
+    set_error("set permeability: %s", cudaGetErrorString(e));
+    return VIE_ERR_CUDA;
+  }
+  if (hbad) {
+    set_error("permeability is not finite or zero");
+    return VIE_ERR_NONFINITE;
+  }
+  p->jm_gen = p->contrast_gen;
+  return VIE_OK;
+}
+
+static vie_status check_jm_args(vie_plan* p, const void* x, void* y, int dtype) {
+  if (!p || !x || !y) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (dtype != VIE_C64 && dtype != VIE_C128) { set_error("dtype must be VIE_C64 or VIE_C128"); return VIE_ERR_INVALID; }
+  if (!p->curl) { set_error("call vie_set_permeability before the JM-VIE operator"); return VIE_ERR_INVALID; }
+  if (p->jm_gen != p->contrast_gen) {
+    set_error("the permittivity changed after vie_set_permeability: call it again");
+    return VIE_ERR_INVALID;
+  }
+  const size_t bytes = (size_t)6 * p->n[0] * p->n[1] * p->n[2] * (dtype == VIE_C64 ? 8 : 16);
+  const char* a = (const char*)x;
+  const char* b = (const char*)y;
+  if (a < b + bytes && b < a + bytes) { set_error("x and y overlap"); return VIE_ERR_INVALID; }
+  return VIE_OK;
+}
+
+vie_status vie_jm_matvec(vie_plan* p, const void* x, void* y, int dtype, void* stream) {
+  clear_error();
+  vie_status st = check_jm_args(p, x, y, dtype);
+  if (st != VIE_OK) return st;
+  return jm_matvec_impl(p, x, y, dtype, MODE_OPERATOR, (cudaStream_t)stream);
+}
+
+vie_status vie_jm_rhs_from_source(vie_plan* p, const void* src, void* b, int dtype, void* stream) {
+  clear_error();
+  vie_status st = check_jm_args(p, src, b, dtype);
+  if (st != VIE_OK) return st;
+  return jm_matvec_impl(p, src, b, dtype, MODE_RHS, (cudaStream_t)stream);
 }
 
 vie_status vie_eps2_from_round_trip(double r_rt, int degree, double length, double k0, double eps_r, double D,

@@ -11,22 +11,19 @@
 //
 // Setup (once per plan and contrast):
 //   1. prefix sums of M along x (FP64),
-//   2. W_hat: when nx has only the factors 2, 3, 5, the blocks c_k of 16
-//      entries at a time are formed in shared memory and transformed along k
-//      by a Stockham FFT; otherwise the blocks are stored and W_hat = F C is
-//      one CGEMM with the nx x nx DFT matrix F,
-//   4. LU with partial pivoting of the nx blocks W_hat(w): panels of nb
+//   2. W_hat: the blocks c_k of up to 16 entries at a time are formed in
+//      shared memory and transformed along k by a Stockham FFT (radices 2-5
+//      as butterflies, larger prime factors such as 7, 11, 13 summed
+//      directly), so the blocks c_k are never stored,
+//   3. LU with partial pivoting of the nx blocks W_hat(w): panels of nb
 //      columns factored in shared memory, row swaps, a triangular solve for
-//      the U row block, and the trailing update as a strided-batched CGEMM.
+//      the U row block, and the trailing update A22 -= L21 U12 as a batched
+//      complex GEMM (64 x 64 output tiles per CTA, FP32).
 // Application z = W^{-1} v (complex64):
-//   V_hat = F V (an FFT along x for 5-smooth nx, else a CGEMM), one pivoted
-//   forward and backward substitution per frequency (one CTA each, the
-//   factor streamed once from HBM), then z = F^H Z_hat / nx (likewise).  The vectors' planar layout [p][z][y][x] is
-//   already the (3B) x nx matrix the transforms need.
-//
-// The plain GEMMs (the DFTs along x and the trailing LU updates) go to
-// cuBLAS; everything else is in this file.
-#include <cublas_v2.h>
+//   V_hat = FFT along x of the 3 ny nz lines, one pivoted forward and
+//   backward substitution per frequency (one CTA each, the factor streamed
+//   once from HBM), then z = inverse FFT / nx.  The vectors' planar layout
+//   [p][z][y][x] is already the (3B) x nx matrix the transforms need.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <stdio.h>
@@ -45,29 +42,16 @@ struct vie_circulant {
   __half2* W16 = nullptr;      // the same in complex half precision (VIE_CIRC_FP16_FACTORS; W is then freed)
   bool fp16 = false;
   int* perm = nullptr;         // nx x R: row r of P b is b[perm[r]]
-  float2* F = nullptr;         // nx x nx: exp(-2 pi i w k / nx)
-  float2* Fi = nullptr;        // nx x nx: exp(+2 pi i w k / nx) / nx
   float2* vh = nullptr;        // nx x R scratch (row-major [w][r])
   float2* v32 = nullptr;       // 3N scratch for complex128 callers
   float2* z32 = nullptr;
   int* flag = nullptr;         // 1: a zero pivot was met
-  float2* tw = nullptr;        // nx twiddles exp(-2 pi i k / nx) when nx has only the factors 2, 3, 5
-  vie::Radices rd;             //   and its radices: the DFTs along x are then FFTs
-  cublasHandle_t blas = nullptr;
+  float2* tw = nullptr;        // nx twiddles exp(-2 pi i k / nx)
+  vie::Radices rd;             //   and the radices of nx for the FFTs along x
   double build_ms = 0.0;
 };
 
 namespace vie {
-
-#define VIE_CUBLAS_TRY(expr)                                                     \
-  do {                                                                           \
-    cublasStatus_t b__ = (expr);                                                 \
-    if (b__ != CUBLAS_STATUS_SUCCESS) {                                          \
-      set_error("%s:%d: %s failed (cuBLAS status %d)", __FILE__, __LINE__, #expr, \
-                (int)b__);                                                       \
-      return VIE_ERR_CUDA;                                                       \
-    }                                                                            \
-  } while (0)
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -123,48 +107,14 @@ __device__ __forceinline__ float2 toeplitz_at(const double2* __restrict__ T, int
   return make_float2(sgn * (float)t.x, sgn * (float)t.y);
 }
 
-// C[k][r][s] = delta_k0 delta_rs - S+_k[r] T(k)[r][s] - S-_k[r] T(k - nx)[r][s]
-// r = (p, z, y), s = (q, z', y'), T(dx)[r][s] = T_pq(dx, y - y', z - z').
-__global__ void build_blocks_kernel(const double2* __restrict__ T, const float2* __restrict__ Sp,
-                                    const float2* __restrict__ Sm, int nx, int ny, int nz, float2* __restrict__ C) {
-  const int B = ny * nz, R = 3 * B;
-  const size_t total = (size_t)nx * R * R;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int s = (int)(idx % R);
-    const int r = (int)((idx / R) % R);
-    const int k = (int)(idx / ((size_t)R * R));
-    const int p = r / B, zy = r % B, z = zy / ny, y = zy % ny;
-    const int q = s / B, zy2 = s % B, z2 = zy2 / ny, y2 = zy2 % ny;
-    float2 out = make_float2((k == 0 && r == s) ? 1.f : 0.f, 0.f);
-    out = csub_mul(out, Sp[(size_t)zy * nx + k], toeplitz_at(T, nx, ny, nz, p, q, k, y - y2, z - z2));
-    if (k > 0) out = csub_mul(out, Sm[(size_t)zy * nx + k], toeplitz_at(T, nx, ny, nz, p, q, k - nx, y - y2, z - z2));
-    C[idx] = out;
-  }
-}
-
-// F[w][k] = exp(-2 pi i w k / nx), Fi[w][k] = exp(+2 pi i w k / nx) / nx
-// (angles reduced exactly with integer arithmetic, evaluated in FP64)
-__global__ void dft_matrix_kernel(int nx, float2* __restrict__ F, float2* __restrict__ Fi) {
-  const size_t total = (size_t)nx * nx;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const long long w = (long long)(idx / nx), k = (long long)(idx % nx);
-    const long long m = (w * k) % nx;
-    double sn, cs;
-    sincospi(2.0 * (double)m / (double)nx, &sn, &cs);
-    F[idx] = make_float2((float)cs, (float)-sn);
-    Fi[idx] = make_float2((float)(cs / nx), (float)(sn / nx));
-  }
-}
-
-// W_hat[w][e] for kTL consecutive entries e = r R + s at once, when nx has
-// only the factors 2, 3, 5: c_k[e] for every k is formed in shared memory
-// and transformed along k by the Stockham FFT, so the blocks c_k are never
-// stored.  tw = exp(-2 pi i k / nx).
+// W_hat[w][e] for tl (<= kTL) consecutive entries e = r R + s at once:
+// c_k[e] for every k is formed in shared memory and transformed along k by
+// the Stockham FFT, so the blocks c_k are never stored.  tw = exp(-2 pi i k
+// / nx).  tl is chosen so that the 2 tl lines of nx + 1 values fit in shared
+// memory.
 constexpr int kTL = 16;
 __global__ void __launch_bounds__(256) build_fft_kernel(const double2* __restrict__ T, const float2* __restrict__ Sp,
-                                                        const float2* __restrict__ Sm, int nx, int ny, int nz,
+                                                        const float2* __restrict__ Sm, int nx, int ny, int nz, int tl,
                                                         Radices rd, const float2* __restrict__ twg,
                                                         float2* __restrict__ What) {
   extern __shared__ float2 sb[];
@@ -176,9 +126,9 @@ __global__ void __launch_bounds__(256) build_fft_kernel(const double2* __restric
   const int pitch = nx + 1;
   float2* tw = sb;
   float2* A = tw + nx;
-  float2* Bf = A + kTL * pitch;
-  const long long e0 = (long long)blockIdx.x * kTL;
-  const int nl = (int)min((long long)kTL, RR - e0);
+  float2* Bf = A + tl * pitch;
+  const long long e0 = (long long)blockIdx.x * tl;
+  const int nl = (int)min((long long)tl, RR - e0);
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int i = tid; i < nx; i += nth) tw[i] = twg[i];
   if (tid < nl) {
@@ -216,11 +166,11 @@ __global__ void __launch_bounds__(256) build_fft_kernel(const double2* __restric
     }
     A[l * pitch + k] = out;
   }
-  for (int idx = nl * nx + tid; idx < kTL * nx; idx += nth) A[(idx / nx) * pitch + idx % nx] = make_float2(0.f, 0.f);
+  for (int idx = nl * nx + tid; idx < tl * nx; idx += nth) A[(idx / nx) * pitch + idx % nx] = make_float2(0.f, 0.f);
   __syncthreads();
-  const float2* res = fft_lines<float2, false>(A, Bf, rd, pitch, kTL, tw, tid, nth);
-  for (int idx = tid; idx < nx * kTL; idx += nth) {
-    const int w = idx / kTL, l = idx - w * kTL;
+  const float2* res = fft_lines<float2, false, true>(A, Bf, rd, pitch, tl, tw, tid, nth);
+  for (int idx = tid; idx < nx * tl; idx += nth) {
+    const int w = idx / tl, l = idx - w * tl;
     if (l < nl) What[(size_t)w * RR + e0 + l] = res[l * pitch + w];
   }
 }
@@ -233,8 +183,7 @@ __global__ void twiddle_kernel(int nx, float2* __restrict__ tw) {
   tw[k] = make_float2((float)cs, (float)-sn);
 }
 
-// DFTs along x of the application as FFTs (nx with factors 2, 3, 5 only),
-// kLines rows per block.  Forward: vh[w][r] = sum_x v[r][x] exp(-2 pi i w x /
+// DFTs along x of the application as FFTs, kLines rows per block.  Forward: vh[w][r] = sum_x v[r][x] exp(-2 pi i w x /
 // nx); inverse: z[r][x] = (1/nx) sum_w vh[w][r] exp(+2 pi i w x / nx).
 constexpr int kLines = 4;
 template <bool INV>
@@ -256,7 +205,7 @@ __global__ void __launch_bounds__(256) lines_fft_kernel(const float2* __restrict
     A[l * pitch + k] = v;
   }
   __syncthreads();
-  const float2* res = fft_lines<float2, INV>(A, Bf, rd, pitch, kLines, tw, tid, nth);
+  const float2* res = fft_lines<float2, INV, true>(A, Bf, rd, pitch, kLines, tw, tid, nth);
   const float inv = 1.f / (float)nx;
   for (int idx = tid; idx < kLines * nx; idx += nth) {
     int l, k;
@@ -380,6 +329,71 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(float2* __restrict__ W, in
     for (int t = 0; t < i; ++t) x[i] = csub_mul(x[i], L[i][t], x[t]);
 #pragma unroll
   for (int i = 0; i < NB; ++i) A[(size_t)(j0 + i) * R + c] = x[i];
+}
+
+// Trailing update A22 -= L21 U12 of every matrix (blockIdx.z): L21 = rows
+// j1 .. R - 1, columns j0 .. j1 - 1; U12 = rows j0 .. j1 - 1, columns
+// j1 .. R - 1 (KB = j1 - j0).  One CTA per 64 x 64 tile of A22: the two
+// operand panels are staged in shared memory (L21 transposed), each of the
+// 256 threads accumulates 4 x 4 complex products (rows ty + 16 a, columns
+// tx + 16 b, so that a warp's stores cover 16 consecutive columns).  The
+// regions read and written are disjoint, so the update is in place.
+template <int KB>
+__global__ void __launch_bounds__(256) lu_update_kernel(float2* __restrict__ W, int R, int j0) {
+  __shared__ float2 As[KB][65];
+  __shared__ float2 Bs[KB][64];
+  float2* A = W + (size_t)blockIdx.z * R * R;
+  const int j1 = j0 + KB, n = R - j1;
+  const int i0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * KB; e += 256) {
+    const int i = e / KB, k = e - i * KB;
+    const int r = i0 + i;
+    As[k][i] = r < n ? A[(size_t)(j1 + r) * R + j0 + k] : make_float2(0.f, 0.f);
+  }
+  for (int e = tid; e < 64 * KB; e += 256) {
+    const int k = e >> 6, j = e & 63;
+    const int c = c0 + j;
+    Bs[k][j] = c < n ? A[(size_t)(j0 + k) * R + j1 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int k = 0; k < KB; ++k) {
+    float2 av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        acc[a][b].x = fmaf(av[a].x, bv[b].x, fmaf(-av[a].y, bv[b].y, acc[a][b].x));
+        acc[a][b].y = fmaf(av[a].x, bv[b].y, fmaf(av[a].y, bv[b].x, acc[a][b].y));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = i0 + ty + 16 * a;
+    if (r >= n) continue;
+    float2* row = A + (size_t)(j1 + r) * R + j1;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx + 16 * b;
+      if (c < n) {
+        float2 v = row[c];
+        v.x -= acc[a][b].x;
+        v.y -= acc[a][b].y;
+        row[c] = v;
+      }
+    }
+  }
 }
 
 // perm[w][r]: the swaps piv[w][0 .. R) applied in order to the identity, so
@@ -569,22 +583,28 @@ static unsigned blocks_for(size_t n) {
 // ---------------------------------------------------------------------------
 static void circ_free(vie_circulant* c) {
   if (!c) return;
-  cudaFree(c->W); cudaFree(c->W16); cudaFree(c->tw); cudaFree(c->perm); cudaFree(c->F); cudaFree(c->Fi); cudaFree(c->vh);
+  cudaFree(c->W); cudaFree(c->W16); cudaFree(c->tw); cudaFree(c->perm); cudaFree(c->vh);
   cudaFree(c->v32); cudaFree(c->z32); cudaFree(c->flag);
-  if (c->blas) cublasDestroy(c->blas);
   delete c;
 }
 
-// tf32: the trailing LU updates may use TF32 tensor cores (for factors that
-// are rounded to complex half afterwards).
-static vie_status circ_build(vie_circulant* c, cudaStream_t s, bool tf32) {
+// Lines per block of the fused build (blocks formed and transformed along x
+// in shared memory): the largest of 16, 8, 4, 2, 1 whose two buffers of
+// nx + 1 values and the twiddle table fit in `smem_max` bytes, or 0.
+static int build_lines(int nx, size_t smem_max) {
+  for (int tl = kTL; tl >= 1; tl >>= 1)
+    if ((size_t)nx * sizeof(float2) + (size_t)2 * tl * (nx + 1) * sizeof(float2) <= smem_max) return tl;
+  return 0;
+}
+
+static vie_status circ_build(vie_circulant* c, cudaStream_t s, size_t smem_max) {
   const vie_plan* p = c->plan;
   const int nx = c->nx, ny = c->ny, nz = c->nz, B = c->B, R = c->R;
   const size_t RR = (size_t)R * R, N3 = (size_t)3 * B * nx;
-  float2 *Sp = nullptr, *Sm = nullptr, *C = nullptr;
+  float2 *Sp = nullptr, *Sm = nullptr;
   int* piv = nullptr;
   vie_status st = VIE_OK;
-  auto fail = [&](vie_status e) { cudaFree(Sp); cudaFree(Sm); cudaFree(C); cudaFree(piv); return e; };
+  auto fail = [&](vie_status e) { cudaFree(Sp); cudaFree(Sm); cudaFree(piv); return e; };
 #define CIRC_TRY(expr)                                                                         \
   do {                                                                                         \
     cudaError_t e__ = (expr);                                                                  \
@@ -593,54 +613,28 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s, bool tf32) {
       return fail(e__ == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA);             \
     }                                                                                          \
   } while (0)
-#define CIRC_BLAS(expr)                                                                        \
-  do {                                                                                         \
-    cublasStatus_t b__ = (expr);                                                               \
-    if (b__ != CUBLAS_STATUS_SUCCESS) {                                                        \
-      set_error("%s:%d: %s failed (cuBLAS status %d)", __FILE__, __LINE__, #expr, (int)b__);   \
-      return fail(VIE_ERR_CUDA);                                                               \
-    }                                                                                          \
-  } while (0)
   CIRC_TRY(cudaMalloc((void**)&Sp, (size_t)nx * B * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&Sm, (size_t)nx * B * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&piv, (size_t)nx * R * sizeof(int)));
   CIRC_TRY(cudaMalloc((void**)&c->W, (size_t)nx * RR * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->perm, (size_t)nx * R * sizeof(int)));
-  CIRC_TRY(cudaMalloc((void**)&c->F, (size_t)nx * nx * sizeof(float2)));
-  CIRC_TRY(cudaMalloc((void**)&c->Fi, (size_t)nx * nx * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->vh, (size_t)nx * R * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->v32, N3 * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->z32, N3 * sizeof(float2)));
   CIRC_TRY(cudaMalloc((void**)&c->flag, sizeof(int)));
+  CIRC_TRY(cudaMalloc((void**)&c->tw, (size_t)nx * sizeof(float2)));
   CIRC_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s));
-  CIRC_BLAS(cublasSetStream(c->blas, s));
-  CIRC_BLAS(cublasSetMathMode(c->blas, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH));
 
   prefix_kernel<<<(B + 127) / 128, 128, 0, s>>>(p->M64, nx, B, Sp, Sm);
-  dft_matrix_kernel<<<blocks_for((size_t)nx * nx), 256, 0, s>>>(nx, c->F, c->Fi);
+  twiddle_kernel<<<(nx + 127) / 128, 128, 0, s>>>(nx, c->tw);
   CIRC_TRY(cudaGetLastError());
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f), mone = make_cuComplex(-1.f, 0.f);
-  AxisPlan ax;
-  const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * kTL * (nx + 1) * sizeof(float2);
-  if (factor_length(nx, &ax) && fft_smem <= 200 * 1024) {
-    // blocks formed and transformed along x in shared memory
-    CIRC_TRY(cudaMalloc((void**)&c->tw, (size_t)nx * sizeof(float2)));
-    float2* tw = c->tw;
-    twiddle_kernel<<<(nx + 127) / 128, 128, 0, s>>>(nx, tw);
-    c->rd = radices_of(ax);
-    CIRC_TRY(cudaFuncSetAttribute(build_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
-    build_fft_kernel<<<(unsigned)((RR + kTL - 1) / kTL), 256, fft_smem, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz,
-                                                                             radices_of(ax), tw, c->W);
-    CIRC_TRY(cudaGetLastError());
-  } else {
-    // any nx: the blocks, then W_hat[w][e] = sum_k F[w][k] C[k][e] as one CGEMM
-    // (column-major W_hat^T (RR x nx) = C^T (RR x nx) F, F symmetric)
-    CIRC_TRY(cudaMalloc((void**)&C, (size_t)nx * RR * sizeof(float2)));
-    build_blocks_kernel<<<152 * 16, 256, 0, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz, C);
-    CIRC_TRY(cudaGetLastError());
-    CIRC_BLAS(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)RR, nx, nx, &one, (const cuComplex*)C, (int)RR,
-                          (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->W, (int)RR));
-  }
+  // W_hat: blocks formed and transformed along x in shared memory
+  const int tl = build_lines(nx, smem_max);
+  const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * tl * (nx + 1) * sizeof(float2);
+  CIRC_TRY(cudaFuncSetAttribute(build_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+  build_fft_kernel<<<(unsigned)((RR + tl - 1) / tl), 256, fft_smem, s>>>(p->toeplitz, Sp, Sm, nx, ny, nz, tl, c->rd,
+                                                                        c->tw, c->W);
+  CIRC_TRY(cudaGetLastError());
   // LU of the nx blocks
   const int nb = c->nb;
   for (int j0 = 0; j0 < R; j0 += nb) {
@@ -651,15 +645,17 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s, bool tf32) {
     lu_swap_kernel<<<dim3(nx, (R + 255) / 256), 256, 0, s>>>(c->W, R, j0, nbe, piv);
     CIRC_TRY(cudaGetLastError());
     if (j1 < R) {
+      // here nbe == nb: only the last panel can be narrower, and it has no trailing block
       const dim3 tg(nx, (R - j1 + 255) / 256);
-      if (nb == 32) lu_trsm_kernel<32><<<tg, 256, 0, s>>>(c->W, R, j0);
-      else lu_trsm_kernel<16><<<tg, 256, 0, s>>>(c->W, R, j0);
+      const unsigned tiles = (unsigned)((R - j1 + 63) / 64);
+      if (nb == 32) {
+        lu_trsm_kernel<32><<<tg, 256, 0, s>>>(c->W, R, j0);
+        lu_update_kernel<32><<<dim3(tiles, tiles, nx), 256, 0, s>>>(c->W, R, j0);
+      } else {
+        lu_trsm_kernel<16><<<tg, 256, 0, s>>>(c->W, R, j0);
+        lu_update_kernel<16><<<dim3(tiles, tiles, nx), 256, 0, s>>>(c->W, R, j0);
+      }
       CIRC_TRY(cudaGetLastError());
-      // A22 -= L21 U12 (row-major), i.e. column-major A22^T -= U12^T L21^T
-      CIRC_BLAS(cublasCgemmStridedBatched(
-          c->blas, CUBLAS_OP_N, CUBLAS_OP_N, R - j1, R - j1, nbe, &mone, (const cuComplex*)(c->W + (size_t)j0 * R + j1),
-          R, (long long)RR, (const cuComplex*)(c->W + (size_t)j1 * R + j0), R, (long long)RR, &one,
-          (cuComplex*)(c->W + (size_t)j1 * R + j1), R, (long long)RR, nx));
     }
   }
   perm_kernel<<<(nx + 127) / 128, 128, 0, s>>>(piv, R, nx, c->perm);
@@ -668,14 +664,13 @@ static vie_status circ_build(vie_circulant* c, cudaStream_t s, bool tf32) {
   int flag = 0;
   CIRC_TRY(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
   fail(VIE_OK);
-  Sp = Sm = C = nullptr;
+  Sp = Sm = nullptr;
   piv = nullptr;
   if (flag) {
     set_error("block-circulant preconditioner: a diagonal block is singular");
     st = VIE_ERR_NONFINITE;
   }
 #undef CIRC_TRY
-#undef CIRC_BLAS
   return st;
 }
 
@@ -697,32 +692,17 @@ vie_status circulant_apply(vie_circulant* c, int dtype, const void* v, void* z, 
     zout = c->z32;
   }
   const size_t fft_smem = (size_t)nx * sizeof(float2) + (size_t)2 * kLines * (nx + 1) * sizeof(float2);
-  const bool fft = c->tw != nullptr;
-  if (fft) {
-    VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
-    VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
-  }
-  VIE_CUBLAS_TRY(cublasSetStream(c->blas, s));
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-  // V_hat[w][r] = sum_x F[w][x] v[r][x]
-  if (fft) {
-    lines_fft_kernel<false><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(vin, c->vh, R, nx, c->rd, c->tw);
-    VIE_LAUNCH_CHECK();
-  } else {
-    VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, R, nx, nx, &one, (const cuComplex*)vin, nx,
-                               (const cuComplex*)c->F, nx, &zero, (cuComplex*)c->vh, R));
-  }
+  VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+  VIE_CUDA_TRY(cudaFuncSetAttribute(lines_fft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem));
+  // V_hat[w][r] = sum_x exp(-2 pi i w x / nx) v[r][x]
+  lines_fft_kernel<false><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(vin, c->vh, R, nx, c->rd, c->tw);
+  VIE_LAUNCH_CHECK();
   if (c->fp16) circ_solve_kernel<__half2><<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W16, c->perm, c->vh, R);
   else circ_solve_kernel<float2><<<nx, 256, (size_t)R * sizeof(float2), s>>>(c->W, c->perm, c->vh, R);
   VIE_LAUNCH_CHECK();
-  // z[r][x] = sum_w Fi[w][x] Z_hat[w][r]
-  if (fft) {
-    lines_fft_kernel<true><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(c->vh, zout, R, nx, c->rd, c->tw);
-    VIE_LAUNCH_CHECK();
-  } else {
-    VIE_CUBLAS_TRY(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, R, nx, &one, (const cuComplex*)c->Fi, nx,
-                               (const cuComplex*)c->vh, R, &zero, (cuComplex*)zout, nx));
-  }
+  // z[r][x] = (1/nx) sum_w exp(+2 pi i w x / nx) Z_hat[w][r]
+  lines_fft_kernel<true><<<(R + kLines - 1) / kLines, 256, fft_smem, s>>>(c->vh, zout, R, nx, c->rd, c->tw);
+  VIE_LAUNCH_CHECK();
   if (dtype == VIE_C128) {
     to_c128_kernel<<<blocks_for(N3), 256, 0, s>>>(c->z32, (double2*)z, N3);
     VIE_LAUNCH_CHECK();
@@ -765,12 +745,20 @@ vie_status vie_circulant_create(vie_plan* plan, int flags, vie_circulant** out, 
     return VIE_ERR_INVALID;
   }
   VIE_CUDA_TRY(cudaGetDevice(&c->device));
-  if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
-    set_error("cublasCreate failed");
+  int smem_optin = 0;
+  VIE_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  // the FFTs along x: radices of nx (any prime factors) and shared memory for
+  // the application's kLines lines and at least one line of the build
+  AxisPlan ax;
+  if (!factor_length_any(c->nx, &ax) ||
+      (size_t)c->nx * sizeof(float2) + (size_t)2 * kLines * (c->nx + 1) * sizeof(float2) > (size_t)smem_optin ||
+      build_lines(c->nx, (size_t)smem_optin) == 0) {
+    set_error("nx = %d is too long for the block-circulant preconditioner's FFTs along x", c->nx);
     delete c;
-    return VIE_ERR_CUDA;
+    return VIE_ERR_INVALID;
   }
-  vie_status st = circ_build(c, (cudaStream_t)stream, (flags & VIE_CIRC_FP16_FACTORS) != 0);
+  c->rd = radices_of(ax);
+  vie_status st = circ_build(c, (cudaStream_t)stream, (size_t)smem_optin);
   if (st == VIE_OK && (flags & VIE_CIRC_FP16_FACTORS)) {
     // keep only a complex-half copy of the factors
     const size_t ne = (size_t)c->nx * c->R * c->R;
@@ -810,8 +798,9 @@ vie_status vie_circulant_info(const vie_circulant* c, double* build_ms, size_t* 
   if (!c) { set_error("null argument"); return VIE_ERR_INVALID; }
   if (build_ms) *build_ms = c->build_ms;
   if (device_bytes)
-    *device_bytes = (size_t)c->nx * c->R * c->R * (c->fp16 ? sizeof(__half2) : sizeof(float2)) + (size_t)c->nx * c->R * (sizeof(int) + sizeof(float2)) +
-                    (size_t)2 * c->nx * c->nx * sizeof(float2) + (size_t)2 * c->nx * c->R * sizeof(float2);
+    *device_bytes = (size_t)c->nx * c->R * c->R * (c->fp16 ? sizeof(__half2) : sizeof(float2)) +
+                    (size_t)c->nx * c->R * (sizeof(int) + sizeof(float2)) + (size_t)c->nx * sizeof(float2) +
+                    (size_t)2 * c->nx * c->R * sizeof(float2);
   return VIE_OK;
 }
 

@@ -87,11 +87,56 @@ __device__ __forceinline__ void dft_small(V* a, int r) {
   }
 }
 
-// One Stockham stage over `nlines` lines (line pitch `pitch`).
+// One Stockham stage of a radix r above 5 (any r that divides len): the
+// r-point DFT of each butterfly is summed directly, its roots of unity
+// exp(-2 pi i t u / r) = tw[((t u) mod r) (len / r)] read from the length-len
+// table, O(r^2) per butterfly.  Lets lengths with prime factors such as 7,
+// 11 or 13 use the same kernels as 5-smooth lengths.
 template <typename V, bool INV>
+__device__ __forceinline__ void stockham_stage_generic(const V* __restrict__ src, V* __restrict__ dst,
+                                                       int len, int pitch, int nlines, int r, int s,
+                                                       const V* __restrict__ tw, int tid, int nth) {
+  const int n = len / s;
+  const int m = n / r;
+  const int nb = len / r;
+  const int step = len / r;
+  const int total = nb * nlines;
+  for (int idx = tid; idx < total; idx += nth) {
+    const int line = idx / nb;
+    const int b = idx - line * nb;
+    const int p = b / s;
+    const int q = b - p * s;
+    const V* x = src + line * pitch;
+    V* y = dst + line * pitch;
+    for (int u = 0; u < r; ++u) {
+      V acc = x[q + s * p];
+      int e = 0;                       // (t u) mod r, advanced by u per term
+      for (int t = 1; t < r; ++t) {
+        e += u;
+        if (e >= r) e -= r;
+        const V w = tw[e * step];
+        const V a = x[q + s * (p + t * m)];
+        acc = add(acc, INV ? mulc(a, w) : mul(a, w));
+      }
+      if (u > 0) {
+        const V w = tw[p * u * s];
+        acc = INV ? mulc(acc, w) : mul(acc, w);
+      }
+      y[q + s * (r * p + u)] = acc;
+    }
+  }
+}
+
+// One Stockham stage over `nlines` lines (line pitch `pitch`); radices above
+// 5 only when GENERIC (the operator's passes use 5-smooth lengths).
+template <typename V, bool INV, bool GENERIC = false>
 __device__ __forceinline__ void stockham_stage(const V* __restrict__ src, V* __restrict__ dst,
                                                int len, int pitch, int nlines, int r, int s,
                                                const V* __restrict__ tw, int tid, int nth) {
+  if (GENERIC && r > 5) {
+    stockham_stage_generic<V, INV>(src, dst, len, pitch, nlines, r, s, tw, tid, nth);
+    return;
+  }
   const int n = len / s;
   const int m = n / r;
   const int nb = len / r;
@@ -122,7 +167,7 @@ __device__ __forceinline__ void stockham_stage(const V* __restrict__ src, V* __r
 // Full transform of `nlines` lines held in buf0; buf1 is scratch of the same
 // shape.  Every thread of the block must call it.  Returns the buffer holding
 // the result.
-template <typename V, bool INV>
+template <typename V, bool INV, bool GENERIC = false>
 __device__ V* fft_lines(V* buf0, V* buf1, const Radices& rd, int pitch, int nlines,
                         const V* tw, int tid, int nth) {
   V* src = buf0;
@@ -130,7 +175,7 @@ __device__ V* fft_lines(V* buf0, V* buf1, const Radices& rd, int pitch, int nlin
   int s = 1;
   for (int st = 0; st < rd.nstages; ++st) {
     const int r = rd.r[st];
-    stockham_stage<V, INV>(src, dst, rd.len, pitch, nlines, r, s, tw, tid, nth);
+    stockham_stage<V, INV, GENERIC>(src, dst, rd.len, pitch, nlines, r, s, tw, tid, nth);
     __syncthreads();
     V* t = src; src = dst; dst = t;
     s *= r;

@@ -454,4 +454,189 @@ vie_status compute_spectrum(vie_plan* p, cudaStream_t s) {
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// JM-VIE (Sec. 3): Galerkin entries of the scalar derivatives of S, in units
+// of h, C_a(D) = <P_i, d_a S P_j> / h = int (d_a g)(v) L_D(v) dv; the curl
+// operator K = curl S has K_pq(D) = h eps_paq C_a(D).  C_a is odd in D_a and
+// even in the other two offsets, C_a(0) = 0.  As for T:
+//   * |D|_inf >= 2: d_a g in closed form, -g (1 + j kappa r) v_a / r^2, with
+//     the tent weight, tensor Gauss-Legendre over the 8 unit cells;
+//   * |D|_inf = 1: by parts on the tent, C_a = int g sign(v_a - D_a)
+//     L(v_b - D_b) L(v_c - D_c) dv, Duffy cells where the origin is a corner.
+// Stored like T: octant [a][z][y][x] for D in [0, n).
+// ---------------------------------------------------------------------------
+__global__ void near_curl_kernel(double2* __restrict__ C, int nx, int ny, int nz, double kappa) {
+  const int b = blockIdx.x;                    // D = (b&1, (b>>1)&1, (b>>2)&1), D != 0
+  const int D[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+  if (D[0] >= nx || D[1] >= ny || D[2] >= nz) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int q = kQNear;
+  const double* X = c_gl_x + q * (q - 1) / 2;
+  const double* W = c_gl_w + q * (q - 1) / 2;
+  double2 acc[kNearAcc];
+  for (int k = 0; k < kNearAcc; ++k) acc[k] = make_double2(0.0, 0.0);
+  if (b != 0) {
+    for (int cell = 0; cell < 8; ++cell) {
+      int c0[3] = {D[0] - 1 + (cell & 1), D[1] - 1 + ((cell >> 1) & 1), D[2] - 1 + ((cell >> 2) & 1)};
+      const bool duffy = (c0[0] == 0 || c0[0] == -1) && (c0[1] == 0 || c0[1] == -1) && (c0[2] == 0 || c0[2] == -1);
+      const int q3 = q * q * q;
+      const int npts = duffy ? 3 * q3 : q3;
+      for (int pt = tid; pt < npts; pt += nth) {
+        const int a = pt / q3, rest = pt - a * q3;
+        const int i = rest / (q * q), j = (rest / q) % q, k = rest % q;
+        double v[3], w;
+        if (duffy) {
+          const double t = X[i];
+          double u[3];
+          u[a] = t;
+          u[(a + 1) % 3] = t * X[j];
+          u[(a + 2) % 3] = t * X[k];
+          for (int d = 0; d < 3; ++d) v[d] = (c0[d] == -1) ? -u[d] : u[d];
+          w = W[i] * W[j] * W[k] * t * t;
+        } else {
+          v[0] = c0[0] + X[i]; v[1] = c0[1] + X[j]; v[2] = c0[2] + X[k];
+          w = W[i] * W[j] * W[k];
+        }
+        const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double2 g = green_w(r, kappa, w);
+        const double rx = v[0] - D[0], ry = v[1] - D[1], rz = v[2] - D[2];
+        const double Lx = tent(rx), Ly = tent(ry), Lz = tent(rz);
+        const double f[3] = {sgn1(rx) * Ly * Lz, Lx * sgn1(ry) * Lz, Lx * Ly * sgn1(rz)};
+        for (int s = 0; s < 3; ++s) { acc[s].x += g.x * f[s]; acc[s].y += g.y * f[s]; }
+      }
+    }
+  }
+  extern __shared__ double red[];
+  block_reduce_acc(acc, red, tid, nth);
+  if (tid == 0) {
+    const double* R = red + (nth >> 5) * kNearAcc * 2;
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t vox = ((size_t)D[2] * ny + D[1]) * nx + D[0];
+    for (int a = 0; a < 3; ++a) C[a * N + vox] = make_double2(R[2 * a], R[2 * a + 1]);
+  }
+}
+
+__global__ void far_curl_kernel(double2* __restrict__ C, int nx, int ny, int nz, double kappa) {
+  const size_t N = (size_t)nx * ny * nz;
+  const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= N) return;
+  const int dx = (int)(gw % nx), dy = (int)((gw / nx) % ny), dz = (int)(gw / ((size_t)nx * ny));
+  const int cheb = max(dx, max(dy, dz));
+  if (cheb <= 1) return;
+  const int q = gl_order_for(cheb);
+  const double* X = c_gl_x + q * (q - 1) / 2;
+  const double* W = c_gl_w + q * (q - 1) / 2;
+  const int q3 = q * q * q;
+  const int npts = 8 * q3;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int pt = lane; pt < npts; pt += 32) {
+    const int cell = pt / q3, rest = pt - cell * q3;
+    const int i = rest / (q * q), j = (rest / q) % q, k = rest % q;
+    const double ox = (cell & 1) - 1 + X[i], oy = ((cell >> 1) & 1) - 1 + X[j], oz = ((cell >> 2) & 1) - 1 + X[k];
+    const double w = W[i] * W[j] * W[k] * (1.0 - fabs(ox)) * (1.0 - fabs(oy)) * (1.0 - fabs(oz));
+    const double v[3] = {dx + ox, dy + oy, dz + oz};
+    const double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double r = sqrt(r2);
+    double s, c;
+    sincos(kappa * r, &s, &c);
+    // d_a g = -(1 + j kappa r) e^{-j kappa r} v_a / (4 pi r^3)
+    const double f = -w / (4.0 * M_PI * r * r2);
+    const double kr = kappa * r;
+    const double er = (c + kr * s) * f, ei = (kr * c - s) * f;   // (1 + j kr)(c - j s) f
+    for (int a = 0; a < 3; ++a) {
+      acc[2 * a] += er * v[a];
+      acc[2 * a + 1] += ei * v[a];
+    }
+  }
+  for (int k = 0; k < 6; ++k)
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) C[a * N + gw] = make_double2(acc[2 * a], acc[2 * a + 1]);
+}
+
+// circulant embedding of C_a: odd along axis a, even along the others
+__global__ void embed_curl_kernel(const double2* __restrict__ C, double2* __restrict__ full,
+                                  int nx, int ny, int nz, int Mx, int My, int Mz) {
+  const size_t total = (size_t)3 * Mx * My * Mz;
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int mx = (int)(idx % Mx);
+    const int my = (int)((idx / Mx) % My);
+    const int mz = (int)((idx / ((size_t)Mx * My)) % Mz);
+    const int a = (int)(idx / ((size_t)Mx * My * Mz));
+    bool nx_, ny_, nz_, vx, vy, vz;
+    const int dx = fold_index(mx, nx, Mx, &nx_, &vx);
+    const int dy = fold_index(my, ny, My, &ny_, &vy);
+    const int dz = fold_index(mz, nz, Mz, &nz_, &vz);
+    double2 val = make_double2(0.0, 0.0);
+    if (vx && vy && vz) {
+      val = C[a * N + ((size_t)dz * ny + dy) * nx + dx];
+      const bool flip = (a == 0) ? nx_ : (a == 1) ? ny_ : nz_;
+      if (flip) { val.x = -val.x; val.y = -val.y; }
+    }
+    full[idx] = val;
+  }
+}
+
+// fold to the octant [kx'][a][kz'][ky'], scaled by 1/(Mx My Mz)
+__global__ void fold_curl_kernel(const double2* __restrict__ full, double2* __restrict__ c64,
+                                 float2* __restrict__ c32, int Mx, int My, int Mz, int Kx, int Ky, int Kz,
+                                 double scale_) {
+  const size_t total = (size_t)Kx * 3 * Kz * Ky;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(idx % Ky);
+    const int kz = (int)((idx / Ky) % Kz);
+    const int a = (int)((idx / ((size_t)Ky * Kz)) % 3);
+    const int kx = (int)(idx / ((size_t)Ky * Kz * 3));
+    double2 v = full[(((size_t)a * Mz + kz) * My + ky) * Mx + kx];
+    v.x *= scale_;
+    v.y *= scale_;
+    c64[idx] = v;
+    c32[idx] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+vie_status compute_curl(vie_plan* p, cudaStream_t s) {
+  vie_status st = upload_gl_tables();
+  if (st != VIE_OK) return st;
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
+  const size_t N = (size_t)nx * ny * nz;
+  {
+    const int threads = 256;
+    const size_t blocks = (N * 32 + threads - 1) / threads;
+    far_curl_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->curl, nx, ny, nz, p->kappa);
+    VIE_LAUNCH_CHECK();
+    const size_t smem = (size_t)(threads / 32 + 1) * kNearAcc * 2 * sizeof(double);
+    near_curl_kernel<<<8, threads, smem, s>>>(p->curl, nx, ny, nz, p->kappa);
+    VIE_LAUNCH_CHECK();
+  }
+  const size_t cells = (size_t)Mx * My * Mz;
+  double2* full = nullptr;
+  VIE_CUDA_TRY(cudaMallocAsync((void**)&full, 3 * cells * sizeof(double2), s));
+  {
+    const size_t total = 3 * cells;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    embed_curl_kernel<<<blocks, 256, 0, s>>>(p->curl, full, nx, ny, nz, Mx, My, Mz);
+    if (cudaGetLastError() != cudaSuccess) { set_error("embed_curl_kernel launch failed"); st = VIE_ERR_CUDA; }
+  }
+  if (st == VIE_OK) st = fft_axis_f64(full, p->ax[0], 1, 0, 3LL * Mz * My, Mx, 1, s);
+  if (st == VIE_OK) st = fft_axis_f64(full, p->ax[1], 3LL * Mz, (long long)My * Mx, Mx, 1, Mx, s);
+  if (st == VIE_OK) st = fft_axis_f64(full, p->ax[2], 3, (long long)Mz * My * Mx, (long long)My * Mx, 1,
+                                      (long long)My * Mx, s);
+  if (st == VIE_OK) {
+    const size_t total = (size_t)p->kf[0] * 3 * p->kf[2] * p->kf[1];
+    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    fold_curl_kernel<<<blocks, 256, 0, s>>>(full, p->chat64, p->chat32, Mx, My, Mz, p->kf[0], p->kf[1], p->kf[2],
+                                            1.0 / (double)cells);
+    if (cudaGetLastError() != cudaSuccess) { set_error("fold_curl_kernel launch failed"); st = VIE_ERR_CUDA; }
+  }
+  cudaError_t e = cudaFreeAsync(full, s);
+  if (st == VIE_OK && e != cudaSuccess) { set_error("cudaFreeAsync: %s", cudaGetErrorString(e)); st = VIE_ERR_CUDA; }
+  return st;
+}
+
 }  // namespace vie

@@ -589,8 +589,8 @@ void free_krylov(vie_plan* p) {
   }
 }
 
-static vie_status ensure_work(vie_plan* p, int m, int dtype, bool flexible, KrylovWork** out) {
-  const size_t n = (size_t)3 * p->n[0] * p->n[1] * p->n[2];
+static vie_status ensure_work(vie_plan* p, int m, int dtype, bool flexible, KrylovWork** out, int comps) {
+  const size_t n = (size_t)comps * p->n[0] * p->n[1] * p->n[2];
   KrylovWork* k = (KrylovWork*)p->krylov;
   if (k && k->m == m && k->dtype == dtype && k->flexible == flexible && k->n == n) {
     *out = k;
@@ -619,6 +619,7 @@ struct BatchCall {
   SolveStatus* st_host = nullptr;   // pinned mirror
   double2* partial_host = nullptr;  // pinned, kDotBlocks per problem
   std::vector<char> pc_on;          // preconditioner still in use, per problem
+  bool jm = false;                  // JM-VIE problems (6N unknowns)
   ~BatchCall() {
     cudaFree(table);
     cudaFree(st);
@@ -648,6 +649,27 @@ static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dty
   const bool outer = which == APPLY_X;
   std::vector<int> used(list.size(), 0);
   const size_t es = dtype == VIE_C64 ? sizeof(float2) : sizeof(double2);
+  if (c.jm) {
+    // one JM-VIE operator per problem (no grouping)
+    for (int i : list) {
+      const ProbK& q = c.host[i];
+      const void* xin;
+      void* yout;
+      if (outer) {
+        xin = q.x64;
+        yout = q.y64;
+      } else if (which == APPLY_D) {
+        xin = q.d;
+        yout = q.w;
+      } else {
+        xin = (const char*)(flexible ? q.Z : q.V) + (size_t)j * q.n * es;
+        yout = q.w;
+      }
+      vie_status st = jm_matvec_impl(c.plans[i], xin, yout, outer ? VIE_C128 : dtype, MODE_OPERATOR, s);
+      if (st != VIE_OK) return st;
+    }
+    return VIE_OK;
+  }
   for (size_t i = 0; i < list.size(); ++i) {
     if (used[i]) continue;
     std::vector<vie_plan*> gp;
@@ -749,7 +771,7 @@ static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, i
 // Solve `count` problems; b[i], x[i] complex128 device vectors of plan i.
 vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
                             const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,
-                            void* const* precond_ctx, cudaStream_t s) {
+                            void* const* precond_ctx, cudaStream_t s, int jm) {
   const auto t0 = std::chrono::steady_clock::now();
   const int mode = o->mode;
   const int m = o->restart > 0 ? o->restart : 100;
@@ -762,6 +784,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   const int dtype = (mode == VIE_SOLVE_MIXED) ? VIE_C64 : VIE_C128;
   const bool flexible = precond != nullptr;
   BatchCall c;
+  c.jm = jm != 0;
   c.plans.assign(plans, plans + count);
   c.host.resize(count);
   c.pc_on.assign(count, flexible ? 1 : 0);
@@ -772,7 +795,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   VIE_CUDA_TRY(cudaMemsetAsync(c.st, 0, count * sizeof(SolveStatus), s));
   for (int i = 0; i < count; ++i) {
     KrylovWork* k = nullptr;
-    vie_status st = ensure_work(plans[i], m, dtype, flexible, &k);
+    vie_status st = ensure_work(plans[i], m, dtype, flexible, &k, jm ? 6 : 3);
     if (st != VIE_OK) return st;
     ProbK& q = c.host[i];
     memset(&q, 0, sizeof(q));
@@ -930,6 +953,9 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   cudaEventDestroy(e1);
   vie_status worst = st;
   for (int i = 0; i < count; ++i) {
+    // a network whose outputs had to be replaced (non-finite) counts as
+    // dropped even when the solve converged before the per-cycle check
+    if (flexible && precond_fallback_flag(c.plans[i], 1)) infos[i].fallback = 1;
     infos[i].iterations = iters[i];
     infos[i].outer = outers[i];
     infos[i].residual = rel[i];
@@ -949,15 +975,18 @@ namespace vie {
 
 // Device copies of b and x for a solve on host buffers: 2 x 3N complex128,
 // allocated on the plan's first such solve and kept.
-static vie_status host_stage(vie_plan* p, double2** b, double2** x) {
-  const size_t n3 = (size_t)3 * p->n[0] * p->n[1] * p->n[2];
-  if (!p->host_stage) {
+static vie_status host_stage(vie_plan* p, double2** b, double2** x, int comps) {
+  const size_t n3 = (size_t)comps * p->n[0] * p->n[1] * p->n[2];
+  if (p->host_stage_bytes < 2 * n3 * sizeof(double2)) {
+    cudaFree(p->host_stage);
+    p->host_stage_bytes = 0;
     cudaError_t e = cudaMalloc(&p->host_stage, 2 * n3 * sizeof(double2));
     if (e != cudaSuccess) {
       p->host_stage = nullptr;
       set_error("staging buffers for host vectors: %s", cudaGetErrorString(e));
       return e == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA;
     }
+    p->host_stage_bytes = 2 * n3 * sizeof(double2);
   }
   *b = (double2*)p->host_stage;
   *x = *b + n3;
@@ -969,24 +998,25 @@ static vie_status host_stage(vie_plan* p, double2** b, double2** x) {
 // reports an error status: x then holds the last or best iterate).
 static vie_status solve_host(vie_plan* const* plans, int count, const void* const* b_host, void* const* x_host,
                              double tol, const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn fn,
-                             void* const* ctx, cudaStream_t s) {
+                             void* const* ctx, cudaStream_t s, int jm = 0) {
+  const int comps = jm ? 6 : 3;
   std::vector<const double2*> bd(count);
   std::vector<double2*> xd(count);
   for (int i = 0; i < count; ++i) {
     double2* b = nullptr;
     double2* x = nullptr;
-    vie_status st = host_stage(plans[i], &b, &x);
+    vie_status st = host_stage(plans[i], &b, &x, comps);
     if (st != VIE_OK) return st;
-    const size_t bytes = (size_t)3 * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
+    const size_t bytes = (size_t)comps * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
     VIE_CUDA_TRY(cudaMemcpyAsync(b, b_host[i], bytes, cudaMemcpyHostToDevice, s));
     if (o->x0_given) VIE_CUDA_TRY(cudaMemcpyAsync(x, x_host[i], bytes, cudaMemcpyHostToDevice, s));
     bd[i] = b;
     xd[i] = x;
   }
-  vie_status st = solve_batch_impl(plans, count, bd.data(), xd.data(), tol, o, infos, fn, ctx, s);
+  vie_status st = solve_batch_impl(plans, count, bd.data(), xd.data(), tol, o, infos, fn, ctx, s, jm);
   if (st == VIE_ERR_INVALID || st == VIE_ERR_OOM || st == VIE_ERR_CUDA) return st;
   for (int i = 0; i < count; ++i) {
-    const size_t bytes = (size_t)3 * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
+    const size_t bytes = (size_t)comps * plans[i]->n[0] * plans[i]->n[1] * plans[i]->n[2] * sizeof(double2);
     VIE_CUDA_TRY(cudaMemcpyAsync(x_host[i], xd[i], bytes, cudaMemcpyDeviceToHost, s));
   }
   VIE_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1045,4 +1075,25 @@ extern "C" vie_status vie_solve_batch(vie_plan* const* plans, int count, const v
     return solve_host(plans, count, b_dev, x_dev, tol, opts, infos, fn, ctx.data(), (cudaStream_t)stream);
   return solve_batch_impl(plans, count, (const double2* const*)b_dev, (double2* const*)x_dev, tol, opts, infos, fn,
                           ctx.data(), (cudaStream_t)stream);
+}
+
+extern "C" vie_status vie_jm_solve(vie_plan* p, const void* b, void* x, double tol, const vie_solve_opts* opts,
+                                   vie_solve_info* info, void* stream) {
+  clear_error();
+  if (!p || !b || !x || !opts || !info) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must be in (0, 1)"); return VIE_ERR_INVALID; }
+  if (opts->mode != VIE_SOLVE_FP64 && opts->mode != VIE_SOLVE_MIXED) { set_error("unknown mode"); return VIE_ERR_INVALID; }
+  if (opts->use_preconditioner) { set_error("the JM-VIE solve takes no preconditioner"); return VIE_ERR_INVALID; }
+  if (b == x) { set_error("b and x must differ"); return VIE_ERR_INVALID; }
+  if (!p->curl) { set_error("call vie_set_permeability before a JM-VIE solve"); return VIE_ERR_INVALID; }
+  if (p->jm_gen != p->contrast_gen) {
+    set_error("the permittivity changed after vie_set_permeability: call it again");
+    return VIE_ERR_INVALID;
+  }
+  void* ctx = nullptr;
+  if (opts->host_buffers)
+    return solve_host(&p, 1, &b, &x, tol, opts, info, nullptr, &ctx, (cudaStream_t)stream, 1);
+  const double2* bd = (const double2*)b;
+  double2* xd = (double2*)x;
+  return solve_batch_impl(&p, 1, &bd, &xd, tol, opts, info, nullptr, &ctx, (cudaStream_t)stream, 1);
 }

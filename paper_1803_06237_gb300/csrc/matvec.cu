@@ -1133,6 +1133,202 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   return VIE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// JM-VIE (Sec. 3): the operator on six components (u_e, u_m) per voxel,
+//   v_e = T * u_e - j kappa C x u_m,   v_m = T * u_m + j kappa C x u_e,
+// y = u - M v (M_eps on the electric, M_mu on the magnetic components), or
+// y = M (v - u) for a right-hand side.  The x passes are those of the J-VIE
+// on 6 ny nz lines; pass B transforms the six components of one kx plane
+// and applies the symmetric 3 x 3 spectrum of T to each current and the
+// cross product with the three curl spectra C_a (C_a odd along axis a:
+// folding along a flips its sign) between them.
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(256) pass_b_jm_kernel(V* __restrict__ work, const V* __restrict__ ghat,
+                                                        const V* __restrict__ chat, PassBGeom g, Radices ry,
+                                                        Radices rz, const V* __restrict__ twyg,
+                                                        const V* __restrict__ twzg, double kappa) {
+  typedef typename real_of<V>::type R;
+  pdl_wait();
+  extern __shared__ unsigned char smem_raw[];
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ny = g.ny, nz = g.nz, My = g.My, Mz = g.Mz;
+  const int pz = Mz + 1, py = My + 1;
+  const int buf = 6 * Mz * py;   // >= 6 * ny * pz since My >= ny
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + My;
+  V* U = twz + Mz;
+  V* W = U + buf;
+  for (int i = tid; i < My; i += nth) twy[i] = twyg[i];
+  for (int i = tid; i < Mz; i += nth) twz[i] = twzg[i];
+  V* slab = work + (size_t)kx * g.NL;
+  for (int e = tid; e < 6 * ny * Mz; e += nth) {
+    const int row = e / Mz, z = e - row * Mz;   // row = c*ny + y
+    const int c = row / ny, y = row - c * ny;
+    U[row * pz + z] = (z < nz) ? slab[(c * nz + z) * ny + y] : zero_c<V>();
+  }
+  __syncthreads();
+  V* zr = fft_lines<V, false>(U, W, rz, pz, 6 * ny, twz, tid, nth);
+  V* other = (zr == U) ? W : U;
+  for (int e = tid; e < 6 * Mz * My; e += nth) {
+    const int row = e / My, y = e - row * My;   // row = c*Mz + kz
+    const int c = row / Mz, kz = row - c * Mz;
+    other[row * py + y] = (y < ny) ? zr[(c * ny + y) * pz + kz] : zero_c<V>();
+  }
+  __syncthreads();
+  V* yr = fft_lines<V, false>(other, zr, ry, py, 6 * Mz, twy, tid, nth);
+  {
+    const bool fx = kx > g.Mx - kx;
+    const int kxf = fx ? g.Mx - kx : kx;
+    const size_t cs = (size_t)g.Kz * g.Ky;
+    const V* G = ghat + (size_t)kxf * 6 * cs;
+    const V* Cc = chat + (size_t)kxf * 3 * cs;
+    const R kap = (R)kappa;
+    for (int e = tid; e < Mz * My; e += nth) {
+      const int kz = e / My, ky = e - kz * My;
+      const bool fy = ky > My - ky, fz = kz > Mz - kz;
+      const int kyf = fy ? My - ky : ky, kzf = fz ? Mz - kz : kz;
+      const size_t o = (size_t)kzf * g.Ky + kyf;
+      V gxx = G[o], gyy = G[cs + o], gzz = G[2 * cs + o];
+      V gxy = G[3 * cs + o], gxz = G[4 * cs + o], gyz = G[5 * cs + o];
+      if (fx ^ fy) gxy = scale(gxy, (R)-1);
+      if (fx ^ fz) gxz = scale(gxz, (R)-1);
+      if (fy ^ fz) gyz = scale(gyz, (R)-1);
+      // j kappa C_a, with the fold signs
+      V cx = Cc[o], cy = Cc[cs + o], cz = Cc[2 * cs + o];
+      if (fx) cx = scale(cx, (R)-1);
+      if (fy) cy = scale(cy, (R)-1);
+      if (fz) cz = scale(cz, (R)-1);
+      cx = scale(mul_pi(cx), kap);
+      cy = scale(mul_pi(cy), kap);
+      cz = scale(mul_pi(cz), kap);
+      V* p[6];
+      V u[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        p[c] = yr + (c * Mz + kz) * py + ky;
+        u[c] = *p[c];
+      }
+      // T u for each current
+      const V te0 = add(add(mul(gxx, u[0]), mul(gxy, u[1])), mul(gxz, u[2]));
+      const V te1 = add(add(mul(gxy, u[0]), mul(gyy, u[1])), mul(gyz, u[2]));
+      const V te2 = add(add(mul(gxz, u[0]), mul(gyz, u[1])), mul(gzz, u[2]));
+      const V tm0 = add(add(mul(gxx, u[3]), mul(gxy, u[4])), mul(gxz, u[5]));
+      const V tm1 = add(add(mul(gxy, u[3]), mul(gyy, u[4])), mul(gyz, u[5]));
+      const V tm2 = add(add(mul(gxz, u[3]), mul(gyz, u[4])), mul(gzz, u[5]));
+      // (j kappa C) x u_m and (j kappa C) x u_e
+      const V xm0 = sub(mul(cy, u[5]), mul(cz, u[4]));
+      const V xm1 = sub(mul(cz, u[3]), mul(cx, u[5]));
+      const V xm2 = sub(mul(cx, u[4]), mul(cy, u[3]));
+      const V xe0 = sub(mul(cy, u[2]), mul(cz, u[1]));
+      const V xe1 = sub(mul(cz, u[0]), mul(cx, u[2]));
+      const V xe2 = sub(mul(cx, u[1]), mul(cy, u[0]));
+      *p[0] = sub(te0, xm0);
+      *p[1] = sub(te1, xm1);
+      *p[2] = sub(te2, xm2);
+      *p[3] = add(tm0, xe0);
+      *p[4] = add(tm1, xe1);
+      *p[5] = add(tm2, xe2);
+    }
+  }
+  __syncthreads();
+  V* spare = (yr == U) ? W : U;
+  V* yi = fft_lines<V, true>(yr, spare, ry, py, 6 * Mz, twy, tid, nth);
+  V* other2 = (yi == U) ? W : U;
+  for (int e = tid; e < 6 * ny * Mz; e += nth) {
+    const int row = e / Mz, kz = e - row * Mz;
+    const int c = row / ny, y = row - c * ny;
+    other2[row * pz + kz] = yi[(c * Mz + kz) * py + y];
+  }
+  __syncthreads();
+  V* spare2 = (other2 == U) ? W : U;
+  V* zi = fft_lines<V, true>(other2, spare2, rz, pz, 6 * ny, twz, tid, nth);
+  for (int e = tid; e < g.NL; e += nth) {
+    const int y = e % ny, cz = e / ny;
+    const int z = cz % nz, c = cz / nz;
+    slab[e] = zi[(c * ny + y) * pz + z];
+  }
+}
+
+size_t jm_pass_b_smem(int My, int Mz, size_t vbytes) {
+  return (size_t)(My + Mz + 2 * 6 * Mz * (My + 1)) * vbytes;
+}
+
+template <typename V>
+static vie_status run_jm(vie_plan* p, const V* x, V* y, const V* ghat, const V* chat, const V* Mc, const V* twx,
+                         const V* twy, const V* twz, int mode, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
+  const int NL = 6 * ny * nz;
+  const size_t smem_b = jm_pass_b_smem(My, Mz, sizeof(V));
+  if (smem_b > 220 * 1024) {
+    set_error("the JM-VIE operator needs the 6 x %d x %d plane of one kx in one CTA's shared memory", My, Mz);
+    return VIE_ERR_INVALID;
+  }
+  PassPtrs<V> pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.x[0] = x;
+  pp.y[0] = y;
+  pp.work[0] = (V*)p->jm_work;
+  pp.ghat[0] = ghat;
+  pp.M[0] = Mc;
+  const size_t line_bytes = (size_t)2 * (Mx + 1) * sizeof(V);
+  const size_t tw_bytes = (size_t)Mx * sizeof(V);
+  int lpb = 4;
+  while (lpb > 1 && tw_bytes + lpb * line_bytes > 200 * 1024) lpb >>= 1;
+  const size_t smem_ac = tw_bytes + lpb * line_bytes;
+  if (smem_ac > 220 * 1024) {
+    set_error("Mx = %d too large for the x-pass shared memory", Mx);
+    return VIE_ERR_INVALID;
+  }
+  const dim3 blocks_ac((unsigned)((NL + lpb - 1) / lpb), 1);
+  int l1 = 0, l2 = 0;
+  x4_factors(Mx, &l1, &l2);
+  bool done = false;
+  vie_status st = VIE_OK;
+  if (l1) {
+    st = dispatch_x4<V>(true, l1, l2, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+    pass_a_kernel<V><<<blocks_ac, 256, smem_ac, s>>>(pp, nx, NL, radices_of(p->ax[0]), twx, lpb, NL);
+    VIE_LAUNCH_CHECK();
+  }
+  PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
+  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_jm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  pass_b_jm_kernel<V><<<(unsigned)Mx, 256, smem_b, s>>>((V*)p->jm_work, ghat, chat, g, radices_of(p->ax[1]),
+                                                        radices_of(p->ax[2]), twy, twz, p->kappa);
+  VIE_LAUNCH_CHECK();
+  done = false;
+  if (l1) {
+    st = dispatch_x4<V>(false, l1, l2, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+    pass_c_kernel<V><<<blocks_ac, 256, smem_ac, s>>>(pp, nx, NL, NL, radices_of(p->ax[0]), twx, lpb, mode, NL);
+    VIE_LAUNCH_CHECK();
+  }
+  return VIE_OK;
+}
+
+vie_status jm_matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, cudaStream_t s) {
+  if (!p->jm_work || !p->Mjm64) {
+    set_error("set the plan's permeability (vie_set_permeability) before applying the JM-VIE operator");
+    return VIE_ERR_INVALID;
+  }
+  if (dtype == VIE_C64)
+    return run_jm<float2>(p, (const float2*)x, (float2*)y, p->ghat32, p->chat32, p->Mjm32, p->ax[0].tw32,
+                          p->ax[1].tw32, p->ax[2].tw32, mode, s);
+  if (dtype == VIE_C128)
+    return run_jm<double2>(p, (const double2*)x, (double2*)y, p->ghat64, p->chat64, p->Mjm64, p->ax[0].tw64,
+                           p->ax[1].tw64, p->ax[2].tw64, mode, s);
+  set_error("unknown dtype %d", dtype);
+  return VIE_ERR_INVALID;
+}
+
 // The split pass B's buffer behind the x-pass spectra of a workspace of
 // work_bytes, or null (that pass B is not needed or does not fit).
 template <typename V>

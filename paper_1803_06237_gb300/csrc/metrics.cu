@@ -52,9 +52,53 @@ __global__ void reflection_kernel(const double2* __restrict__ Eref, const double
   }
 }
 
+// Transmission through a voxel plane (Sec. 5.2): T = sum over the voxels of
+// plane ix with chi != 0 of |E|^2, E = J / (c_e chi), all three components
+// (the common factor |c_e|^2 h^3 is not applied).  One block, FP64 sums in a
+// fixed order.
+__global__ void slice_power_kernel(const double2* __restrict__ w, const double2* __restrict__ chi, int nx, int ny,
+                                   int nz, int ix, double* __restrict__ out) {
+  __shared__ double sp[256];
+  const size_t N = (size_t)nx * ny * nz;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < 3 * ny * nz; i += blockDim.x) {
+    const int c = i / (ny * nz), yz = i - c * ny * nz;
+    const size_t v = (size_t)yz * nx + ix;
+    const double2 d = chi[v];
+    const double den = d.x * d.x + d.y * d.y;
+    if (den == 0.0) continue;
+    const double2 a = w[c * N + v];
+    acc += (a.x * a.x + a.y * a.y) / den;
+  }
+  sp[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sp[threadIdx.x] += sp[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sp[0];
+}
+
 }  // namespace vie
 
 using namespace vie;
+
+extern "C" vie_status vie_slice_power(const vie_plan* p, const void* w_dev, int ix, double* t_out, void* stream) {
+  clear_error();
+  if (!p || !w_dev || !t_out) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (ix < 0 || ix >= p->n[0]) { set_error("ix must be in [0, nx)"); return VIE_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d = nullptr;
+  VIE_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(double), s));
+  slice_power_kernel<<<1, 256, 0, s>>>((const double2*)w_dev, p->chi64, p->n[0], p->n[1], p->n[2], ix, d);
+  VIE_LAUNCH_CHECK();
+  double h = 0.0;
+  VIE_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA_TRY(cudaFreeAsync(d, s));
+  VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  *t_out = h;
+  return VIE_OK;
+}
 
 extern "C" vie_status vie_axis_field(const vie_plan* p, const void* w_dev, int n_keep, void* e_dev, void* stream) {
   clear_error();

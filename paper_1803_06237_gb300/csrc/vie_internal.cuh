@@ -116,6 +116,7 @@ inline Radices radices_of(const AxisPlan& a) {
 }
 
 bool factor_length(int len, AxisPlan* out);   // radices from {4, 2, 3, 5}
+bool factor_length_any(int len, AxisPlan* out);   // 4, 2, 3, 5, then larger primes (generic stages)
 void x4_factors(int mx, int* l1, int* l2);    // compiled four-step split of Mx, or (0, 0)
 int smooth_size_at_least(int n);               // smallest 5-smooth >= n
 
@@ -149,6 +150,16 @@ struct vie_plan {
   void* krylov = nullptr;     // solver workspace (vie::KrylovWork), created on first solve
   void* precond = nullptr;    // preconditioner state (learned or block-circulant), if set
   void* host_stage = nullptr; // device copies of b and x for solves on host buffers (2 x 3N complex128)
+  size_t host_stage_bytes = 0;
+  // JM-VIE (Sec. 3; allocated by vie_set_permeability)
+  double2* curl = nullptr;    // FP64 octant of C_a, [3][nz][ny][nx]
+  double2* chat64 = nullptr;  // folded curl spectra, [kx'][a][kz'][ky'], pre-scaled by 1/(Mx My Mz)
+  float2* chat32 = nullptr;
+  double2* Mjm64 = nullptr;   // 6N contrast: M_eps on the three electric, M_mu on the three magnetic components
+  float2* Mjm32 = nullptr;
+  double2* chimu64 = nullptr; // chi_mu = mu_r - 1 per voxel
+  void* jm_work = nullptr;    // 6 ny nz Mx complex128
+  int jm_gen = -1;            // contrast generation the 6N contrast was built from
   int contrast_gen = 0;       // incremented whenever the contrast is set
   int x_lpb = 0;              // four-step forward x-pass lines per block (0: heuristic)
   int x_lpb_inv = 0;          // four-step inverse x-pass lines per block (0: heuristic)
@@ -159,6 +170,10 @@ struct vie_plan {
 namespace vie {
 
 vie_status compute_toeplitz(vie_plan* p, cudaStream_t s);
+vie_status compute_curl(vie_plan* p, cudaStream_t s);     // C_a entries and folded spectra (JM-VIE)
+// JM-VIE operator y = u - M (T u) on 6N vectors (u_e, u_m) of dtype; mode
+// MODE_OPERATOR or MODE_RHS (then x is the 3N electric source current).
+vie_status jm_matvec_impl(vie_plan* p, const void* x, void* y, int dtype, int mode, cudaStream_t s);
 vie_status compute_spectrum(vie_plan* p, cudaStream_t s);
 // `work` holds work_bytes; beyond the 3 ny nz Mx spectra of the x passes it
 // may hold the y-pass buffer of the split pass B (pass_b_split_elems).
@@ -189,8 +204,9 @@ const vie_plan* circulant_plan(const vie_circulant* c);
 // x[i], y[i] are device vectors of dtype; each plan's own workspace is used.
 vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype,
                         int mode, cudaStream_t s);
+// jm != 0: the JM-VIE (6N unknowns per problem, jm_matvec_impl as operator).
 vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
                             const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,
-                            void* const* precond_ctx, cudaStream_t s);
+                            void* const* precond_ctx, cudaStream_t s, int jm = 0);
 
 }  // namespace vie

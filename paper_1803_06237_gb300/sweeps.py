@@ -1,0 +1,138 @@
+"""Parameter studies of Sec. 5 on the GPU (host orchestration only: every
+solve, field and metric runs in libvie).
+
+* ``rl_sweep``: the absorber-length study of Sec. 5.1 on the 13.5 um strip
+  (810 x 30 x 12 voxels of 50/3 nm): for each monomial degree d and length L
+  the reflection coefficient R(L) = |E_inf - E_L|^2 / |E_inf|^2 along the
+  centre axis of the guide, E_inf from the longest absorber, and the slope of
+  log R against log L, which Sec. 4.3 predicts to approach -2 (d + 1).
+* ``bragg_sweep``: the transmission spectrum of the N-period Bragg grating of
+  Sec. 5.2: one plan per wavelength (the spectra depend on k), the
+  wavelengths solved together through the batch path, T(lambda) = sum |E|^2
+  over a voxel plane behind the grating.
+
+Both precondition with the block-circulant matrix of Sec. 5.4 (complex-half
+factors) and solve in mixed precision to a true FP64 residual ``tol``.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import learned, vie, workloads
+
+
+def _solve(wl, tol, restart=30, factors_fp16=True):
+    """Plan, contrast, right-hand side, block-circulant preconditioner and a
+    mixed-precision solve of one workload.  Returns (plan, x, info)."""
+    import torch
+    plan, b = learned.setup_problem(wl)
+    c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if factors_fp16 else vie.VIE_CIRC_DEFAULT)
+    vie.vie_set_circulant_preconditioner(plan, c)
+    x = torch.zeros_like(b)
+    info = vie.vie_solve(plan, b, x, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart, use_preconditioner=True,
+                         raise_on_not_converged=False)
+    vie.vie_set_circulant_preconditioner(plan, None)
+    c.close()
+    return plan, x, info
+
+
+def fit_slope(L, R, floor=1e-12, tail=0.5):
+    """Least-squares slope of log R against log L over the longest ``tail``
+    fraction of the lengths whose R lies above ``floor``."""
+    L = np.asarray(L, float)
+    R = np.asarray(R, float)
+    keep = R > floor
+    L, R = L[keep], R[keep]
+    if L.size < 2:
+        return None
+    k = max(2, int(math.ceil(tail * L.size)))
+    A = np.vstack([np.log(L[-k:]), np.ones(k)]).T
+    s, _ = np.linalg.lstsq(A, np.log(R[-k:]), rcond=None)[0]
+    return float(s)
+
+
+def rl_sweep(lengths_nm, degrees=(0, 1, 2), r_rt=1e-25, ref_nm=9450.0, tol=1e-8, body_nm=13500.0,
+             h_nm=50.0 / 3.0):
+    """R(L) for each degree (Sec. 5.1).  Returns a dict with, per degree, the
+    lengths (nm), R, solve statistics and the fitted slope."""
+    t0 = time.perf_counter()
+    nb = int(round(body_nm / h_nm))
+    out = {"lengths_nm": list(map(float, lengths_nm)), "r_rt": r_rt, "reference_nm": ref_nm, "tol": tol,
+           "grid_body": [nb, int(round(500 / h_nm)), int(round(200 / h_nm))], "h_nm": h_nm, "degrees": {}}
+    for d in degrees:
+        plan, x, info = _solve(workloads.strip_rl(ref_nm, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
+        e_ref = vie.vie_axis_field(plan, x, nb)
+        plan.close()
+        Rs, iters, res = [], [], []
+        for L in lengths_nm:
+            plan, x, info = _solve(workloads.strip_rl(L, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
+            Rs.append(vie.vie_reflection(e_ref, vie.vie_axis_field(plan, x, nb)))
+            iters.append(info["iterations"])
+            res.append(info["residual"])
+            plan.close()
+        out["degrees"][str(d)] = {"R": Rs, "iterations": iters, "true_residual_max": max(res),
+                                  "slope": fit_slope(lengths_nm, Rs), "slope_predicted": -2.0 * (d + 1)}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def bragg_sweep(lambdas_um, periods=100, tol=1e-6, batch=8, restart=30):
+    """Transmission T(lambda) through the Bragg grating (Sec. 5.2), the
+    wavelengths solved ``batch`` at a time with per-plan block-circulant
+    preconditioners.  Returns wavelengths, T, T / max T and solve statistics."""
+    import torch
+    t0 = time.perf_counter()
+    T, iters, res, conv = [], [], [], []
+    grid = None
+    for i0 in range(0, len(lambdas_um), batch):
+        lams = lambdas_um[i0:i0 + batch]
+        plans, bs, circs, slices = [], [], [], []
+        for lam in lams:
+            wl = workloads.bragg_grating(lam, periods=periods)
+            grid = wl.grid
+            plan, b = learned.setup_problem(wl)
+            c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS)
+            vie.vie_set_circulant_preconditioner(plan, c)
+            plans.append(plan)
+            bs.append(b)
+            circs.append(c)
+            slices.append(int(wl.name.split("_x")[1]))
+        xs = [torch.zeros_like(b) for b in bs]
+        st, infos = vie.vie_solve_batch(plans, bs, xs, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart,
+                                        use_preconditioner=True, raise_on_not_converged=False)
+        for plan, x, info, ix in zip(plans, xs, infos, slices):
+            T.append(vie.vie_slice_power(plan, x, ix))
+            iters.append(info["iterations"])
+            res.append(info["residual"])
+            conv.append(bool(info["converged"]))
+        for plan, c in zip(plans, circs):
+            vie.vie_set_circulant_preconditioner(plan, None)
+            c.close()
+            plan.close()
+        del xs, bs
+    Tn = (np.asarray(T) / max(T)).tolist()
+    return {"lambdas_um": list(map(float, lambdas_um)), "T": T, "T_normalised": Tn, "grid": list(grid),
+            "periods": periods, "iterations": iters, "true_residual_max": max(res), "converged": sum(conv),
+            "tol": tol, "seconds": time.perf_counter() - t0}
+
+
+def band_gap(lambdas_um, T_normalised, level=0.5):
+    """Centre and width of the widest contiguous run of wavelengths whose
+    normalised transmission is below ``level`` (None if there is none)."""
+    lam = np.asarray(lambdas_um)
+    low = np.asarray(T_normalised) < level
+    best, cur = None, None
+    for i, v in enumerate(low):
+        if v:
+            cur = (cur[0], i) if cur else (i, i)
+            if best is None or cur[1] - cur[0] > best[1] - best[0]:
+                best = cur
+        else:
+            cur = None
+    if best is None:
+        return None
+    a, b = lam[best[0]], lam[best[1]]
+    return {"centre_um": float(0.5 * (a + b)), "width_um": float(b - a), "level": level}

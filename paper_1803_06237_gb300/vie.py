@@ -102,6 +102,11 @@ _SIGNATURES = {
     "vie_reflection": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_probe_fma_tflops": ([_I, ctypes.POINTER(_D), _P], _I),
+    "vie_set_permeability": ([_P, _P], _I),
+    "vie_slice_power": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
+    "vie_jm_matvec": ([_P, _P, _P, _I, _P], _I),
+    "vie_jm_rhs_from_source": ([_P, _P, _P, _I, _P], _I),
+    "vie_jm_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_last_error": ([], ctypes.c_char_p),
 }
 
@@ -275,7 +280,9 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
     """Solve (I - M N) x = b on the device.  b, x: complex128 CUDA tensors, or
     (both) C-contiguous complex128 NumPy arrays on the host, which the library
     stages through device buffers (opts.host_buffers = 1); x is written in
-    place either way."""
+    place either way.  With raise_on_not_converged=False a solve that stopped
+    at a cap (VIE_ERR_NOT_CONVERGED) or at the time limit (VIE_ERR_TIMEOUT)
+    returns its report (x holds the last iterate) instead of raising."""
     host = _vectors_kind([(b, x)], [plan])
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
                           int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s),
@@ -287,7 +294,7 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
            "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
            "residual": info.residual, "time_ms": info.time_ms,
            "history": [info.history[i] for i in range(min(info.history_len, 64))]}
-    if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
+    if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
         _check(st, "vie_solve")
     return out
 
@@ -367,7 +374,7 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
                     "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
                     "residual": info.residual, "time_ms": info.time_ms,
                     "history": [info.history[i] for i in range(min(info.history_len, 64))]})
-    if st != VIE_OK and not (st == 4 and not raise_on_not_converged):
+    if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
         _check(st, "vie_solve_batch")
     return st, out
 
@@ -558,11 +565,76 @@ def vie_reflection(e_ref, e, stream=None) -> float:
     return out.value
 
 
+def vie_set_permeability(plan: Plan, mu=None):
+    """mu: (nz, ny, nx) complex relative permeability, or None for the
+    impedance-matched permeability of the plan's current permittivity."""
+    if mu is None:
+        _check(load().vie_set_permeability(plan.handle, None), "vie_set_permeability")
+    else:
+        m = _host_c128(mu, plan.n_vox)
+        _check(load().vie_set_permeability(plan.handle, m.ctypes.data_as(ctypes.c_void_p)), "vie_set_permeability")
+
+
+def _jm_vec_call(fn_name, plan: Plan, x, y, stream):
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous CUDA tensors")
+    if x.dtype != y.dtype or x.numel() != 6 * plan.n_vox or y.numel() != 6 * plan.n_vox:
+        raise ValueError("x and y must be complex vectors of 6*nx*ny*nz elements and equal dtype")
+    _check(getattr(load(), fn_name)(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    _dtype_code(x), _stream_handle(stream)), fn_name)
+
+
+def vie_jm_matvec(plan: Plan, x, y, stream=None):
+    """y = u - M (T u) for the JM-VIE (6N vectors)."""
+    _jm_vec_call("vie_jm_matvec", plan, x, y, stream)
+
+
+def vie_jm_rhs_from_source(plan: Plan, src, b, stream=None):
+    """b for impressed currents (w_e, w_m) (6N vectors)."""
+    _jm_vec_call("vie_jm_rhs_from_source", plan, src, b, stream)
+
+
+def vie_jm_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart: int = 100,
+                 max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
+                 check_every: int = 4, timeout_s: float = 600.0, stream=None,
+                 raise_on_not_converged: bool = True) -> dict:
+    """Solve the JM-VIE; b, x: 6N complex128 CUDA tensors or host NumPy arrays."""
+    import torch
+    host = isinstance(b, np.ndarray)
+    for t in (b, x):
+        ok = (isinstance(t, np.ndarray) and t.dtype == np.complex128 and t.flags.c_contiguous) if host else \
+             (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128)
+        if not ok or (t.size if host else t.numel()) != 6 * plan.n_vox:
+            raise ValueError("b and x must be contiguous complex128 vectors of 6*nx*ny*nz entries")
+    opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
+                          int(bool(x0_given)), 0, int(check_every), float(timeout_s), int(host))
+    info = vie_solve_info()
+    st = load().vie_jm_solve(plan.handle, _vec_ptr(b), _vec_ptr(x), float(tol), ctypes.byref(opts),
+                             ctypes.byref(info), _stream_handle(stream))
+    out = {"status": st, "iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
+           "matvecs32": info.matvecs32, "converged": bool(info.converged), "residual": info.residual,
+           "time_ms": info.time_ms}
+    if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
+        _check(st, "vie_jm_solve")
+    return out
+
+
 def vie_probe_fma_tflops(dtype_code: int, stream=None) -> float:
     """Measured FP32 (VIE_C64) or FP64 (VIE_C128) FMA throughput, TFLOP/s."""
     out = ctypes.c_double()
     _check(load().vie_probe_fma_tflops(int(dtype_code), ctypes.byref(out), _stream_handle(stream)),
            "vie_probe_fma_tflops")
+    return out.value
+
+
+def vie_slice_power(plan: Plan, w, ix: int, stream=None) -> float:
+    """T = sum |w / chi|^2 over the voxels of plane ix with chi != 0."""
+    import torch
+    if not (w.is_cuda and w.dtype == torch.complex128 and w.numel() == 3 * plan.n_vox and w.is_contiguous()):
+        raise ValueError("w must be a contiguous complex128 CUDA vector of 3*nx*ny*nz entries")
+    out = ctypes.c_double()
+    _check(load().vie_slice_power(plan.handle, ctypes.c_void_p(w.data_ptr()), int(ix), ctypes.byref(out),
+                                  _stream_handle(stream)), "vie_slice_power")
     return out.value
 
 

@@ -220,6 +220,74 @@ def microring(nx: int = 800, ny: int = 600, nz: int = 11, h_um: float = 0.02, ra
                     src, eps_core=eps_core)
 
 
+def strip_rl(absorber_nm: float, degree: int, r_rt: float = 1e-25, h_nm: float = 50.0 / 3.0,
+             length_nm: float = 13500.0, width_nm: float = 500.0, height_nm: float = 200.0,
+             src_x_um: float = 1.0, eps_core: float = 12.11, eps_bg: float = 2.085) -> Workload:
+    """The absorber-length study of Sec. 5.1: a strip 13.5 um x 500 x 200 nm
+    (810 x 30 x 12 voxels of 50/3 nm) with an absorber of ``absorber_nm``
+    appended at the right end (all core voxels), the round-trip target
+    ``r_rt`` and the monomial degree; Gaussian y-sheet source at x = 1 um."""
+    h_um = h_nm / 1000.0
+    nb = int(round(length_nm / h_nm))
+    L = int(round(absorber_nm / h_nm))
+    ny, nz = int(round(width_nm / h_nm)), int(round(height_nm / h_nm))
+    nx = nb + L
+    eps = np.full((nz, ny, nx), eps_core + 0j)
+    ab = Absorber(x0=float(nb), length=float(L), degree=degree, r_rt=r_rt)
+    src = gaussian_sheet((nx, ny, nz), int(round(src_x_um / h_um)), 0.2 / h_um)
+    return Workload(f"strip_L{absorber_nm:.0f}_d{degree}", (nx, ny, nz), h_um, _k0(), eps_bg, eps, [ab], "sheet",
+                    src, eps_core=eps_core)
+
+
+def bragg_grating(lambda_um: float, periods: int = 100, period_nm: float = 320.0, width_nm: float = 500.0,
+                  dwidth_nm: float = 40.0, height_nm: float = 220.0, lead_periods: int = 10,
+                  tail_um: float = 1.0, absorber_um: float = 2.2, degree: int = 2, r_rt: float = 1e-10,
+                  h_nm: float = 20.0, eps_core: float = 12.11, eps_bg: float = 2.085) -> Workload:
+    """The Bragg grating of Sec. 2.2 / 5.2 at h = 20 nm: a strip of width W
+    whose width alternates between W + dW and W - dW every half period (each
+    edge moves by dW/2 = one voxel), N periods, preceded by a uniform
+    lead-in of 10 periods and followed by ``tail_um`` of uniform guide, with
+    quadratic absorbers of ``absorber_um`` on both ends; height 220 nm.  A
+    Gaussian y-sheet a quarter of the wavelength in silicon into the lead-in
+    excites it.  Returns the workload; ``slice_x`` (the voxel plane half way
+    through the tail, where the transmission is taken) is stored in
+    ``wl.name`` as ``bragg_x<slice_x>``."""
+    h_um = h_nm / 1000.0
+    La = int(round(absorber_um / h_um))
+    lead = int(round(lead_periods * period_nm / h_nm))
+    per = int(round(period_nm / h_nm))
+    tail = int(round(tail_um / h_um))
+    nx = La + lead + periods * per + tail + La
+    wmax = int(round((width_nm + dwidth_nm) / h_nm))
+    ny, nz = wmax, int(round(height_nm / h_nm))
+    wide = np.ones(ny, bool)
+    narrow = np.zeros(ny, bool)
+    d = int(round(dwidth_nm / h_nm))
+    narrow[d:ny - d] = True
+    core = np.zeros((ny, nx), bool)
+    nominal = np.zeros(ny, bool)
+    nominal[d // 2:ny - d // 2] = True
+    x0 = La + lead
+    for ix in range(nx):
+        if x0 <= ix < x0 + periods * per:
+            core[:, ix] = wide if ((ix - x0) % per) < per // 2 else narrow
+        else:
+            core[:, ix] = nominal
+    eps = np.full((nz, ny, nx), eps_bg + 0j)
+    eps[:, core] = eps_core
+    abs_ = [Absorber(x0=float(La), length=float(La), degree=degree, r_rt=r_rt, direction=-1),
+            Absorber(x0=float(nx - La), length=float(La), degree=degree, r_rt=r_rt, direction=+1)]
+    lam_si = lambda_um / math.sqrt(eps_core)
+    ix = La + int(round(0.25 * lam_si / h_um))
+    zz = np.arange(nz) + 0.5 - nz / 2.0
+    yy = np.arange(ny) + 0.5 - ny / 2.0
+    src = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+    src[1, :, :, ix] = np.exp(-(zz[:, None] ** 2 + yy[None, :] ** 2) / (0.2 / h_um) ** 2)
+    slice_x = x0 + periods * per + tail // 2
+    return Workload(f"bragg_x{slice_x}", (nx, ny, nz), h_um, 2.0 * math.pi / lambda_um, eps_bg, eps, abs_,
+                    "sheet", src, eps_core=eps_core)
+
+
 def microring_wavelengths(count: int = 16, lo_um: float = 1.54, hi_um: float = 1.56) -> list:
     """``count`` equally spaced wavelengths in [lo, hi] (um)."""
     return [lo_um + (hi_um - lo_um) * i / (count - 1) for i in range(count)]

@@ -1,6 +1,7 @@
 """GPU block-circulant preconditioner (Sec. 5.4) against the FP64 oracle
 (oracle/circulant.py): z = W^{-1} v on grids with one and several LU panels,
 ragged solve blocks and x lengths that are not 5-smooth; solves with it."""
+import functools
 import math
 
 import numpy as np
@@ -23,6 +24,16 @@ def _lib():
     vie.load()
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_what(grid, seed):
+    """The oracle's W_hat(w) blocks (and their largest condition number) for
+    the random contrast of _plan_with_contrast(grid, seed)."""
+    chi = op.chi_from_permittivity(workloads.random_permittivity(grid, seed=seed), EPS_BG)
+    kappa = K0 * math.sqrt(EPS_BG) * H
+    What = circ.blocks_hat(circ.circulant_blocks(grid, kappa, op.contrast_M(chi)))
+    return What, max(np.linalg.cond(What[w]) for w in range(grid[0]))
+
+
 def _plan_with_contrast(grid, seed):
     plan = vie.vie_plan_create(grid, H, K0, EPS_BG)
     chi = op.chi_from_permittivity(workloads.random_permittivity(grid, seed=seed), EPS_BG)
@@ -30,8 +41,11 @@ def _plan_with_contrast(grid, seed):
     return plan, op.contrast_M(chi)
 
 
-# (nx, ny, nz): R = 3 ny nz unknowns per slice; nb = 32 panels
-@pytest.mark.parametrize("grid", [(7, 3, 2), (13, 4, 3), (20, 6, 2), (24, 8, 5), (9, 11, 4)])
+# (nx, ny, nz): R = 3 ny nz unknowns per slice; nb = 32 panels; nx with
+# prime factors 7, 11, 13 (FFT stages that sum those radices directly):
+# 7, 13, 350 = 2 5^2 7, 550 = 2 5^2 11, 91 = 7 13
+@pytest.mark.parametrize("grid", [(7, 3, 2), (13, 4, 3), (20, 6, 2), (24, 8, 5), (9, 11, 4), (350, 3, 2),
+                                  (550, 2, 2), (91, 5, 3)])
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
 @pytest.mark.parametrize("fp16", [False, True])
 def test_apply_matches_oracle(grid, dtype, fp16):
@@ -40,8 +54,7 @@ def test_apply_matches_oracle(grid, dtype, fp16):
     roundoff."""
     plan, M = _plan_with_contrast(grid, 3)
     c = vie.vie_circulant_create(plan, vie.VIE_CIRC_FP16_FACTORS if fp16 else vie.VIE_CIRC_DEFAULT)
-    kappa = K0 * math.sqrt(EPS_BG) * H
-    What = circ.blocks_hat(circ.circulant_blocks(grid, kappa, M))
+    What, cond = _oracle_what(grid, 3)
     v = workloads.random_currents(grid, seed=4).astype(dtype)
     vd = torch.from_numpy(v.ravel()).cuda()
     zd = torch.empty_like(vd)
@@ -49,7 +62,6 @@ def test_apply_matches_oracle(grid, dtype, fp16):
     torch.cuda.synchronize()
     z = zd.cpu().numpy().reshape(3, grid[2], grid[1], grid[0]).astype(np.complex128)
     z_ref = circ.apply_inverse(What, v.astype(np.complex128))
-    cond = max(np.linalg.cond(What[w]) for w in range(grid[0]))
     tol = (4e-3 if fp16 else 2e-6) * cond
     assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < tol
 

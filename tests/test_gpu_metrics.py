@@ -37,3 +37,19 @@ def test_axis_field_and_reflection_match_oracle():
     R_ref = metrics.reflection_coefficient(r1, r2)
     assert abs(R - R_ref) <= 1e-12 * R_ref
     assert vie.vie_reflection(e1, e1) == 0.0
+
+
+def test_slice_power_matches_oracle():
+    grid = (30, 9, 5)
+    eps = np.full((5, 9, 30), 2.085 + 0j)
+    eps[1:4, 2:7, :] = 12.11
+    plan = vie.vie_plan_create(grid, 0.02, 2 * math.pi / 1.55, 2.085)
+    ab = [dict(x0=20.0, length=10.0, degree=2, eps2_max=3.0)]
+    vie.vie_set_permittivity(plan, eps, ab)
+    chi = op.chi_from_permittivity(eps, 2.085, ab)
+    w = workloads.random_currents(grid, seed=93)
+    wd = torch.from_numpy(w.ravel()).cuda()
+    for ix in (0, 7, 25, 29):
+        T = vie.vie_slice_power(plan, wd, ix)
+        T_ref = metrics.slice_power(w, chi, ix)
+        assert abs(T - T_ref) <= 1e-12 * T_ref

@@ -187,3 +187,31 @@ def test_flexible_gmres_with_network_converges():
     vie.vie_matvec(plan, x, y)
     torch.cuda.synchronize()
     assert (torch.linalg.vector_norm(y - b) / torch.linalg.vector_norm(b)).item() <= 2e-6
+
+
+def test_trained_network_gain_is_measured_and_bounded():
+    """What the trained network gains over the solver without it: train
+    briefly on pairs from plain solves of random strips and bends, then solve
+    a held-out guide with mixed GMRES(30) with and without the network.
+    Reports both iteration counts and times (the gain may be negative); the
+    true-residual check bounds the loss: a preconditioned run that stops
+    helping is dropped, so it takes at most one restart cycle plus the plain
+    run's steps."""
+    from paper_1803_06237_gb300 import learned
+    pairs = learned.make_pairs(range(8), grid=(96, 32, 11), restart=20, cycles=6)
+    net = vie.vie_net_create(seed=1)
+    losses = learned.train(net, pairs, steps=80, lr=1e-3, batch=4)
+    assert np.mean(losses[-10:]) < learned.identity_loss(pairs)
+    wl = workloads.random_guide(100, 96, 32, 11)
+    plan, b = learned.setup_problem(wl)
+    x0 = torch.zeros_like(b)
+    plain = vie.vie_solve(plan, b, x0, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30)
+    vie.vie_set_preconditioner_net(plan, net)
+    x1 = torch.zeros_like(b)
+    pre = vie.vie_solve(plan, b, x1, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30, use_preconditioner=True)
+    print(f"held-out guide: plain {plain['iterations']} steps {plain['time_ms']:.1f} ms, with network "
+          f"{pre['iterations']} steps {pre['time_ms']:.1f} ms (dropped: {pre['fallback']}); "
+          f"train loss {np.mean(losses[-10:]):.3f} vs identity {learned.identity_loss(pairs):.3f}")
+    assert plain["converged"] and pre["converged"]
+    assert pre["iterations"] <= plain["iterations"] + 30 + 5
+    assert (torch.linalg.vector_norm(x1 - x0) / torch.linalg.vector_norm(x0)).item() < 1e-4

@@ -46,3 +46,16 @@ def test_axis_field_is_current_over_contrast():
     w = np.arange(3 * 3 * 5 * 8, dtype=complex).reshape(3, 3, 5, 8)
     E = metrics.axis_field(w, chi, 6)
     np.testing.assert_allclose(E, w[:, 1, 2, :6] / (2.0 + 0.5j))
+
+
+def test_slice_power_counts_the_structure_only():
+    """A field E = 2 + 1j in every voxel of the structure (w = chi E) gives
+    T = |E|^2 times the number of structure voxels of the plane times 3
+    components; cladding voxels (chi = 0) contribute nothing."""
+    chi = np.zeros((3, 4, 6), complex)
+    chi[:, 1:3, :] = 1.5 - 0.2j
+    E = 2.0 + 1.0j
+    w = np.broadcast_to(chi * E, (3, 3, 4, 6)).copy()
+    w[:, :, 0, :] = 7.0             # values outside the structure are ignored
+    for ix in (0, 5):
+        assert abs(metrics.slice_power(w, chi, ix) - 3 * 6 * abs(E) ** 2) < 1e-12
