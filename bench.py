@@ -436,7 +436,8 @@ def _timed_solve(plan, b, mode, restart, use_pc, keep=None):
     wall = (time.perf_counter() - t) * 1e3
     return {"ms": wall, "device_ms": info["time_ms"], "iterations": info["iterations"], "cycles": info["outer"],
             "matvecs_c128": info["matvecs64"], "matvecs_c64": info["matvecs32"], "converged": info["converged"],
-            "true_residual": info["residual"], "preconditioner_dropped": info["fallback"], "restart": restart}
+            "true_residual": info["residual"], "preconditioner_dropped": info["fallback"], "restart": restart,
+            "graph_cycles": info["graph_cycles"], "reorth_steps": info["reorth_steps"]}
 
 
 def microring_section(args, fp32_peak, reps=40, reps64=8):
@@ -849,7 +850,8 @@ def profile_solve(iters: int):
         x = torch.zeros_like(b)
         info = vie.vie_solve(plan, b, x, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30, max_iters=iters,
                              raise_on_not_converged=False)
-    print(json.dumps({"profile_solve": iters, "iterations": info["iterations"], "time_ms": info["time_ms"]}))
+    print(json.dumps({"profile_solve": iters, "iterations": info["iterations"], "time_ms": info["time_ms"],
+                      "graph_cycles": info["graph_cycles"], "reorth_steps": info["reorth_steps"]}))
 
 
 def profile_net(reps: int):

@@ -198,6 +198,10 @@ typedef struct {
   double time_ms;         /* device time of the solve */
   int history_len;        /* entries used in history */
   double history[64];     /* true relative residual at the start of each cycle */
+  int graph_cycles;       /* cycles run as one CUDA graph launch (the steps'
+                             control flow on the device); the others ran from
+                             the host loop */
+  int reorth_steps;       /* Arnoldi steps that took the second Gram-Schmidt pass */
 } vie_solve_info;
 
 /* Solve (I - M N) x = b on the device (the paper's system of Sec. 3.1,

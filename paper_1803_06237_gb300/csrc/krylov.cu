@@ -2,8 +2,10 @@
 // arXiv:1803.06237; the paper solves it with GMRES at tolerance 1e-8, Sec. 5),
 // for one problem or a batch of problems of uneven sizes.
 //
-// * Arnoldi with classical Gram-Schmidt applied twice (CGS2) in three fused
-//   sweeps over the basis.  Products and each thread's short partial sums use
+// * Arnoldi with classical Gram-Schmidt and a second pass when the first
+//   one lost too much of the vector (the Daniel-Gragg-Kaufman-Stewart
+//   criterion ||w'|| < ||w|| / sqrt 2, decided on the device; the second pass
+//   then runs as in CGS2, otherwise its kernels return at once).  Products and each thread's short partial sums use
 //   the vectors' precision (FP32 for complex64: this GPU's FP64 rate is a
 //   small fraction of its FP32 rate); every sum across threads and blocks is
 //   FP64, in a fixed order.  The Hessenberg matrix, Givens rotations and the
@@ -45,6 +47,8 @@ struct SolveStatus {
   double target;     // absolute residual target of the cycle
   double resid;      // |g_{j+1}| (current residual estimate)
   double inv_h;      // 1 / h_{j+1,j}
+  int reorth;        // 1: the current step needs the second Gram-Schmidt pass
+  int reorth_count;  // steps of this cycle that took the second pass
 };
 
 // Everything a kernel needs about one problem.
@@ -181,9 +185,9 @@ __device__ __forceinline__ void store_group(A (&acc)[kGroup], int i0, int nv, do
 // grid (chunks, groups of kGroup vectors, problems): every block handles one
 // chunk of elements for one group of vectors.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict__ P, int nv) {
+__global__ void __launch_bounds__(kThreads) dots_kernel(const ProbK* __restrict__ P, int nv, int pass) {
   const ProbK& q = P[blockIdx.z];
-  if (!q.st->active) return;
+  if (!q.st->active || (pass == 1 && !q.st->reorth)) return;
   const int i0 = blockIdx.y * kGroup;
   const V* __restrict__ Vb = (const V*)q.V;
   const V* __restrict__ w = (const V*)q.w;
@@ -214,7 +218,7 @@ constexpr int kUpdGroup = 16;   // basis loads in flight per thread in the updat
 template <typename V>
 __global__ void __launch_bounds__(kThreads) update_kernel(const ProbK* __restrict__ P, int nv, int pass) {
   const ProbK& q = P[blockIdx.y];
-  if (!q.st->active) return;
+  if (!q.st->active || (pass == 1 && !q.st->reorth)) return;
   typedef typename Acc<V>::T A;
   typedef typename Acc<V>::R AR;
   extern __shared__ unsigned char hs_raw[];
@@ -249,14 +253,31 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const ProbK* __restric
     w[k] = out;
     nrm += out.x * out.x + out.y * out.y;
   }
-  if (pass == 1) block_store_sum(nrm, q.partial + blockIdx.x);
+  block_store_sum(nrm, q.partial + blockIdx.x);
+}
+
+// After the first pass: ||w'||^2 from the update's partials and ||h1||^2 from
+// the coefficients; the second pass is needed when ||w'||^2 < (||w'||^2 +
+// ||h1||^2) / 2, i.e. ||w'|| < ||w|| / sqrt 2 (||w||^2 = ||w'||^2 + ||h1||^2 for an
+// orthonormal basis).  One block per problem.
+__global__ void __launch_bounds__(kThreads) reorth_decide_kernel(const ProbK* __restrict__ P, int nblk, int nv) {
+  const ProbK& q = P[blockIdx.x];
+  if (!q.st->active) return;
+  const double w2 = block_sum_partials(q.partial, nblk);
+  if (threadIdx.x == 0) {
+    double h2 = 0.0;
+    for (int i = 0; i < nv; ++i) h2 += q.hcol[i].x * q.hcol[i].x + q.hcol[i].y * q.hcol[i].y;
+    const int r = (w2 < 0.5 * (w2 + h2)) ? 1 : 0;
+    q.st->reorth = r;
+    q.st->reorth_count += r;
+  }
 }
 
 // pass 0: hcol[i] = sum_b partial; pass 1: h2[i] = sum_b partial, hcol[i] += h2[i].
 // Fixed summation order (deterministic).  grid (nv, problems).
 __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const ProbK* __restrict__ P, int nblk, int pass) {
   const ProbK& q = P[blockIdx.y];
-  if (!q.st->active) return;
+  if (!q.st->active || (pass == 1 && !q.st->reorth)) return;
   const int i = blockIdx.x;
   __shared__ double sre[kThreads], sim[kThreads];
   double re = 0.0, im = 0.0;
@@ -323,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) init_cycle_kernel(const ProbK* __res
     st->target = q.target;
     st->resid = beta;
     st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->reorth_count = 0;
   }
 }
 
@@ -620,6 +642,7 @@ struct BatchCall {
   double2* partial_host = nullptr;  // pinned, kDotBlocks per problem
   std::vector<char> pc_on;          // preconditioner still in use, per problem
   bool jm = false;                  // JM-VIE problems (6N unknowns)
+  bool last_cycle_graph = false;    // the last cycle ran as a graph launch
   ~BatchCall() {
     cudaFree(table);
     cudaFree(st);
@@ -710,49 +733,180 @@ static vie_status read_status(BatchCall& c, cudaStream_t s) {
   return VIE_OK;
 }
 
-// One GMRES cycle of at most m steps for the problems of `list` (whose
-// records are on the device and whose status was just initialised).
+// One Arnoldi step j for the problems of `list`: preconditioner (flexible),
+// operator, Gram-Schmidt with the device-side second-pass decision, the FP64
+// Givens step and the next basis vector.  Problems whose status is inactive
+// return at once from every Krylov kernel.
+// `list` is the table the kernels index (all problems of the cycle), `live`
+// the problems whose preconditioner and operator are applied.
 template <typename V>
-static vie_status run_cycle(BatchCall& c, const std::vector<int>& list, int m, int dtype, int max_steps,
-                            int check_every, bool flexible, vie_precond_fn precond, void* const* precond_ctx,
-                            cudaStream_t s) {
+static vie_status enqueue_step(BatchCall& c, const std::vector<int>& list, const std::vector<int>& live, int j, int m,
+                               int dtype, bool flexible, vie_precond_fn precond, void* const* precond_ctx,
+                               unsigned gx, cudaStream_t s) {
+  const unsigned P = (unsigned)list.size();
+  if (flexible) {
+    for (int i : live) {
+      const ProbK& q = c.host[i];
+      const char* vj = (const char*)q.V + (size_t)j * q.n * sizeof(V);
+      char* zj = (char*)q.Z + (size_t)j * q.n * sizeof(V);
+      if (c.pc_on[i]) {
+        vie_status ps = precond(precond_ctx[i], dtype, vj, zj, s);
+        if (ps != VIE_OK) return ps;
+      } else {
+        VIE_CUDA_TRY(cudaMemcpyAsync(zj, vj, q.n * sizeof(V), cudaMemcpyDeviceToDevice, s));
+      }
+    }
+  }
+  vie_status ms = apply_list(c, live, dtype, APPLY_Z, j, flexible, s);
+  if (ms != VIE_OK) return ms;
+  const int nv = j + 1;
+  // h1 = V^H w, w -= V h1 (+ norm); if needed h2 = V^H w, w -= V h2 (+ norm); column h1 + h2
+  const dim3 gdots(kDotBlocks, (unsigned)((nv + kGroup - 1) / kGroup), P);
+  const size_t hs_bytes = nv * sizeof(typename Acc<V>::T);
+  dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv, 0);
+  reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
+  update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 0);
+  reorth_decide_kernel<<<P, kThreads, 0, s>>>(c.table, (int)gx, nv);
+  dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv, 1);
+  reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
+  update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 1);
+  arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, (int)gx, m + 1, j);
+  next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
+  VIE_LAUNCH_CHECK();
+  return VIE_OK;
+}
+
+// Condition of the next step's graph node: 1 while any problem of the list
+// is still active.
+__global__ void next_step_condition_kernel(const ProbK* __restrict__ P, int count, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int i = 0; i < count; ++i) any |= P[i].st->active;
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// A whole GMRES cycle as one CUDA graph: the start vector, then one
+// conditional (IF) node per Arnoldi step whose body ends by setting the next
+// step's condition from the problems' device status, then the back
+// substitution and the update of x.  Launched once per cycle, it runs every
+// step on the device with no host round trip; the steps after the last
+// active problem stopped are skipped by the device.  The instantiated graph
+// is kept while the list of problems, the preconditioner switches and the
+// step count stay the same (the records' table is one device buffer).
+struct CycleGraph {
+  std::vector<int> list;
+  std::vector<char> pc;
+  int jmax = 0, m = 0, dtype = 0;
+  bool flexible = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  bool broken = false;         // capture or instantiation failed once: use the host loop
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+template <typename V>
+static vie_status build_cycle_graph(BatchCall& c, CycleGraph& G, const std::vector<int>& list, int m, int jmax,
+                                    int dtype, bool flexible, vie_precond_fn precond, void* const* precond_ctx,
+                                    unsigned gx) {
+  if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+  if (G.graph) { cudaGraphDestroy(G.graph); G.graph = nullptr; }
+  if (!G.cap) VIE_CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+  const unsigned P = (unsigned)list.size();
+  VIE_CUDA_TRY(cudaGraphCreate(&G.graph, 0));
+  // handles: [0] start (always), [1 + j] step j (step 0 always, later steps
+  // set by the step before), [jmax + 1] finish (always)
+  std::vector<cudaGraphConditionalHandle> h(jmax + 2);
+  for (int k = 0; k < jmax + 2; ++k) {
+    const unsigned def = (k == 0 || k == 1 || k == jmax + 1) ? 1u : 0u;
+    VIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&h[k], G.graph, def, cudaGraphCondAssignDefault));
+  }
+  cudaGraphNode_t prev = nullptr;
+  for (int k = 0; k < jmax + 2; ++k) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h[k];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VIE_CUDA_TRY(cudaGraphAddNode(&node, G.graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    VIE_CUDA_TRY(cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    vie_status st = VIE_OK;
+    if (k == 0) {
+      start_vector_kernel<V><<<dim3(gx, P), kThreads, 0, G.cap>>>(c.table);
+    } else if (k <= jmax) {
+      st = enqueue_step<V>(c, list, list, k - 1, m, dtype, flexible, precond, precond_ctx, gx, G.cap);
+      if (st == VIE_OK && k < jmax) next_step_condition_kernel<<<1, 32, 0, G.cap>>>(c.table, (int)P, h[k + 1]);
+    } else {
+      backsolve_kernel<<<P, kThreads, 0, G.cap>>>(c.table, m + 1);
+      update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(typename Acc<V>::T), G.cap>>>(c.table);
+    }
+    cudaGraph_t out = body;
+    cudaError_t e = cudaStreamEndCapture(G.cap, &out);
+    if (st != VIE_OK) return st;
+    if (e != cudaSuccess) {
+      set_error("capture of a GMRES step: %s", cudaGetErrorString(e));
+      return VIE_ERR_CUDA;
+    }
+    prev = node;
+  }
+  VIE_CUDA_TRY(cudaGraphInstantiate(&G.exec, G.graph, 0));
+  G.list = list;
+  G.pc.clear();
+  for (int i : list) G.pc.push_back(c.pc_on[i]);
+  G.jmax = jmax;
+  G.m = m;
+  G.dtype = dtype;
+  G.flexible = flexible;
+  return VIE_OK;
+}
+
+// One GMRES cycle of at most m steps for the problems of `list` (whose
+// records are on the device and whose status was just initialised): as one
+// graph launch (above), or, if the graph cannot be built, from the host with
+// a status read every check_every steps.
+template <typename V>
+static vie_status run_cycle(BatchCall& c, CycleGraph& G, const std::vector<int>& list, int m, int dtype,
+                            int max_steps, int check_every, bool flexible, vie_precond_fn precond,
+                            void* const* precond_ctx, cudaStream_t s) {
   const unsigned P = (unsigned)list.size();
   size_t nmax = 0;
   for (int i : list) nmax = c.host[i].n > nmax ? c.host[i].n : nmax;
   const unsigned gx = grid_for(nmax);
+  const int jmax = max_steps < m ? max_steps : m;
+  if (!G.broken) {
+    std::vector<char> pc;
+    for (int i : list) pc.push_back(c.pc_on[i]);
+    const bool same = G.exec && G.list == list && G.pc == pc && G.jmax == jmax && G.m == m && G.dtype == dtype &&
+                      G.flexible == flexible;
+    vie_status st = VIE_OK;
+    if (!same) {
+      st = build_cycle_graph<V>(c, G, list, m, jmax, dtype, flexible, precond, precond_ctx, gx);
+      if (st != VIE_OK) {
+        // conditional graph nodes unavailable here: fall back to the host loop
+        G.broken = true;
+        cudaGetLastError();
+        clear_error();
+      }
+    }
+    if (!G.broken) {
+      VIE_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+      c.last_cycle_graph = true;
+      return read_status(c, s);
+    }
+  }
+  c.last_cycle_graph = false;
   start_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table);
   VIE_LAUNCH_CHECK();
   std::vector<int> live = list;       // problems still iterating in this cycle
-  const int jmax = max_steps < m ? max_steps : m;
   for (int j = 0; j < jmax && !live.empty(); ++j) {
-    if (flexible) {
-      for (int i : live) {
-        const ProbK& q = c.host[i];
-        const char* vj = (const char*)q.V + (size_t)j * q.n * sizeof(V);
-        char* zj = (char*)q.Z + (size_t)j * q.n * sizeof(V);
-        if (c.pc_on[i]) {
-          vie_status ps = precond(precond_ctx[i], dtype, vj, zj, s);
-          if (ps != VIE_OK) return ps;
-        } else {
-          VIE_CUDA_TRY(cudaMemcpyAsync(zj, vj, q.n * sizeof(V), cudaMemcpyDeviceToDevice, s));
-        }
-      }
-    }
-    vie_status ms = apply_list(c, live, dtype, APPLY_Z, j, flexible, s);
-    if (ms != VIE_OK) return ms;
-    const int nv = j + 1;
-    // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2 (+ norm); column h1 + h2
-    const dim3 gdots(kDotBlocks, (unsigned)((nv + kGroup - 1) / kGroup), P);
-    const size_t hs_bytes = nv * sizeof(typename Acc<V>::T);
-    dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv);
-    reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 0);
-    update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 0);
-    dots_kernel<V><<<gdots, kThreads, 0, s>>>(c.table, nv);
-    reduce_partials_kernel<<<dim3(nv, P), kThreads, 0, s>>>(c.table, kDotBlocks, 1);
-    update_kernel<V><<<dim3(gx, P), kThreads, hs_bytes, s>>>(c.table, nv, 1);
-    arnoldi_step_kernel<<<P, kThreads, 0, s>>>(c.table, (int)gx, m + 1, j);
-    next_vector_kernel<V><<<dim3(gx, P), kThreads, 0, s>>>(c.table, j);
-    VIE_LAUNCH_CHECK();
+    vie_status st = enqueue_step<V>(c, list, live, j, m, dtype, flexible, precond, precond_ctx, gx, s);
+    if (st != VIE_OK) return st;
     if ((j + 1) % check_every == 0 || j + 1 == jmax) {
       vie_status rs = read_status(c, s);
       if (rs != VIE_OK) return rs;
@@ -784,6 +938,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   const int dtype = (mode == VIE_SOLVE_MIXED) ? VIE_C64 : VIE_C128;
   const bool flexible = precond != nullptr;
   BatchCall c;
+  CycleGraph graph;
   c.jm = jm != 0;
   c.plans.assign(plans, plans + count);
   c.host.resize(count);
@@ -824,6 +979,8 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   std::vector<int> iters(count, 0), outers(count, 0);
   std::vector<double> rel(count, 0.0), prev_rel(count, 0.0);
   std::vector<vie_status> result(count, VIE_OK);
+  std::vector<int> trial(count, 0);         // preconditioner judging: 0 not yet, 1 plain cycle running, 2 done
+  std::vector<double> pc_rate(count, 0.0);  // log residual reduction per step of the preconditioned cycle
   for (int i = 0; i < count; ++i) {
     double t = 0.0;
     for (int k = 0; k < kDotBlocks; ++k) t += c.partial_host[(size_t)i * kDotBlocks + k].x;
@@ -865,6 +1022,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
       if (c.pc_on[i] && outers[i] > 0 && rel[i] > 0.9 * prev_rel[i]) {
         c.pc_on[i] = 0;
         infos[i].fallback = 1;
+        trial[i] = 2;
       }
       prev_rel[i] = rel[i];
       if (iters[i] >= max_iters || outers[i] >= max_outer) { result[i] = VIE_ERR_NOT_CONVERGED; continue; }
@@ -901,13 +1059,17 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
       int steps_left = max_iters;
       for (int i : inner) steps_left = (max_iters - iters[i]) < steps_left ? (max_iters - iters[i]) : steps_left;
       if (dtype == VIE_C64)
-        st = run_cycle<float2>(c, inner, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+        st = run_cycle<float2>(c, graph, inner, m, dtype, steps_left, check_every, flexible, precond, precond_ctx,
+                               s);
       else
-        st = run_cycle<double2>(c, inner, m, dtype, steps_left, check_every, flexible, precond, precond_ctx, s);
+        st = run_cycle<double2>(c, graph, inner, m, dtype, steps_left, check_every, flexible, precond,
+                                precond_ctx, s);
       if (st != VIE_OK) break;
       std::vector<int> again;
       for (int i : inner) {
         const int steps = c.st_host[i].j;
+        infos[i].graph_cycles += c.last_cycle_graph ? 1 : 0;
+        infos[i].reorth_steps += c.st_host[i].reorth_count;
         iters[i] += steps;
         if (dtype == VIE_C64) infos[i].matvecs32 += steps; else infos[i].matvecs64 += steps;
         if (steps == 0) {
@@ -915,14 +1077,30 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
           set_error("Krylov cycle made no progress (breakdown at the first step) for problem %d", i);
           continue;
         }
-        // a preconditioned cycle that cut the residual by less than 10 %, or a
-        // non-finite network output, switches this problem to the identity
-        if (c.pc_on[i] && !c.st_host[i].converged) {
-          const bool stalled = c.st_host[i].resid > 0.9 * c.st_host[i].beta;
+        // The true residual judges the preconditioner against plain GMRES.  A
+        // preconditioned cycle that cut the residual by less than 10 %, or a
+        // non-finite network output, switches this problem to the identity.
+        // For a learned network (whose quality nothing guarantees) the first
+        // preconditioned cycle that ends without reaching its target is
+        // followed by one plain cycle; the network is kept only if its cycle
+        // reduced the residual faster per step.
+        const SolveStatus& sh = c.st_host[i];
+        const double rate = (steps > 0 && sh.resid > 0.0 && sh.beta > 0.0) ? log(sh.beta / sh.resid) / steps : 0.0;
+        if (trial[i] == 1) {
+          trial[i] = 2;
+          if (rate >= pc_rate[i]) infos[i].fallback = 1;   // plain was as fast: stay plain
+          else c.pc_on[i] = 1;
+        } else if (c.pc_on[i] && !sh.converged) {
+          const bool stalled = sh.resid > 0.9 * sh.beta;
           const bool broken = precond_fallback_flag(c.plans[i], 1) != 0;
           if (stalled || broken) {
             c.pc_on[i] = 0;
             infos[i].fallback = 1;
+            trial[i] = 2;
+          } else if (trial[i] == 0 && !sh.breakdown && precond_is_learned(c.plans[i])) {
+            pc_rate[i] = rate;
+            trial[i] = 1;
+            c.pc_on[i] = 0;
           }
         }
         const bool more = mode == VIE_SOLVE_MIXED && !c.st_host[i].converged && !c.st_host[i].breakdown &&

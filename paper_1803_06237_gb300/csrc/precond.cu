@@ -799,6 +799,10 @@ vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx) {
   return VIE_OK;
 }
 
+int precond_is_learned(const vie_plan* p) {
+  return (p && p->precond && ((PrecondCtx*)p->precond)->net) ? 1 : 0;
+}
+
 int precond_fallback_flag(vie_plan* p, int clear) {
   if (!p || !p->precond) return 0;
   PrecondCtx* c = (PrecondCtx*)p->precond;

@@ -197,6 +197,7 @@ void free_krylov(vie_plan* p);
 void free_precond(vie_plan* p);
 vie_status precond_get(vie_plan* p, vie_precond_fn* fn, void** ctx);
 int precond_fallback_flag(vie_plan* p, int clear);   // non-finite network output seen
+int precond_is_learned(const vie_plan* p);            // the plan's preconditioner is a network
 vie_status circulant_apply(vie_circulant* c, int dtype, const void* v, void* z, cudaStream_t s);
 const vie_plan* circulant_plan(const vie_circulant* c);
 

@@ -16,7 +16,6 @@ factors) and solve in mixed precision to a true FP64 residual ``tol``.
 """
 from __future__ import annotations
 
-import math
 import time
 
 import numpy as np
@@ -39,18 +38,20 @@ def _solve(wl, tol, restart=30, factors_fp16=True):
     return plan, x, info
 
 
-def fit_slope(L, R, floor=1e-12, tail=0.5):
-    """Least-squares slope of log R against log L over the longest ``tail``
-    fraction of the lengths whose R lies above ``floor``."""
+def fit_slope(L, R, lo=None, hi=None, floor=1e-12):
+    """Least-squares slope of log R against log L over the lengths in
+    [lo, hi] whose R lies above ``floor`` (None if fewer than two remain).
+    The study fits between twice the shortest length and half the reference
+    length: the shortest absorbers are not yet adiabatic, and as L approaches
+    the reference length E_L approaches E_inf itself."""
     L = np.asarray(L, float)
     R = np.asarray(R, float)
-    keep = R > floor
+    keep = (R > floor) & (L >= (lo if lo is not None else -np.inf)) & (L <= (hi if hi is not None else np.inf))
     L, R = L[keep], R[keep]
     if L.size < 2:
         return None
-    k = max(2, int(math.ceil(tail * L.size)))
-    A = np.vstack([np.log(L[-k:]), np.ones(k)]).T
-    s, _ = np.linalg.lstsq(A, np.log(R[-k:]), rcond=None)[0]
+    A = np.vstack([np.log(L), np.ones(L.size)]).T
+    s, _ = np.linalg.lstsq(A, np.log(R), rcond=None)[0]
     return float(s)
 
 
@@ -73,8 +74,10 @@ def rl_sweep(lengths_nm, degrees=(0, 1, 2), r_rt=1e-25, ref_nm=9450.0, tol=1e-8,
             iters.append(info["iterations"])
             res.append(info["residual"])
             plan.close()
+        lo, hi = 2.0 * min(lengths_nm), 0.5 * ref_nm
         out["degrees"][str(d)] = {"R": Rs, "iterations": iters, "true_residual_max": max(res),
-                                  "slope": fit_slope(lengths_nm, Rs), "slope_predicted": -2.0 * (d + 1)}
+                                  "slope": fit_slope(lengths_nm, Rs, lo, hi), "slope_window_nm": [lo, hi],
+                                  "slope_predicted": -2.0 * (d + 1)}
     out["seconds"] = time.perf_counter() - t0
     return out
 

@@ -55,7 +55,7 @@ class vie_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("matvecs64", ctypes.c_int),
                 ("matvecs32", ctypes.c_int), ("converged", ctypes.c_int), ("fallback", ctypes.c_int),
                 ("residual", ctypes.c_double), ("time_ms", ctypes.c_double), ("history_len", ctypes.c_int),
-                ("history", ctypes.c_double * 64)]
+                ("history", ctypes.c_double * 64), ("graph_cycles", ctypes.c_int), ("reorth_steps", ctypes.c_int)]
 
 
 VIE_SOLVE_FP64 = 0
@@ -293,7 +293,8 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
     out = {"status": st, "iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
            "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
            "residual": info.residual, "time_ms": info.time_ms,
-           "history": [info.history[i] for i in range(min(info.history_len, 64))]}
+           "history": [info.history[i] for i in range(min(info.history_len, 64))],
+           "graph_cycles": info.graph_cycles, "reorth_steps": info.reorth_steps}
     if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
         _check(st, "vie_solve")
     return out
@@ -373,7 +374,8 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
         out.append({"iterations": info.iterations, "outer": info.outer, "matvecs64": info.matvecs64,
                     "matvecs32": info.matvecs32, "converged": bool(info.converged), "fallback": bool(info.fallback),
                     "residual": info.residual, "time_ms": info.time_ms,
-                    "history": [info.history[i] for i in range(min(info.history_len, 64))]})
+                    "history": [info.history[i] for i in range(min(info.history_len, 64))],
+                    "graph_cycles": info.graph_cycles, "reorth_steps": info.reorth_steps})
     if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
         _check(st, "vie_solve_batch")
     return st, out

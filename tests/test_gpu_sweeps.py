@@ -21,6 +21,9 @@ def _lib():
 def test_fit_slope_of_a_power_law():
     L = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
     assert abs(sweeps.fit_slope(L, 3e-4 * L ** -4.0) + 4.0) < 1e-12
+    R = 3e-4 * L ** -4.0
+    R[-1] = 1e-3                       # outside the window: ignored
+    assert abs(sweeps.fit_slope(L, R, 2.0, 8.0) + 4.0) < 1e-12
     assert sweeps.fit_slope(L, np.full(5, 1e-15)) is None
 
 
