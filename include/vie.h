@@ -58,8 +58,9 @@ enum {
                                  5-smooth size >= 2n - 1) */
   VIE_PLAN_AUTOTUNE = 2       /* time complex64 operator applications for the
                                  three smallest 5-smooth sizes >= 2n - 1 per axis
-                                 and 2 or 4 lines per forward and per inverse
-                                 x-pass block, keep the
+                                 and the x-pass variants (four-step with 2 or 4
+                                 lines per block, three-factor with 1 or 2)
+                                 of the forward and the inverse pass, keep the
                                  fastest (any M >= 2n - 1 embeds the operator
                                  exactly); ignored with VIE_PLAN_CIRC_2N */
 };
@@ -72,8 +73,12 @@ typedef struct {
   double setup_ms;            /* device time of entries + spectrum */
   double tune_ms;             /* host time spent by VIE_PLAN_AUTOTUNE (0 without) */
   int tune_candidates;        /* configurations timed (0 without) */
-  int x_lines_per_block;      /* forward x-pass lines per block chosen by the tuner (0: heuristic) */
-  int x_lines_per_block_inverse; /* inverse x-pass lines per block chosen by the tuner (0: heuristic) */
+  int x_lines_per_block;      /* forward x pass chosen by the tuner: > 0 four-step
+                                 register FFT with that many lines per block,
+                                 < 0 three-factor register FFT with -value lines
+                                 per block, 0 the default (three-factor where
+                                 compiled for Mx, else four-step) */
+  int x_lines_per_block_inverse; /* the same for the inverse x pass */
 } vie_plan_info;
 
 /* Graded absorber of Sec. 4.1-4.2: eps'' = eps2_max * u^degree with

@@ -371,12 +371,19 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
         p->ax[0] = ax[0][cx];
         p->ax[1] = ax[1][cy];
         p->ax[2] = ax[2][cz];
-        int l1 = 0, l2 = 0;
+        int l1 = 0, l2 = 0, a1 = 0, a2 = 0, a3 = 0;
         x4_factors(p->m[0], &l1, &l2);
-        const int lpbs[2] = {2, 4};
-        for (int li = 0; li < (l1 ? 4 : 1); ++li) {   // (forward, inverse) lines per block
-          p->x_lpb = l1 ? lpbs[li & 1] : 0;
-          p->x_lpb_inv = l1 ? lpbs[li >> 1] : 0;
+        x3_factors(p->m[0], &a1, &a2, &a3);
+        // x-pass variants: four-step with 2 or 4 lines per block, three-factor
+        // with 1 or 2 (negative codes), for the forward and the inverse pass
+        std::vector<int> modes;
+        if (l1) { modes.push_back(2); modes.push_back(4); }
+        if (a1) { modes.push_back(-1); modes.push_back(-2); }
+        if (modes.empty()) modes.push_back(0);
+        const int nm = (int)modes.size();
+        for (int li = 0; li < nm * nm; ++li) {   // (forward, inverse) variants
+          p->x_lpb = modes[li % nm];
+          p->x_lpb_inv = modes[li / nm];
           vie_status ms = VIE_OK;
           for (int r = 0; r < 3 && ms == VIE_OK; ++r)
             ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);

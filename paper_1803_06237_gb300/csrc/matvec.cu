@@ -908,6 +908,284 @@ __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
   }
 }
 
+// ---------------------------------------------------------------------------
+// x passes with a three-factor register FFT, Mx = L1 L2 L3 (compile time),
+// for lines too few to keep the SMs busy with one thread per sub-FFT of the
+// four-step split (759 lines of the 600 x 23 x 11 guide give 30k threads at
+// Mx = 40 x 30, six warps per SM).  Index maps (M = L2 L3):
+//   input  n  = n1 + L1 (m2 + L2 m3),  output k = kM + M k1, kM = k3 + L3 k2;
+//   step 1: thread (l, n1, m2) transforms the L3 values over m3 and multiplies
+//           by w_M^(m2 k3) = w_Mx^(L1 m2 k3);
+//   step 2: thread (l, n1, k3) transforms the L2 values over m2 and multiplies
+//           by w_Mx^(n1 kM);
+//   step 3: thread (l, kM) transforms the L1 values over n1.
+// LPB lines per block, lanes fastest over the lines.  NX > 0 fixes the line
+// length: the forward pass drops m3 >= NX / (L1 L2) (zero padding) and the
+// inverse pass keeps k1 < NX / M (the crop).  The inverse pass runs the same
+// steps with conjugate twiddles on spectrum index n (the workspace) and
+// spatial index k, then applies the contrast epilogue.
+// ---------------------------------------------------------------------------
+template <int L1, int L2, int L3>
+struct X3 {
+  static constexpr int MX = L1 * L2 * L3;
+  static constexpr int M = L2 * L3;
+  static constexpr int T1 = L1 * L2, T2 = L1 * L3, T3 = L2 * L3;
+  static constexpr int NT = (T1 > T2 ? (T1 > T3 ? T1 : T3) : (T2 > T3 ? T2 : T3));
+};
+
+template <typename V, int L1, int L2, int L3, int LPB, bool INV>
+__device__ __forceinline__ void x3_steps12(V* __restrict__ S1, V* __restrict__ S2, const V* __restrict__ twx,
+                                           const V* __restrict__ tw2, const V* __restrict__ tw3, int R1, int R2,
+                                           V (&a)[L3], int tid) {
+  typedef X3<L1, L2, L3> G;
+  // step 1 (a holds this thread's L3 inputs over m3)
+  if (tid < LPB * G::T1) {
+    const int l = tid % LPB, r = tid / LPB;           // r = n1 + L1 m2
+    const int m2 = r / L1;
+    reg_fft<V, INV, L3>(a, tw3);
+#pragma unroll
+    for (int k3 = 0; k3 < L3; ++k3) {
+      const V t = (k3 == 0 || m2 == 0) ? a[k3] : (INV ? mulc(a[k3], twx[L1 * m2 * k3]) : mul(a[k3], twx[L1 * m2 * k3]));
+      S1[k3 * R1 + r * LPB + l] = t;
+    }
+  }
+  __syncthreads();
+  // step 2
+  if (tid < LPB * G::T2) {
+    const int l = tid % LPB, r = tid / LPB;           // r = n1 + L1 k3
+    const int n1 = r % L1, k3 = r / L1;
+    V b[L2];
+#pragma unroll
+    for (int m2 = 0; m2 < L2; ++m2) b[m2] = S1[k3 * R1 + (n1 + L1 * m2) * LPB + l];
+    reg_fft<V, INV, L2>(b, tw2);
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      const int kM = k3 + L3 * k2;
+      const V t = (n1 == 0 || kM == 0) ? b[k2] : (INV ? mulc(b[k2], twx[n1 * kM]) : mul(b[k2], twx[n1 * kM]));
+      S2[kM * R2 + n1 * LPB + l] = t;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename V, int L1, int L2, int L3, int LPB, int NX>
+__global__ void __launch_bounds__(LPB * X3<L1, L2, L3>::NT) pass_a3_kernel(
+    const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
+  typedef X3<L1, L2, L3> G;
+  static_assert(NX == 0 || NX % (L1 * L2) == 0, "compiled line length must divide by L1 L2");
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  V* __restrict__ work = pp.work[blockIdx.y];
+  constexpr int R1 = pitch_mod16(G::T1 * LPB, LPB);
+  constexpr int R2 = pitch_mod16(L1 * LPB, LPB);
+  extern __shared__ unsigned char smem_raw[];
+  V* twx = reinterpret_cast<V*>(smem_raw);
+  V* tw1 = twx + G::MX;
+  V* tw2 = tw1 + L1;
+  V* tw3 = tw2 + L2;
+  V* S1 = tw3 + L3;                // [k3][R1]: (n1 + L1 m2, l)
+  V* S2 = S1 + L3 * R1;            // [kM][R2]: (n1, l)
+  V* Xs = S2 + G::M * R2;          // [l][P]
+  const int P = pitch_mod16(nx, LPB);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * LPB;
+  const int nl = min(LPB, NL - l0);
+  pdl_launch_dependents();
+  {
+    for (int i = tid; i < G::MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
+    pdl_wait();
+    const V* src = x + (size_t)l0 * nx;
+    for (int l = 0; l < nl; ++l)
+      for (int n = tid; n < nx; n += nth) __pipeline_memcpy_async(Xs + l * P + n, src + (size_t)l * nx + n, sizeof(V));
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+  }
+  __syncthreads();
+  for (int i = tid; i < L1; i += nth) tw1[i] = twx[i * (G::MX / L1)];
+  for (int i = tid; i < L2; i += nth) tw2[i] = twx[i * (G::MX / L2)];
+  for (int i = tid; i < L3; i += nth) tw3[i] = twx[i * (G::MX / L3)];
+  __syncthreads();
+  V a[L3];
+  if (tid < LPB * G::T1) {
+    const int l = tid % LPB, r = tid / LPB;
+    const int n1 = r % L1, m2 = r / L1;
+#pragma unroll
+    for (int m3 = 0; m3 < L3; ++m3) {
+      const int n = n1 + L1 * (m2 + L2 * m3);
+      const bool in = NX > 0 ? (m3 < NX / (L1 * L2)) : (n < nx);
+      a[m3] = (l < nl && in) ? Xs[l * P + n] : zero_c<V>();
+    }
+  }
+  x3_steps12<V, L1, L2, L3, LPB, false>(S1, S2, twx, tw2, tw3, R1, R2, a, tid);
+  // step 3: X[kM + M k1], written transposed (work[k][line])
+  if (tid < LPB * G::T3) {
+    const int l = tid % LPB, kM = tid / LPB;
+    V c[L1];
+#pragma unroll
+    for (int n1 = 0; n1 < L1; ++n1) c[n1] = S2[kM * R2 + n1 * LPB + l];
+    reg_fft<V, false, L1>(c, tw1);
+    if (l < nl) {
+      const int line = l0 + l, grp = line / gsz;
+      V* dst = work + (size_t)grp * G::MX * gsz + (line - grp * gsz);
+#pragma unroll
+      for (int k1 = 0; k1 < L1; ++k1) dst[(size_t)(kM + G::M * k1) * gsz] = c[k1];
+    }
+  }
+}
+
+template <typename V, int L1, int L2, int L3, int LPB, int NX>
+__global__ void __launch_bounds__(LPB * X3<L1, L2, L3>::NT) pass_c3_kernel(
+    const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode,
+    int gsz) {
+  typedef X3<L1, L2, L3> G;
+  static_assert(NX == 0 || NX % G::M == 0, "compiled line length must divide by L2 L3");
+  const V* __restrict__ work = pp.work[blockIdx.y];
+  const V* __restrict__ x = pp.x[blockIdx.y];
+  const V* __restrict__ Mc = pp.M[blockIdx.y];
+  V* __restrict__ y = pp.y[blockIdx.y];
+  constexpr int R1 = pitch_mod16(G::T1 * LPB, LPB);
+  constexpr int R2 = pitch_mod16(L1 * LPB, LPB);
+  extern __shared__ unsigned char smem_raw[];
+  V* twx = reinterpret_cast<V*>(smem_raw);
+  V* tw1 = twx + G::MX;
+  V* tw2 = tw1 + L1;
+  V* tw3 = tw2 + L2;
+  V* S1 = tw3 + L3;
+  V* S2 = S1 + L3 * R1;
+  V* Ys = S2 + G::M * R2;          // [l][P] the inverse transform, x < nx
+  const int P = pitch_mod16(nx, LPB);
+  V* Xs = Ys + LPB * P;            // the block's rows of x (epilogue operand)
+  V* Ms = Xs + LPB * nx;           // the matching rows of M
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int l0 = blockIdx.x * LPB;
+  const int nl = min(LPB, NL - l0);
+  pdl_launch_dependents();
+  {
+    for (int i = tid; i < G::MX; i += nth) __pipeline_memcpy_async(twx + i, twxg + i, sizeof(V));
+    __pipeline_commit();
+    if (mode != MODE_PLAIN) {
+      for (int l = 0; l < nl; ++l) {
+        const V* msrc = Mc + (size_t)((l0 + l) % nyz) * nx;
+        for (int i = tid; i < nx; i += nth) __pipeline_memcpy_async(Ms + l * nx + i, msrc + i, sizeof(V));
+      }
+    }
+    pdl_wait();
+    if (mode != MODE_PLAIN) {
+      const V* xsrc = x + (size_t)l0 * nx;
+      for (int e = tid; e < nl * nx; e += nth) __pipeline_memcpy_async(Xs + e, xsrc + e, sizeof(V));
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(1);      // twiddles only
+  }
+  __syncthreads();
+  for (int i = tid; i < L1; i += nth) tw1[i] = twx[i * (G::MX / L1)];
+  for (int i = tid; i < L2; i += nth) tw2[i] = twx[i * (G::MX / L2)];
+  for (int i = tid; i < L3; i += nth) tw3[i] = twx[i * (G::MX / L3)];
+  __syncthreads();
+  V a[L3];
+  if (tid < LPB * G::T1) {
+    const int l = tid % LPB, r = tid / LPB;
+    const int n1 = r % L1, m2 = r / L1;
+    const int line = l0 + (l < nl ? l : 0), grp = line / gsz;
+    const V* src = work + (size_t)grp * G::MX * gsz + (line - grp * gsz);
+#pragma unroll
+    for (int m3 = 0; m3 < L3; ++m3)
+      a[m3] = (l < nl) ? src[(size_t)(n1 + L1 * (m2 + L2 * m3)) * gsz] : zero_c<V>();
+  }
+  x3_steps12<V, L1, L2, L3, LPB, true>(S1, S2, twx, tw2, tw3, R1, R2, a, tid);
+  if (tid < LPB * G::T3) {
+    const int l = tid % LPB, kM = tid / LPB;
+    V c[L1];
+#pragma unroll
+    for (int n1 = 0; n1 < L1; ++n1) c[n1] = S2[kM * R2 + n1 * LPB + l];
+    reg_fft<V, true, L1>(c, tw1);
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) {
+      const int xo = kM + G::M * k1;
+      if (NX > 0 ? (k1 < NX / G::M) : (xo < nx)) Ys[l * P + xo] = c[k1];
+    }
+  }
+  __syncthreads();
+  __pipeline_wait_prior(0);
+  __syncthreads();
+  {
+    const int total = nl * nx;
+    const size_t g0 = (size_t)l0 * nx;
+    for (int e = tid; e < total; e += nth) {
+      const int l = e / nx, ix = e - l * nx;
+      const V uu = Ys[l * P + ix];
+      if (mode == MODE_PLAIN) { y[g0 + e] = uu; continue; }
+      const V wv = Xs[e], mv = Ms[e];
+      y[g0 + e] = (mode == MODE_OPERATOR) ? sub(wv, mul(mv, uu)) : mul(mv, sub(uu, wv));
+    }
+  }
+}
+
+// Mx = L1 L2 L3 factorisations with a three-factor register x pass, and the
+// compiled line lengths.
+#define VIE_PASS_X3_SIZES(X) X(10, 12, 10)
+#define VIE_PASS_X3_FIXED(X) X(10, 12, 10, 600)
+
+template <typename V, int L1, int L2, int L3, int LPB, int NX>
+static vie_status launch_x3_lpb(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL,
+                                const V* twx, int mode, cudaStream_t s, bool* done, int gsz) {
+  typedef X3<L1, L2, L3> G;
+  constexpr int R1 = pitch_mod16(G::T1 * LPB, LPB);
+  constexpr int R2 = pitch_mod16(L1 * LPB, LPB);
+  const int P = pitch_mod16(nx, LPB);
+  const bool operands = !forward && mode != MODE_PLAIN;
+  const size_t smem = (size_t)(G::MX + L1 + L2 + L3 + L3 * R1 + G::M * R2 + LPB * P +
+                               (forward ? 0 : (operands ? 2 * LPB * nx : 0))) * sizeof(V);
+  if (smem > 200 * 1024) { *done = false; return VIE_OK; }
+  const dim3 blocks((unsigned)((NL + LPB - 1) / LPB), (unsigned)count);
+  const dim3 threads(LPB * G::NT);
+  if (forward) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_a3_kernel<V, L1, L2, L3, LPB, NX>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA_TRY(launch_pdl(pass_a3_kernel<V, L1, L2, L3, LPB, NX>, blocks, threads, smem, s, pp, nx, NL, twx, gsz));
+  } else {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_c3_kernel<V, L1, L2, L3, LPB, NX>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA_TRY(launch_pdl(pass_c3_kernel<V, L1, L2, L3, LPB, NX>, blocks, threads, smem, s, pp, nx, nyz, NL, twx,
+                            mode, gsz));
+  }
+  VIE_LAUNCH_CHECK();
+  *done = true;
+  return VIE_OK;
+}
+
+// lpb: 1 or 2 lines per block (0: 2)
+template <typename V, int L1, int L2, int L3, int NX = 0>
+static vie_status launch_x3(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL, const V* twx,
+                            int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
+  if (lpb == 1) return launch_x3_lpb<V, L1, L2, L3, 1, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+  return launch_x3_lpb<V, L1, L2, L3, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+}
+
+// factors (L1, L2, L3) of Mx with a compiled three-factor kernel, or (0, 0, 0)
+void x3_factors(int mx, int* l1, int* l2, int* l3) {
+  *l1 = *l2 = *l3 = 0;
+#define VIE_X(a, b, c) if (mx == a * b * c && *l1 == 0) { *l1 = a; *l2 = b; *l3 = c; }
+  VIE_PASS_X3_SIZES(VIE_X)
+#undef VIE_X
+}
+
+template <typename V>
+static vie_status dispatch_x3(bool forward, int l1, int l2, int l3, const PassPtrs<V>& pp, int count, int nx,
+                              int nyz, int NL, const V* twx, int mode, cudaStream_t s, bool* done, int lpb,
+                              int gsz) {
+  *done = false;
+#define VIE_Y(a, b, c, d)                                        \
+  if (l1 == a && l2 == b && l3 == c && nx == d)                   \
+    return launch_x3<V, a, b, c, d>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb, gsz);
+  VIE_PASS_X3_FIXED(VIE_Y)
+#undef VIE_Y
+#define VIE_X(a, b, c) \
+  if (l1 == a && l2 == b && l3 == c) return launch_x3<V, a, b, c>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, lpb, gsz);
+  VIE_PASS_X3_SIZES(VIE_X)
+#undef VIE_X
+  return VIE_OK;
+}
+
 // Mx = L1 x L2 factorisations with a four-step register x pass.
 #define VIE_PASS_X4_SIZES(X) \
   X(40, 30) X(24, 25) X(24, 30) X(30, 30) X(45, 25) X(45, 30) X(50, 30) X(40, 40) X(20, 20)
@@ -1087,12 +1365,21 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   }
   const size_t smem_b = (size_t)(My + Mz + 2 * 3 * Mz * (My + 1)) * sizeof(V);
   const dim3 blocks_ac((unsigned)((NL + lpb - 1) / lpb), (unsigned)count);
-  int l1 = 0, l2 = 0;
+  int l1 = 0, l2 = 0, a1 = 0, a2 = 0, a3 = 0;
   x4_factors(Mx, &l1, &l2);
+  x3_factors(Mx, &a1, &a2, &a3);
   bool done = false;
   vie_status st = VIE_OK;
-  if (l1) {
-    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb, NL);
+  // x passes: three-factor kernels (x_lpb < 0: -x_lpb lines per block; 0:
+  // the default where they exist), else four-step (x_lpb > 0), else generic
+  if (a1 && p->x_lpb <= 0) {
+    st = dispatch_x3<V>(true, a1, a2, a3, pp, count, nx, ny * nz, NL, twx, mode, s, &done,
+                        p->x_lpb < 0 ? -p->x_lpb : 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done && l1) {
+    st = dispatch_x4<V>(true, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb > 0 ? p->x_lpb : 0,
+                        NL);
     if (st != VIE_OK) return st;
   }
   if (!done) {
@@ -1120,8 +1407,14 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
     VIE_LAUNCH_CHECK();
   }
   done = false;
-  if (l1) {
-    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done, p->x_lpb_inv, NL);
+  if (a1 && p->x_lpb_inv <= 0) {
+    st = dispatch_x3<V>(false, a1, a2, a3, pp, count, nx, ny * nz, NL, twx, mode, s, &done,
+                        p->x_lpb_inv < 0 ? -p->x_lpb_inv : 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done && l1) {
+    st = dispatch_x4<V>(false, l1, l2, pp, count, nx, ny * nz, NL, twx, mode, s, &done,
+                        p->x_lpb_inv > 0 ? p->x_lpb_inv : 0, NL);
     if (st != VIE_OK) return st;
   }
   if (!done) {
@@ -1283,11 +1576,16 @@ static vie_status run_jm(vie_plan* p, const V* x, V* y, const V* ghat, const V* 
     return VIE_ERR_INVALID;
   }
   const dim3 blocks_ac((unsigned)((NL + lpb - 1) / lpb), 1);
-  int l1 = 0, l2 = 0;
+  int l1 = 0, l2 = 0, a1 = 0, a2 = 0, a3 = 0;
   x4_factors(Mx, &l1, &l2);
+  x3_factors(Mx, &a1, &a2, &a3);
   bool done = false;
   vie_status st = VIE_OK;
-  if (l1) {
+  if (a1) {
+    st = dispatch_x3<V>(true, a1, a2, a3, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done && l1) {
     st = dispatch_x4<V>(true, l1, l2, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
     if (st != VIE_OK) return st;
   }
@@ -1302,7 +1600,11 @@ static vie_status run_jm(vie_plan* p, const V* x, V* y, const V* ghat, const V* 
                                                         radices_of(p->ax[2]), twy, twz, p->kappa);
   VIE_LAUNCH_CHECK();
   done = false;
-  if (l1) {
+  if (a1) {
+    st = dispatch_x3<V>(false, a1, a2, a3, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
+    if (st != VIE_OK) return st;
+  }
+  if (!done && l1) {
     st = dispatch_x4<V>(false, l1, l2, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);
     if (st != VIE_OK) return st;
   }

@@ -118,6 +118,7 @@ inline Radices radices_of(const AxisPlan& a) {
 bool factor_length(int len, AxisPlan* out);   // radices from {4, 2, 3, 5}
 bool factor_length_any(int len, AxisPlan* out);   // 4, 2, 3, 5, then larger primes (generic stages)
 void x4_factors(int mx, int* l1, int* l2);    // compiled four-step split of Mx, or (0, 0)
+void x3_factors(int mx, int* l1, int* l2, int* l3);   // compiled three-factor split of Mx, or zeros
 int smooth_size_at_least(int n);               // smallest 5-smooth >= n
 
 // ---------------------------------------------------------------------------
@@ -161,8 +162,9 @@ struct vie_plan {
   void* jm_work = nullptr;    // 6 ny nz Mx complex128
   int jm_gen = -1;            // contrast generation the 6N contrast was built from
   int contrast_gen = 0;       // incremented whenever the contrast is set
-  int x_lpb = 0;              // four-step forward x-pass lines per block (0: heuristic)
-  int x_lpb_inv = 0;          // four-step inverse x-pass lines per block (0: heuristic)
+  int x_lpb = 0;              // forward x pass: > 0 four-step with that many lines per block,
+                              // < 0 three-factor with -x_lpb lines per block, 0 heuristic
+  int x_lpb_inv = 0;          // the same for the inverse x pass
   double tune_ms = 0.0;       // VIE_PLAN_AUTOTUNE host time
   int tune_candidates = 0;
 };
