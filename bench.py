@@ -819,8 +819,10 @@ def reference_arm(args):
 def studies(args):
     """The parameter studies of Sec. 5 (one JSON line each): R(L) on the
     13.5 um strip for d = 0, 1, 2 at R_rt = 1e-25 and 1e-10 (lengths 450 ..
-    9450 nm, reference 9450 nm), and the transmission of the 100-period Bragg
-    grating at 101 wavelengths in [1.52, 1.57] um."""
+    9000 nm, reference 9450 nm); electric against matched electric and
+    magnetic loss on a 3 um strip (d = 1, 2, lengths 900 .. 4500 nm); and the
+    transmission of the 100-period Bragg grating at 101 wavelengths in
+    [1.52, 1.57] um."""
     from paper_1803_06237_gb300 import build, sweeps, vie
     build.build_library()
     vie.load()
@@ -829,6 +831,12 @@ def studies(args):
         for r_rt in (1e-25, 1e-10):
             out = sweeps.rl_sweep(lengths, degrees=(0, 1, 2), r_rt=r_rt, ref_nm=9450.0, tol=1e-8)
             print(json.dumps({"study": "absorber_length", **out}), flush=True)
+        # electric + matched magnetic loss on a 3 um strip (JM-VIE, plain GMRES)
+        short = [900.0 * i for i in range(1, 6)]
+        for matched in (False, True):
+            out = sweeps.rl_sweep(short, degrees=(1, 2), r_rt=1e-25, ref_nm=9000.0, tol=1e-8, body_nm=3000.0,
+                                  matched=matched)
+            print(json.dumps({"study": "absorber_length_matching", **out}), flush=True)
     if args.bragg_sweep:
         lams = [1.52 + 0.0005 * i for i in range(101)]
         out = sweeps.bragg_sweep(lams, periods=100, tol=1e-6, batch=8)
@@ -885,6 +893,30 @@ def profile_microring(reps: int):
     plan.close()
 
 
+def profile_jm(reps: int):
+    """The JM-VIE operator (matched permeability) on the benchmark guide:
+    `reps` complex64 applications, for kernel launch lists."""
+    import torch
+
+    from paper_1803_06237_gb300 import build, learned, vie, workloads
+    build.build_library()
+    vie.load()
+    plan, _ = learned.setup_problem(workloads.waveguide())
+    vie.vie_set_permeability(plan, None)
+    x = torch.randn(6 * plan.n_vox, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(reps):
+        vie.vie_jm_matvec(plan, x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        vie.vie_jm_matvec(plan, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_jm": reps, "ms_per_matvec": e0.elapsed_time(e1) / reps}))
+
+
 def profile_circulant(reps: int):
     """Block-circulant builds (complex64 factors, then complex-half factors)
     and `reps` applications of each on the benchmark guide: a short, fixed
@@ -930,6 +962,8 @@ def main():
                     help="only build the block-circulant preconditioner and apply it (for kernel launch lists)")
     ap.add_argument("--profile-microring", type=int, default=0,
                     help="only build the ring resonator's plan and apply the operator (for kernel launch lists)")
+    ap.add_argument("--profile-jm", type=int, default=0,
+                    help="only run JM-VIE operator applications on the guide (for kernel launch lists)")
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
@@ -954,6 +988,9 @@ def main():
         return
     if args.profile_net:
         profile_net(args.profile_net)
+        return
+    if args.profile_jm:
+        profile_jm(args.profile_jm)
         return
     if args.profile_circulant:
         profile_circulant(args.profile_circulant)

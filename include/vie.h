@@ -78,7 +78,8 @@ typedef struct {
                                  < 0 three-factor register FFT with -value lines
                                  per block, 0 the default (three-factor where
                                  compiled for Mx, else four-step) */
-  int x_lines_per_block_inverse; /* the same for the inverse x pass */
+  int x_lines_per_block_inverse; /* the same for the inverse x pass (its default:
+                                    four-step where compiled for Mx) */
 } vie_plan_info;
 
 /* Graded absorber of Sec. 4.1-4.2: eps'' = eps2_max * u^degree with

@@ -1371,7 +1371,8 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
   bool done = false;
   vie_status st = VIE_OK;
   // x passes: three-factor kernels (x_lpb < 0: -x_lpb lines per block; 0:
-  // the default where they exist), else four-step (x_lpb > 0), else generic
+  // the default for the forward pass where they exist), else four-step
+  // (x_lpb > 0), else generic
   if (a1 && p->x_lpb <= 0) {
     st = dispatch_x3<V>(true, a1, a2, a3, pp, count, nx, ny * nz, NL, twx, mode, s, &done,
                         p->x_lpb < 0 ? -p->x_lpb : 0, NL);
@@ -1407,7 +1408,10 @@ static vie_status run_passes(const vie_plan* p, const PassPtrs<V>& pp, int count
     VIE_LAUNCH_CHECK();
   }
   done = false;
-  if (a1 && p->x_lpb_inv <= 0) {
+  // inverse: three-factor only when chosen (x_lpb_inv < 0) or when no
+  // four-step kernel exists for Mx; the four-step inverse, whose blocks read
+  // 32-byte rows of the transposed workspace, measured faster on the guide
+  if (a1 && (p->x_lpb_inv < 0 || (p->x_lpb_inv == 0 && !l1))) {
     st = dispatch_x3<V>(false, a1, a2, a3, pp, count, nx, ny * nz, NL, twx, mode, s, &done,
                         p->x_lpb_inv < 0 ? -p->x_lpb_inv : 0, NL);
     if (st != VIE_OK) return st;

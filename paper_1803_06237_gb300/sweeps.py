@@ -5,7 +5,9 @@ solve, field and metric runs in libvie).
   (810 x 30 x 12 voxels of 50/3 nm): for each monomial degree d and length L
   the reflection coefficient R(L) = |E_inf - E_L|^2 / |E_inf|^2 along the
   centre axis of the guide, E_inf from the longest absorber, and the slope of
-  log R against log L, which Sec. 4.3 predicts to approach -2 (d + 1).
+  log R against log L, which Sec. 4.3 predicts to approach -2 (d + 1); with
+  ``matched`` the absorbers also carry the matched magnetic loss of Sec. 4.2
+  (JM-VIE), which Sec. 5.1 reports to lower R by about a factor 100.
 * ``bragg_sweep``: the transmission spectrum of the N-period Bragg grating of
   Sec. 5.2: one plan per wavelength (the spectra depend on k), the
   wavelengths solved together through the batch path, T(lambda) = sum |E|^2
@@ -38,6 +40,28 @@ def _solve(wl, tol, restart=30, factors_fp16=True):
     return plan, x, info
 
 
+def _solve_matched(wl, tol, restart=60):
+    """The same strip with magnetic loss matched to the electric one (Sec. 4.2,
+    mu'' = eps''/eps'), the round-trip target met with D = 4 (Sec. 4.3): the
+    JM-VIE driven by the electric sheet, mixed precision, no preconditioner.
+    Returns (plan, electric half of the solution, info)."""
+    import torch
+    ab = wl.absorbers[0]
+    e2 = vie.vie_eps2_from_round_trip(ab.r_rt, ab.degree, ab.length * wl.h_um, wl.k0_per_um, wl.eps_core, 4.0)
+    plan = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, wl.eps, [dict(x0=ab.x0, length=ab.length, degree=ab.degree, eps2_max=e2)])
+    vie.vie_set_permeability(plan, None)
+    n3 = 3 * plan.n_vox
+    src = torch.zeros(2 * n3, dtype=torch.complex128, device="cuda")
+    src[:n3] = torch.from_numpy(np.ascontiguousarray(wl.src.ravel())).cuda()
+    b = torch.empty_like(src)
+    vie.vie_jm_rhs_from_source(plan, src, b)
+    x = torch.zeros_like(b)
+    info = vie.vie_jm_solve(plan, b, x, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart,
+                            raise_on_not_converged=False)
+    return plan, x[:n3].contiguous(), info
+
+
 def fit_slope(L, R, lo=None, hi=None, floor=1e-12):
     """Least-squares slope of log R against log L over the lengths in
     [lo, hi] whose R lies above ``floor`` (None if fewer than two remain).
@@ -56,20 +80,24 @@ def fit_slope(L, R, lo=None, hi=None, floor=1e-12):
 
 
 def rl_sweep(lengths_nm, degrees=(0, 1, 2), r_rt=1e-25, ref_nm=9450.0, tol=1e-8, body_nm=13500.0,
-             h_nm=50.0 / 3.0):
-    """R(L) for each degree (Sec. 5.1).  Returns a dict with, per degree, the
-    lengths (nm), R, solve statistics and the fitted slope."""
+             h_nm=50.0 / 3.0, matched=False):
+    """R(L) for each degree (Sec. 5.1), electric loss only (J-VIE with the
+    block-circulant preconditioner) or with matched magnetic loss (JM-VIE,
+    ``matched``).  Returns a dict with, per degree, the lengths (nm), R, solve
+    statistics and the fitted slope."""
     t0 = time.perf_counter()
     nb = int(round(body_nm / h_nm))
+    solve = _solve_matched if matched else _solve
     out = {"lengths_nm": list(map(float, lengths_nm)), "r_rt": r_rt, "reference_nm": ref_nm, "tol": tol,
-           "grid_body": [nb, int(round(500 / h_nm)), int(round(200 / h_nm))], "h_nm": h_nm, "degrees": {}}
+           "grid_body": [nb, int(round(500 / h_nm)), int(round(200 / h_nm))], "h_nm": h_nm,
+           "loss": "electric and matched magnetic (JM-VIE)" if matched else "electric (J-VIE)", "degrees": {}}
     for d in degrees:
-        plan, x, info = _solve(workloads.strip_rl(ref_nm, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
+        plan, x, info = solve(workloads.strip_rl(ref_nm, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
         e_ref = vie.vie_axis_field(plan, x, nb)
         plan.close()
         Rs, iters, res = [], [], []
         for L in lengths_nm:
-            plan, x, info = _solve(workloads.strip_rl(L, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
+            plan, x, info = solve(workloads.strip_rl(L, d, r_rt, h_nm=h_nm, length_nm=body_nm), tol)
             Rs.append(vie.vie_reflection(e_ref, vie.vie_axis_field(plan, x, nb)))
             iters.append(info["iterations"])
             res.append(info["residual"])
