@@ -261,9 +261,12 @@ vie_status vie_solve_batch(vie_plan* const* plans, int count, const void* const*
 /* of v scaled to unit RMS, re/im of chi), 4 levels (2x2 average pooling in  */
 /* x and y), 32 channels, 3x3x3 convolutions with zero padding, ReLU,        */
 /* nearest upsampling with additive skips, 6 output channels; BF16 weights,  */
-/* FP32 master weights and Adam.  Training keeps FP32 activations; the      */
-/* inference path runs every convolution as an implicit GEMM on the tcgen05 */
-/* tensor cores with channels-last BF16 activations, FP32 accumulation.     */
+/* FP32 master weights and Adam.  Inference and (by default) training run   */
+/* every convolution on the tcgen05 tensor cores with channels-last BF16    */
+/* activations and FP32 accumulation: forward and input-gradient            */
+/* convolutions as implicit GEMMs over positions, weight gradients as GEMMs */
+/* over positions with 27 taps x 32 x 32 outputs.  VIE_TRAIN_FP32 selects   */
+/* the FP32 SIMT training kernels instead (FP32 activations).               */
 /* The preconditioner is z = v + Net(v): an untrained network (output layer */
 /* at zero) is the identity.                                                */
 /* Parameter layout (FP32): per layer enc0..enc3, dec2, dec1, dec0, out:     */
@@ -299,6 +302,13 @@ vie_status vie_net_apply(vie_net* net, const vie_plan* plan, const void* v_dev,
 vie_status vie_net_accumulate(vie_net* net, const vie_plan* plan, const void* r_dev,
                               const void* e_dev, double* loss, void* stream);
 vie_status vie_net_zero_grad(vie_net* net);
+
+/* Precision of vie_net_accumulate: VIE_TRAIN_TENSOR_BF16 (default; BF16
+ * activations and gradient tensors, tensor cores, FP32 accumulation) or
+ * VIE_TRAIN_FP32 (FP32 activations, SIMT kernels).  Errors: VIE_ERR_INVALID. */
+#define VIE_TRAIN_TENSOR_BF16 0
+#define VIE_TRAIN_FP32 1
+vie_status vie_net_set_training(vie_net* net, int mode);
 
 /* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the accumulated gradients
  * times grad_scale, refresh of the BF16 weights, gradients cleared. */

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     float bias[NP];
 #pragma unroll
-    for (int o = 0; o < NP; ++o) bias[o] = o < a.co ? __ldg(a.bias + o) : 0.f;
+    for (int o = 0; o < NP; ++o) bias[o] = (a.bias && o < a.co) ? __ldg(a.bias + o) : 0.f;
     double inv = 0.0;
     if constexpr (MODE == TC_UNPACK_C64 || MODE == TC_UNPACK_C128) {
       const double ss = *a.sumsq;
@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
           float u[NP];
 #pragma unroll
           for (int o = 0; o < NP; ++o) u[o] = bf16_round(fmaxf(acc[o] + bias[o], 0.f));
+          if (a.out) store_bf16_row<NP>(a.out + vox * NP, u);
           for (int oy = 0; oy < 2; ++oy) {
             const int fy = 2 * y + oy;
             if (fy >= a.d2.ny) continue;
@@ -287,6 +288,32 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv_tc_kernel(const __grid_con
               store_bf16_row<NP>(a.out2 + fv * NP, o8);
             }
           }
+        }
+      } else if constexpr (MODE == TC_LINEAR_F32) {
+        if (valid) {
+          float4* d = reinterpret_cast<float4*>(a.outf + vox * NP);
+#pragma unroll
+          for (int i = 0; i < NP / 4; ++i)
+            d[i] = make_float4(acc[4 * i] + bias[4 * i], acc[4 * i + 1] + bias[4 * i + 1],
+                               acc[4 * i + 2] + bias[4 * i + 2], acc[4 * i + 3] + bias[4 * i + 3]);
+        }
+      } else if constexpr (MODE == TC_GRAD_BF16) {
+        if (valid) {
+          if (a.skip) {
+            const uint4* mk = reinterpret_cast<const uint4*>(a.skip + vox * NP);
+#pragma unroll
+            for (int i = 0; i < NP / 8; ++i) {
+              const uint4 w = mk[i];
+              const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(h2[k]);
+                if (!(f.x > 0.f)) acc[8 * i + 2 * k] = 0.f;
+                if (!(f.y > 0.f)) acc[8 * i + 2 * k + 1] = 0.f;
+              }
+            }
+          }
+          store_bf16_row<NP>(a.out + vox * NP, acc);
         }
       } else {
         if (valid) {
@@ -352,7 +379,7 @@ void tc_pick_tile(Dims d, bool pool, int* bx, int* by) {
 }
 
 static vie_status encode(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
-                         const cuuint64_t* strides, const cuuint32_t* box, int C) {
+                         const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swz) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -360,8 +387,7 @@ static vie_status encode(CUtensorMap* map, const void* base, int rank, const cuu
   }
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -374,14 +400,25 @@ vie_status tc_encode_act(CUtensorMap* map, const __nv_bfloat16* base, int C, Dim
   const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
   const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * d.nx, (cuuint64_t)C * 2 * d.nx * d.ny};
   const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)bx, (cuuint32_t)(by + 2), 1};
-  return encode(map, base, 4, dims, strides, box, C);
+  return encode(map, base, 4, dims, strides, box, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+vie_status tc_encode_planar(CUtensorMap* map, const __nv_bfloat16* base, int rows, Dims d, int nxp) {
+  if (nxp % 64 || rows > 256) {
+    set_error("planar tensor map: row length %d must be a multiple of 64, rows %d at most 256", nxp, rows);
+    return VIE_ERR_INVALID;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)nxp, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)rows};
+  const cuuint64_t strides[3] = {(cuuint64_t)nxp * 2, (cuuint64_t)nxp * 2 * d.ny, (cuuint64_t)nxp * 2 * d.ny * d.nz};
+  const cuuint32_t box[4] = {64, 1, 1, (cuuint32_t)rows};
+  return encode(map, base, 4, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 vie_status tc_encode_w(CUtensorMap* map, const __nv_bfloat16* w, int C, int N) {
   const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)N, 27};
   const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * N};
   const cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)N, 1};
-  return encode(map, w, 3, dims, strides, box, C);
+  return encode(map, w, 3, dims, strides, box, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
 struct DevInfo {
@@ -472,6 +509,9 @@ vie_status tc_conv(const CUtensorMap& A, const CUtensorMap& W, int C, int NP, in
   if (C == 32 && NP == 32 && mode == TC_RELU_BF16) return launch_conv<32, 32, TC_RELU_BF16>(A, W, args, s);
   if (C == 32 && NP == 16 && mode == TC_UNPACK_C64) return launch_conv<32, 16, TC_UNPACK_C64>(A, W, args, s);
   if (C == 32 && NP == 16 && mode == TC_UNPACK_C128) return launch_conv<32, 16, TC_UNPACK_C128>(A, W, args, s);
+  if (C == 32 && NP == 16 && mode == TC_LINEAR_F32) return launch_conv<32, 16, TC_LINEAR_F32>(A, W, args, s);
+  if (C == 16 && NP == 32 && mode == TC_GRAD_BF16) return launch_conv<16, 32, TC_GRAD_BF16>(A, W, args, s);
+  if (C == 32 && NP == 32 && mode == TC_GRAD_BF16) return launch_conv<32, 32, TC_GRAD_BF16>(A, W, args, s);
   set_error("no tensor-core convolution for C=%d NP=%d mode=%d", C, NP, mode);
   return VIE_ERR_INVALID;
 }

@@ -1548,6 +1548,292 @@ __global__ void __launch_bounds__(256) pass_b_jm_kernel(V* __restrict__ work, co
   }
 }
 
+// The JM-VIE pass B with register FFTs (as pass_b_reg_kernel, six
+// components): one CTA per kx, z and y lines of the six components in
+// registers, the N spectrum and the curl spectra of this kx staged in shared
+// memory while the forward transforms run.
+template <typename V, int MY, int MZ, int NY, int NZ>
+__global__ void __launch_bounds__(256) pass_b_reg_jm_kernel(V* __restrict__ work, const V* __restrict__ ghat,
+                                                            const V* __restrict__ chat, PassBGeom g,
+                                                            const V* __restrict__ twyg, const V* __restrict__ twzg,
+                                                            double kappa) {
+  typedef typename real_of<V>::type R;
+  constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
+  constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
+  extern __shared__ unsigned char smem_raw[];
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + MY;
+  V* S1 = twz + MZ;
+  V* S2 = S1 + 6 * MZ * PY;
+  V* Gs = S2 + 6 * g.ny * PZ;          // N spectrum chunk (6 Kz Ky), then the curl chunk (3 Kz Ky)
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ny = NY > 0 ? NY : g.ny, nz = NZ > 0 ? NZ : g.nz;
+  const bool fx = kx > g.Mx - kx;
+  const int kxf = fx ? g.Mx - kx : kx;
+  const int cs = g.Kz * g.Ky;
+  pdl_launch_dependents();
+  for (int i = tid; i < MY; i += nth) __pipeline_memcpy_async(twy + i, twyg + i, sizeof(V));
+  for (int i = tid; i < MZ; i += nth) __pipeline_memcpy_async(twz + i, twzg + i, sizeof(V));
+  __pipeline_commit();
+  {
+    const V* G = ghat + (size_t)kxf * 6 * cs;
+    const V* C = chat + (size_t)kxf * 3 * cs;
+    for (int i = tid; i < 6 * cs; i += nth) __pipeline_memcpy_async(Gs + i, G + i, sizeof(V));
+    for (int i = tid; i < 3 * cs; i += nth) __pipeline_memcpy_async(Gs + 6 * cs + i, C + i, sizeof(V));
+    __pipeline_commit();
+  }
+  pdl_wait();
+  __pipeline_wait_prior(1);
+  __syncthreads();
+  V* slab = work + (size_t)kx * g.NL;
+  for (int line = tid; line < 6 * ny; line += nth) {
+    const int c = line / ny, y = line - c * ny;
+    V a[MZ];
+#pragma unroll
+    for (int z = 0; z < MZ; ++z) a[z] = (z < nz) ? slab[(c * nz + z) * ny + y] : zero_c<V>();
+    reg_fft<V, false, MZ>(a, twz);
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) S1[(c * MZ + kz) * PY + y] = a[kz];
+  }
+  __syncthreads();
+  for (int line = tid; line < 6 * MZ; line += nth) {
+    V a[MY];
+#pragma unroll
+    for (int y = 0; y < MY; ++y) a[y] = (y < ny) ? S1[line * PY + y] : zero_c<V>();
+    reg_fft<V, false, MY>(a, twy);
+#pragma unroll
+    for (int ky = 0; ky < MY; ++ky) S1[line * PY + ky] = a[ky];
+  }
+  __pipeline_wait_prior(0);
+  __syncthreads();
+  {
+    const V* G = Gs;
+    const V* Cc = Gs + 6 * cs;
+    const R kap = (R)kappa;
+    for (int e = tid; e < MZ * MY; e += nth) {
+      const int kz = e / MY, ky = e - kz * MY;
+      const bool fy = ky > MY - ky, fz = kz > MZ - kz;
+      const int kyf = fy ? MY - ky : ky, kzf = fz ? MZ - kz : kz;
+      const int o = kzf * g.Ky + kyf;
+      V gxx = G[o], gyy = G[cs + o], gzz = G[2 * cs + o];
+      V gxy = G[3 * cs + o], gxz = G[4 * cs + o], gyz = G[5 * cs + o];
+      if (fx ^ fy) gxy = scale(gxy, (R)-1);
+      if (fx ^ fz) gxz = scale(gxz, (R)-1);
+      if (fy ^ fz) gyz = scale(gyz, (R)-1);
+      V cx = Cc[o], cy = Cc[cs + o], cz = Cc[2 * cs + o];
+      if (fx) cx = scale(cx, (R)-1);
+      if (fy) cy = scale(cy, (R)-1);
+      if (fz) cz = scale(cz, (R)-1);
+      cx = scale(mul_pi(cx), kap);
+      cy = scale(mul_pi(cy), kap);
+      cz = scale(mul_pi(cz), kap);
+      V u[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) u[c] = S1[(c * MZ + kz) * PY + ky];
+      const V te0 = add(add(mul(gxx, u[0]), mul(gxy, u[1])), mul(gxz, u[2]));
+      const V te1 = add(add(mul(gxy, u[0]), mul(gyy, u[1])), mul(gyz, u[2]));
+      const V te2 = add(add(mul(gxz, u[0]), mul(gyz, u[1])), mul(gzz, u[2]));
+      const V tm0 = add(add(mul(gxx, u[3]), mul(gxy, u[4])), mul(gxz, u[5]));
+      const V tm1 = add(add(mul(gxy, u[3]), mul(gyy, u[4])), mul(gyz, u[5]));
+      const V tm2 = add(add(mul(gxz, u[3]), mul(gyz, u[4])), mul(gzz, u[5]));
+      S1[(0 * MZ + kz) * PY + ky] = sub(te0, sub(mul(cy, u[5]), mul(cz, u[4])));
+      S1[(1 * MZ + kz) * PY + ky] = sub(te1, sub(mul(cz, u[3]), mul(cx, u[5])));
+      S1[(2 * MZ + kz) * PY + ky] = sub(te2, sub(mul(cx, u[4]), mul(cy, u[3])));
+      S1[(3 * MZ + kz) * PY + ky] = add(tm0, sub(mul(cy, u[2]), mul(cz, u[1])));
+      S1[(4 * MZ + kz) * PY + ky] = add(tm1, sub(mul(cz, u[0]), mul(cx, u[2])));
+      S1[(5 * MZ + kz) * PY + ky] = add(tm2, sub(mul(cx, u[1]), mul(cy, u[0])));
+    }
+  }
+  __syncthreads();
+  for (int line = tid; line < 6 * MZ; line += nth) {
+    const int c = line / MZ, kz = line - c * MZ;
+    V a[MY];
+#pragma unroll
+    for (int ky = 0; ky < MY; ++ky) a[ky] = S1[line * PY + ky];
+    reg_fft<V, true, MY>(a, twy);
+#pragma unroll
+    for (int y = 0; y < MY; ++y)
+      if (y < ny) S2[(c * ny + y) * PZ + kz] = a[y];
+  }
+  __syncthreads();
+  for (int line = tid; line < 6 * ny; line += nth) {
+    const int c = line / ny, y = line - c * ny;
+    V a[MZ];
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) a[kz] = S2[line * PZ + kz];
+    reg_fft<V, true, MZ>(a, twz);
+#pragma unroll
+    for (int z = 0; z < MZ; ++z)
+      if (z < nz) slab[(c * nz + z) * ny + y] = a[z];
+  }
+}
+
+template <typename V, int MY, int MZ, int NY, int NZ>
+static vie_status try_pass_b_reg_jm(V* work, const V* ghat, const V* chat, const PassBGeom& g, const V* twy,
+                                    const V* twz, double kappa, cudaStream_t s, bool* done) {
+  *done = false;
+  // complex128 lines of these lengths would spill registers (the six-current
+  // multiply holds 12 spectra): those keep the generic JM pass
+  if constexpr (sizeof(V) == sizeof(float2)) {
+    constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
+    constexpr int PZ = (MZ % 2 == 0) ? MZ + 1 : MZ;
+    const size_t smem = (size_t)(MY + MZ + 6 * MZ * PY + 6 * g.ny * PZ + 9 * g.Kz * g.Ky) * sizeof(V);
+    if (smem > 220 * 1024) return VIE_OK;
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_reg_jm_kernel<V, MY, MZ, NY, NZ>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int lines = 6 * (g.ny > MZ ? g.ny : MZ);
+    int threads = ((lines + 31) / 32) * 32;
+    if (threads > 256) threads = 256;
+    VIE_CUDA_TRY(launch_pdl(pass_b_reg_jm_kernel<V, MY, MZ, NY, NZ>, dim3((unsigned)g.Mx), dim3(threads), smem, s,
+                            work, ghat, chat, g, twy, twz, kappa));
+    *done = true;
+  }
+  return VIE_OK;
+}
+
+// register JM pass B for the compiled cross-sections (the guide's 23 x 11
+// with My 45 or 48 and Mz 24)
+template <typename V>
+static vie_status dispatch_pass_b_reg_jm(V* work, const V* ghat, const V* chat, const PassBGeom& g, const V* twy,
+                                         const V* twz, double kappa, cudaStream_t s, bool* done) {
+  *done = false;
+#define VIE_Y(a, b, c, d)                                  \
+  if (g.My == a && g.Mz == b && g.ny == c && g.nz == d)     \
+    return try_pass_b_reg_jm<V, a, b, c, d>(work, ghat, chat, g, twy, twz, kappa, s, done);
+  VIE_PASS_B_REG_FIXED(VIE_Y)
+#undef VIE_Y
+  return VIE_OK;
+}
+
+// One line of `len` values at a[0], a[stride], ...: gathered into the warp's
+// scratch pair (sa, sb), transformed with Stockham stages by the 32 lanes of
+// the warp (warp-synchronous), scattered back.  Every lane of the warp calls
+// it with the same arguments.
+template <typename V, bool INV>
+__device__ void fft_line_warp(V* a, int stride, V* sa, V* sb, const Radices& rd, const V* tw, int lane) {
+  for (int i = lane; i < rd.len; i += 32) sa[i] = a[(size_t)i * stride];
+  __syncwarp();
+  V* src = sa;
+  V* dst = sb;
+  int s = 1;
+  for (int st = 0; st < rd.nstages; ++st) {
+    const int r = rd.r[st];
+    stockham_stage<V, INV>(src, dst, rd.len, rd.len, 1, r, s, tw, lane, 32);
+    __syncwarp();
+    V* t = src; src = dst; dst = t;
+    s *= r;
+  }
+  for (int i = lane; i < rd.len; i += 32) a[(size_t)i * stride] = src[i];
+  __syncwarp();
+}
+
+// The JM-VIE pass B for planes too large for two plane buffers in shared
+// memory: one plane buffer P[(c Mz + kz) (My + 1) + ky] and, per warp, a
+// scratch pair of the longer line length; each line is transformed by one
+// warp.  z lines (stride My + 1) only for y < ny and, on the way back, only
+// the z < nz outputs are written to the slab.
+template <typename V>
+__global__ void __launch_bounds__(256) pass_b_jm_lines_kernel(V* __restrict__ work, const V* __restrict__ ghat,
+                                                              const V* __restrict__ chat, PassBGeom g, Radices ry,
+                                                              Radices rz, const V* __restrict__ twyg,
+                                                              const V* __restrict__ twzg, double kappa) {
+  typedef typename real_of<V>::type R;
+  pdl_wait();
+  extern __shared__ unsigned char smem_raw[];
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
+  const int ny = g.ny, nz = g.nz, My = g.My, Mz = g.Mz;
+  const int py = My + 1;
+  const int lmax = My > Mz ? My : Mz;
+  V* twy = reinterpret_cast<V*>(smem_raw);
+  V* twz = twy + My;
+  V* P = twz + Mz;
+  V* scr = P + 6 * Mz * py + warp * 2 * lmax;
+  for (int i = tid; i < My; i += nth) twy[i] = twyg[i];
+  for (int i = tid; i < Mz; i += nth) twz[i] = twzg[i];
+  V* slab = work + (size_t)kx * g.NL;
+  for (int e = tid; e < 6 * Mz * py; e += nth) {
+    const int row = e / py, y = e - row * py;   // row = c*Mz + z
+    const int c = row / Mz, z = row - c * Mz;
+    P[e] = (z < nz && y < ny) ? slab[(c * nz + z) * ny + y] : zero_c<V>();
+  }
+  __syncthreads();
+  for (int line = warp; line < 6 * ny; line += nwarps) {
+    const int c = line / ny, y = line - c * ny;
+    fft_line_warp<V, false>(P + (size_t)c * Mz * py + y, py, scr, scr + lmax, rz, twz, lane);
+  }
+  __syncthreads();
+  for (int line = warp; line < 6 * Mz; line += nwarps)
+    fft_line_warp<V, false>(P + (size_t)line * py, 1, scr, scr + lmax, ry, twy, lane);
+  __syncthreads();
+  {
+    const bool fx = kx > g.Mx - kx;
+    const int kxf = fx ? g.Mx - kx : kx;
+    const size_t cs = (size_t)g.Kz * g.Ky;
+    const V* G = ghat + (size_t)kxf * 6 * cs;
+    const V* Cc = chat + (size_t)kxf * 3 * cs;
+    const R kap = (R)kappa;
+    for (int e = tid; e < Mz * My; e += nth) {
+      const int kz = e / My, ky = e - kz * My;
+      const bool fy = ky > My - ky, fz = kz > Mz - kz;
+      const int kyf = fy ? My - ky : ky, kzf = fz ? Mz - kz : kz;
+      const size_t o = (size_t)kzf * g.Ky + kyf;
+      V gxx = G[o], gyy = G[cs + o], gzz = G[2 * cs + o];
+      V gxy = G[3 * cs + o], gxz = G[4 * cs + o], gyz = G[5 * cs + o];
+      if (fx ^ fy) gxy = scale(gxy, (R)-1);
+      if (fx ^ fz) gxz = scale(gxz, (R)-1);
+      if (fy ^ fz) gyz = scale(gyz, (R)-1);
+      V cx = Cc[o], cy = Cc[cs + o], cz = Cc[2 * cs + o];
+      if (fx) cx = scale(cx, (R)-1);
+      if (fy) cy = scale(cy, (R)-1);
+      if (fz) cz = scale(cz, (R)-1);
+      cx = scale(mul_pi(cx), kap);
+      cy = scale(mul_pi(cy), kap);
+      cz = scale(mul_pi(cz), kap);
+      V* q[6];
+      V u[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        q[c] = P + (c * Mz + kz) * py + ky;
+        u[c] = *q[c];
+      }
+      const V te0 = add(add(mul(gxx, u[0]), mul(gxy, u[1])), mul(gxz, u[2]));
+      const V te1 = add(add(mul(gxy, u[0]), mul(gyy, u[1])), mul(gyz, u[2]));
+      const V te2 = add(add(mul(gxz, u[0]), mul(gyz, u[1])), mul(gzz, u[2]));
+      const V tm0 = add(add(mul(gxx, u[3]), mul(gxy, u[4])), mul(gxz, u[5]));
+      const V tm1 = add(add(mul(gxy, u[3]), mul(gyy, u[4])), mul(gyz, u[5]));
+      const V tm2 = add(add(mul(gxz, u[3]), mul(gyz, u[4])), mul(gzz, u[5]));
+      *q[0] = sub(te0, sub(mul(cy, u[5]), mul(cz, u[4])));
+      *q[1] = sub(te1, sub(mul(cz, u[3]), mul(cx, u[5])));
+      *q[2] = sub(te2, sub(mul(cx, u[4]), mul(cy, u[3])));
+      *q[3] = add(tm0, sub(mul(cy, u[2]), mul(cz, u[1])));
+      *q[4] = add(tm1, sub(mul(cz, u[0]), mul(cx, u[2])));
+      *q[5] = add(tm2, sub(mul(cx, u[1]), mul(cy, u[0])));
+    }
+  }
+  __syncthreads();
+  for (int line = warp; line < 6 * Mz; line += nwarps)
+    fft_line_warp<V, true>(P + (size_t)line * py, 1, scr, scr + lmax, ry, twy, lane);
+  __syncthreads();
+  for (int line = warp; line < 6 * ny; line += nwarps) {
+    const int c = line / ny, y = line - c * ny;
+    fft_line_warp<V, true>(P + (size_t)c * Mz * py + y, py, scr, scr + lmax, rz, twz, lane);
+  }
+  __syncthreads();
+  for (int e = tid; e < g.NL; e += nth) {
+    const int y = e % ny, cz = e / ny;
+    const int z = cz % nz, c = cz / nz;
+    slab[e] = P[(c * Mz + z) * py + y];
+  }
+}
+
+size_t jm_pass_b_lines_smem(int My, int Mz, size_t vbytes) {
+  const int lmax = My > Mz ? My : Mz;
+  return (size_t)(My + Mz + 6 * Mz * (My + 1) + 8 * 2 * lmax) * vbytes;
+}
+
 size_t jm_pass_b_smem(int My, int Mz, size_t vbytes) {
   return (size_t)(My + Mz + 2 * 6 * Mz * (My + 1)) * vbytes;
 }
@@ -1559,7 +1845,8 @@ static vie_status run_jm(vie_plan* p, const V* x, V* y, const V* ghat, const V* 
   const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
   const int NL = 6 * ny * nz;
   const size_t smem_b = jm_pass_b_smem(My, Mz, sizeof(V));
-  if (smem_b > 220 * 1024) {
+  const size_t smem_bl = jm_pass_b_lines_smem(My, Mz, sizeof(V));
+  if (smem_bl > 220 * 1024) {
     set_error("the JM-VIE operator needs the 6 x %d x %d plane of one kx in one CTA's shared memory", My, Mz);
     return VIE_ERR_INVALID;
   }
@@ -1599,10 +1886,23 @@ static vie_status run_jm(vie_plan* p, const V* x, V* y, const V* ghat, const V* 
     VIE_LAUNCH_CHECK();
   }
   PassBGeom g{ny, nz, NL, Mx, My, Mz, p->kf[1], p->kf[2]};
-  VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_jm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  pass_b_jm_kernel<V><<<(unsigned)Mx, 256, smem_b, s>>>((V*)p->jm_work, ghat, chat, g, radices_of(p->ax[1]),
-                                                        radices_of(p->ax[2]), twy, twz, p->kappa);
-  VIE_LAUNCH_CHECK();
+  st = dispatch_pass_b_reg_jm<V>((V*)p->jm_work, ghat, chat, g, twy, twz, p->kappa, s, &done);
+  if (st != VIE_OK) return st;
+  if (!done && smem_b <= 220 * 1024) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_jm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    pass_b_jm_kernel<V><<<(unsigned)Mx, 256, smem_b, s>>>((V*)p->jm_work, ghat, chat, g, radices_of(p->ax[1]),
+                                                          radices_of(p->ax[2]), twy, twz, p->kappa);
+    VIE_LAUNCH_CHECK();
+    done = true;
+  }
+  if (!done) {
+    VIE_CUDA_TRY(cudaFuncSetAttribute(pass_b_jm_lines_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_bl));
+    pass_b_jm_lines_kernel<V><<<(unsigned)Mx, 256, smem_bl, s>>>((V*)p->jm_work, ghat, chat, g,
+                                                                 radices_of(p->ax[1]), radices_of(p->ax[2]), twy,
+                                                                 twz, p->kappa);
+    VIE_LAUNCH_CHECK();
+  }
   done = false;
   if (a1) {
     st = dispatch_x3<V>(false, a1, a2, a3, pp, 1, nx, NL, NL, twx, mode, s, &done, 0, NL);

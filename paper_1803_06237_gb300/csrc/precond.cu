@@ -27,7 +27,7 @@
 #include "net.cuh"
 #include "vie_internal.cuh"
 
-namespace vie { struct TcCache; }
+namespace vie { struct TcCache; struct TcTrain; }
 
 struct vie_net {
   int device = 0;
@@ -39,7 +39,10 @@ struct vie_net {
   __nv_bfloat16* wbf = nullptr;   // BF16 copy of the parameters (same offsets)
   __nv_bfloat16* wflip = nullptr; // per layer w'[c][o][26 - t] (backward data)
   __nv_bfloat16* wpack = nullptr; // per layer tensor-core layout wp[tap][o][c] (inference)
+  __nv_bfloat16* wpackf = nullptr;// per layer flipped weights in that layout (tensor-core backward data)
   vie::TcCache* tc = nullptr;     // inference workspace and tensor maps
+  vie::TcTrain* train = nullptr;  // tensor-core training workspace and tensor maps
+  int train_mode = VIE_TRAIN_TENSOR_BF16;
   long step = 0;
   float* ws = nullptr;            // activation workspace
   size_t ws_cap = 0;
@@ -50,28 +53,6 @@ struct vie_net {
 };
 
 namespace vie {
-
-constexpr int kNumLayers = 8;
-struct LayerDef { int ci, co; };
-// enc0..enc3, dec2, dec1, dec0, out
-static const LayerDef kLayerDefs[kNumLayers] = {{8, 32}, {32, 32}, {32, 32}, {32, 32},
-                                               {32, 32}, {32, 32}, {32, 32}, {32, 6}};
-enum { ENC0 = 0, ENC1, ENC2, ENC3, DEC2, DEC1, DEC0, OUTL };
-
-static size_t layer_w_off(int l) {
-  size_t off = 0;
-  for (int i = 0; i < l; ++i) off += (size_t)kLayerDefs[i].co * kLayerDefs[i].ci * 27 + kLayerDefs[i].co;
-  return off;
-}
-static size_t layer_b_off(int l) { return layer_w_off(l) + (size_t)kLayerDefs[l].co * kLayerDefs[l].ci * 27; }
-static size_t total_params() { return layer_w_off(kNumLayers); }
-
-static size_t pack_size(int l) { return (size_t)27 * tc_npad(kLayerDefs[l].co) * tc_cpad(kLayerDefs[l].ci); }
-static size_t pack_off(int l) {
-  size_t off = 0;
-  for (int i = 0; i < l; ++i) off += pack_size(i);
-  return off;
-}
 
 // ---------------------------------------------------------------------------
 // convolution (forward; also the backward-data pass with flipped weights)
@@ -654,8 +635,6 @@ struct TcCache {
   bool wmaps = false;
 };
 
-// level of each layer: enc0..enc3, dec2, dec1, dec0, out
-static const int kLayerLevel[kNumLayers] = {0, 1, 2, 3, 2, 1, 0, 0};
 
 static size_t tc_ws_elems(const Dims* L) {
   size_t t = 16 * L[0].vox() + 32 * L[0].vox();         // X, u_0
@@ -856,7 +835,7 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
   struct { void** p; size_t sz; } a[] = {
       {(void**)&n->master, np * 4}, {(void**)&n->grad, np * 4}, {(void**)&n->m1, np * 4}, {(void**)&n->m2, np * 4},
       {(void**)&n->wbf, np * 2},    {(void**)&n->wflip, np * 2}, {(void**)&n->scal, 8 * sizeof(double)},
-      {(void**)&n->wpack, pack_off(kNumLayers) * 2},
+      {(void**)&n->wpack, pack_off(kNumLayers) * 2}, {(void**)&n->wpackf, packf_off(kNumLayers) * 2},
       {(void**)&n->bad, sizeof(int)}};
   for (auto& e : a) {
     cudaError_t err = cudaMalloc(e.p, e.sz);
@@ -886,9 +865,10 @@ vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
 vie_status vie_net_destroy(vie_net* n) {
   if (!n) return VIE_OK;
   cudaFree(n->master); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2); cudaFree(n->wbf); cudaFree(n->wflip);
-  cudaFree(n->wpack);
+  cudaFree(n->wpack); cudaFree(n->wpackf);
   cudaFree(n->ws); cudaFree(n->partial); cudaFree(n->scal); cudaFree(n->bad);
   tc_free(n->tc);
+  tc_train_free(n->train);
   delete n;
   return VIE_OK;
 }
@@ -922,6 +902,23 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   clear_error();
   if (!n || !p || !r_dev || !e_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
   cudaStream_t s = (cudaStream_t)stream;
+  if (n->train_mode == VIE_TRAIN_TENSOR_BF16) {
+    // flipped, transposed weights of every layer in the tensor-core layout
+    for (int l = 0; l < kNumLayers; ++l) {
+      const int ci = kLayerDefs[l].ci, co = kLayerDefs[l].co;
+      flip_kernel<<<ew_blocks((size_t)co * ci * 27), 256, 0, s>>>(W(n, l), ci, co, n->wflip + layer_w_off(l));
+      const size_t m = packf_size(l);
+      pack_mma_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n->wflip + layer_w_off(l), co, ci,
+                                                                          tc_cpad(co), tc_npad(ci),
+                                                                          n->wpackf + packf_off(l));
+    }
+    VIE_LAUNCH_CHECK();
+    TcTrainParams P{n->wpack, n->wpackf, n->master, n->grad, n->bad};
+    double l = 0.0;
+    vie_status st = tc_train_accumulate(&n->train, P, p->n, p->chi64, (const float2*)r_dev, (const float2*)e_dev, &l, s);
+    if (loss) *loss = l;
+    return st;
+  }
   NetTensors T;
   vie_status st = layout(n, p->n, &T);
   if (st != VIE_OK) return st;
@@ -943,6 +940,17 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   VIE_CUDA_TRY(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s));
   VIE_CUDA_TRY(cudaStreamSynchronize(s));
   if (loss) *loss = h[2] > 0 ? h[1] / h[2] : 0.0;
+  return VIE_OK;
+}
+
+vie_status vie_net_set_training(vie_net* n, int mode) {
+  clear_error();
+  if (!n) { set_error("null argument"); return VIE_ERR_INVALID; }
+  if (mode != VIE_TRAIN_TENSOR_BF16 && mode != VIE_TRAIN_FP32) {
+    set_error("training mode must be VIE_TRAIN_TENSOR_BF16 or VIE_TRAIN_FP32");
+    return VIE_ERR_INVALID;
+  }
+  n->train_mode = mode;
   return VIE_OK;
 }
 

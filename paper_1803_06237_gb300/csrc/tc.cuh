@@ -94,16 +94,16 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 
 // ---- MMA -------------------------------------------------------------------
 // Shared-memory matrix descriptor of a K-major operand tile whose rows are
-// `row_bytes` long (32 or 64 bytes, one row per M or N index), written by a
-// TMA load with the matching swizzle: 8-row groups are 8 * row_bytes apart
-// (stride byte offset), the leading byte offset is unused for swizzled
-// K-major tiles (encoded as 1), descriptor version 1, swizzle code 4 (64 B)
-// or 6 (32 B) in bits 61-63.
+// `row_bytes` long (32, 64 or 128 bytes, one row per M or N index), written
+// by a TMA load with the matching swizzle: 8-row groups are 8 * row_bytes
+// apart (stride byte offset), the leading byte offset is unused for
+// swizzled K-major tiles (encoded as 1), descriptor version 1, swizzle code
+// 2 (128 B), 4 (64 B) or 6 (32 B) in bits 61-63.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int row_bytes) {
   const uint64_t start = (saddr & 0x3FFFFu) >> 4;
   const uint64_t lbo = 1;
   const uint64_t sbo = (uint64_t)(8 * row_bytes) >> 4;
-  const uint64_t swz = row_bytes == 64 ? 4 : 6;
+  const uint64_t swz = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);
   return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (swz << 61);
 }
 

@@ -86,6 +86,7 @@ _SIGNATURES = {
     "vie_net_apply": ([_P, _P, _P, _P, _I, _P], _I),
     "vie_net_accumulate": ([_P, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
     "vie_net_zero_grad": ([_P], _I),
+    "vie_net_set_training": ([_P, _I], _I),
     "vie_net_adam_step": ([_P, ctypes.c_float, ctypes.c_float, _P], _I),
     "vie_net_status": ([_P, ctypes.POINTER(_I), _I], _I),
     "vie_circulant_create": ([_P, _I, ctypes.POINTER(_P), _P], _I),
@@ -511,6 +512,14 @@ def vie_net_accumulate(net: Net, plan: Plan, r, e, stream=None) -> float:
                                      ctypes.c_void_p(e.data_ptr()), ctypes.byref(loss), _stream_handle(stream)),
            "vie_net_accumulate")
     return loss.value
+
+
+VIE_TRAIN_TENSOR_BF16 = 0
+VIE_TRAIN_FP32 = 1
+
+
+def vie_net_set_training(net: Net, mode: int):
+    _check(load().vie_net_set_training(net.handle, int(mode)), "vie_net_set_training")
 
 
 def vie_net_zero_grad(net: Net):

@@ -43,7 +43,9 @@ def _plan(grid, seed, h=0.03, eps_bg=2.085):
     return plan, Me, Mm
 
 
-@pytest.mark.parametrize("grid", [(5, 4, 3), (17, 6, 5), (33, 9, 4)])
+# (6, 23, 11): the strip cross-section, circulant 45 x 24, whose complex64
+# pass B runs the register kernel with the cross-section compiled in
+@pytest.mark.parametrize("grid", [(5, 4, 3), (17, 6, 5), (33, 9, 4), (6, 23, 11)])
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_jm_operator_and_rhs_match_oracle(grid, dtype):
     plan, Me, Mm = _plan(grid, 41)
@@ -72,6 +74,23 @@ def test_jm_operator_and_rhs_match_oracle(grid, dtype):
     torch.cuda.synchronize()
     b_ref = jm.rhs_from_source(Gh, Ch, grid, Me, Mm, ue, kappa).ravel()
     assert rel_l2(b.cpu().numpy().astype(np.complex128), b_ref) <= TOL[dtype]
+    plan.close()
+
+
+# planes whose two-buffer pass B does not fit in shared memory (complex128
+# 60 x 24, complex64 100 x 24): the one-buffer kernel with a line per warp
+@pytest.mark.parametrize("grid,dtype", [((3, 30, 12), torch.complex128), ((3, 50, 12), torch.complex64)])
+def test_jm_large_plane_matches_oracle(grid, dtype):
+    plan, Me, Mm = _plan(grid, 44)
+    kappa = plan.info()["kappa"]
+    Gh, Ch = _oracle_spectra(grid, kappa)
+    u = np.concatenate([workloads.random_currents(grid, seed=45), workloads.random_currents(grid, seed=46)])
+    x = torch.from_numpy(u.ravel()).to(dtype).cuda()
+    y = torch.empty_like(x)
+    vie.vie_jm_matvec(plan, x, y)
+    torch.cuda.synchronize()
+    y_ref = jm.matvec(Gh, Ch, grid, Me, Mm, u, kappa).ravel()
+    assert rel_l2(y.cpu().numpy().astype(np.complex128), y_ref) <= TOL[dtype]
     plan.close()
 
 

@@ -128,9 +128,25 @@ def test_forward_matches_oracle(grid, dtype):
         assert np.linalg.norm(dz - dz_ref) / np.linalg.norm(dz_ref) < 2e-2
 
 
-def test_gradients_match_oracle():
-    grid = (21, 9, 5)
+# Tensor-core training stores every activation and every gradient tensor in
+# BF16 (relative rounding <= 2^-9, rms ~2^-9 / sqrt(3) = 0.11 %); a gradient
+# of the first layers passes through ~16 such roundings (8 forward, 8
+# backward), sqrt(16) x 0.11 % = 0.45 % if independent.  Bound: 2e-2 per
+# layer (relative L2), and the loss within 1 %.
+TC_GRAD_TOL = 2e-2
+
+
+@pytest.mark.parametrize("mode,grid,tol,ltol", [
+    (vie.VIE_TRAIN_FP32, (21, 9, 5), 2e-3, 1e-5),
+    (vie.VIE_TRAIN_TENSOR_BF16, (21, 9, 5), TC_GRAD_TOL, 1e-2),
+    (vie.VIE_TRAIN_TENSOR_BF16, (130, 23, 11), TC_GRAD_TOL, 1e-2)])
+def test_gradients_match_oracle(mode, grid, tol, ltol):
+    """Every weight and bias gradient of one sample against the FP64 oracle's
+    backward pass (same BF16 weights): FP32 training kernels, and the
+    tensor-core path on a grid of one tile and on one of several x chunks
+    and tiles with ragged edges at every level."""
     plan, chi, net = _setup(grid, 7)
+    vie.vie_net_set_training(net, mode)
     p = _oracle_params(vie.vie_net_get_params(net))
     nx, ny, nz = grid
     r = workloads.random_currents(grid, seed=8).astype(np.complex64)
@@ -147,19 +163,25 @@ def test_gradients_match_oracle():
     l_ref = float(np.sum((y - E) ** 2) / den)
     dy = 2.0 * (y - E) / den
     g, _ = cn.backward(p, cache, dy)
-    assert abs(loss - l_ref) <= 1e-5 * l_ref
+    assert abs(loss - l_ref) <= ltol * l_ref, (loss, l_ref)
     off = 0
+    worst = 0.0
     for name, ci, co in cn.LAYERS:
         for part, size in (("w", co * ci * 27), ("b", co)):
             a = g_gpu[off:off + size].astype(np.float64)
             b = g[f"{name}.{part}"].ravel()
             off += size
-            assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-12, (name, part)
+            err = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30)
+            worst = max(worst, err)
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b) + 1e-12, (name, part, err)
+    print(f"mode {mode} grid {grid}: worst relative gradient error {worst:.2e}")
 
 
-def test_adam_step_reduces_the_loss():
+@pytest.mark.parametrize("mode", [vie.VIE_TRAIN_TENSOR_BF16, vie.VIE_TRAIN_FP32])
+def test_adam_step_reduces_the_loss(mode):
     grid = (16, 8, 3)
     plan, chi, net = _setup(grid, 11)
+    vie.vie_net_set_training(net, mode)
     r = torch.from_numpy(workloads.random_currents(grid, seed=12).astype(np.complex64).ravel()).cuda()
     e = torch.from_numpy(workloads.random_currents(grid, seed=13).astype(np.complex64).ravel()).cuda()
     losses = []
