@@ -844,6 +844,87 @@ def studies(args):
         print(json.dumps({"study": "bragg_transmission", **out}), flush=True)
 
 
+def train_study(n_problems: int, epochs: int):
+    """The learned preconditioner at the benchmark's training size: pairs from
+    plain solves of n_problems seeded random strips and bends (160 x 40 x 11,
+    widths 350-550 nm, up to 20 pairs each: 1000 problems give ~20k pairs),
+    `epochs` passes of Adam (mini-batches of 16) with the tensor-core
+    training kernels, then on held-out problems: the mean loss against the
+    identity's, and flexible GMRES(30) to 1e-6 with the judged network
+    against plain GMRES(30), on five random guides and on the 600 x 23 x 11
+    benchmark guide."""
+    import torch
+
+    from paper_1803_06237_gb300 import build, learned, vie, workloads
+    build.build_library()
+    vie.load()
+    t0 = time.perf_counter()
+    pairs, solver = learned.make_pairs_many(range(10000, 10000 + n_problems))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    held, held_solver = learned.make_pairs_many(range(90000, 90020))
+    net = vie.vie_net_create(seed=1)
+    steps = epochs * len(pairs) // 16
+    per_epoch = max(1, len(pairs) // 16)
+    t2 = time.perf_counter()
+    losses = learned.train(net, pairs, steps=steps, lr=1e-3, batch=16)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    out = {"study": "learned_preconditioner_training", "problems": n_problems, "pairs": len(pairs),
+           "grid": [160, 40, 11], "epochs": epochs, "adam_steps": steps, "batch": 16,
+           "pair_generation_s": t1 - t0, "train_s": t3 - t2,
+           "ms_per_sample": (t3 - t2) * 1e3 / (steps * 16),
+           "loss_per_epoch": [float(np.mean(losses[i * per_epoch:(i + 1) * per_epoch])) for i in range(epochs)],
+           "identity_loss_train": learned.identity_loss(pairs),
+           "held_out": {"pairs": len(held), "identity_loss": learned.identity_loss(held),
+                        "network_loss": learned.mean_loss(net, held)}}
+    del pairs
+    solves = []
+    for seed in list(range(90000, 90005)) + [None]:
+        wl = workloads.waveguide() if seed is None else workloads.random_guide(seed)
+        plan, b = learned.setup_problem(wl)
+        row = {"problem": "guide_600x23x11" if seed is None else f"random_guide_{seed}"}
+        for name, pc in (("plain", False), ("learned", True)):
+            vie.vie_set_preconditioner_net(plan, net if pc else None)
+            x = torch.zeros_like(b)
+            info = vie.vie_solve(plan, b, x, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=30, use_preconditioner=pc,
+                                 raise_on_not_converged=False)
+            row[name] = {"iterations": info["iterations"], "ms": info["time_ms"], "converged": info["converged"],
+                         "dropped": bool(info["fallback"])}
+        vie.vie_set_preconditioner_net(plan, None)
+        plan.close()
+        solves.append(row)
+    out["solves"] = solves
+    print(json.dumps(out), flush=True)
+
+
+def profile_train(reps: int):
+    """`reps` training samples (forward, loss, backward) of a network with
+    random parameters on a random 160 x 40 x 11 guide, tensor-core path: a
+    short launch sequence for kernel launch lists.  Prints the time per
+    sample (CUDA events)."""
+    import torch
+
+    from paper_1803_06237_gb300 import build, learned, vie, workloads
+    build.build_library()
+    vie.load()
+    plan, _ = learned.setup_problem(workloads.random_guide(3))
+    n3 = 3 * plan.n_vox
+    g = torch.Generator(device="cuda").manual_seed(5)
+    r = torch.randn(n3, dtype=torch.complex64, device="cuda", generator=g)
+    e = torch.randn(n3, dtype=torch.complex64, device="cuda", generator=g)
+    net = vie.vie_net_create(seed=1)
+    vie.vie_net_accumulate(net, plan, r, e)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        vie.vie_net_accumulate(net, plan, r, e)
+    ev1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_train": reps, "ms_per_sample": ev0.elapsed_time(ev1) / max(reps, 1),
+                      "status": vie.vie_net_status(net)}))
+
+
 def profile_solve(iters: int):
     """One mixed-precision solve of the benchmark guide capped at `iters`
     Arnoldi steps (restart 30), run twice: a short, fixed launch sequence for
@@ -964,6 +1045,8 @@ def main():
                     help="only build the ring resonator's plan and apply the operator (for kernel launch lists)")
     ap.add_argument("--profile-jm", type=int, default=0,
                     help="only run JM-VIE operator applications on the guide (for kernel launch lists)")
+    ap.add_argument("--profile-train", type=int, default=0,
+                    help="only run tensor-core training samples (for kernel launch lists)")
     ap.add_argument("--profile-net", type=int, default=0,
                     help="only run network applications (for kernel launch lists)")
     ap.add_argument("--no-net", action="store_true")
@@ -977,17 +1060,27 @@ def main():
                     help="only run the absorber-length study of Sec. 5.1 (R(L) and slopes) and print it")
     ap.add_argument("--bragg-sweep", action="store_true",
                     help="only run the Bragg-grating transmission spectrum of Sec. 5.2 and print it")
+    ap.add_argument("--train-study", type=int, default=0, metavar="PROBLEMS",
+                    help="only train the learned preconditioner on pairs from PROBLEMS random guides and "
+                         "measure it on held-out problems")
+    ap.add_argument("--train-epochs", type=int, default=3)
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run a capped mixed solve (for kernel launch lists)")
     args = ap.parse_args()
     if args.rl_sweep or args.bragg_sweep:
         studies(args)
         return
+    if args.train_study:
+        train_study(args.train_study, args.train_epochs)
+        return
     if args.profile_solve:
         profile_solve(args.profile_solve)
         return
     if args.profile_net:
         profile_net(args.profile_net)
+        return
+    if args.profile_train:
+        profile_train(args.profile_train)
         return
     if args.profile_jm:
         profile_jm(args.profile_jm)

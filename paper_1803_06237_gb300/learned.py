@@ -79,6 +79,49 @@ def make_pairs(seeds, grid=(160, 40, 11), restart=20, cycles=12, tol=1e-6):
     return pairs
 
 
+def make_pairs_many(seeds, grid=(160, 40, 11), restart=10, cycles=20, tol=1e-6):
+    """make_pairs for many problems with bounded device memory: one plan
+    solves the problems in turn (its permittivity reset for each, so one
+    solver workspace serves all), and each problem keeps a clone of it that
+    holds only its contrast and operator workspace, which the network reads
+    chi from during training.  Returns (pairs, solver plan)."""
+    import torch
+    pairs = []
+    solver = None
+    for seed in seeds:
+        wl = workloads.random_guide(seed, *grid)
+        if solver is None:
+            solver, b = setup_problem(wl)
+        else:
+            vie.vie_set_permittivity(solver, wl.eps, _absorbers(wl))
+            src = torch.from_numpy(np.ascontiguousarray(wl.src.ravel())).cuda()
+            b = torch.empty_like(src)
+            vie.vie_rhs_from_source(solver, src, b)
+        keep = vie.vie_plan_clone(solver)
+        vie.vie_set_permittivity(keep, wl.eps, _absorbers(wl))
+        xs = torch.zeros_like(b)
+        vie.vie_solve(solver, b, xs, tol, mode=vie.VIE_SOLVE_MIXED, restart=30, raise_on_not_converged=False)
+        x = torch.zeros_like(b)
+        for _ in range(cycles):
+            vie.vie_solve(solver, b, x, tol, mode=vie.VIE_SOLVE_MIXED, restart=restart, max_iters=restart,
+                          max_outer=1, x0_given=True, raise_on_not_converged=False)
+            e = (xs - x).to(torch.complex64)
+            if torch.linalg.vector_norm(e).item() <= 1e-5 * torch.linalg.vector_norm(xs).item():
+                break
+            r = torch.empty_like(e)
+            vie.vie_matvec(keep, e, r)
+            pairs.append(Pair(keep, r, e))
+    return pairs, solver
+
+
+def mean_loss(net, pairs) -> float:
+    """Mean loss of the network over pairs (gradients are accumulated and
+    then cleared)."""
+    vals = [vie.vie_net_accumulate(net, p.plan, p.r, p.e) for p in pairs]
+    vie.vie_net_zero_grad(net)
+    return float(np.mean(vals))
+
+
 def identity_loss(pairs) -> float:
     """Mean of |e - r|^2 / |e|^2 over the pairs: the loss of z = r."""
     import torch
