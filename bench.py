@@ -542,7 +542,7 @@ def solve_section(plan, wl, absorbers, args):
                            "identity_loss": learned.identity_loss(pairs),
                            "pair_generation_s": t1 - t0, "train_s": t2 - t1,
                            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
-                           "net_apply_ms": net_ms}
+                           "net_apply_ms": net_ms, "precision": "bf16 tensor cores, fp32 accumulation"}
         vie.vie_set_preconditioner_net(plan, None)
     if args.circulant:
         out["circulant"] = circulant_section(plan, b, args)
@@ -837,6 +837,9 @@ def studies(args):
             out = sweeps.rl_sweep(short, degrees=(1, 2), r_rt=1e-25, ref_nm=9000.0, tol=1e-8, body_nm=3000.0,
                                   matched=matched)
             print(json.dumps({"study": "absorber_length_matching", **out}), flush=True)
+    if args.microring_sweep:
+        out = sweeps.microring_sweep(count=args.microring_sweep)
+        print(json.dumps({"study": "microring_transmission", **out}), flush=True)
     if args.bragg_sweep:
         lams = [1.52 + 0.0005 * i for i in range(101)]
         out = sweeps.bragg_sweep(lams, periods=100, tol=1e-6, batch=8)
@@ -844,22 +847,27 @@ def studies(args):
         print(json.dumps({"study": "bragg_transmission", **out}), flush=True)
 
 
-def train_study(n_problems: int, epochs: int):
-    """The learned preconditioner at the benchmark's training size: pairs from
-    plain solves of n_problems seeded random strips and bends (160 x 40 x 11,
-    widths 350-550 nm, up to 20 pairs each: 1000 problems give ~20k pairs),
-    `epochs` passes of Adam (mini-batches of 16) with the tensor-core
-    training kernels, then on held-out problems: the mean loss against the
-    identity's, and flexible GMRES(30) to 1e-6 with the judged network
-    against plain GMRES(30), on five random guides and on the 600 x 23 x 11
-    benchmark guide."""
+def train_study(n_pairs: int, epochs: int):
+    """The learned preconditioner at the benchmark's training size: at least
+    n_pairs pairs from plain solves of seeded random strips and bends
+    (160 x 40 x 11, widths 350-550 nm, up to 20 pairs per problem, problems
+    added 100 at a time), `epochs` passes of Adam (mini-batches of 16) with
+    the tensor-core training kernels, then on held-out problems: the mean
+    loss against the identity's, and flexible GMRES(30) to 1e-6 with the
+    judged network against plain GMRES(30), on five random guides and on the
+    600 x 23 x 11 benchmark guide."""
     import torch
 
     from paper_1803_06237_gb300 import build, learned, vie, workloads
     build.build_library()
     vie.load()
     t0 = time.perf_counter()
-    pairs, solver = learned.make_pairs_many(range(10000, 10000 + n_problems))
+    pairs, solvers, n_problems = [], [], 0
+    while len(pairs) < n_pairs:
+        more, solver = learned.make_pairs_many(range(10000 + n_problems, 10000 + n_problems + 100))
+        pairs += more
+        solvers.append(solver)
+        n_problems += 100
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     held, held_solver = learned.make_pairs_many(range(90000, 90020))
@@ -1060,14 +1068,16 @@ def main():
                     help="only run the absorber-length study of Sec. 5.1 (R(L) and slopes) and print it")
     ap.add_argument("--bragg-sweep", action="store_true",
                     help="only run the Bragg-grating transmission spectrum of Sec. 5.2 and print it")
-    ap.add_argument("--train-study", type=int, default=0, metavar="PROBLEMS",
-                    help="only train the learned preconditioner on pairs from PROBLEMS random guides and "
+    ap.add_argument("--microring-sweep", type=int, default=0, metavar="WAVELENGTHS",
+                    help="only solve the ring resonator at WAVELENGTHS wavelengths in [1.54, 1.56] um in one batch")
+    ap.add_argument("--train-study", type=int, default=0, metavar="PAIRS",
+                    help="only train the learned preconditioner on at least PAIRS pairs from random guides and "
                          "measure it on held-out problems")
     ap.add_argument("--train-epochs", type=int, default=3)
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run a capped mixed solve (for kernel launch lists)")
     args = ap.parse_args()
-    if args.rl_sweep or args.bragg_sweep:
+    if args.rl_sweep or args.bragg_sweep or args.microring_sweep:
         studies(args)
         return
     if args.train_study:

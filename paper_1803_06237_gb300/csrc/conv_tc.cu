@@ -403,13 +403,15 @@ vie_status tc_encode_act(CUtensorMap* map, const __nv_bfloat16* base, int C, Dim
   return encode(map, base, 4, dims, strides, box, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-vie_status tc_encode_planar(CUtensorMap* map, const __nv_bfloat16* base, int rows, Dims d, int nxp) {
-  if (nxp % 64 || rows > 256) {
-    set_error("planar tensor map: row length %d must be a multiple of 64, rows %d at most 256", nxp, rows);
+vie_status tc_encode_planar(CUtensorMap* map, const __nv_bfloat16* base, int rows, Dims d, int nxp,
+                            size_t row_stride) {
+  if (nxp % 64 || rows > 256 || row_stride < (size_t)nxp * d.ny * d.nz || row_stride % 8) {
+    set_error("planar tensor map: row length %d must be a multiple of 64, rows %d at most 256, row stride %zu",
+              nxp, rows, row_stride);
     return VIE_ERR_INVALID;
   }
   const cuuint64_t dims[4] = {(cuuint64_t)nxp, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)rows};
-  const cuuint64_t strides[3] = {(cuuint64_t)nxp * 2, (cuuint64_t)nxp * 2 * d.ny, (cuuint64_t)nxp * 2 * d.ny * d.nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)nxp * 2, (cuuint64_t)nxp * 2 * d.ny, (cuuint64_t)row_stride * 2};
   const cuuint32_t box[4] = {64, 1, 1, (cuuint32_t)rows};
   return encode(map, base, 4, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }

@@ -93,10 +93,12 @@ void tc_pick_tile(Dims d, bool pool, int* bx, int* by);
 // {C, bx, by + 2, 1}; packed weights [27][N][C] with the box {C, N, 1}.
 vie_status tc_encode_act(CUtensorMap* map, const __nv_bfloat16* base, int C, Dims d, int bx, int by);
 vie_status tc_encode_w(CUtensorMap* map, const __nv_bfloat16* w, int C, int N);
-// Planar BF16 tensor [rows][nz][ny][nxp] (nxp a multiple of 64) with the
-// box {64, 1, 1, rows} and the 128-byte swizzle: one K-major operand tile of
+// Planar BF16 tensor [rows][nz][ny][nxp] (nxp a multiple of 64, rows
+// row_stride elements apart, row_stride >= nz ny nxp) with the box
+// {64, 1, 1, rows} and the 128-byte swizzle: one K-major operand tile of
 // `rows` rows by 64 positions along x (the weight-gradient GEMM).
-vie_status tc_encode_planar(CUtensorMap* map, const __nv_bfloat16* base, int rows, Dims d, int nxp);
+vie_status tc_encode_planar(CUtensorMap* map, const __nv_bfloat16* base, int rows, Dims d, int nxp,
+                            size_t row_stride);
 
 // One 3x3x3 convolution (zero padding) as an implicit GEMM on the tensor
 // cores: M = the 128 input positions of a tile, N = 3 x the output channels

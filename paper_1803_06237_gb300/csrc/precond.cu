@@ -484,12 +484,21 @@ static vie_status layout(vie_net* net, const int n[3], NetTensors* T) {
   return VIE_OK;
 }
 
+// The tensor-core layouts of the BF16 weights, refreshed whenever they
+// change: wpack (forward) and wpackf (the flipped transpose, for the input
+// gradients of tensor-core training).
 static vie_status pack_weights(vie_net* net, cudaStream_t s) {
   for (int l = 0; l < kNumLayers; ++l) {
+    const int ci = kLayerDefs[l].ci, co = kLayerDefs[l].co;
     const size_t n = pack_size(l);
     pack_mma_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        net->wbf + layer_w_off(l), kLayerDefs[l].ci, kLayerDefs[l].co, tc_cpad(kLayerDefs[l].ci),
-        tc_npad(kLayerDefs[l].co), net->wpack + pack_off(l));
+        net->wbf + layer_w_off(l), ci, co, tc_cpad(ci), tc_npad(co), net->wpack + pack_off(l));
+    flip_kernel<<<ew_blocks((size_t)co * ci * 27), 256, 0, s>>>(net->wbf + layer_w_off(l), ci, co,
+                                                                net->wflip + layer_w_off(l));
+    const size_t m = packf_size(l);
+    pack_mma_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(net->wflip + layer_w_off(l), co, ci,
+                                                                        tc_cpad(co), tc_npad(ci),
+                                                                        net->wpackf + packf_off(l));
   }
   VIE_LAUNCH_CHECK();
   return VIE_OK;
@@ -903,16 +912,6 @@ vie_status vie_net_accumulate(vie_net* n, const vie_plan* p, const void* r_dev, 
   if (!n || !p || !r_dev || !e_dev) { set_error("null argument"); return VIE_ERR_INVALID; }
   cudaStream_t s = (cudaStream_t)stream;
   if (n->train_mode == VIE_TRAIN_TENSOR_BF16) {
-    // flipped, transposed weights of every layer in the tensor-core layout
-    for (int l = 0; l < kNumLayers; ++l) {
-      const int ci = kLayerDefs[l].ci, co = kLayerDefs[l].co;
-      flip_kernel<<<ew_blocks((size_t)co * ci * 27), 256, 0, s>>>(W(n, l), ci, co, n->wflip + layer_w_off(l));
-      const size_t m = packf_size(l);
-      pack_mma_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n->wflip + layer_w_off(l), co, ci,
-                                                                          tc_cpad(co), tc_npad(ci),
-                                                                          n->wpackf + packf_off(l));
-    }
-    VIE_LAUNCH_CHECK();
     TcTrainParams P{n->wpack, n->wpackf, n->master, n->grad, n->bad};
     double l = 0.0;
     vie_status st = tc_train_accumulate(&n->train, P, p->n, p->chi64, (const float2*)r_dev, (const float2*)e_dev, &l, s);

@@ -12,14 +12,15 @@
 //                    of the layer's input where that input is a ReLU output;
 //   weight gradient  dW[t][o][c] = sum_p dPre[p][o] In[p + t - 1][c], a GEMM
 //                    over the positions p (dw_tc_kernel below);
-//   bias gradient    db[o] = sum_p dPre[p][o];
+//   bias gradient    db[o] = sum_p dPre[p][o] (summed while the GEMM operands
+//                    are written);
 // and element-wise steps for the upsampling (sum of the 2 x 2 children) and
 // the pooling (a quarter, half or all of the parent's gradient), each with
 // the ReLU mask of the tensor it produces the gradient of.
 //
 // The weight-gradient GEMM: for a chunk of 64 positions along x of one
 // (z, y) row, A is 128 x 64 (rows dx * 32 + o: the output gradient shifted
-// by dx - 1 along x, written planar by dw_shift_planar_kernel) and, for each
+// by dx - 1 along x, written planar by dw_operands_kernel) and, for each
 // of the nine (dz, dy) taps, B is C x 64 (the layer input of row
 // (z + dz - 1, y + dy - 1), planar, the TMA zero-filling rows outside the
 // grid).  Nine accumulators of 128 x C in tensor memory collect a CTA's
@@ -36,54 +37,65 @@ namespace vie {
 constexpr int kDwChunk = 64;       // positions along x per K chunk
 constexpr int kDwMaxStages = 8;
 constexpr int kDwThreads = 192;
+constexpr int kDwMinChunks = 4;    // chunks per CTA at least, where the level allows
 
 // ---------------------------------------------------------------------------
 // planar operands of the weight-gradient GEMM
 // ---------------------------------------------------------------------------
-// A[dx * 32 + o][z][y][x] = g[z][y][x - dx + 1][o] for dx < 3, o < NPo and
-// 0 <= x - dx + 1 < nx, x < nx; 0 elsewhere (rows 96..127 included).  One
-// block per (64-position chunk, y, z).
-__global__ void __launch_bounds__(256) dw_shift_planar_kernel(const __nv_bfloat16* __restrict__ g, int NPo, Dims d,
-                                                              int nxp, __nv_bfloat16* __restrict__ A) {
+// The two operands in one launch (grid.x = 2 x the chunks per row; blocks
+// below nxc write A, the others B), one block per (64-position chunk, y, z);
+// rows are `plane` elements apart (the level-0 plane at every level):
+//   A[dx * 32 + o][z][y][x] = g[z][y][x - dx + 1][o] for dx < 3, o < NPo and
+//     0 <= x - dx + 1 < nx, x < nx; 0 elsewhere (rows 96..127 are zeroed
+//     once when the buffer is laid out and never written);
+//   B[c][z][y][x] = in[z][y][x][c] for x < nx, 0 for nx <= x < nxp;
+// and the A blocks add their chunk's sum of g over positions to the bias
+// gradient gb[o] (o < co).
+__global__ void __launch_bounds__(256) dw_operands_kernel(const __nv_bfloat16* __restrict__ g, int NPo, int co,
+                                                          const __nv_bfloat16* __restrict__ in, int C, Dims d,
+                                                          int nxp, int nxc, size_t plane, __nv_bfloat16* __restrict__ A,
+                                                          __nv_bfloat16* __restrict__ B, float* __restrict__ gb) {
   __shared__ __nv_bfloat16 t[kDwChunk + 2][33];
-  const int x0 = blockIdx.x * kDwChunk, y = blockIdx.y, z = blockIdx.z;
+  __shared__ float bsum[8][33];
+  const bool isA = (int)blockIdx.x < nxc;
+  const int x0 = (isA ? blockIdx.x : blockIdx.x - nxc) * kDwChunk, y = blockIdx.y, z = blockIdx.z;
   const size_t row = (size_t)z * d.ny + y;
-  for (int i = threadIdx.x; i < (kDwChunk + 2) * 32; i += blockDim.x) {
-    const int j = i >> 5, o = i & 31;
-    const int x = x0 - 1 + j;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-    if (o < NPo && x >= 0 && x < d.nx) v = g[(row * d.nx + x) * NPo + o];
-    t[j][o] = v;
-  }
-  __syncthreads();
-  const size_t plane = (size_t)d.nz * d.ny * nxp;
   const size_t base = row * nxp + x0;
-  for (int i = threadIdx.x; i < 128 * kDwChunk; i += blockDim.x) {
-    const int r = i / kDwChunk, xl = i - r * kDwChunk;
-    const int dx = r >> 5, o = r & 31;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-    if (dx < 3 && x0 + xl < d.nx) v = t[xl - dx + 2][o];
-    A[r * plane + base + xl] = v;
-  }
-}
-
-// B[c][z][y][x] = in[z][y][x][c] for x < nx, 0 for nx <= x < nxp.
-__global__ void __launch_bounds__(256) dw_planar_kernel(const __nv_bfloat16* __restrict__ in, int C, Dims d, int nxp,
-                                                        __nv_bfloat16* __restrict__ B) {
-  __shared__ __nv_bfloat16 t[kDwChunk][33];
-  const int x0 = blockIdx.x * kDwChunk, y = blockIdx.y, z = blockIdx.z;
-  const size_t row = (size_t)z * d.ny + y;
-  for (int i = threadIdx.x; i < kDwChunk * C; i += blockDim.x) {
-    const int j = i / C, c = i - j * C;
-    const int x = x0 + j;
-    t[j][c] = x < d.nx ? in[(row * d.nx + x) * C + c] : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  const size_t plane = (size_t)d.nz * d.ny * nxp;
-  const size_t base = row * nxp + x0;
-  for (int i = threadIdx.x; i < C * kDwChunk; i += blockDim.x) {
-    const int c = i / kDwChunk, xl = i - c * kDwChunk;
-    B[c * plane + base + xl] = t[xl][c];
+  if (isA) {
+    float acc = 0.f;   // thread (j, o) sums g over its positions j = tid >> 5, + 8, ...
+    for (int i = threadIdx.x; i < (kDwChunk + 2) * 32; i += blockDim.x) {
+      const int j = i >> 5, o = i & 31;
+      const int x = x0 - 1 + j;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (o < NPo && x >= 0 && x < d.nx) v = g[(row * d.nx + x) * NPo + o];
+      t[j][o] = v;
+      if (j >= 1 && j <= kDwChunk) acc += __bfloat162float(v);   // positions x0 .. x0 + 63 of this chunk
+    }
+    bsum[threadIdx.x >> 5][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float sum = 0.f;
+      for (int k = 0; k < 8; ++k) sum += bsum[k][threadIdx.x];
+      if (threadIdx.x < co) atomicAdd(gb + threadIdx.x, sum);
+    }
+    for (int i = threadIdx.x; i < 96 * kDwChunk; i += blockDim.x) {
+      const int r = i / kDwChunk, xl = i - r * kDwChunk;
+      const int dx = r >> 5, o = r & 31;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (x0 + xl < d.nx) v = t[xl - dx + 2][o];
+      A[r * plane + base + xl] = v;
+    }
+  } else {
+    for (int i = threadIdx.x; i < kDwChunk * C; i += blockDim.x) {
+      const int j = i / C, c = i - j * C;
+      const int x = x0 + j;
+      t[j][c] = x < d.nx ? in[(row * d.nx + x) * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C * kDwChunk; i += blockDim.x) {
+      const int c = i / kDwChunk, xl = i - c * kDwChunk;
+      B[c * plane + base + xl] = t[xl][c];
+    }
   }
 }
 
@@ -216,34 +228,20 @@ __global__ void __launch_bounds__(kDwThreads, 1) dw_tc_kernel(const __grid_const
   }
 }
 
-// grad[(o ci + c) 27 + t] += sum_b partial[b][t][o][c]
+// grad[(o ci + c) 27 + t] += sum_b partial[b][t][o][c]: thread i runs over
+// the partial layout (t, o, c) so that the reads of every b are coalesced,
+// blockIdx.y takes every gridDim.y-th b and adds its share atomically
 __global__ void dw_reduce_kernel(const float* __restrict__ partial, int nb, int C, int ci, int co,
                                  float* __restrict__ grad) {
-  const int n = co * ci * 27;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int t = i % 27, c = (i / 27) % ci, o = i / (27 * ci);
-    float acc = 0.f;
-    for (int b = 0; b < nb; ++b) acc += partial[(((size_t)b * 27 + t) * 32 + o) * C + c];
-    grad[i] += acc;
-  }
-}
-
-// gb[o] += sum_v g[v][o] for o < co (g channels-last, NP channels)
-__global__ void __launch_bounds__(256) db_cl_kernel(const __nv_bfloat16* __restrict__ g, size_t vox, int NP, int co,
-                                                    float* __restrict__ gb) {
-  __shared__ float red[8][33];
-  const int o = threadIdx.x & 31, lane_v = threadIdx.x >> 5;
+  const int n = 27 * 32 * C;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = i % C, o = (i / C) % 32, t = i / (32 * C);
+  if (o >= co || c >= ci) return;
   float acc = 0.f;
-  if (o < NP)
-    for (size_t v = (size_t)blockIdx.x * 8 + lane_v; v < vox; v += (size_t)gridDim.x * 8)
-      acc += __bfloat162float(g[v * NP + o]);
-  red[lane_v][o] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float t = 0.f;
-    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    if (threadIdx.x < co) atomicAdd(gb + threadIdx.x, t);
-  }
+#pragma unroll 4
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) acc += partial[(size_t)b * n + i];
+  atomicAdd(grad + (o * ci + c) * 27 + t, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +400,7 @@ struct TcTrain {
   // dpre[l], the input gradients of the decoders (ddecin_l) and encoders (da_l)
   __nv_bfloat16 *dY = nullptr, *dpre[kNumLayers] = {}, *ddecin[3] = {}, *da[4] = {};
   __nv_bfloat16 *Apl = nullptr, *Bpl = nullptr;   // planar GEMM operands (level 0 size)
+  size_t plane0 = 0;                               // their row stride (elements)
   float* Yf = nullptr;                             // network output [V0][16]
   size_t yf_cap = 0;
   float* partial = nullptr;                        // [sms][27][32][32]
@@ -412,6 +411,8 @@ struct TcTrain {
   CUtensorMap mG[kNumLayers], mWf[kNumLayers];     // backward-data input (the layer's output gradient) / weights
   CUtensorMap mPa[kNumLayers], mPb[kNumLayers];    // weight-gradient operands
   int sms = 0, smem_optin = 0;
+  const void* wpack_enc = nullptr;                 // weights the maps mW / mWf point at
+  const void* wpackf_enc = nullptr;
 };
 
 static int nxp_of(int nx) { return (nx + kDwChunk - 1) / kDwChunk * kDwChunk; }
@@ -479,6 +480,9 @@ static vie_status tc_train_prepare(TcTrain** pt, const TcTrainParams& P, const i
     for (int l = 0; l < kNumLayers; ++l) T->dpre[l] = take(32 * T->L[kLayerLevel[l]].vox());
     T->Apl = take(128 * plane0);
     T->Bpl = take(32 * plane0);
+    T->plane0 = plane0;
+    // rows 96..127 of A (no dx block) stay zero
+    VIE_CUDA_TRY(cudaMemset(T->Apl + 96 * plane0, 0, 32 * plane0 * sizeof(__nv_bfloat16)));
     // forward maps: the inputs of enc0..enc3, dec2, dec1, dec0, out
     const __nv_bfloat16* in[kNumLayers] = {T->X, T->a[1], T->a[2], T->a[3], T->decin[2], T->decin[1], T->decin[0],
                                            T->u[0]};
@@ -494,21 +498,26 @@ static vie_status tc_train_prepare(TcTrain** pt, const TcTrainParams& P, const i
                          T->byb[l]);
       if (st != VIE_OK) return st;
       const int nxp = nxp_of(d.nx);
-      if ((st = tc_encode_planar(&T->mPa[l], T->Apl, 128, d, nxp)) != VIE_OK) return st;
-      if ((st = tc_encode_planar(&T->mPb[l], T->Bpl, tc_cpad(kLayerDefs[l].ci), d, nxp)) != VIE_OK) return st;
+      if ((st = tc_encode_planar(&T->mPa[l], T->Apl, 128, d, nxp, plane0)) != VIE_OK) return st;
+      if ((st = tc_encode_planar(&T->mPb[l], T->Bpl, tc_cpad(kLayerDefs[l].ci), d, nxp, plane0)) != VIE_OK)
+        return st;
     }
     T->n[0] = n[0];
     T->n[1] = n[1];
     T->n[2] = n[2];
   }
-  // weight maps (the packed weights live in the network; re-encoded each
-  // call in case the network changed)
+  // weight maps (the packed weights live in the network: encoded again
+  // only when they move)
+  if (T->wpack_enc == P.wpack && T->wpackf_enc == P.wpackf) return VIE_OK;
+  T->wpack_enc = nullptr;
   for (int l = 0; l < kNumLayers; ++l) {
     vie_status st = tc_encode_w(&T->mW[l], P.wpack + pack_off(l), tc_cpad(kLayerDefs[l].ci), tc_npad(kLayerDefs[l].co));
     if (st != VIE_OK) return st;
     st = tc_encode_w(&T->mWf[l], P.wpackf + packf_off(l), tc_cpad(kLayerDefs[l].co), tc_npad(kLayerDefs[l].ci));
     if (st != VIE_OK) return st;
   }
+  T->wpack_enc = P.wpack;
+  T->wpackf_enc = P.wpackf;
   return VIE_OK;
 }
 
@@ -525,9 +534,9 @@ static vie_status weight_grad_tc(const TcTrain* T, const TcTrainParams& P, int l
   const int ci = kLayerDefs[layer].ci, co = kLayerDefs[layer].co;
   const int C = tc_cpad(ci), NPo = tc_npad(co);
   const int nxp = nxp_of(d.nx);
-  const dim3 grid((unsigned)(nxp / kDwChunk), (unsigned)d.ny, (unsigned)d.nz);
-  dw_shift_planar_kernel<<<grid, 256, 0, s>>>(g, NPo, d, nxp, T->Apl);
-  dw_planar_kernel<<<grid, 256, 0, s>>>(in, C, d, nxp, T->Bpl);
+  const int nxc = nxp / kDwChunk;
+  dw_operands_kernel<<<dim3((unsigned)(2 * nxc), (unsigned)d.ny, (unsigned)d.nz), 256, 0, s>>>(
+      g, NPo, co, in, C, d, nxp, nxc, T->plane0, T->Apl, T->Bpl, P.grad + layer_b_off(layer));
   VIE_LAUNCH_CHECK();
   constexpr size_t kSB32 = 128 * 128 + 9 * 32 * 128, kSB16 = 128 * 128 + 9 * 16 * 128;
   const size_t fixed = 1024 + 2 * kDwMaxStages * 8 + 64;
@@ -545,8 +554,12 @@ static vie_status weight_grad_tc(const TcTrain* T, const TcTrainParams& P, int l
   a.stages = stages;
   a.partial = T->partial;
   a.bad = P.bad;
+  // at least kDwMinChunks chunks per CTA where the level is small: fewer
+  // partial sums to write and reduce
   const long nchunks = (long)d.nz * d.ny * a.nxc;
-  const int nb = (int)(nchunks < T->sms ? nchunks : T->sms);
+  long want = (nchunks + kDwMinChunks - 1) / kDwMinChunks;
+  if (want < 1) want = 1;
+  const int nb = (int)(want < T->sms ? want : T->sms);
   if (C == 32) {
     VIE_CUDA_TRY(cudaFuncSetAttribute(dw_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dw_tc_kernel<32><<<nb, kDwThreads, smem, s>>>(T->mPa[layer], T->mPb[layer], a);
@@ -555,9 +568,9 @@ static vie_status weight_grad_tc(const TcTrain* T, const TcTrainParams& P, int l
     dw_tc_kernel<16><<<nb, kDwThreads, smem, s>>>(T->mPa[layer], T->mPb[layer], a);
   }
   VIE_LAUNCH_CHECK();
-  dw_reduce_kernel<<<ew_grid((size_t)co * ci * 27), 256, 0, s>>>(T->partial, nb, C, ci, co,
-                                                                 P.grad + layer_w_off(layer));
-  db_cl_kernel<<<ew_grid(d.vox() * 32), 256, 0, s>>>(g, d.vox(), NPo, co, P.grad + layer_b_off(layer));
+  const int nred = 27 * 32 * C, slices = nb < 16 ? nb : 16;
+  dw_reduce_kernel<<<dim3((unsigned)((nred + 255) / 256), (unsigned)slices), 256, 0, s>>>(
+      T->partial, nb, C, ci, co, P.grad + layer_w_off(layer));
   VIE_LAUNCH_CHECK();
   return VIE_OK;
 }
