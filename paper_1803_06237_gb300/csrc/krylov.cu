@@ -69,6 +69,7 @@ struct ProbK {
   double* cs;
   double2* sn;
   double2* partial;        // (m + 2) x kDotBlocks partial sums
+  double2* Q;              // product of the cycle's rotations, (m + 1) x (m + 1) row-major (cooperative step)
   SolveStatus* st;
   void* rin;               // inner residual (inner type): start of the next inner cycle
   void* d;                 // last cycle's correction Z y (inner type)
@@ -543,6 +544,479 @@ __global__ void __launch_bounds__(kThreads) update_x_kernel(const ProbK* __restr
 }
 
 // ---------------------------------------------------------------------------
+// The whole Gram-Schmidt step in one cooperative launch
+// ---------------------------------------------------------------------------
+// One block of 512 threads per SM (all resident: cooperative launch); the
+// phases of a step are separated by a grid barrier instead of kernel
+// boundaries:
+//   dots (pass 1) | reduce -> h1 | w -= V h1, |w'|^2 | decide second pass
+//   [ dots (pass 2) | reduce -> h2, h1 + h2 | w -= V h2, |w''|^2 ] |
+//   h_{j+1,j}, v_{j+1} = w / h_{j+1,j}, Givens step (one block per problem)
+// with the same element chunks, partial sums and fixed summation orders as
+// the separate kernels above (the decision and ||w|| are computed
+// identically by every block).  Every barrier wait is bounded: a block that
+// waited kBarrierCycles sets the abort word and every block returns.  Values
+// another block wrote in this launch (partials, coefficients) are read with
+// ld.global.cg, past the SM's L1.
+constexpr int kCoopThreadsMax = 1024;
+// threads per block of the cooperative step (up to 128 registers: the
+// complex64 dots keep all coefficients of a step in registers)
+template <typename V> constexpr int coop_threads() { return 512; }
+constexpr int kCoopDotsMax = 32;   // complex64 dots with all vectors in one sweep up to this basis size
+constexpr int kCoopMaxProblems = 64;
+constexpr long long kBarrierCycles = 2000000000LL;   // ~1 s
+
+// bar[0] arrivals, bar[1] generation, bar[2] abort (a wait gave up)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vabort = bar + 2;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*vabort) { ok = 0; break; }
+        if (clock64() - t0 > kBarrierCycles) { atomicExch(bar + 2, 1u); ok = 0; break; }
+      }
+    }
+    __threadfence();
+    ok_s = ok && !*vabort;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// kGroup complex sums of the block -> partial[(i0 + u) * nblk + blockIdx.x]
+template <typename A>
+__device__ __forceinline__ void coop_store_group(A (&acc)[kGroup], int i0, int nv, double2* __restrict__ partial,
+                                                 int nblk) {
+  __shared__ double2 red[kCoopThreadsMax / 32][kGroup];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < kGroup; ++u) {
+    acc[u].x = warp_sum(acc[u].x);
+    acc[u].y = warp_sum(acc[u].y);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) red[warp][u] = make_double2((double)acc[u].x, (double)acc[u].y);
+  __syncthreads();
+  if (threadIdx.x < kGroup && i0 + threadIdx.x < nv) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t.x += red[w][threadIdx.x].x;
+      t.y += red[w][threadIdx.x].y;
+    }
+    partial[(size_t)(i0 + threadIdx.x) * nblk + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// dots of the block's chunk with vectors 0 .. nv-1 -> partial slots 0 .. nv-1.
+// Complex64 with nv <= kCoopDotsMax: one sweep over the chunk, w[k] read once
+// and all nv products accumulated in registers (like the update); otherwise
+// kGroup vectors per sweep.
+template <typename V>
+__device__ void coop_dots(const ProbK& q, int nv, int nblk) {
+  typedef typename Acc<V>::T A;
+  const V* __restrict__ Vb = (const V*)q.V;
+  const V* __restrict__ w = (const V*)q.w;
+  const size_t n = q.n;
+  const Chunk ch = chunk_of(n);
+  if constexpr (sizeof(V) == sizeof(float2)) {
+    if (nv <= kCoopDotsMax) {
+      A acc[kCoopDotsMax];
+#pragma unroll
+      for (int u = 0; u < kCoopDotsMax; ++u) acc[u] = zero_acc<A>();
+      // two elements per iteration (k, k + blockDim): twice the loads in flight
+      for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += 2 * (size_t)blockDim.x) {
+        const size_t k2 = k + blockDim.x;
+        const bool two = k2 < ch.k1;
+        const V c = w[k];
+        const V c2 = two ? w[k2] : V{};
+#pragma unroll
+        for (int i0 = 0; i0 < kCoopDotsMax; i0 += kGroup) {
+          if (i0 < nv) {
+            V a[kGroup], b[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+              a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
+              b[u] = (two && i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k2] : V{};
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+              acc[i0 + u].x += a[u].x * c.x + a[u].y * c.y + b[u].x * c2.x + b[u].y * c2.y;
+              acc[i0 + u].y += a[u].x * c.y - a[u].y * c.x + b[u].x * c2.y - b[u].y * c2.x;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i0 = 0; i0 < kCoopDotsMax; i0 += kGroup) {
+        if (i0 < nv) {
+          A grp[kGroup];
+#pragma unroll
+          for (int u = 0; u < kGroup; ++u) grp[u] = acc[i0 + u];
+          coop_store_group(grp, i0, nv, q.partial, nblk);
+        }
+      }
+      return;
+    }
+  }
+  for (int i0 = 0; i0 < nv; i0 += kGroup) {
+    A acc[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) acc[u] = zero_acc<A>();
+    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+      const V c = w[k];
+      V a[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        acc[u].x += a[u].x * c.x + a[u].y * c.y;
+        acc[u].y += a[u].x * c.y - a[u].y * c.x;
+      }
+    }
+    coop_store_group(acc, i0, nv, q.partial, nblk);
+  }
+}
+
+// sum of partial[slot * nblk + 0 .. nblk) by one warp in a fixed order
+__device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__ part, int nblk) {
+  const int lane = threadIdx.x & 31;
+  double2 t = make_double2(0.0, 0.0);
+  for (int b0 = 0; b0 < nblk; b0 += 8 * 32) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < nblk ? __ldcg(part + b) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      t.x += v[u].x;
+      t.y += v[u].y;
+    }
+  }
+  t.x = warp_sum(t.x);
+  t.y = warp_sum(t.y);
+  t.x = __shfl_sync(0xffffffffu, t.x, 0);
+  t.y = __shfl_sync(0xffffffffu, t.y, 0);
+  return t;
+}
+
+// w -= V h over the block's chunk (h: nv coefficients in shared memory), |w|^2
+// of the chunk -> partial[slot * nblk + blockIdx.x]
+template <typename V>
+__device__ void coop_update(const ProbK& q, int nv, const typename Acc<V>::T* hs, int slot, int nblk) {
+  typedef typename Acc<V>::T A;
+  typedef typename Acc<V>::R AR;
+  const V* __restrict__ Vb = (const V*)q.V;
+  V* __restrict__ w = (V*)q.w;
+  const size_t n = q.n;
+  const Chunk ch = chunk_of(n);
+  AR nrm = 0;
+  // complex64: two elements per iteration (k, k + blockDim), twice the loads
+  // in flight; complex128 (registers) one
+  constexpr int E = sizeof(V) == sizeof(float2) ? 2 : 1;
+  for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += E * (size_t)blockDim.x) {
+    const size_t k2 = k + blockDim.x;
+    const bool two = E == 2 && k2 < ch.k1;
+    const V w0 = w[k];
+    const V w1 = two ? w[k2] : V{};
+    A acc, acc2;
+    acc.x = w0.x;
+    acc.y = w0.y;
+    acc2.x = w1.x;
+    acc2.y = w1.y;
+    for (int i0 = 0; i0 < nv; i0 += kUpdGroup) {
+      V a[kUpdGroup], b[E == 2 ? kUpdGroup : 1];
+#pragma unroll
+      for (int u = 0; u < kUpdGroup; ++u) {
+        a[u] = (i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k] : V{};
+        if constexpr (E == 2) b[u] = (two && i0 + u < nv) ? Vb[(size_t)(i0 + u) * n + k2] : V{};
+      }
+#pragma unroll
+      for (int u = 0; u < kUpdGroup; ++u) {
+        if (i0 + u < nv) {
+          const A h = hs[i0 + u];
+          acc.x -= a[u].x * h.x - a[u].y * h.y;
+          acc.y -= a[u].x * h.y + a[u].y * h.x;
+          if constexpr (E == 2) {
+            acc2.x -= b[u].x * h.x - b[u].y * h.y;
+            acc2.y -= b[u].x * h.y + b[u].y * h.x;
+          }
+        }
+      }
+    }
+    V out;
+    out.x = acc.x;
+    out.y = acc.y;
+    w[k] = out;
+    nrm += out.x * out.x + out.y * out.y;
+    if (two) {
+      V out2;
+      out2.x = acc2.x;
+      out2.y = acc2.y;
+      w[k2] = out2;
+      nrm += out2.x * out2.x + out2.y * out2.y;
+    }
+  }
+  __shared__ double red[kCoopThreadsMax / 32];
+  AR t = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) u += red[i];
+    q.partial[(size_t)slot * nblk + blockIdx.x] = make_double2(u, 0.0);
+  }
+  __syncthreads();
+}
+
+// pairs (problem, vector) distributed over the warps of the grid: coefficient
+// = sum of that vector's partials; pass 0 writes hcol, pass 1 h2 and hcol += h2
+__device__ void coop_reduce(const ProbK* __restrict__ P, int count, const int* sel, int nv, int nblk, int pass) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int pairs = count * nv;
+  for (int pi = blockIdx.x * wpb + warp; pi < pairs; pi += gridDim.x * wpb) {
+    const int p = pi / nv, i = pi - p * nv;
+    if (!sel[p]) continue;
+    const ProbK& q = P[p];
+    const double2 t = warp_sum_partials(q.partial + (size_t)i * nblk, nblk);
+    if (lane == 0) {
+      if (pass == 0) {
+        q.hcol[i] = t;
+      } else {
+        const double2 h1 = __ldcg(q.hcol + i);
+        q.h2[i] = t;
+        q.hcol[i] = make_double2(h1.x + t.x, h1.y + t.y);
+      }
+    }
+  }
+}
+
+// The FP64 least-squares step of problem q for column j by the block that
+// owns q.  The rotations of the cycle are kept multiplied out, Q = O_{j-1}
+// ... O_0 ((j + 1) x (j + 1), row-major, ld = m + 1 = ldh), so that applying
+// them to the new column is a matrix-vector product (a warp per row, lanes
+// over the columns, fixed-order reduction) instead of a chain of j
+// dependent rotations; thread 0 then forms the new rotation O_j on
+// (r_j, h_{j+1,j}), updates g and the status, and Q's rows j and j + 1 are
+// replaced by O_j applied to (row j, e_{j+1}).  sh: j + 2 double2.
+__device__ void coop_givens(const ProbK& q, int j, int ldh, double hn, double inv, double2* sh) {
+  double2* r = sh;
+  __shared__ double2 rot[2];   // (c, 0), s
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ldq = ldh;
+  __syncthreads();
+  for (int i = warp; i <= j; i += nw) {
+    double re = 0.0, im = 0.0;
+    for (int k = lane; k <= j; k += 32) {
+      const double2 g = j == 0 ? make_double2(1.0, 0.0) : q.Q[(size_t)i * ldq + k];
+      const double2 h = __ldcg(q.hcol + k);
+      re += g.x * h.x - g.y * h.y;
+      im += g.x * h.y + g.y * h.x;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) r[i] = make_double2(re, im);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolveStatus* st = q.st;
+    const double2 a = r[j], b = make_double2(hn, 0.0);
+    const double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
+    const double den = hypot(aa, ab);
+    double c;
+    double2 s;
+    if (den == 0.0) {
+      c = 1.0; s = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0; s = make_double2(1.0, 0.0);
+    } else {
+      c = aa / den;
+      const double2 ua = make_double2(a.x / aa, a.y / aa);
+      s = make_double2((ua.x * b.x + ua.y * b.y) / den, (ua.y * b.x - ua.x * b.y) / den);
+    }
+    q.cs[j] = c;
+    q.sn[j] = s;
+    rot[0] = make_double2(c, 0.0);
+    rot[1] = s;
+    r[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    r[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = q.g[j];
+    const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    q.g[j + 1] = g1;
+    q.g[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = hypot(g1.x, g1.y);
+    st->j = j + 1;
+    st->resid = res;
+    if (!(isfinite(hn) && isfinite(res))) {
+      st->breakdown = 1;
+      st->active = 0;
+      st->j = j;
+    } else {
+      if (res <= st->target) {
+        st->converged = 1;
+        st->active = 0;
+      }
+      if (hn <= 1e-300 || hn <= 1e-14 * st->beta) {
+        st->breakdown = 1;
+        st->active = 0;
+      }
+      st->inv_h = inv;
+    }
+  }
+  __syncthreads();
+  double2* H = q.H + (size_t)j * ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i] = r[i];
+  // Q <- O_j diag(Q, 1): rows j and j + 1 over columns 0 .. j + 1; column
+  // j + 1 of the rows above is zero
+  const double c = rot[0].x;
+  const double2 s = rot[1];
+  for (int k = threadIdx.x; k <= j + 1; k += blockDim.x) {
+    double2 gj;
+    if (k == j + 1) gj = make_double2(0.0, 0.0);
+    else if (j == 0) gj = make_double2(k == 0 ? 1.0 : 0.0, 0.0);
+    else gj = q.Q[(size_t)j * ldq + k];
+    const double2 e = make_double2(k == j + 1 ? 1.0 : 0.0, 0.0);
+    // row j' = c gj + s e ; row j+1' = -conj(s) gj + c e
+    q.Q[(size_t)j * ldq + k] = make_double2(c * gj.x + (s.x * e.x - s.y * e.y), c * gj.y + (s.x * e.y + s.y * e.x));
+    q.Q[(size_t)(j + 1) * ldq + k] =
+        make_double2(-(s.x * gj.x + s.y * gj.y) + c * e.x, -(s.x * gj.y - s.y * gj.x) + c * e.y);
+  }
+  for (int i = threadIdx.x; i < j; i += blockDim.x) q.Q[(size_t)i * ldq + j + 1] = make_double2(0.0, 0.0);
+}
+
+// Step j (nv = j + 1 basis vectors) for the count problems of P after the
+// operator has written w; with set_next, the last block to finish also sets
+// the condition `next` of the following step's graph node.  Dynamic shared
+// memory: nv coefficients, then (j + 2) + j double2 and j double for the
+// Givens step.
+template <typename V>
+__global__ void __launch_bounds__(coop_threads<V>(), 1) arnoldi_coop_kernel(const ProbK* __restrict__ P, int count,
+                                                                      int nv, int ldh, unsigned* bar,
+                                                                      cudaGraphConditionalHandle next, int set_next) {
+  typedef typename Acc<V>::T A;
+  const int j = nv - 1;
+  const int nblk = gridDim.x;
+  const unsigned nb = gridDim.x;
+  __shared__ int act[kCoopMaxProblems], reo[kCoopMaxProblems];
+  __shared__ double hn_s[kCoopMaxProblems];
+  __shared__ int any_reo;
+  extern __shared__ unsigned char coop_raw[];
+  A* hs = reinterpret_cast<A*>(coop_raw);                                   // nv coefficients
+  double2* col = reinterpret_cast<double2*>(coop_raw + ((nv * sizeof(A) + 15) / 16) * 16);
+  for (int p = threadIdx.x; p < count; p += blockDim.x) act[p] = P[p].st->active;
+  __syncthreads();
+  // dots, pass 1
+  for (int p = 0; p < count; ++p)
+    if (act[p]) coop_dots<V>(P[p], nv, nblk);
+  if (!grid_barrier(bar, nb)) return;
+  coop_reduce(P, count, act, nv, nblk, 0);
+  if (!grid_barrier(bar, nb)) return;
+  for (int p = 0; p < count; ++p) {
+    if (!act[p]) continue;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = acc_from<A>(__ldcg(P[p].hcol + i));
+    __syncthreads();
+    coop_update<V>(P[p], nv, hs, nv, nblk);
+  }
+  if (!grid_barrier(bar, nb)) return;
+  // second-pass decision (identical in every block): ||w'||^2 < (||w'||^2 + ||h1||^2) / 2
+  if (threadIdx.x < 32) {
+    int any = 0;
+    for (int p = 0; p < count; ++p) {
+      int r = 0;
+      if (act[p]) {
+        const ProbK& q = P[p];
+        const double w2 = warp_sum_partials(q.partial + (size_t)nv * nblk, nblk).x;
+        double h2 = 0.0;
+        for (int i = threadIdx.x; i < nv; i += 32) {
+          const double2 h = __ldcg(q.hcol + i);
+          h2 += h.x * h.x + h.y * h.y;
+        }
+        h2 = warp_sum(h2);
+        h2 = __shfl_sync(0xffffffffu, h2, 0);
+        r = (w2 < 0.5 * (w2 + h2)) ? 1 : 0;
+        if (threadIdx.x == 0 && blockIdx.x == 0) {
+          q.st->reorth = r;
+          q.st->reorth_count += r;
+        }
+      }
+      if (threadIdx.x == 0) reo[p] = r;
+      any |= r;
+    }
+    if (threadIdx.x == 0) any_reo = any;
+  }
+  __syncthreads();
+  if (any_reo) {
+    for (int p = 0; p < count; ++p)
+      if (reo[p]) coop_dots<V>(P[p], nv, nblk);
+    if (!grid_barrier(bar, nb)) return;
+    coop_reduce(P, count, reo, nv, nblk, 1);
+    if (!grid_barrier(bar, nb)) return;
+    for (int p = 0; p < count; ++p) {
+      if (!reo[p]) continue;
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = acc_from<A>(__ldcg(P[p].h2 + i));
+      __syncthreads();
+      coop_update<V>(P[p], nv, hs, nv + 1, nblk);
+    }
+    if (!grid_barrier(bar, nb)) return;
+  }
+  // h_{j+1,j} = ||w|| (same order in every block), v_{j+1}, Givens step
+  if (threadIdx.x < 32)
+    for (int p = 0; p < count; ++p)
+      if (act[p]) {
+        const double t = warp_sum_partials(P[p].partial + (size_t)(reo[p] ? nv + 1 : nv) * nblk, nblk).x;
+        if (threadIdx.x == 0) hn_s[p] = sqrt(t);
+      }
+  __syncthreads();
+  for (int p = 0; p < count; ++p) {
+    if (!act[p]) continue;
+    const ProbK& q = P[p];
+    const double hn = hn_s[p];
+    const double inv = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+    const typename Acc<V>::R sc = (typename Acc<V>::R)inv;
+    const V* __restrict__ w = (const V*)q.w;
+    V* __restrict__ v = (V*)q.V + (size_t)(j + 1) * q.n;
+    const Chunk ch = chunk_of(q.n);
+    for (size_t k = ch.k0 + threadIdx.x; k < ch.k1; k += blockDim.x) {
+      V a = w[k];
+      a.x *= sc;
+      a.y *= sc;
+      v[k] = a;
+    }
+    if (blockIdx.x == (unsigned)(p % nblk)) coop_givens(q, j, ldh, hn, inv, col);
+  }
+  if (set_next) {
+    // the last block to finish (ticket in bar[3]) sets the condition of the
+    // next step's graph node: 1 while any problem is still active
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(bar + 3, 1u) == nb - 1) {
+        __threadfence();
+        int any = 0;
+        for (int p = 0; p < count; ++p) any |= __ldcg(&P[p].st->active);
+        cudaGraphSetConditional(next, any ? 1u : 0u);
+        atomicExch(bar + 3, 0u);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct KrylovWork {
@@ -564,6 +1038,7 @@ struct KrylovWork {
   double* cs = nullptr;
   double2* sn = nullptr;
   double2* partial = nullptr;
+  double2* Q = nullptr;     // rotation product (cooperative step)
   void* rin = nullptr;      // inner residual (mixed mode)
   void* d = nullptr;        // inner correction (mixed mode)
 };
@@ -571,7 +1046,7 @@ struct KrylovWork {
 static void free_work(KrylovWork* k) {
   cudaFree(k->V); cudaFree(k->Z); cudaFree(k->w); cudaFree(k->x64); cudaFree(k->r64); cudaFree(k->y64);
   cudaFree(k->H); cudaFree(k->hcol); cudaFree(k->h2); cudaFree(k->g); cudaFree(k->ysol); cudaFree(k->cs);
-  cudaFree(k->sn); cudaFree(k->partial); cudaFree(k->rin); cudaFree(k->d);
+  cudaFree(k->sn); cudaFree(k->partial); cudaFree(k->Q); cudaFree(k->rin); cudaFree(k->d);
   *k = KrylovWork();
 }
 
@@ -586,6 +1061,7 @@ static vie_status alloc_work(KrylovWork* k, size_t n, int m, int dtype, bool fle
       {(void**)&k->ysol, (m + 1) * sizeof(double2)}, {(void**)&k->cs, (m + 1) * sizeof(double)},
       {(void**)&k->sn, (m + 1) * sizeof(double2)},
       {(void**)&k->partial, (size_t)(m + 2) * kDotBlocks * sizeof(double2)},
+      {(void**)&k->Q, (size_t)(m + 1) * (m + 1) * sizeof(double2)},
       {&k->rin, n * es}, {&k->d, n * es}};
   for (auto& e : a) {
     cudaError_t err = cudaMalloc(e.p, e.sz);
@@ -643,13 +1119,38 @@ struct BatchCall {
   std::vector<char> pc_on;          // preconditioner still in use, per problem
   bool jm = false;                  // JM-VIE problems (6N unknowns)
   bool last_cycle_graph = false;    // the last cycle ran as a graph launch
+  unsigned* bar = nullptr;          // grid barrier of the cooperative step (arrivals, generation, abort)
+  unsigned* bar_host = nullptr;     // pinned copy of the abort word
+  int coop_blocks = 0;              // blocks of the cooperative step (0: separate kernels)
   ~BatchCall() {
     cudaFree(table);
     cudaFree(st);
+    cudaFree(bar);
     cudaFreeHost(st_host);
     cudaFreeHost(partial_host);
+    cudaFreeHost(bar_host);
   }
 };
+
+// Blocks of the cooperative Gram-Schmidt step for inner type V: one per SM
+// at most as many as fit resident, capped at kDotBlocks (the partial-sum
+// stride); 0 where cooperative launch is not available.
+template <typename V>
+static int coop_blocks_for(int m) {
+  int dev = 0, coop = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t dyn = (size_t)(m + 1) * sizeof(typename Acc<V>::T) + 16 + (size_t)(2 * m + 2) * sizeof(double2) +
+                     (size_t)m * sizeof(double);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, arnoldi_coop_kernel<V>, coop_threads<V>(), dyn) !=
+                   cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = sms * (per > 1 ? 1 : per);
+  return nb > kDotBlocks ? kDotBlocks : nb;
+}
 
 static vie_status upload_list(BatchCall& c, const std::vector<int>& list, cudaStream_t s) {
   std::vector<ProbK> t(list.size());
@@ -729,7 +1230,12 @@ static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dty
 
 static vie_status read_status(BatchCall& c, cudaStream_t s) {
   VIE_CUDA_TRY(cudaMemcpyAsync(c.st_host, c.st, c.plans.size() * sizeof(SolveStatus), cudaMemcpyDeviceToHost, s));
+  if (c.bar) VIE_CUDA_TRY(cudaMemcpyAsync(c.bar_host, c.bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   VIE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (c.bar && *c.bar_host) {
+    set_error("a grid barrier of the Gram-Schmidt step timed out");
+    return VIE_ERR_TIMEOUT;
+  }
   return VIE_OK;
 }
 
@@ -742,7 +1248,9 @@ static vie_status read_status(BatchCall& c, cudaStream_t s) {
 template <typename V>
 static vie_status enqueue_step(BatchCall& c, const std::vector<int>& list, const std::vector<int>& live, int j, int m,
                                int dtype, bool flexible, vie_precond_fn precond, void* const* precond_ctx,
-                               unsigned gx, cudaStream_t s) {
+                               unsigned gx, cudaStream_t s, cudaGraphConditionalHandle next = 0,
+                               bool* next_set = nullptr) {
+  if (next_set) *next_set = false;
   const unsigned P = (unsigned)list.size();
   if (flexible) {
     for (int i : live) {
@@ -760,6 +1268,27 @@ static vie_status enqueue_step(BatchCall& c, const std::vector<int>& list, const
   vie_status ms = apply_list(c, live, dtype, APPLY_Z, j, flexible, s);
   if (ms != VIE_OK) return ms;
   const int nv = j + 1;
+  if (c.coop_blocks > 0 && P <= (unsigned)kCoopMaxProblems) {
+    // the whole Gram-Schmidt step, ||w||, v_{j+1} and the Givens step in one
+    // cooperative launch
+    const size_t dyn = ((nv * sizeof(typename Acc<V>::T) + 15) / 16) * 16 + (size_t)(2 * j + 2) * sizeof(double2) +
+                       (size_t)j * sizeof(double);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c.coop_blocks);
+    cfg.blockDim = dim3(coop_threads<V>());
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int set_next = next_set ? 1 : 0;
+    VIE_CUDA_TRY(cudaLaunchKernelEx(&cfg, arnoldi_coop_kernel<V>, (const ProbK*)c.table, (int)P, nv, m + 1, c.bar,
+                                    next, set_next));
+    if (next_set) *next_set = true;
+    return VIE_OK;
+  }
   // h1 = V^H w, w -= V h1 (+ norm); if needed h2 = V^H w, w -= V h2 (+ norm); column h1 + h2
   const dim3 gdots(kDotBlocks, (unsigned)((nv + kGroup - 1) / kGroup), P);
   const size_t hs_bytes = nv * sizeof(typename Acc<V>::T);
@@ -840,8 +1369,11 @@ static vie_status build_cycle_graph(BatchCall& c, CycleGraph& G, const std::vect
     if (k == 0) {
       start_vector_kernel<V><<<dim3(gx, P), kThreads, 0, G.cap>>>(c.table);
     } else if (k <= jmax) {
-      st = enqueue_step<V>(c, list, list, k - 1, m, dtype, flexible, precond, precond_ctx, gx, G.cap);
-      if (st == VIE_OK && k < jmax) next_step_condition_kernel<<<1, 32, 0, G.cap>>>(c.table, (int)P, h[k + 1]);
+      bool set = false;
+      st = enqueue_step<V>(c, list, list, k - 1, m, dtype, flexible, precond, precond_ctx, gx, G.cap,
+                           k < jmax ? h[k + 1] : 0, k < jmax ? &set : nullptr);
+      if (st == VIE_OK && k < jmax && !set)
+        next_step_condition_kernel<<<1, 32, 0, G.cap>>>(c.table, (int)P, h[k + 1]);
     } else {
       backsolve_kernel<<<P, kThreads, 0, G.cap>>>(c.table, m + 1);
       update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(typename Acc<V>::T), G.cap>>>(c.table);
@@ -948,6 +1480,12 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
   VIE_CUDA_TRY(cudaMallocHost((void**)&c.st_host, count * sizeof(SolveStatus)));
   VIE_CUDA_TRY(cudaMallocHost((void**)&c.partial_host, (size_t)count * kDotBlocks * sizeof(double2)));
   VIE_CUDA_TRY(cudaMemsetAsync(c.st, 0, count * sizeof(SolveStatus), s));
+  VIE_CUDA_TRY(cudaMalloc((void**)&c.bar, 4 * sizeof(unsigned)));
+  VIE_CUDA_TRY(cudaMallocHost((void**)&c.bar_host, sizeof(unsigned)));
+  VIE_CUDA_TRY(cudaMemsetAsync(c.bar, 0, 4 * sizeof(unsigned), s));
+  c.coop_blocks = (count <= kCoopMaxProblems)
+                      ? (dtype == VIE_C64 ? coop_blocks_for<float2>(m) : coop_blocks_for<double2>(m))
+                      : 0;
   for (int i = 0; i < count; ++i) {
     KrylovWork* k = nullptr;
     vie_status st = ensure_work(plans[i], m, dtype, flexible, &k, jm ? 6 : 3);
@@ -956,7 +1494,7 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
     memset(&q, 0, sizeof(q));
     q.V = k->V; q.Z = flexible ? k->Z : k->V; q.w = k->w; q.n = k->n; q.b = b[i];
     q.x64 = k->x64; q.r64 = k->r64; q.y64 = k->y64; q.H = k->H; q.hcol = k->hcol; q.h2 = k->h2; q.g = k->g;
-    q.ysol = k->ysol; q.cs = k->cs; q.sn = k->sn; q.partial = k->partial; q.st = c.st + i;
+    q.ysol = k->ysol; q.cs = k->cs; q.sn = k->sn; q.partial = k->partial; q.Q = k->Q; q.st = c.st + i;
     q.rin = k->rin; q.d = mode == VIE_SOLVE_MIXED ? k->d : nullptr; q.from_inner = 0;
     memset(&infos[i], 0, sizeof(vie_solve_info));
   }
