@@ -487,6 +487,14 @@ vie_status vie_matvec_static_scratch(const vie_plan* plan, const void* x_dev,
  * Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA. */
 vie_status vie_probe_fma_tflops(int dtype, double* tflops, void* stream);
 
+/* Failure detection of the solver's grid barrier (the cooperative
+ * Gram-Schmidt step; no counterpart in the paper): one barrier over one
+ * block per SM in which block absent_block (-1: none) does not take part.
+ * The other blocks give up after wait_ms (0 < wait_ms <= 2000) and set the
+ * abort word; *aborted = 1 then, 0 when the barrier completed.  Synchronous.
+ * Errors: VIE_ERR_INVALID, VIE_ERR_CUDA. */
+vie_status vie_probe_grid_barrier(int absent_block, double wait_ms, int* aborted);
+
 /* Thread-local description of the last error ("" if none). */
 const char* vie_last_error(void);
 

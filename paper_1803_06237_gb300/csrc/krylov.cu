@@ -566,8 +566,9 @@ constexpr int kCoopDotsMax = 32;   // complex64 dots with all vectors in one swe
 constexpr int kCoopMaxProblems = 64;
 constexpr long long kBarrierCycles = 2000000000LL;   // ~1 s
 
-// bar[0] arrivals, bar[1] generation, bar[2] abort (a wait gave up)
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+// bar[0] arrivals, bar[1] generation, bar[2] abort (a wait gave up after
+// `limit` SM clocks)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long limit = kBarrierCycles) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -584,7 +585,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
       const long long t0 = clock64();
       while (*vgen == g) {
         if (*vabort) { ok = 0; break; }
-        if (clock64() - t0 > kBarrierCycles) { atomicExch(bar + 2, 1u); ok = 0; break; }
+        if (clock64() - t0 > limit) { atomicExch(bar + 2, 1u); ok = 0; break; }
       }
     }
     __threadfence();
@@ -1812,4 +1813,58 @@ extern "C" vie_status vie_jm_solve(vie_plan* p, const void* b, void* x, double t
   const double2* bd = (const double2*)b;
   double2* xd = (double2*)x;
   return solve_batch_impl(&p, 1, &bd, &xd, tol, opts, info, nullptr, &ctx, (cudaStream_t)stream, 1);
+}
+
+namespace vie {
+// One grid barrier of the cooperative step in which block `absent` does not
+// take part (it returns first): the other blocks' waits run out after
+// `limit` clocks and set the abort word.
+__global__ void barrier_probe_kernel(unsigned* bar, int absent, long long limit) {
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(bar, gridDim.x, limit);
+}
+}  // namespace vie
+
+extern "C" vie_status vie_probe_grid_barrier(int absent_block, double wait_ms, int* aborted) {
+  using namespace vie;
+  clear_error();
+  if (!aborted || wait_ms <= 0.0 || wait_ms > 2000.0) {
+    set_error("aborted must be non-null and wait_ms in (0, 2000]");
+    return VIE_ERR_INVALID;
+  }
+  int dev = 0, sms = 0, clk_khz = 0, coop = 0;
+  VIE_CUDA_TRY(cudaGetDevice(&dev));
+  VIE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VIE_CUDA_TRY(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev));
+  VIE_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) {
+    set_error("cooperative launch is not available on this device");
+    return VIE_ERR_INVALID;
+  }
+  if (absent_block >= sms) {
+    set_error("absent_block must be below the number of SMs (%d)", sms);
+    return VIE_ERR_INVALID;
+  }
+  unsigned* bar = nullptr;
+  VIE_CUDA_TRY(cudaMalloc((void**)&bar, 4 * sizeof(unsigned)));
+  cudaMemset(bar, 0, 4 * sizeof(unsigned));
+  const long long limit = (long long)(wait_ms * (double)clk_khz);   // clk_khz clocks per ms
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)sms);
+  cfg.blockDim = dim3(32);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, barrier_probe_kernel, bar, absent_block, limit);
+  unsigned h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  if (e != cudaSuccess) {
+    set_error("barrier probe: %s", cudaGetErrorString(e));
+    return VIE_ERR_CUDA;
+  }
+  *aborted = h ? 1 : 0;
+  return VIE_OK;
 }

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "vie_reflection": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "vie_solve": ([_P, _P, _P, _D, ctypes.POINTER(vie_solve_opts), ctypes.POINTER(vie_solve_info), _P], _I),
     "vie_probe_fma_tflops": ([_I, ctypes.POINTER(_D), _P], _I),
+    "vie_probe_grid_barrier": ([_I, _D, ctypes.POINTER(_I)], _I),
     "vie_set_permeability": ([_P, _P], _I),
     "vie_slice_power": ([_P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "vie_jm_matvec": ([_P, _P, _P, _I, _P], _I),
@@ -628,6 +629,15 @@ def vie_jm_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, rest
     if st != VIE_OK and not (st in (4, 5) and not raise_on_not_converged):
         _check(st, "vie_jm_solve")
     return out
+
+
+def vie_probe_grid_barrier(absent_block: int, wait_ms: float) -> bool:
+    """One grid barrier with block absent_block (-1: none) missing; True if
+    the other blocks gave up after wait_ms (the solver's barrier timeout)."""
+    out = _I()
+    _check(load().vie_probe_grid_barrier(int(absent_block), float(wait_ms), ctypes.byref(out)),
+           "vie_probe_grid_barrier")
+    return bool(out.value)
 
 
 def vie_probe_fma_tflops(dtype_code: int, stream=None) -> float:

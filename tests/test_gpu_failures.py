@@ -131,3 +131,18 @@ def test_solve_on_host_buffers_matches_device_solve():
     st, infos = vie.vie_solve_batch([plan, plan2], bs, xs, 1e-8, mode=vie.VIE_SOLVE_MIXED, restart=30)
     assert st == 0 and all(i["converged"] for i in infos)
     assert rel_l2(xs[0], xd.cpu().numpy()) <= 1e-6
+
+
+def test_grid_barrier_wait_runs_out_and_reports():
+    """The solver's cooperative Gram-Schmidt step separates its phases with a
+    grid barrier whose waits are bounded: with one block missing, the others
+    give up after the limit and set the abort word (which the solver reports
+    as VIE_ERR_TIMEOUT); with every block present the barrier completes.
+    The context stays usable."""
+    import time
+    t0 = time.perf_counter()
+    assert vie.vie_probe_grid_barrier(3, 50.0) is True
+    assert time.perf_counter() - t0 < 30.0
+    assert vie.vie_probe_grid_barrier(-1, 50.0) is False
+    x = torch.ones(8, device="cuda")
+    assert float(x.sum().item()) == 8.0
