@@ -370,6 +370,7 @@ def gpu_arm(args):
         "alu_peaks_measured": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
                                "how": "FMA chains on every SM, CUDA events (vie_probe_fma_tflops)"},
         "c128_operator": c128_section(plan, wl, info, fp64_peak, alg_flops),
+        "cufft_reference": cufft_reference(wl, info, per_step_ms),
     }
     if not args.no_net:
         result["net_inference"] = net_section(plan, wl.grid)
@@ -419,6 +420,46 @@ def c128_section(plan, wl, info, fp64_peak, alg_flops, reps=100):
                     "peak_source": "measured FP64 FMA throughput"},
             "hbm": {"achieved": alg_bytes / ms / 1e6, "peak": hbm_peak, "unit": "GB/s",
                     "frac": alg_bytes / ms / 1e6 / hbm_peak, "algorithmic_bytes": alg_bytes, "peak_source": kind}}
+
+
+def cufft_reference(wl, info, our_ms, reps=50):
+    """Reference point only (not the product path): the same operator shape
+    written with PyTorch's FFTs (cuFFT) and element-wise ops: pad the three
+    components into the circulant embedding, 3-D forward FFT, the symmetric
+    3x3 spectral multiply with six full spectra (random values: timing
+    only), inverse FFT, crop, y = x - M (N x).  Complex64, CUDA events."""
+    import torch
+    Mx, My, Mz = info["m"]
+    nx, ny, nz = wl.grid
+    g = torch.Generator(device="cuda").manual_seed(7)
+    G = torch.randn((6, Mz, My, Mx), dtype=torch.complex64, device="cuda", generator=g)
+    Mc = torch.randn((nz, ny, nx), dtype=torch.complex64, device="cuda", generator=g)
+    x = torch.randn((3, nz, ny, nx), dtype=torch.complex64, device="cuda", generator=g)
+    pad = torch.zeros((3, Mz, My, Mx), dtype=torch.complex64, device="cuda")
+
+    def apply(x):
+        pad.zero_()
+        pad[:, :nz, :ny, :nx] = x
+        X = torch.fft.fftn(pad, dim=(1, 2, 3))
+        Y = torch.stack([G[0] * X[0] + G[3] * X[1] + G[4] * X[2],
+                         G[3] * X[0] + G[1] * X[1] + G[5] * X[2],
+                         G[4] * X[0] + G[5] * X[1] + G[2] * X[2]])
+        y = torch.fft.ifftn(Y, dim=(1, 2, 3))[:, :nz, :ny, :nx]
+        return x - Mc * y
+
+    for _ in range(3):
+        apply(x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        apply(x)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"ms_per_matvec": ms, "matvecs_per_s": 1e3 / ms, "ours_over_cufft_speedup": ms / our_ms,
+            "what": "torch.fft.fftn/ifftn (cuFFT) on the 3 x %d x %d x %d embedding + PyTorch element-wise "
+                    "multiply, crop and contrast; random spectra; reference point only" % (Mx, My, Mz)}
 
 
 def _timed_solve(plan, b, mode, restart, use_pc, keep=None):
