@@ -563,7 +563,11 @@ constexpr int kCoopThreadsMax = 1024;
 // complex64 dots keep all coefficients of a step in registers)
 template <typename V> constexpr int coop_threads() { return 512; }
 constexpr int kCoopDotsMax = 32;   // complex64 dots with all vectors in one sweep up to this basis size
-constexpr int kCoopMaxProblems = 64;
+// Batches of more problems take the separate kernels, whose launches carry
+// one grid plane per problem (measured on the 48 uneven guides: 5.61 s with
+// the separate kernels, 5.84 s with every block looping over the 48 problems
+// in each phase of the cooperative step).
+constexpr int kCoopMaxProblems = 8;
 constexpr long long kBarrierCycles = 2000000000LL;   // ~1 s
 
 // bar[0] arrivals, bar[1] generation, bar[2] abort (a wait gave up after

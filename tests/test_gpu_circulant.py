@@ -43,9 +43,11 @@ def _plan_with_contrast(grid, seed):
 
 # (nx, ny, nz): R = 3 ny nz unknowns per slice; nb = 32 panels; nx with
 # prime factors 7, 11, 13 (FFT stages that sum those radices directly):
-# 7, 13, 350 = 2 5^2 7, 550 = 2 5^2 11, 91 = 7 13
+# 7, 13, 350 = 2 5^2 7, 550 = 2 5^2 11, 91 = 7 13; (6, 23, 11): the strip's
+# cross-section, R = 759 unknowns per slice (24 panels, a ragged last one),
+# the factorisation of the benchmark guide
 @pytest.mark.parametrize("grid", [(7, 3, 2), (13, 4, 3), (20, 6, 2), (24, 8, 5), (9, 11, 4), (350, 3, 2),
-                                  (550, 2, 2), (91, 5, 3)])
+                                  (550, 2, 2), (91, 5, 3), (6, 23, 11)])
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
 @pytest.mark.parametrize("fp16", [False, True])
 def test_apply_matches_oracle(grid, dtype, fp16):

@@ -94,6 +94,47 @@ def test_jm_large_plane_matches_oracle(grid, dtype):
     plan.close()
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-5)])
+def test_jm_full_size_reciprocity(dtype, tol):
+    """The full 600 x 23 x 11 guide with electric and magnetic contrast and
+    dense random inputs, a property that holds at any size: the JM-VIE's
+    integral part L = [[N, -j kappa K], [j kappa K, N]] (Sec. 3) has N
+    symmetric and the curl part K symmetric as a bilinear form (its kernel is
+    odd), so L^T = S L S with S = diag(I, -I) (reciprocity with magnetic
+    currents): v^T L u = (S u)^T L (S v).  L w is recovered as
+    diag(M_eps, M_mu)^{-1} (w - A w)."""
+    wl = workloads.waveguide()
+    nx, ny, nz = grid = wl.grid
+    rng = np.random.Generator(np.random.PCG64(64))
+    eps = wl.eps_bg * (2.0 + 3.0 * rng.random((nz, ny, nx))) - 1j * rng.random((nz, ny, nx))
+    mu = 2.0 + rng.random((nz, ny, nx)) - 0.5j * rng.random((nz, ny, nx))
+    plan = vie.vie_plan_create(grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, eps)
+    vie.vie_set_permeability(plan, mu)
+    Me = op.contrast_M(op.chi_from_permittivity(eps, wl.eps_bg))
+    Mm = jm.mu_contrast(mu)
+    Mi = np.concatenate([np.broadcast_to(1.0 / Me, (3, nz, ny, nx)), np.broadcast_to(1.0 / Mm, (3, nz, ny, nx))]).ravel()
+    np_dtype = np.complex128 if dtype == torch.complex128 else np.complex64
+    n3 = 3 * nx * ny * nz
+    sgn = np.concatenate([np.ones(n3), -np.ones(n3)])
+
+    def L(w):
+        x = torch.from_numpy(w).to(dtype).cuda()
+        y = torch.empty_like(x)
+        vie.vie_jm_matvec(plan, x, y)
+        torch.cuda.synchronize()
+        return (w - y.cpu().numpy().astype(np.complex128)) * Mi
+
+    u = np.concatenate([workloads.random_currents(grid, seed=65), workloads.random_currents(grid, seed=66)]).ravel()
+    v = np.concatenate([workloads.random_currents(grid, seed=67), workloads.random_currents(grid, seed=68)]).ravel()
+    u = u.astype(np_dtype).astype(np.complex128)
+    v = v.astype(np_dtype).astype(np.complex128)
+    Lu, LSv = L(u), L(sgn * v)
+    a, b = np.dot(v, Lu), np.dot(sgn * u, LSv)
+    assert abs(a - b) <= tol * np.linalg.norm(v) * np.linalg.norm(Lu), (a, b)
+    plan.close()
+
+
 def test_jm_zero_permeability_contrast_decouples():
     """mu_r = 1 and zero magnetic input: the electric half of the JM operator
     is the J-VIE operator, the magnetic half is M_mu (...) = 0 plus u_m = 0."""

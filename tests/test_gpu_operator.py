@@ -164,6 +164,31 @@ def test_full_size_waveguide_sampled(dtype, tol):
     assert np.isfinite(y).all()
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-5)])
+def test_full_size_reciprocity(dtype, tol):
+    """The full 600 x 23 x 11 guide with dense random inputs, a property that
+    holds at any size: the dyadic Green's function is symmetric under the
+    exchange of source and observation point, so the Galerkin operator N
+    (Sec. 3.1) is complex symmetric, u^T N v = v^T N u.  N v is recovered as
+    M^{-1} (v - A v) from applications of A = I - M N, every voxel's contrast
+    with |M| >= 1/2."""
+    wl = workloads.waveguide()
+    nx, ny, nz = grid = wl.grid
+    rng = np.random.Generator(np.random.PCG64(61))
+    eps = wl.eps_bg * (2.0 + 3.0 * rng.random((nz, ny, nx))) - 1j * rng.random((nz, ny, nx))
+    plan = vie.vie_plan_create(grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+    vie.vie_set_permittivity(plan, eps)
+    Mi = np.broadcast_to(1.0 / op.contrast_M(op.chi_from_permittivity(eps, wl.eps_bg)), (3, nz, ny, nx)).ravel()
+    np_dtype = np.complex128 if dtype == torch.complex128 else np.complex64
+    u = workloads.random_currents(grid, seed=62).astype(np_dtype).astype(np.complex128)
+    v = workloads.random_currents(grid, seed=63).astype(np_dtype).astype(np.complex128)
+    Nu = (u.ravel() - _apply(plan, u, dtype)) * Mi
+    Nv = (v.ravel() - _apply(plan, v, dtype)) * Mi
+    a, b = np.dot(u.ravel(), Nv), np.dot(v.ravel(), Nu)
+    assert abs(a - b) <= tol * np.linalg.norm(u) * np.linalg.norm(Nv), (a, b)
+    plan.close()
+
+
 def test_bad_inputs_report_errors():
     grid = (4, 3, 2)
     plan = vie.vie_plan_create(grid, 0.02, K0, 2.085)
