@@ -730,6 +730,20 @@ def batch_section(args):
                                     raise_on_not_converged=False)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t
+    # the same 48 solves as one graph launch (device-side decisions between
+    # cycles and refinement steps)
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st_r, infos_r = vie.vie_solve_batch(plans, bs, xs, 1e-6, mode=vie.VIE_SOLVE_MIXED, restart=args.restart_mixed,
+                                        raise_on_not_converged=False, resident=True)
+    torch.cuda.synchronize()
+    wall_r = time.perf_counter() - t
+    resident = {"solve_s": wall_r, "device_s": infos_r[0]["time_ms"] / 1e3, "status": st_r,
+                "converged": sum(1 for i in infos_r if i["converged"]),
+                "max_true_residual": max(i["residual"] for i in infos_r),
+                "iterations_total": sum(i["iterations"] for i in infos_r),
+                "note": "the whole solve as one CUDA graph launch (conditional WHILE/IF nodes)"}
     # the same 48 solves with a block-circulant preconditioner per guide
     # (complex-half factors), setup timed separately
     torch.cuda.synchronize()
@@ -770,6 +784,7 @@ def batch_section(args):
             "max_true_residual": max(i["residual"] for i in infos),
             "iterations_total": sum(i["iterations"] for i in infos),
             "grouped_matvec_ms": ms, "grouped_matvecs_per_s": len(plans) * 1e3 / ms,
+            "resident": resident,
             "circulant": {"setup_s": circ_setup, "solve_s": wall_c, "status": st_c,
                           "converged": sum(1 for i in infos_c if i["converged"]),
                           "max_true_residual": max(i["residual"] for i in infos_c),

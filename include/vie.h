@@ -186,6 +186,14 @@ typedef struct {
                              (pageable or pinned), staged through device
                              buffers of 2 x 3N complex128 that the plan
                              allocates on first use and keeps */
+  int resident;           /* 1: without a preconditioner, run the whole solve
+                             (true residuals, refinement steps, cycles and
+                             their decisions) as one CUDA graph launch with
+                             device-side control (conditional WHILE/IF nodes;
+                             the time limit is checked on the device at each
+                             refinement step); 0: one graph launch per cycle,
+                             decisions on the host between cycles.  Falls
+                             back to 0 where conditional nodes are missing. */
 } vie_solve_opts;
 
 typedef struct {

@@ -51,6 +51,21 @@ struct SolveStatus {
   int reorth_count;  // steps of this cycle that took the second pass
 };
 
+// Device-side state of one problem in a device-resident solve (the whole
+// refinement loop in one graph launch): the decisions the host loop takes
+// between cycles, taken by small kernels instead.
+struct ResState {
+  int open;          // needs another refinement step (a true residual)
+  int inner;         // needs another inner cycle in this refinement step
+  int result;        // vie_status of the problem (VIE_OK while running)
+  int converged;
+  int iters, outers, rounds, hist_len;
+  int matvecs64, matvecs32, graph_cycles, reorth_steps;
+  double target;     // absolute target of the next cycle
+  double rel;        // last true relative residual
+  double history[64];
+};
+
 // Everything a kernel needs about one problem.
 struct ProbK {
   void* V;                 // (m + 1) basis vectors of the inner type
@@ -76,6 +91,7 @@ struct ProbK {
   double bnorm;            // ||b||
   double target;           // absolute target of the next cycle
   int from_inner;          // 1: the next cycle starts from rin, 0: from r64
+  ResState* rs;            // device-resident solve: the problem's state (null in the host loop)
 };
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2((double)v.x, (double)v.y); }
@@ -321,6 +337,7 @@ __global__ void __launch_bounds__(kThreads) norm2_b_kernel(const ProbK* __restri
 // r = b - y (complex128) with norm partials of r
 __global__ void __launch_bounds__(kThreads) residual_kernel(const ProbK* __restrict__ P) {
   const ProbK& q = P[blockIdx.y];
+  if (q.rs && !q.rs->open) return;
   double s = 0.0;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
     const double2 v = make_double2(q.b[k].x - q.y64[k].x, q.b[k].y - q.y64[k].y);
@@ -333,6 +350,18 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(const ProbK* __restr
 // One block per problem: beta = ||r|| from the residual partials, status and g.
 __global__ void __launch_bounds__(kThreads) init_cycle_kernel(const ProbK* __restrict__ P, int nblk, int m) {
   const ProbK& q = P[blockIdx.x];
+  if (q.rs && !q.rs->inner) {
+    // device-resident solve: this problem takes no cycle now
+    if (threadIdx.x == 0) {
+      SolveStatus* st = q.st;
+      st->active = 0;
+      st->j = 0;
+      st->converged = 0;
+      st->breakdown = 0;
+      st->reorth_count = 0;
+    }
+    return;
+  }
   const double beta = sqrt(block_sum_partials(q.partial, nblk));
   for (int i = threadIdx.x; i <= m; i += blockDim.x) q.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
   if (threadIdx.x == 0) {
@@ -342,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) init_cycle_kernel(const ProbK* __res
     st->converged = 0;
     st->breakdown = isfinite(beta) ? 0 : 1;
     st->beta = beta;
-    st->target = q.target;
+    st->target = q.rs ? q.rs->target : q.target;
     st->resid = beta;
     st->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
     st->reorth_count = 0;
@@ -367,6 +396,7 @@ __global__ void __launch_bounds__(kThreads) start_vector_kernel(const ProbK* __r
 template <typename V>
 __global__ void __launch_bounds__(kThreads) inner_from_outer_kernel(const ProbK* __restrict__ P) {
   const ProbK& q = P[blockIdx.y];
+  if (q.rs && !q.rs->inner) return;
   V* __restrict__ rin = (V*)q.rin;
   double s = 0.0;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < q.n; k += (size_t)gridDim.x * blockDim.x) {
@@ -381,6 +411,7 @@ __global__ void __launch_bounds__(kThreads) inner_from_outer_kernel(const ProbK*
 template <typename V>
 __global__ void __launch_bounds__(kThreads) inner_residual_kernel(const ProbK* __restrict__ P) {
   const ProbK& q = P[blockIdx.y];
+  if (q.rs && !q.rs->inner) return;
   V* __restrict__ rin = (V*)q.rin;
   const V* __restrict__ ad = (const V*)q.w;
   typename Acc<V>::R s = 0;
@@ -1022,6 +1053,141 @@ __global__ void __launch_bounds__(coop_threads<V>(), 1) arnoldi_coop_kernel(cons
 }
 
 // ---------------------------------------------------------------------------
+// Device-resident solve: the decisions between cycles as kernels
+// ---------------------------------------------------------------------------
+// Control block of a device-resident solve: the time limit (globaltimer) and
+// the iteration counters of its two loops, which bound them whatever the
+// per-problem state says.
+struct ResCtl {
+  unsigned long long t0;        // globaltimer at the first outer step
+  unsigned long long limit_ns;  // time limit of the solve
+  int outer_iters;              // outer-loop iterations run
+  int cap_outer;                // at most this many
+  int inner_iters;              // inner-loop iterations in the current outer step
+  int pad;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One block per problem, after the true residual r = b - A x of the open
+// problems: beta = ||r||, the relative residual and its history, then the
+// outcome of the problem (converged, non-finite, caps, time limit) or the
+// target of the next inner cycles (the host loop's refinement step).
+__global__ void __launch_bounds__(kThreads) outer_decide_kernel(const ProbK* __restrict__ P, int nblk, double tol,
+                                                               double inner_tol, int mixed, int max_iters,
+                                                               int max_outer, ResCtl* ctl) {
+  const ProbK& q = P[blockIdx.x];
+  ResState* rs = q.rs;
+  __shared__ int open;
+  if (threadIdx.x == 0) {
+    open = rs->open;
+    if (!open) rs->inner = 0;
+  }
+  __syncthreads();
+  if (!open) return;
+  const double beta = sqrt(block_sum_partials(q.partial, nblk));
+  if (threadIdx.x != 0) return;
+  if (ctl->t0 == 0ull) atomicCAS(&ctl->t0, 0ull, global_ns());
+  rs->matvecs64++;
+  const double rel = beta / q.bnorm;
+  rs->rel = rel;
+  if (rs->outers < 64) rs->history[rs->outers] = rel;
+  rs->hist_len = rs->outers + 1 < 64 ? rs->outers + 1 : 64;
+  rs->inner = 0;
+  if (!isfinite(beta)) {
+    rs->result = VIE_ERR_NONFINITE;
+    rs->open = 0;
+  } else if (beta <= tol * q.bnorm) {
+    rs->converged = 1;
+    rs->open = 0;
+  } else if (rs->iters >= max_iters || rs->outers >= max_outer) {
+    rs->result = VIE_ERR_NOT_CONVERGED;
+    rs->open = 0;
+  } else if (global_ns() - ctl->t0 > ctl->limit_ns) {
+    rs->result = VIE_ERR_TIMEOUT;
+    rs->open = 0;
+  } else {
+    // plain mode goes for tol ||b||; mixed asks the complex64 cycles for a
+    // reduction inner_tol, never below half the outer target
+    rs->target = mixed ? fmax(inner_tol * beta, 0.5 * tol * q.bnorm) : tol * q.bnorm;
+    rs->inner = 1;
+    rs->rounds = 0;
+  }
+}
+
+// any problem with an inner cycle to run: the inner loop's condition
+__global__ void outer_finalize_kernel(const ProbK* __restrict__ P, int count, ResCtl* ctl,
+                                      cudaGraphConditionalHandle h_in) {
+  int any = 0;
+  for (int p = threadIdx.x; p < count; p += blockDim.x) any |= P[p].rs->inner;
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) {
+    ctl->inner_iters = 0;
+    cudaGraphSetConditional(h_in, any ? 1u : 0u);
+  }
+}
+
+// the steps of the next cycle: step 0 runs, the later ones as the steps set them
+__global__ void reset_steps_kernel(const cudaGraphConditionalHandle* __restrict__ h, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) cudaGraphSetConditional(h[k], k == 0 ? 1u : 0u);
+}
+
+// After a cycle (one warp): step counts, the outcome of the cycle, and whether
+// the problem takes another inner cycle (mixed mode) or the next true
+// residual; the inner loop's condition.
+__global__ void inner_decide_kernel(const ProbK* __restrict__ P, int count, int mixed, int max_iters, ResCtl* ctl,
+                                    cudaGraphConditionalHandle h_in) {
+  int any = 0;
+  for (int p = threadIdx.x; p < count; p += blockDim.x) {
+    ResState* rs = P[p].rs;
+    if (!rs->inner) continue;
+    const SolveStatus* st = P[p].st;
+    const int steps = st->j;
+    rs->iters += steps;
+    if (mixed) rs->matvecs32 += steps; else rs->matvecs64 += steps;
+    rs->graph_cycles += 1;
+    rs->reorth_steps += st->reorth_count;
+    if (steps == 0) {
+      rs->result = VIE_ERR_NOT_CONVERGED;
+      rs->open = 0;
+      rs->inner = 0;
+      continue;
+    }
+    const bool more = mixed && !st->converged && !st->breakdown && rs->rounds + 1 < kMaxInnerCycles &&
+                      rs->iters < max_iters;
+    rs->rounds += 1;
+    if (more) {
+      rs->matvecs32 += 1;      // A d for the inner residual
+      any = 1;
+    } else {
+      rs->inner = 0;
+      rs->outers += 1;
+    }
+  }
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) {
+    ctl->inner_iters += 1;
+    cudaGraphSetConditional(h_in, (any && ctl->inner_iters < kMaxInnerCycles) ? 1u : 0u);
+  }
+}
+
+// End of an outer step: the outer loop's condition
+__global__ void outer_end_kernel(const ProbK* __restrict__ P, int count, ResCtl* ctl,
+                                 cudaGraphConditionalHandle h_out) {
+  int any = 0;
+  for (int p = threadIdx.x; p < count; p += blockDim.x) any |= P[p].rs->open;
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) {
+    ctl->outer_iters += 1;
+    cudaGraphSetConditional(h_out, (any && ctl->outer_iters < ctl->cap_outer) ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct KrylovWork {
@@ -1127,7 +1293,12 @@ struct BatchCall {
   unsigned* bar = nullptr;          // grid barrier of the cooperative step (arrivals, generation, abort)
   unsigned* bar_host = nullptr;     // pinned copy of the abort word
   int coop_blocks = 0;              // blocks of the cooperative step (0: separate kernels)
+  bool resident = false;            // the whole solve runs as one graph launch
+  ResState* rs = nullptr;           // device, one per problem (resident solve)
+  ResCtl* ctl = nullptr;            // device (resident solve)
   ~BatchCall() {
+    cudaFree(rs);
+    cudaFree(ctl);
     cudaFree(table);
     cudaFree(st);
     cudaFree(bar);
@@ -1204,6 +1375,7 @@ static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dty
     std::vector<vie_plan*> gp;
     std::vector<const void*> gx;
     std::vector<void*> gy;
+    std::vector<const int*> gl;       // per plan the device flag that skips it when 0
     const vie_plan* a = c.plans[list[i]];
     for (size_t k = i; k < list.size(); ++k) {
       if (used[k]) continue;
@@ -1211,23 +1383,28 @@ static vie_status apply_list(BatchCall& c, const std::vector<int>& list, int dty
       if (a->n[0] == b->n[0] && a->n[1] == b->n[1] && a->n[2] == b->n[2] && a->m[0] == b->m[0] &&
           a->m[1] == b->m[1] && a->m[2] == b->m[2]) {
         const ProbK& q = c.host[list[k]];
+        const int pi = list[k];
         used[k] = 1;
         gp.push_back(c.plans[list[k]]);
         if (outer) {
           gx.push_back(q.x64);
           gy.push_back(q.y64);
+          gl.push_back(c.resident ? &c.rs[pi].open : nullptr);
         } else if (which == APPLY_D) {
           gx.push_back(q.d);
           gy.push_back(q.w);
+          gl.push_back(c.resident ? &c.rs[pi].inner : nullptr);
         } else {
+          // an Arnoldi step: problems that stopped in this cycle are skipped
           const char* zb = (const char*)(flexible ? q.Z : q.V);
           gx.push_back(zb + (size_t)j * q.n * es);
           gy.push_back(q.w);
+          gl.push_back(&c.st[pi].active);
         }
       }
     }
     vie_status st = matvec_group(gp.data(), (int)gp.size(), gx.data(), gy.data(), outer ? VIE_C128 : dtype,
-                                 MODE_OPERATOR, s);
+                                 MODE_OPERATOR, s, gl.data());
     if (st != VIE_OK) return st;
   }
   return VIE_OK;
@@ -1459,6 +1636,254 @@ static vie_status run_cycle(BatchCall& c, CycleGraph& G, const std::vector<int>&
   return read_status(c, s);
 }
 
+// ---------------------------------------------------------------------------
+// Device-resident solve: the whole refinement loop as one graph launch
+// ---------------------------------------------------------------------------
+// Appends a conditional node (handle h, IF or WHILE) after *prev in g and
+// returns its body graph; *prev becomes the new node.
+static vie_status add_cond(cudaGraph_t g, cudaGraphNode_t* prev, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  VIE_CUDA_TRY(cudaGraphAddNode(&node, g, *prev ? prev : nullptr, nullptr, *prev ? 1 : 0, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  *prev = node;
+  return VIE_OK;
+}
+
+// Appends a segment of launches, captured from fn(stream), as the body of an
+// always-true IF node (so that segments and conditional nodes chain by
+// explicit dependencies).
+template <typename F>
+static vie_status add_segment(cudaGraph_t g, cudaGraphNode_t* prev, cudaStream_t cap, F fn) {
+  cudaGraphConditionalHandle h;
+  VIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraph_t body;
+  vie_status st = add_cond(g, prev, h, cudaGraphCondTypeIf, &body);
+  if (st != VIE_OK) return st;
+  VIE_CUDA_TRY(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  st = fn(cap);
+  cudaGraph_t out = body;
+  const cudaError_t e = cudaStreamEndCapture(cap, &out);
+  if (st != VIE_OK) return st;
+  if (e != cudaSuccess) {
+    set_error("capture into a solve graph: %s", cudaGetErrorString(e));
+    return VIE_ERR_CUDA;
+  }
+  return VIE_OK;
+}
+
+struct ResidentGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphConditionalHandle* steps_dev = nullptr;   // the step handles, for reset_steps_kernel
+  ~ResidentGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(steps_dev);
+  }
+};
+
+// Captures fn(stream) into an existing (conditional body) graph.
+template <typename F>
+static vie_status capture_into(cudaGraph_t body, cudaStream_t cap, F fn) {
+  VIE_CUDA_TRY(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  vie_status st = fn(cap);
+  cudaGraph_t out = body;
+  const cudaError_t e = cudaStreamEndCapture(cap, &out);
+  if (st != VIE_OK) return st;
+  if (e != cudaSuccess) {
+    set_error("capture into a solve graph: %s", cudaGetErrorString(e));
+    return VIE_ERR_CUDA;
+  }
+  return VIE_OK;
+}
+
+// The solve as one graph (plain GMRES or mixed-precision refinement, no
+// preconditioner), all problems in c.table with their ResState:
+//   WHILE (any problem open, outer steps < cap)
+//     A x (complex128, open problems), r = b - A x, outer_decide,
+//     [mixed: rin = r in complex64]
+//     WHILE (any problem with an inner cycle, rounds < kMaxInnerCycles)
+//       init_cycle, reset of the step conditions, start vector
+//       IF step 0 .. IF step jmax-1 (each sets the next step's condition)
+//       back substitution, x += Z y
+//       inner_decide, [mixed: A d and rin -= A d for problems going on]
+//     outer_end
+template <typename V>
+static vie_status build_resident_graph(BatchCall& c, ResidentGraph& R, const std::vector<int>& all, int m,
+                                       int jmax, int dtype, bool mixed, double tol, double inner_tol, int max_iters,
+                                       int max_outer, unsigned gx) {
+  const unsigned P = (unsigned)all.size();
+  const int mx = mixed ? 1 : 0;
+  VIE_CUDA_TRY(cudaStreamCreateWithFlags(&R.cap, cudaStreamNonBlocking));
+  VIE_CUDA_TRY(cudaGraphCreate(&R.graph, 0));
+  cudaGraphConditionalHandle h_out, h_in;
+  VIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_out, R.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t top = nullptr;
+  cudaGraph_t B_out, B_in;
+  vie_status st = add_cond(R.graph, &top, h_out, cudaGraphCondTypeWhile, &B_out);
+  if (st != VIE_OK) return st;
+  VIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_in, B_out, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t po = nullptr;
+  st = add_segment(B_out, &po, R.cap, [&](cudaStream_t cs) -> vie_status {
+    vie_status a = apply_list(c, all, dtype, APPLY_X, 0, false, cs);
+    if (a != VIE_OK) return a;
+    residual_kernel<<<dim3(kDotBlocks, P), kThreads, 0, cs>>>(c.table);
+    outer_decide_kernel<<<P, kThreads, 0, cs>>>(c.table, kDotBlocks, tol, inner_tol, mx, max_iters, max_outer, c.ctl);
+    outer_finalize_kernel<<<1, 32, 0, cs>>>(c.table, (int)P, c.ctl, h_in);
+    if (mixed) inner_from_outer_kernel<float2><<<dim3(kDotBlocks, P), kThreads, 0, cs>>>(c.table);
+    VIE_LAUNCH_CHECK();
+    return VIE_OK;
+  });
+  if (st != VIE_OK) return st;
+  st = add_cond(B_out, &po, h_in, cudaGraphCondTypeWhile, &B_in);
+  if (st != VIE_OK) return st;
+  st = add_segment(B_out, &po, R.cap, [&](cudaStream_t cs) -> vie_status {
+    outer_end_kernel<<<1, 32, 0, cs>>>(c.table, (int)P, c.ctl, h_out);
+    VIE_LAUNCH_CHECK();
+    return VIE_OK;
+  });
+  if (st != VIE_OK) return st;
+  // the inner loop's body: one cycle
+  std::vector<cudaGraphConditionalHandle> hs(jmax);
+  for (int k = 0; k < jmax; ++k)
+    VIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&hs[k], B_in, k == 0 ? 1 : 0, cudaGraphCondAssignDefault));
+  VIE_CUDA_TRY(cudaMalloc((void**)&R.steps_dev, jmax * sizeof(cudaGraphConditionalHandle)));
+  VIE_CUDA_TRY(cudaMemcpy(R.steps_dev, hs.data(), jmax * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice));
+  cudaGraphNode_t pi = nullptr;
+  st = add_segment(B_in, &pi, R.cap, [&](cudaStream_t cs) -> vie_status {
+    init_cycle_kernel<<<P, kThreads, 0, cs>>>(c.table, kDotBlocks, m);
+    reset_steps_kernel<<<1, 256, 0, cs>>>(R.steps_dev, jmax);
+    start_vector_kernel<V><<<dim3(gx, P), kThreads, 0, cs>>>(c.table);
+    VIE_LAUNCH_CHECK();
+    return VIE_OK;
+  });
+  if (st != VIE_OK) return st;
+  for (int k = 0; k < jmax; ++k) {
+    cudaGraph_t body;
+    st = add_cond(B_in, &pi, hs[k], cudaGraphCondTypeIf, &body);
+    if (st != VIE_OK) return st;
+    st = capture_into(body, R.cap, [&](cudaStream_t cs) -> vie_status {
+      bool set = false;
+      const bool last = k + 1 >= jmax;
+      vie_status e = enqueue_step<V>(c, all, all, k, m, dtype, false, nullptr, nullptr, gx, cs,
+                                     last ? 0 : hs[k + 1], last ? nullptr : &set);
+      if (e != VIE_OK) return e;
+      if (!last && !set) next_step_condition_kernel<<<1, 32, 0, cs>>>(c.table, (int)P, hs[k + 1]);
+      VIE_LAUNCH_CHECK();
+      return VIE_OK;
+    });
+    if (st != VIE_OK) return st;
+  }
+  st = add_segment(B_in, &pi, R.cap, [&](cudaStream_t cs) -> vie_status {
+    backsolve_kernel<<<P, kThreads, 0, cs>>>(c.table, m + 1);
+    update_x_kernel<V><<<dim3(gx, P), kThreads, (size_t)m * sizeof(typename Acc<V>::T), cs>>>(c.table);
+    inner_decide_kernel<<<1, 32, 0, cs>>>(c.table, (int)P, mx, max_iters, c.ctl, h_in);
+    VIE_LAUNCH_CHECK();
+    if (mixed) {
+      vie_status a = apply_list(c, all, dtype, APPLY_D, 0, false, cs);
+      if (a != VIE_OK) return a;
+      inner_residual_kernel<float2><<<dim3(kDotBlocks, P), kThreads, 0, cs>>>(c.table);
+      VIE_LAUNCH_CHECK();
+    }
+    return VIE_OK;
+  });
+  if (st != VIE_OK) return st;
+  VIE_CUDA_TRY(cudaGraphInstantiate(&R.exec, R.graph, 0));
+  return VIE_OK;
+}
+
+// The solve as one graph launch (build_resident_graph).  *used = false when
+// the graph cannot be built here; the caller then runs the host loop.
+template <typename V>
+static vie_status solve_resident(BatchCall& c, int count, int m, int dtype, bool mixed, double tol,
+                                 double inner_tol, int max_iters, int max_outer, double timeout,
+                                 double2* const* x, vie_solve_info* infos, cudaStream_t s, bool* used) {
+  *used = false;
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) all[i] = i;
+  VIE_CUDA_TRY(cudaMalloc((void**)&c.rs, count * sizeof(ResState)));
+  VIE_CUDA_TRY(cudaMalloc((void**)&c.ctl, sizeof(ResCtl)));
+  std::vector<ResState> rh(count);
+  memset(rh.data(), 0, count * sizeof(ResState));
+  for (int i = 0; i < count; ++i) {
+    rh[i].open = c.host[i].bnorm != 0.0 ? 1 : 0;
+    rh[i].converged = c.host[i].bnorm == 0.0 ? 1 : 0;
+    c.host[i].rs = c.rs + i;
+    c.host[i].from_inner = mixed ? 1 : 0;
+  }
+  ResCtl ch;
+  memset(&ch, 0, sizeof(ch));
+  ch.limit_ns = (unsigned long long)(timeout * 1e9);
+  ch.cap_outer = max_outer + 2;
+  VIE_CUDA_TRY(cudaMemcpyAsync(c.rs, rh.data(), count * sizeof(ResState), cudaMemcpyHostToDevice, s));
+  VIE_CUDA_TRY(cudaMemcpyAsync(c.ctl, &ch, sizeof(ResCtl), cudaMemcpyHostToDevice, s));
+  c.resident = true;
+  vie_status st = upload_list(c, all, s);   // synchronises: the host copies above have landed
+  if (st != VIE_OK) return st;
+  size_t nmax = 0;
+  for (int i = 0; i < count; ++i) nmax = c.host[i].n > nmax ? c.host[i].n : nmax;
+  const unsigned gx = grid_for(nmax);
+  const int jmax = max_iters < m ? max_iters : m;
+  ResidentGraph R;
+  st = build_resident_graph<V>(c, R, all, m, jmax, dtype, mixed, tol, inner_tol, max_iters, max_outer, gx);
+  if (st != VIE_OK) {
+    // conditional graph nodes unavailable here: the host loop takes over
+    cudaGetLastError();
+    clear_error();
+    c.resident = false;
+    for (int i = 0; i < count; ++i) c.host[i].rs = nullptr;
+    return VIE_OK;
+  }
+  *used = true;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  VIE_CUDA_TRY(cudaGraphLaunch(R.exec, s));
+  cudaEventRecord(e1, s);
+  for (int i = 0; i < count; ++i)
+    VIE_CUDA_TRY(cudaMemcpyAsync(x[i], c.host[i].x64, c.host[i].n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  st = read_status(c, s);   // also reports a grid barrier that gave up
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != VIE_OK) return st;
+  VIE_CUDA_TRY(cudaMemcpy(rh.data(), c.rs, count * sizeof(ResState), cudaMemcpyDeviceToHost));
+  vie_status worst = VIE_OK;
+  bool timed_out = false;
+  for (int i = 0; i < count; ++i) {
+    const ResState& r = rh[i];
+    vie_solve_info& inf = infos[i];
+    inf.iterations = r.iters;
+    inf.outer = r.outers;
+    inf.residual = c.host[i].bnorm != 0.0 ? r.rel : 0.0;
+    inf.converged = r.converged;
+    inf.matvecs64 += r.matvecs64;
+    inf.matvecs32 += r.matvecs32;
+    inf.graph_cycles = r.graph_cycles;
+    inf.reorth_steps = r.reorth_steps;
+    inf.history_len = r.hist_len;
+    for (int k = 0; k < r.hist_len && k < 64; ++k) inf.history[k] = r.history[k];
+    inf.time_ms = ms;
+    vie_status res = (vie_status)r.result;
+    if (!r.converged && res == VIE_OK) res = VIE_ERR_NOT_CONVERGED;   // the loops' own caps
+    if (res == VIE_ERR_TIMEOUT) timed_out = true;
+    if (worst == VIE_OK && res != VIE_OK) worst = res;
+  }
+  if (timed_out) set_error("solve exceeded %.1f s", timeout);
+  else if (worst == VIE_ERR_NOT_CONVERGED) set_error("not converged: a problem stopped above the tolerance (see its info)");
+  return worst;
+}
+
 // Solve `count` problems; b[i], x[i] complex128 device vectors of plan i.
 vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
                             const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,
@@ -1538,6 +1963,20 @@ vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* co
       infos[i].converged = 1;
     } else {
       list.push_back(i);
+    }
+  }
+  // without a preconditioner, on request: the whole loop as one graph launch
+  if (o->resident && !flexible && !jm && !list.empty()) {
+    bool used = false;
+    vie_status rs_st = dtype == VIE_C64
+                           ? solve_resident<float2>(c, count, m, dtype, mode == VIE_SOLVE_MIXED, tol, inner_tol,
+                                                    max_iters, max_outer, timeout, x, infos, s, &used)
+                           : solve_resident<double2>(c, count, m, dtype, mode == VIE_SOLVE_MIXED, tol, inner_tol,
+                                                     max_iters, max_outer, timeout, x, infos, s, &used);
+    if (used || rs_st != VIE_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rs_st;
     }
   }
   st = VIE_OK;

@@ -45,7 +45,16 @@ struct PassPtrs {
   const V* ghat[kMaxBatch];
   const V* M[kMaxBatch];
   V* work2[kMaxBatch];        // y-pass buffer of the split pass B (or null)
+  const int* live[kMaxBatch]; // per problem: null, or a device flag; 0 skips the problem (its blocks return)
 };
+
+// A problem whose live flag is 0 is skipped by every block of every pass
+// (blockIdx.y is the problem in all grouped launches).
+template <typename V>
+__device__ __forceinline__ bool skip_problem(const PassPtrs<V>& pp) {
+  const int* f = pp.live[blockIdx.y];
+  return f != nullptr && *(const volatile int*)f == 0;
+}
 
 // ---------------------------------------------------------------------------
 // pass A
@@ -54,6 +63,7 @@ template <typename V>
 __global__ void __launch_bounds__(256) pass_a_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int NL,
                                                      Radices rx, const V* __restrict__ twg, int lines_per_block,
                                                      int gsz) {
+  if (skip_problem(pp)) return;
   pdl_wait();
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
@@ -91,6 +101,7 @@ template <typename V>
 __global__ void __launch_bounds__(256) pass_b_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                      Radices ry, Radices rz, const V* __restrict__ twyg,
                                                      const V* __restrict__ twzg) {
+  if (skip_problem(pp)) return;
   pdl_wait();
   V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ ghat = pp.ghat[blockIdx.y];
@@ -199,6 +210,7 @@ __global__ void __launch_bounds__(256) pass_b_cluster_kernel(const __grid_consta
                                                              ClusterGeom q, Radices ry, Radices rz,
                                                              const V* __restrict__ twyg,
                                                              const V* __restrict__ twzg) {
+  if (skip_problem(pp)) return;
   namespace cgr = cooperative_groups;
   cgr::cluster_group cluster = cgr::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -372,6 +384,7 @@ constexpr int kBzThreads = 3 * 4 * kBzCells;
 template <typename V, int MZ, int NZ>
 __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 4 : 1)
     pass_bz_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g, int tiles, const V* __restrict__ twzg) {
+  if (skip_problem(pp)) return;
   constexpr int C4 = 4 * kBzCells;
   constexpr int KZ = MZ / 2 + 1;
   const int nz = NZ > 0 ? NZ : g.nz, nl3 = 3 * nz;
@@ -536,6 +549,7 @@ static vie_status dispatch_pass_bz(const PassPtrs<V>& pp, int count, const PassB
 template <typename V, int MY, int MZ, int NY, int NZ>
 __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                          const V* __restrict__ twyg, const V* __restrict__ twzg) {
+  if (skip_problem(pp)) return;
   V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ ghat = pp.ghat[blockIdx.y];
   constexpr int PY = (MY % 2 == 0) ? MY + 1 : MY;
@@ -704,6 +718,7 @@ template <typename V>
 __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ PassPtrs<V> pp, int nx, int nyz,
                                                      int NL, Radices rx, const V* __restrict__ twg,
                                                      int lines_per_block, int mode, int gsz) {
+  if (skip_problem(pp)) return;
   pdl_wait();
   const V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ x = pp.x[blockIdx.y];
@@ -759,6 +774,7 @@ __host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb
 template <typename V, int L1, int L2, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
+  if (skip_problem(pp)) return;
   static_assert(NX == 0 || (NX % L1 == 0 && NX % L2 == 0), "compiled line length must divide by L1 and L2");
   const V* __restrict__ x = pp.x[blockIdx.y];
   V* __restrict__ work = pp.work[blockIdx.y];
@@ -823,6 +839,7 @@ template <typename V, int L1, int L2, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_c4_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode,
     int gsz) {
+  if (skip_problem(pp)) return;
   const V* __restrict__ work = pp.work[blockIdx.y];
   const V* __restrict__ x = pp.x[blockIdx.y];
   const V* __restrict__ Mc = pp.M[blockIdx.y];
@@ -971,6 +988,7 @@ __device__ __forceinline__ void x3_steps12(V* __restrict__ S1, V* __restrict__ S
 template <typename V, int L1, int L2, int L3, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * X3<L1, L2, L3>::NT) pass_a3_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
+  if (skip_problem(pp)) return;
   typedef X3<L1, L2, L3> G;
   static_assert(NX == 0 || NX % (L1 * L2) == 0, "compiled line length must divide by L1 L2");
   const V* __restrict__ x = pp.x[blockIdx.y];
@@ -1036,6 +1054,7 @@ template <typename V, int L1, int L2, int L3, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * X3<L1, L2, L3>::NT) pass_c3_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int nyz, int NL, const V* __restrict__ twxg, int mode,
     int gsz) {
+  if (skip_problem(pp)) return;
   typedef X3<L1, L2, L3> G;
   static_assert(NX == 0 || NX % G::M == 0, "compiled line length must divide by L2 L3");
   const V* __restrict__ work = pp.work[blockIdx.y];
@@ -1961,7 +1980,7 @@ static vie_status run_one(vie_plan* p, const V* x, V* y, const V* ghat, const V*
 
 template <typename V>
 static vie_status group_passes(vie_plan* const* plans, int count, const void* const* x, void* const* y, int mode,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* const* live) {
   const vie_plan* p0 = plans[0];
   const bool f32 = sizeof(V) == sizeof(float2);
   const V* twx = f32 ? (const V*)p0->ax[0].tw32 : (const V*)p0->ax[0].tw64;
@@ -1979,6 +1998,7 @@ static vie_status group_passes(vie_plan* const* plans, int count, const void* co
       pp.work2[k] = split_buffer<V>(q, (V*)q->work, q->work_bytes);
       pp.ghat[k] = f32 ? (const V*)q->ghat32 : (const V*)q->ghat64;
       pp.M[k] = f32 ? (const V*)q->M32 : (const V*)q->M64;
+      pp.live[k] = live ? live[i0 + k] : nullptr;
     }
     vie_status st = run_passes<V>(p0, pp, c, twx, twy, twz, mode, s);
     if (st != VIE_OK) return st;
@@ -1987,9 +2007,9 @@ static vie_status group_passes(vie_plan* const* plans, int count, const void* co
 }
 
 vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype, int mode,
-                        cudaStream_t s) {
-  if (dtype == VIE_C64) return group_passes<float2>(plans, count, x, y, mode, s);
-  if (dtype == VIE_C128) return group_passes<double2>(plans, count, x, y, mode, s);
+                        cudaStream_t s, const int* const* live) {
+  if (dtype == VIE_C64) return group_passes<float2>(plans, count, x, y, mode, s, live);
+  if (dtype == VIE_C128) return group_passes<double2>(plans, count, x, y, mode, s, live);
   set_error("unknown dtype %d", dtype);
   return VIE_ERR_INVALID;
 }

@@ -205,8 +205,10 @@ const vie_plan* circulant_plan(const vie_circulant* c);
 
 // Operator application for `count` plans of one shape (same n and m);
 // x[i], y[i] are device vectors of dtype; each plan's own workspace is used.
+// live (optional): per plan a device flag read when the passes run; plans
+// whose flag is 0 are skipped (y untouched).
 vie_status matvec_group(vie_plan* const* plans, int count, const void* const* x, void* const* y, int dtype,
-                        int mode, cudaStream_t s);
+                        int mode, cudaStream_t s, const int* const* live = nullptr);
 // jm != 0: the JM-VIE (6N unknowns per problem, jm_matvec_impl as operator).
 vie_status solve_batch_impl(vie_plan* const* plans, int count, const double2* const* b, double2* const* x, double tol,
                             const vie_solve_opts* o, vie_solve_info* infos, vie_precond_fn precond,

@@ -48,7 +48,7 @@ class vie_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("x0_given", ctypes.c_int),
                 ("use_preconditioner", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("host_buffers", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("host_buffers", ctypes.c_int), ("resident", ctypes.c_int)]
 
 
 class vie_solve_info(ctypes.Structure):
@@ -278,7 +278,7 @@ def vie_eps2_from_round_trip(r_rt, degree, length, k0, eps_r, D=2.0, eta=1.0) ->
 def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart: int = 100,
               max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
               use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
-              stream=None, raise_on_not_converged: bool = True) -> dict:
+              stream=None, raise_on_not_converged: bool = True, resident: bool = False) -> dict:
     """Solve (I - M N) x = b on the device.  b, x: complex128 CUDA tensors, or
     (both) C-contiguous complex128 NumPy arrays on the host, which the library
     stages through device buffers (opts.host_buffers = 1); x is written in
@@ -288,7 +288,7 @@ def vie_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, restart
     host = _vectors_kind([(b, x)], [plan])
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
                           int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s),
-                          int(host))
+                          int(host), int(bool(resident)))
     info = vie_solve_info()
     st = load().vie_solve(plan.handle, _vec_ptr(b), _vec_ptr(x), float(tol),
                           ctypes.byref(opts), ctypes.byref(info), _stream_handle(stream))
@@ -355,7 +355,7 @@ def vie_matvec_batch(plans, xs, ys, stream=None):
 def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, restart: int = 100,
                     max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 200, x0_given: bool = False,
                     use_preconditioner: bool = False, check_every: int = 4, timeout_s: float = 600.0,
-                    stream=None, raise_on_not_converged: bool = True):
+                    stream=None, raise_on_not_converged: bool = True, resident: bool = False):
     """Solve every (plan, b, x) together (CUDA tensors, or host NumPy arrays
     as in vie_solve); returns (status, [info dict per problem])."""
     n = len(plans)
@@ -366,7 +366,7 @@ def vie_solve_batch(plans, bs, xs, tol: float, mode: int = VIE_SOLVE_MIXED, rest
         raise ValueError("every b and x must be of one kind: all CUDA tensors or all host arrays")
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
                           int(bool(x0_given)), int(bool(use_preconditioner)), int(check_every), float(timeout_s),
-                          int(host))
+                          int(host), int(bool(resident)))
     infos = (vie_solve_info * n)()
     st = load().vie_solve_batch(_ptr_array([p.handle.value for p in plans]), n,
                                 _ptr_array([_vec_ptr(b).value for b in bs]), _ptr_array([_vec_ptr(x).value for x in xs]),
@@ -619,7 +619,7 @@ def vie_jm_solve(plan: Plan, b, x, tol: float, mode: int = VIE_SOLVE_MIXED, rest
         if not ok or (t.size if host else t.numel()) != 6 * plan.n_vox:
             raise ValueError("b and x must be contiguous complex128 vectors of 6*nx*ny*nz entries")
     opts = vie_solve_opts(int(mode), int(restart), int(max_iters), float(inner_tol), int(max_outer),
-                          int(bool(x0_given)), 0, int(check_every), float(timeout_s), int(host))
+                          int(bool(x0_given)), 0, int(check_every), float(timeout_s), int(host), 0)
     info = vie_solve_info()
     st = load().vie_jm_solve(plan.handle, _vec_ptr(b), _vec_ptr(x), float(tol), ctypes.byref(opts),
                              ctypes.byref(info), _stream_handle(stream))

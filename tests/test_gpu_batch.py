@@ -87,8 +87,12 @@ def test_grouped_operator_large_planes(dtype):
         assert rel_l2(y.cpu().numpy().astype(np.complex128), ref) <= tol
 
 
+@pytest.mark.parametrize("resident", [False, True])
 @pytest.mark.parametrize("mode,tol", [(vie.VIE_SOLVE_MIXED, 1e-6), (vie.VIE_SOLVE_FP64, 1e-8)])
-def test_batched_solve_matches_single_solves_and_oracle(mode, tol):
+def test_batched_solve_matches_single_solves_and_oracle(mode, tol, resident):
+    """Four uneven guides solved together (the host loop between cycles, or
+    the whole solve as one graph launch with device-side decisions) against
+    single solves and the oracle's residual."""
     specs = [(60, 15, 0, 0.5), (80, 20, 2, 2.0), (60, 25, 3, 2.0), (100, 30, 1, 0.5)]
     plans, bs, wls = [], [], []
     for nx, L, d, e2 in specs:
@@ -102,7 +106,7 @@ def test_batched_solve_matches_single_solves_and_oracle(mode, tol):
         bs.append(b)
         wls.append((wl, ab))
     xs = [torch.zeros_like(b) for b in bs]
-    st, infos = vie.vie_solve_batch(plans, bs, xs, tol, mode=mode, restart=40)
+    st, infos = vie.vie_solve_batch(plans, bs, xs, tol, mode=mode, restart=40, resident=resident)
     assert st == 0
     for p, b, x, info, (wl, ab) in zip(plans, bs, xs, infos, wls):
         assert info["converged"] and info["residual"] <= tol
@@ -114,3 +118,34 @@ def test_batched_solve_matches_single_solves_and_oracle(mode, tol):
         M = op.contrast_M(op.chi_from_permittivity(wl.eps, wl.eps_bg, ab))
         r = oracle_matvec(wl.grid, wl.kappa, M, x.cpu().numpy().reshape(3, *wl.grid[::-1])).ravel() - b.cpu().numpy()
         assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()) <= 2 * tol
+
+
+def test_resident_solve_time_limit_and_single_problem():
+    """The device-resident solve checks its time limit on the device at each
+    refinement step: a limit of a microsecond stops a batch of two with
+    VIE_ERR_TIMEOUT (x holds the iterate reached); a single problem solved
+    resident takes the same steps as the host loop and reaches the same x."""
+    specs = [(60, 15, 2, 2.0), (80, 20, 2, 2.0)]
+    plans, bs = [], []
+    for nx, L, d, e2 in specs:
+        wl, ab = _guide(nx, L, d, e2, nx)
+        p = vie.vie_plan_create(wl.grid, wl.h_um, wl.k0_per_um, wl.eps_bg)
+        vie.vie_set_permittivity(p, wl.eps, ab)
+        src = torch.from_numpy(wl.src.ravel()).cuda()
+        b = torch.empty_like(src)
+        vie.vie_rhs_from_source(p, src, b)
+        plans.append(p)
+        bs.append(b)
+    xs = [torch.zeros_like(b) for b in bs]
+    st, infos = vie.vie_solve_batch(plans, bs, xs, 1e-10, mode=vie.VIE_SOLVE_MIXED, restart=30, resident=True,
+                                    timeout_s=1e-6, raise_on_not_converged=False)
+    assert st == 5, st
+    for info in infos:
+        assert not info["converged"]
+    x1 = torch.zeros_like(bs[0])
+    x2 = torch.zeros_like(bs[0])
+    i1 = vie.vie_solve(plans[0], bs[0], x1, 1e-8, mode=vie.VIE_SOLVE_MIXED, restart=30, resident=True)
+    i2 = vie.vie_solve(plans[0], bs[0], x2, 1e-8, mode=vie.VIE_SOLVE_MIXED, restart=30)
+    assert i1["converged"] and i2["converged"]
+    assert i1["iterations"] == i2["iterations"]
+    assert rel_l2(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-6
