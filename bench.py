@@ -335,16 +335,23 @@ def gpu_arm(args):
     hbm_peak, peak_kind = _peaks()
     alu_peak = fp32_peak
     achieved_tf = alg_flops / t_s / 1e12
+    # DRAM bytes per application from the committed ncu capture, when the
+    # plan runs the x-pass kernels that capture measured (else null).  The
+    # default codes (0) are, for this guide's 759 lines, the three-factor
+    # forward and the four-step inverse pass, both five lines per block.
+    x_passes = [info["x_lines_per_block"] or -5, info["x_lines_per_block_inverse"] or 5]
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get("matvec_c64_waveguide_bytes")
+            tj = json.load(open(tp))
+            if tj.get("x_passes") == x_passes:
+                traffic = tj.get("matvec_c64_waveguide_bytes")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / alu_peak, "traffic": traffic,
-                "kernel": "complex64 operator application (passes A, B, C)",
+                "kernel": "complex64 operator application (passes A, B, C)", "x_passes": x_passes,
                 "algorithmic_flops_per_launch": alg_flops, "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": "measured FP32 FMA throughput (vie_probe_fma_tflops); nominal %.1f = "
                                "152 SMs x 128 lanes x 2 flop x 2.07 GHz" % FP32_TFLOPS,

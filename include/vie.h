@@ -77,7 +77,9 @@ typedef struct {
                                  register FFT with that many lines per block,
                                  < 0 three-factor register FFT with -value lines
                                  per block, 0 the default (three-factor where
-                                 compiled for Mx, else four-step) */
+                                 compiled for Mx, else four-step; five lines
+                                 per block in complex64 when that makes one
+                                 block per SM, e.g. nx = 600 with 759 lines) */
   int x_lines_per_block_inverse; /* the same for the inverse x pass (its default:
                                     four-step where compiled for Mx) */
 } vie_plan_info;

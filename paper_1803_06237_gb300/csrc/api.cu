@@ -295,13 +295,15 @@ static void free_plan(vie_plan* p) {
 using namespace vie;
 
 // VIE_PLAN_AUTOTUNE: every combination of the three smallest 5-smooth
-// sizes >= 2n - 1 per axis and, where the x passes are four-step kernels, 2
-// or 4 lines per block for the forward and for the inverse x pass is timed (3 warm-up applications, then the
-// best of two bursts of 10 complex64 operator applications, CUDA events) on
-// a zero spectrum and contrast (the time does not depend on the values); the
-// fastest is kept.  Under a profiler that serialises kernels the timings,
-// and so the choice, are not those of a plain run.  Candidates the passes
-// reject (shared-memory limits) are skipped.
+// sizes >= 2n - 1 per axis and of the compiled x-pass shapes (four-step or
+// three-factor, lines per block) for the forward and for the inverse x pass
+// is timed (3 warm-up applications, then the best of two bursts of 10
+// complex64 operator applications, CUDA events) on a zero spectrum and
+// contrast (the time does not depend on the values); the fastest is kept if
+// it beats the default configuration by more than 2 %.  Under a profiler
+// that serialises kernels the timings, and so the choice, are not those of a
+// plain run.  Candidates the passes reject (shared-memory limits) are
+// skipped.
 static vie_status autotune(vie_plan* p, cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
   int cand[3][3];
@@ -361,51 +363,68 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
   p->M32 = M;
   float best = 1e30f;
   int bm[3] = {p->m[0], p->m[1], p->m[2]}, blpb = 0, blpbi = 0, count = 0;
+  // time the plan's present configuration: > 0 the best burst in ms, 0 when
+  // a pass rejected it, < 0 on a CUDA error (the message is set)
+  auto measure = [&]() -> float {
+    vie_status ms = VIE_OK;
+    for (int r = 0; r < 3 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
+    float t = 1e30f;
+    for (int rep = 0; rep < 2 && ms == VIE_OK; ++rep) {   // best of two bursts
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 10 && ms == VIE_OK; ++r) ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
+      cudaEventRecord(e1, s);
+      const cudaError_t se = cudaStreamSynchronize(s);
+      if (se != cudaSuccess) {
+        set_error("autotune: %s", cudaGetErrorString(se));
+        return -1.f;
+      }
+      float tr = 0.f;
+      cudaEventElapsedTime(&tr, e0, e1);
+      if (tr < t) t = tr;
+    }
+    if (ms != VIE_OK) { clear_error(); return 0.f; }
+    ++count;
+    return t;
+  };
+  auto set_config = [&](int cx, int cy, int cz) {
+    p->m[0] = cand[0][cx];
+    p->m[1] = cand[1][cy];
+    p->m[2] = cand[2][cz];
+    for (int a = 0; a < 3; ++a) p->kf[a] = p->m[a] / 2 + 1;
+    p->ax[0] = ax[0][cx];
+    p->ax[1] = ax[1][cy];
+    p->ax[2] = ax[2][cz];
+  };
+  // the default configuration first (smallest sizes, heuristic x passes):
+  // a candidate replaces it only when more than 2 % faster, so that timing
+  // noise between near-equal shapes does not change the plan from run to run
+  set_config(0, 0, 0);
+  p->x_lpb = 0;
+  p->x_lpb_inv = 0;
+  const float t_default = measure();
+  if (t_default < 0.f) { cleanup(); return VIE_ERR_CUDA; }
   for (int cx = 0; cx < 3; ++cx)
     for (int cy = 0; cy < 3; ++cy)
       for (int cz = 0; cz < 3; ++cz) {
-        p->m[0] = cand[0][cx];
-        p->m[1] = cand[1][cy];
-        p->m[2] = cand[2][cz];
-        for (int a = 0; a < 3; ++a) p->kf[a] = p->m[a] / 2 + 1;
-        p->ax[0] = ax[0][cx];
-        p->ax[1] = ax[1][cy];
-        p->ax[2] = ax[2][cz];
+        set_config(cx, cy, cz);
         int l1 = 0, l2 = 0, a1 = 0, a2 = 0, a3 = 0;
         x4_factors(p->m[0], &l1, &l2);
         x3_factors(p->m[0], &a1, &a2, &a3);
         // x-pass variants: four-step with 2 or 4 lines per block, three-factor
-        // with 1 or 2 (negative codes), for the forward and the inverse pass
+        // with 1 or 2 (negative codes), and 5 of either where five-line blocks
+        // fill the SMs once, for the forward and the inverse pass
         std::vector<int> modes;
-        if (l1) { modes.push_back(2); modes.push_back(4); }
-        if (a1) { modes.push_back(-1); modes.push_back(-2); }
+        const bool five = x_lines_five((long)NL, 1) && p->n[0] == 600;
+        if (l1) { modes.push_back(2); modes.push_back(4); if (five) modes.push_back(5); }
+        if (a1) { modes.push_back(-1); modes.push_back(-2); if (five) modes.push_back(-5); }
         if (modes.empty()) modes.push_back(0);
         const int nm = (int)modes.size();
         for (int li = 0; li < nm * nm; ++li) {   // (forward, inverse) variants
           p->x_lpb = modes[li % nm];
           p->x_lpb_inv = modes[li / nm];
-          vie_status ms = VIE_OK;
-          for (int r = 0; r < 3 && ms == VIE_OK; ++r)
-            ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
-          float t = 1e30f;
-          for (int rep = 0; rep < 2 && ms == VIE_OK; ++rep) {   // best of two bursts
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 10 && ms == VIE_OK; ++r)
-              ms = matvec_impl(p, x, y, VIE_C64, MODE_OPERATOR, work, work_bytes, s);
-            cudaEventRecord(e1, s);
-            const cudaError_t se = cudaStreamSynchronize(s);
-            if (se != cudaSuccess) {
-              set_error("autotune: %s", cudaGetErrorString(se));
-              cleanup();
-              return VIE_ERR_CUDA;
-            }
-            float tr = 0.f;
-            cudaEventElapsedTime(&tr, e0, e1);
-            if (tr < t) t = tr;
-          }
-          if (ms != VIE_OK) { clear_error(); continue; }
-          ++count;
-          if (t < best) {
+          const float t = measure();
+          if (t < 0.f) { cleanup(); return VIE_ERR_CUDA; }
+          if (t > 0.f && t < best) {
             best = t;
             bm[0] = p->m[0]; bm[1] = p->m[1]; bm[2] = p->m[2];
             blpb = p->x_lpb;
@@ -413,6 +432,11 @@ static vie_status autotune(vie_plan* p, cudaStream_t s) {
           }
         }
       }
+  if (t_default > 0.f && !(best < 0.98f * t_default)) {
+    for (int a = 0; a < 3; ++a) bm[a] = cand[a][0];
+    blpb = 0;
+    blpbi = 0;
+  }
   cleanup();
   if (count == 0) { set_error("autotune: no candidate configuration ran"); return VIE_ERR_INVALID; }
   for (int a = 0; a < 3; ++a) {

@@ -1172,11 +1172,15 @@ static vie_status launch_x3_lpb(bool forward, const PassPtrs<V>& pp, int count, 
   return VIE_OK;
 }
 
-// lpb: 1 or 2 lines per block (0: 2)
+// lpb: 1, 2 or 5 lines per block (0: 5 by the rule above where compiled, else 2)
 template <typename V, int L1, int L2, int L3, int NX = 0>
 static vie_status launch_x3(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL, const V* twx,
                             int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
   if (lpb == 1) return launch_x3_lpb<V, L1, L2, L3, 1, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+  if constexpr (sizeof(V) == sizeof(float2) && NX > 0) {
+    if (lpb == 5 || (lpb == 0 && x_lines_five(NL, count)))
+      return launch_x3_lpb<V, L1, L2, L3, 5, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+  }
   return launch_x3_lpb<V, L1, L2, L3, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
 }
 
@@ -1251,15 +1255,19 @@ static vie_status launch_x4(bool forward, const PassPtrs<V>& pp, int count, int 
   if constexpr (sizeof(V) == sizeof(float2) || (L1 <= 30 && L2 <= 30)) {
     if constexpr (sizeof(V) == sizeof(float2)) {
       const long blocks8 = (long)((NL + 7) / 8) * count;
-      if (lpb == 8 || (lpb == 0 && !forward && blocks8 >= 4L * 152)) {
+      if (lpb == 8 || (lpb == 0 && !forward && blocks8 >= 4L * kSMs)) {
         vie_status st = launch_x4_lpb<V, L1, L2, 8, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
         if (st != VIE_OK || *done) return st;
       }
     }
+    if constexpr (sizeof(V) == sizeof(float2) && NX > 0) {
+      if (lpb == 5 || (lpb == 0 && x_lines_five(NL, count)))
+        return launch_x4_lpb<V, L1, L2, 5, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
+    }
     const long blocks4 = (long)((NL + 3) / 4) * count;
     if (lpb == 2) return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     if (lpb == 4) return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
-    if (blocks4 < 152)
+    if (blocks4 < kSMs)
       return launch_x4_lpb<V, L1, L2, 2, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
     return launch_x4_lpb<V, L1, L2, 4, NX>(forward, pp, count, nx, nyz, NL, twx, mode, s, done, gsz);
   } else {

@@ -171,6 +171,16 @@ struct vie_plan {
 
 namespace vie {
 
+// GB300 streaming multiprocessors (grid sizing of the x passes)
+constexpr int kSMs = 152;
+// Five lines per x-pass block when that gives one block per SM where four
+// lines would give more (the 600 x 23 x 11 guide: 759 lines, 152 blocks of
+// five against 190 of four, 38 SMs then running two).  Compiled for the
+// complex64 x passes with the line length fixed at 600.
+inline bool x_lines_five(long NL, int count) {
+  return (NL + 4) / 5 * count <= kSMs && (NL + 3) / 4 * count > kSMs;
+}
+
 vie_status compute_toeplitz(vie_plan* p, cudaStream_t s);
 vie_status compute_curl(vie_plan* p, cudaStream_t s);     // C_a entries and folded spectra (JM-VIE)
 // JM-VIE operator y = u - M (T u) on 6N vectors (u_e, u_m) of dtype; mode
