@@ -379,8 +379,9 @@ static vie_status launch_pass_b_cluster(const PassPtrs<V>& pp, int count, const 
 constexpr int kBzCells = 16;
 constexpr int kBzThreads = 3 * 4 * kBzCells;
 
-// NZ > 0 fixes nz at compile time (the zero padding and the cropped outputs
-// then drop out of the register FFTs); NZ = 0 reads it from g.
+// NZ > 0 fixes nz at compile time (the zero padding is not loaded and the
+// cropped outputs are dead code; the additions of the padding zeros stay,
+// since IEEE arithmetic keeps x + 0); NZ = 0 reads it from g.
 template <typename V, int MZ, int NZ>
 __global__ void __launch_bounds__(kBzThreads, sizeof(V) == sizeof(float2) ? 4 : 1)
     pass_bz_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g, int tiles, const V* __restrict__ twzg) {
@@ -544,8 +545,9 @@ static vie_status dispatch_pass_bz(const PassPtrs<V>& pp, int count, const PassB
 // threads walking their own rows hit distinct banks.
 //   S1: (c, kz) y-lines, pitch PY;  S2: (c, y) z-lines, pitch PZ.
 // ---------------------------------------------------------------------------
-// NY, NZ > 0 fix the cross-section at compile time: the zero padding and the
-// cropped outputs then drop out of the register butterflies.
+// NY, NZ > 0 fix the cross-section at compile time: the zero padding is not
+// loaded and the cropped outputs are dead code (the first-stage additions of
+// the padding zeros stay: IEEE arithmetic keeps x + 0).
 template <typename V, int MY, int MZ, int NY, int NZ>
 __global__ void __launch_bounds__(256) pass_b_reg_kernel(const __grid_constant__ PassPtrs<V> pp, PassBGeom g,
                                                          const V* __restrict__ twyg, const V* __restrict__ twzg) {
@@ -769,8 +771,9 @@ __global__ void __launch_bounds__(256) pass_c_kernel(const __grid_constant__ Pas
 __host__ __device__ constexpr int pitch_mod16(int n, int lpb) { return n + ((lpb - n % 16) % 16 + 16) % 16; }
 
 // NX > 0 (a multiple of L1 for pass A, of L2 for pass C) fixes the line
-// length at compile time: the zero padding of the forward transform and the
-// cropped outputs of the inverse drop out of the register butterflies.
+// length at compile time: the zero padding of the forward transform is not
+// loaded and the cropped outputs of the inverse are dead code (the additions
+// of the padding zeros stay: IEEE arithmetic keeps x + 0).
 template <typename V, int L1, int L2, int LPB, int NX>
 __global__ void __launch_bounds__(LPB * (L1 > L2 ? L1 : L2)) pass_a4_kernel(
     const __grid_constant__ PassPtrs<V> pp, int nx, int NL, const V* __restrict__ twxg, int gsz) {
