@@ -320,6 +320,26 @@ def gpu_arm(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     e2e_value = whole_job_rate(world, Ke, e2e_ms)
 
+    # spread of the per-application time, outside the timed region: 20 bursts
+    # of ten applications from the same input pool, each burst between two
+    # CUDA events on the launching stream; median and 10th / 90th percentiles
+    try:
+        nb, bl = 20, 10
+        bev = [torch.cuda.Event(enable_timing=True) for _ in range(nb + 1)]
+        bev[0].record(stream)
+        for b_ in range(nb):
+            for i in range(bl):
+                j = b_ * bl + i
+                vie.vie_matvec(plan, xs[j % pool], ys[j % pool], stream)
+            bev[b_ + 1].record(stream)
+        torch.cuda.synchronize()
+        per_us = [bev[b_].elapsed_time(bev[b_ + 1]) * 1e3 / bl for b_ in range(nb)]
+        p10, p50, p90 = (float(v) for v in np.percentile(per_us, [10, 50, 90]))
+        spread = {"median": p50, "p10": p10, "p90": p90, "unit": "us per application", "bursts": nb,
+                  "applications_per_burst": bl}
+    except Exception as exc:                  # reported, never fatal to the line
+        spread = {"error": str(exc)[:200]}
+
     # measured FP32 / FP64 FMA rates (the ALU roofline), outside the timed region
     fp32_peak = vie.vie_probe_fma_tflops(vie.VIE_C64)
     fp64_peak = vie.vie_probe_fma_tflops(vie.VIE_C128)
@@ -368,6 +388,7 @@ def gpu_arm(args):
                                 if args.autotune else None),
                    "input_pool_vectors": pool, "l2": f"inputs+outputs cycle through {2 * pool * vec_bytes / 2**20:.0f} MiB > 129 MB L2",
                    "parallelism": f"{world} independent replicas"},
+        "step_time_spread": spread,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,
                 "steps": Ke},
         "gpu_launches": 3 * K,
