@@ -1175,7 +1175,8 @@ static vie_status launch_x3_lpb(bool forward, const PassPtrs<V>& pp, int count, 
   return VIE_OK;
 }
 
-// lpb: 1, 2 or 5 lines per block (0: 5 by the rule above where compiled, else 2)
+// lpb: 1, 2 or 5 lines per block (0: 5 where x_lines_five holds and the
+// complex64 kernel with the line length compiled in exists, else 2)
 template <typename V, int L1, int L2, int L3, int NX = 0>
 static vie_status launch_x3(bool forward, const PassPtrs<V>& pp, int count, int nx, int nyz, int NL, const V* twx,
                             int mode, cudaStream_t s, bool* done, int lpb, int gsz) {
