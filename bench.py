@@ -229,6 +229,23 @@ def whole_job_rate(world: int, steps: int, ms: float) -> float:
     return world * steps / (ms / 1e3)
 
 
+def captured_traffic(info: dict, path: str | None = None):
+    """(x_passes, DRAM bytes per guide operator application) from the
+    committed ncu capture, the bytes only when the plan runs the x-pass
+    kernels that capture measured (else None).  The default codes (0) are,
+    for the guide's 759 lines, the three-factor forward and the four-step
+    inverse pass, both with five lines per block."""
+    x_passes = [info["x_lines_per_block"] or -5, info["x_lines_per_block_inverse"] or 5]
+    tp = path or os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(tp))
+    except (OSError, ValueError):
+        return x_passes, None
+    if tj.get("x_passes") != x_passes:
+        return x_passes, None
+    return x_passes, tj.get("matvec_c64_waveguide_bytes")
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -355,20 +372,7 @@ def gpu_arm(args):
     hbm_peak, peak_kind = _peaks()
     alu_peak = fp32_peak
     achieved_tf = alg_flops / t_s / 1e12
-    # DRAM bytes per application from the committed ncu capture, when the
-    # plan runs the x-pass kernels that capture measured (else null).  The
-    # default codes (0) are, for this guide's 759 lines, the three-factor
-    # forward and the four-step inverse pass, both five lines per block.
-    x_passes = [info["x_lines_per_block"] or -5, info["x_lines_per_block_inverse"] or 5]
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("x_passes") == x_passes:
-                traffic = tj.get("matvec_c64_waveguide_bytes")
-        except Exception:
-            traffic = None
+    x_passes, traffic = captured_traffic(info)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / alu_peak, "traffic": traffic,
                 "kernel": "complex64 operator application (passes A, B, C)", "x_passes": x_passes,
