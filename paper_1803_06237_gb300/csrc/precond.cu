@@ -656,7 +656,11 @@ static size_t tc_ws_elems(const Dims* L) {
 static vie_status tc_prepare(vie_net* net, const int n[3], TcCache** out) {
   if (!net->tc) net->tc = new TcCache();
   TcCache* c = net->tc;
-  if (!c->norm) VIE_CUDA_TRY(cudaMalloc((void**)&c->norm, (kTcNormBlocks + 1) * sizeof(double)));
+  if (!c->norm) {   // assigned only on success, so a failed allocation is retried
+    double* buf = nullptr;
+    VIE_CUDA_TRY(cudaMalloc((void**)&buf, (kTcNormBlocks + 1) * sizeof(double)));
+    c->norm = buf;
+  }
   if (!c->wmaps) {
     for (int l = 0; l < kNumLayers; ++l) {
       vie_status st = tc_encode_w(&c->mW[l], net->wpack + pack_off(l), tc_cpad(kLayerDefs[l].ci),

@@ -429,13 +429,22 @@ void tc_train_free(TcTrain* t) {
 static vie_status tc_train_prepare(TcTrain** pt, const TcTrainParams& P, const int n[3]) {
   if (!*pt) *pt = new TcTrain();
   TcTrain* T = *pt;
-  if (!T->sms) {
+  // keyed on the buffers, so that a failed allocation is retried next time
+  if (!T->partial || !T->norm) {
     int dev = 0;
     VIE_CUDA_TRY(cudaGetDevice(&dev));
     VIE_CUDA_TRY(cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev));
     VIE_CUDA_TRY(cudaDeviceGetAttribute(&T->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    VIE_CUDA_TRY(cudaMalloc((void**)&T->partial, (size_t)T->sms * 27 * 32 * 32 * sizeof(float)));
-    VIE_CUDA_TRY(cudaMalloc((void**)&T->norm, (kTcNormBlocks + 4) * sizeof(double)));
+    if (!T->partial) {
+      float* buf = nullptr;
+      VIE_CUDA_TRY(cudaMalloc((void**)&buf, (size_t)T->sms * 27 * 32 * 32 * sizeof(float)));
+      T->partial = buf;
+    }
+    if (!T->norm) {
+      double* buf = nullptr;
+      VIE_CUDA_TRY(cudaMalloc((void**)&buf, (kTcNormBlocks + 4) * sizeof(double)));
+      T->norm = buf;
+    }
   }
   const bool same = T->ws && T->n[0] == n[0] && T->n[1] == n[1] && T->n[2] == n[2];
   if (!same) {
@@ -453,14 +462,18 @@ static vie_status tc_train_prepare(TcTrain** pt, const TcTrainParams& P, const i
       cudaFree(T->ws);
       T->ws = nullptr;
       T->cap = 0;
-      VIE_CUDA_TRY(cudaMalloc((void**)&T->ws, need * sizeof(__nv_bfloat16)));
+      __nv_bfloat16* buf = nullptr;
+      VIE_CUDA_TRY(cudaMalloc((void**)&buf, need * sizeof(__nv_bfloat16)));
+      T->ws = buf;
       T->cap = need;
     }
     if (16 * V0 > T->yf_cap) {
       cudaFree(T->Yf);
       T->Yf = nullptr;
       T->yf_cap = 0;
-      VIE_CUDA_TRY(cudaMalloc((void**)&T->Yf, 16 * V0 * sizeof(float)));
+      float* buf = nullptr;
+      VIE_CUDA_TRY(cudaMalloc((void**)&buf, 16 * V0 * sizeof(float)));
+      T->Yf = buf;
       T->yf_cap = 16 * V0;
     }
     __nv_bfloat16* p = T->ws;
