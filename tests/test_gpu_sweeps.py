@@ -18,15 +18,6 @@ def _lib():
     vie.load()
 
 
-def test_fit_slope_of_a_power_law():
-    L = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
-    assert abs(sweeps.fit_slope(L, 3e-4 * L ** -4.0) + 4.0) < 1e-12
-    R = 3e-4 * L ** -4.0
-    R[-1] = 1e-3                       # outside the window: ignored
-    assert abs(sweeps.fit_slope(L, R, 2.0, 8.0) + 4.0) < 1e-12
-    assert sweeps.fit_slope(L, np.full(5, 1e-15)) is None
-
-
 def test_reflection_falls_with_absorber_length_and_degree():
     """A 1.5 um strip (90 x 30 x 12 voxels of 50/3 nm) with absorbers of 225,
     450 and 900 nm against a 1800 nm reference, d = 0 and 1, R_rt = 1e-25."""
