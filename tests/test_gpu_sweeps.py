@@ -3,7 +3,6 @@
 (R falls with the absorber length, faster for a smoother profile) and the
 Bragg-grating transmission of Sec. 5.2 through the batch path (the batched
 solve of several wavelengths equals their single solves)."""
-import numpy as np
 import pytest
 import torch
 
