@@ -112,9 +112,12 @@ typedef struct {
 vie_status vie_plan_create(vie_plan** out, const int n[3], double h, double k0,
                            double eps_bg, int flags);
 
-/* Release every device buffer of the plan.  NULL is accepted. */
+/* Release every device buffer of the plan.  NULL is accepted.  Always
+ * VIE_OK. */
 vie_status vie_plan_destroy(vie_plan* plan);
 
+/* Fill *info (sizes, memory, setup and tuning figures above).  Host only.
+ * Errors: VIE_ERR_INVALID (NULL argument). */
 vie_status vie_plan_get_info(const vie_plan* plan, vie_plan_info* info);
 
 /* Contrast from a relative permittivity map (step a1; Sec. 3, M_eps):
@@ -143,14 +146,15 @@ vie_status vie_matvec(vie_plan* plan, const void* x_dev, void* y_dev, int dtype,
 
 /* Right-hand side of the J-VIE for an impressed current w_src radiating in
  * the background (Sec. 3, integral representation: e_inc = (1/c_e)(N - I) w_src):
- * b = c_e M e_inc = M ((N - I) w_src).  Same layout, types and rules as
- * vie_matvec. */
+ * b = c_e M e_inc = M ((N - I) w_src).  Same layout, types, rules and errors
+ * as vie_matvec. */
 vie_status vie_rhs_from_source(vie_plan* plan, const void* src_dev, void* b_dev,
                                int dtype, void* stream);
 
 /* Copy the FP64 Toeplitz octant T_pq(Delta), Delta in [0,nx)x[0,ny)x[0,nz),
  * to the host: 6*nx*ny*nz complex128 in [comp][z][y][x] order with the
- * component order xx, yy, zz, xy, xz, yz.  Synchronous. */
+ * component order xx, yy, zz, xy, xz, yz.  out_host is caller-owned.
+ * Synchronous.  Errors: VIE_ERR_INVALID (NULL argument), VIE_ERR_CUDA. */
 vie_status vie_get_toeplitz(const vie_plan* plan, double* out_host);
 
 /* eps''_max for a target round-trip reflection (Sec. 4.3 closed form with
@@ -292,25 +296,39 @@ size_t vie_net_param_count(void);
  * from `seed`.  Errors: VIE_ERR_INVALID, VIE_ERR_OOM, VIE_ERR_CUDA. */
 vie_status vie_net_create(vie_net** out, const float* params_host, size_t count,
                           unsigned long long seed);
+/* Release the network (NULL accepted; always VIE_OK).  It must not be set
+ * as a plan's preconditioner (vie_set_preconditioner_net) at the time. */
 vie_status vie_net_destroy(vie_net* net);
 
-/* Copy the FP32 parameters / accumulated gradients to the host. */
+/* Copy the FP32 parameters / accumulated gradients (vie_net_param_count()
+ * floats, caller-owned host array) to the host.  Synchronous.  Errors:
+ * VIE_ERR_INVALID (NULL argument), VIE_ERR_CUDA. */
 vie_status vie_net_get_params(const vie_net* net, float* out_host);
 vie_status vie_net_get_grads(const vie_net* net, float* out_host);
 
 /* z = v + |v|_rms Net(v / |v|_rms, chi of the plan) on the plan's grid; v_dev
  * and z_dev are device vectors (3*nx*ny*nz of dtype, not overlapping).  A
  * non-finite output entry is replaced by v and recorded (vie_net_status).
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID (NULL argument, dtype,
+ * a grid whose tensor maps cannot be encoded), VIE_ERR_OOM (first use on a
+ * grid: activation workspace), VIE_ERR_CUDA; non-finite outputs and
+ * timed-out waits are reported by vie_net_status, not here. */
 vie_status vie_net_apply(vie_net* net, const vie_plan* plan, const void* v_dev,
                          void* z_dev, int dtype, void* stream);
 
 /* One training sample (r, e) with A e = r (complex64 device vectors): forward
  * pass on r, loss |r + Net(r) - e|^2 / |e|^2 (all scaled by the RMS of r),
  * backward pass; gradients are ADDED to the network's accumulators.  *loss
- * receives the sample's loss.  Synchronises `stream`. */
+ * receives the sample's loss.  Synchronises `stream`.  Errors:
+ * VIE_ERR_INVALID (NULL argument, a grid whose tensor maps cannot be
+ * encoded), VIE_ERR_OOM (first use on a grid: training workspace),
+ * VIE_ERR_CUDA.  A bounded wait inside a tensor-core kernel that ran out is
+ * recorded for vie_net_status (flag 2); the sample's gradients are then not
+ * valid. */
 vie_status vie_net_accumulate(vie_net* net, const vie_plan* plan, const void* r_dev,
                               const void* e_dev, double* loss, void* stream);
+/* Clear the accumulated gradients.  Synchronous.  Errors: VIE_ERR_INVALID
+ * (NULL), VIE_ERR_CUDA. */
 vie_status vie_net_zero_grad(vie_net* net);
 
 /* Precision of vie_net_accumulate: VIE_TRAIN_TENSOR_BF16 (default; BF16
@@ -321,13 +339,14 @@ vie_status vie_net_zero_grad(vie_net* net);
 vie_status vie_net_set_training(vie_net* net, int mode);
 
 /* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the accumulated gradients
- * times grad_scale, refresh of the BF16 weights, gradients cleared. */
+ * times grad_scale, refresh of the BF16 weights, gradients cleared.
+ * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID (NULL), VIE_ERR_CUDA. */
 vie_status vie_net_adam_step(vie_net* net, float lr, float grad_scale, void* stream);
 
 /* Status of the applications since the last clear (synchronises the device):
  * *flag = 0 all fine, 1 a non-finite output was replaced by v, 2 a wait inside
  * a tensor-core convolution timed out (its output is not valid).  clear != 0
- * resets it. */
+ * resets it.  Errors: VIE_ERR_INVALID (NULL argument), VIE_ERR_CUDA. */
 vie_status vie_net_status(vie_net* net, int* flag, int clear);
 
 /* ------------------------------------------------------------------------ */
@@ -361,16 +380,23 @@ vie_status vie_circulant_create(vie_plan* plan, int flags, vie_circulant** out, 
 /* z = W^{-1} v for device vectors of 3*nx*ny*nz entries of dtype (VIE_C64
  * or VIE_C128; computed in complex64 either way, with complex-half factors
  * if built with VIE_CIRC_FP16_FACTORS), not overlapping.
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.  Errors: VIE_ERR_INVALID (NULL argument, dtype,
+ * the plan's contrast changed since the build), VIE_ERR_CUDA. */
 vie_status vie_circulant_apply(vie_circulant* c, const void* v_dev, void* z_dev, int dtype, void* stream);
 
-/* Setup time (ms, host clock around the build) and device bytes held. */
+/* Setup time (ms, host clock around the build) and device bytes held
+ * (either pointer may be NULL).  Host only.  Errors: VIE_ERR_INVALID (NULL
+ * c). */
 vie_status vie_circulant_info(const vie_circulant* c, double* build_ms, size_t* device_bytes);
+/* Release the factors (NULL accepted; always VIE_OK).  It must not be set as
+ * a plan's preconditioner at the time. */
 vie_status vie_circulant_destroy(vie_circulant* c);
 
 /* Use `c` (NULL: none) as the right preconditioner of this plan's solves
  * with opts->use_preconditioner = 1, replacing any network set with
- * vie_set_preconditioner.  `c` must have been built for this plan. */
+ * vie_set_preconditioner.  `c` must have been built for this plan; the plan
+ * keeps a reference, not a copy.  Errors: VIE_ERR_INVALID (NULL plan, `c`
+ * built for another plan). */
 vie_status vie_set_circulant_preconditioner(vie_plan* plan, vie_circulant* c);
 
 /* Use the learned network with the given FP32 parameters as the right
@@ -386,7 +412,8 @@ vie_status vie_set_preconditioner(vie_plan* plan, const void* weights, size_t by
 
 /* Same, with a network object the caller keeps (e.g. while training it):
  * `net` (NULL: none) becomes the right preconditioner; the plan keeps a
- * reference, and the caller must not destroy the network while it is set. */
+ * reference, and the caller must not destroy the network while it is set.
+ * Errors: VIE_ERR_INVALID (NULL plan). */
 vie_status vie_set_preconditioner_net(vie_plan* plan, vie_net* net);
 
 /* ------------------------------------------------------------------------ */
@@ -425,7 +452,7 @@ vie_status vie_jm_matvec(vie_plan* plan, const void* x_dev, void* y_dev, int dty
 /* Right-hand side for impressed currents (w_e, w_m) (6N, scaled like u)
  * radiating in the background: e_inc = (N - I) w_e - j kappa C x w_m,
  * eta h_inc = (N - I) w_m + j kappa C x w_e, b = (M_eps e_inc, M_mu eta h_inc).
- * Same rules as vie_jm_matvec. */
+ * Same rules and errors as vie_jm_matvec. */
 vie_status vie_jm_rhs_from_source(vie_plan* plan, const void* src_dev, void* b_dev, int dtype, void* stream);
 
 /* Solve the JM-VIE for 6N complex128 vectors b and x (device pointers, or
